@@ -1,0 +1,377 @@
+#!/usr/bin/env python
+"""Benchmark: certified accounts/s on 500 accounts x 10,000 assets (K = 64).
+
+One step = one prism_solve_batch call over a book of 500 accounts (input
+packing, ADMM iterations, FP64 polish and certification, output unpacking).
+Only accounts returned with status CERTIFIED (KKT and feasibility <= 1e-6)
+count. Under torchrun each rank solves its own disjoint book of 500 accounts
+(weak scaling, no data-path collective).
+
+  value  device-resident lane: inputs already in HBM, CUDA events on the solve stream
+  e2e    the same call with pinned host inputs/outputs (copies inside the timed region)
+
+--impl reference times the FP64 CPU oracle on the host cores instead (a
+bounded sample of accounts per step), on the same workload and metric.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "accounts/s at KKT res<=1e-6, 500 accts x 10k assets; batched-BF16 vs plain FP32"
+WORKLOAD = "500 accounts x 10,000 assets, K=64, 20 sector bands, L1 turnover (seeded synthetic)"
+M_ACCOUNTS = 500
+
+# algorithmic bytes per account-entry moved by one launch of each kernel class
+#   gemm_P : read X (FP32, or its BF16 hi+lo split: 4 B)
+#   gemm_x : read z, y (8 B), write v (4 B)
+#   prox   : read v, z, y and w0, l, u, c (28 B); write z, y and X (12 B)
+ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1:
+        import torch.distributed as dist
+        if not dist.is_initialized():
+            dist.init_process_group("nccl" if os.environ.get("BENCH_BACKEND", "nccl") == "nccl" else "gloo")
+        return dist, dist.get_rank(), ws, int(os.environ.get("LOCAL_RANK", "0"))
+    return None, 0, 1, 0
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (reference arm and cpu_baseline)
+# ---------------------------------------------------------------------------
+def _oracle_worker(args):
+    first, seed = args
+    from oracle.active_set import account_problem
+    from paper_2606_23367_gb300.workloads import make_workload
+    uni, batch = make_workload(1, seed=seed, first_account=first, M=1)
+    t = time.perf_counter()
+    account_problem(uni, batch, 0).solve()
+    return time.perf_counter() - t
+
+
+def _oracle_pool(n):
+    for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+        os.environ[var] = "1"
+    return mp.get_context("spawn").Pool(n)
+
+
+def _cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(pool, n_workers, accounts):
+    """Wall-clock accounts/s of the oracle over a list of account ids."""
+    t = time.perf_counter()
+    pool.map(_oracle_worker, [(a, 0) for a in accounts], chunksize=1)
+    return len(accounts) / (time.perf_counter() - t)
+
+
+def run_reference(args, rank):
+    if rank != 0:
+        return
+    n = max(1, min(_cores(), 16))
+    pool = _oracle_pool(n)
+    try:
+        pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)       # spawn / import warm-up
+        rates = []
+        for s in range(args.warmup + args.steps):
+            acc = [(s * n + k) % M_ACCOUNTS for k in range(n)]
+            r = oracle_rate(pool, n, acc)
+            if s >= args.warmup:
+                rates.append(r)
+    finally:
+        pool.close()
+        pool.join()
+    value = statistics.median(rates) if rates else 0.0
+    sample = f"{n} accounts per step (one per worker), FP64 active-set oracle, workload accounts 0..{M_ACCOUNTS - 1}"
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "accounts/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1000.0 * n / value if value else None, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": WORKLOAD, "solver": "FP64 primal active-set oracle (CPU)"},
+            "cpu_baseline": {"value": value, "unit": "accounts/s", "cores": n, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "accounts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------------------
+# GPU arm
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    FIELDS = "timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown," \
+             "clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(gpu_id)], stdout=self.fh, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self, t0=None, t1=None):
+        """Summarise the samples taken between wall-clock times t0 and t1 (all if None)."""
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.fh.close()
+        rows = [ln.strip().split(",") for ln in open(self.path) if ln.strip()]
+        os.unlink(self.path)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        import datetime
+        for r in rows:
+            try:
+                ts = datetime.datetime.strptime(r[0].strip(), "%Y/%m/%d %H:%M:%S.%f").timestamp()
+                if t0 is not None and not (t0 <= ts <= t1):
+                    continue
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for k, nm in enumerate(names):
+                if len(r) > 4 + k and r[4 + k].strip().lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def run_gpu(args, dist, rank, world, local_rank):
+    import numpy as np
+    import torch
+    from paper_2606_23367_gb300 import build, prism
+    from paper_2606_23367_gb300.workloads import make_workload
+
+    torch.cuda.set_device(local_rank)
+    build.build()
+    prism.load_library()
+    precision = {"bf16": prism.PRISM_BATCHED_BF16, "fp32": prism.PRISM_BATCHED_FP32}[args.precision]
+    uni, batch = make_workload(1, first_account=rank * M_ACCOUNTS, M=M_ACCOUNTS)
+    M, S = batch.n_accounts, uni.n_sectors
+    nnz = int(batch.offsets[-1])
+    dev = torch.device("cuda", local_rank)
+    stream = torch.cuda.current_stream(dev)
+    h = prism.create_universe(uni, device=local_rank)
+
+    def tens(x, dt, where):
+        t = torch.from_numpy(np.ascontiguousarray(x)).to(dt)
+        return t.to(dev) if where == "dev" else t.pin_memory()
+
+    def inputs(where):
+        return dict(offsets=tens(batch.offsets, torch.int64, where), w0=tens(batch.w0, torch.float64, where),
+                    lower=tens(batch.lower, torch.float64, where), upper=tens(batch.upper, torch.float64, where),
+                    tc=tens(batch.tc, torch.float64, where), band_lo=tens(batch.band_lo, torch.float64, where),
+                    band_hi=tens(batch.band_hi, torch.float64, where),
+                    turnover_cap=tens(batch.turnover_cap, torch.float64, where))
+
+    def outputs(where):
+        mk = (lambda *s, dt=torch.float64: torch.zeros(*s, dtype=dt, device=dev)) if where == "dev" else \
+             (lambda *s, dt=torch.float64: torch.zeros(*s, dtype=dt).pin_memory())
+        return dict(w=mk(nnz), status=mk(M, dt=torch.int32), iters=mk(M, dt=torch.int32), nu=mk(M),
+                    lambda_band=mk(M, S), theta=mk(M), diag=mk(M, prism.PRISM_NDIAG))
+
+    opts = dict(precision=precision, cuda_stream=stream.cuda_stream)
+
+    def step(inp, out, **extra):
+        return prism.prism_solve_batch(h, inp["offsets"], inp["w0"], inp["lower"], inp["upper"], inp["tc"],
+                                       inp["band_lo"], inp["band_hi"], turnover_cap=inp["turnover_cap"],
+                                       out=out, **opts, **extra)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    def timed(inp, out, K):
+        launches = 0
+        st_dev = out["status"].device.type == "cuda"
+        cert = torch.zeros((), dtype=torch.int64, device=dev)
+        barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(K):
+            r = step(inp, out)
+            launches += r["n_launches"]
+            # counted on the solve stream, before the next call overwrites the status
+            cert += (out["status"] == prism.PRISM_CERTIFIED).sum() if st_dev else \
+                int((out["status"] == prism.PRISM_CERTIFIED).sum())
+        e1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        return e0.elapsed_time(e1), int(cert.item()), launches
+
+    def max_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def sum_over_ranks(x):
+        if dist is None:
+            return x
+        t = torch.tensor([x], dtype=torch.float64, device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.SUM)
+        return float(t.item())
+
+    # ---- device-resident lane (the clock sampler starts before the warm-up so that
+    # its start-up does not overlap the timed region)
+    gpu_id = local_rank
+    try:
+        gpu_id = str(torch.cuda.get_device_properties(dev).uuid)
+        if not gpu_id.startswith("GPU-"):
+            gpu_id = "GPU-" + gpu_id
+    except Exception:
+        gpu_id = local_rank
+    clk = Clocks(gpu_id)
+    din, dout = inputs("dev"), outputs("dev")
+    for _ in range(args.warmup):
+        step(din, dout)
+    torch.cuda.synchronize()
+    t_wall0 = time.time()
+    ms, cert, launches = timed(din, dout, args.steps)
+    t_wall1 = time.time()
+    clocks = clk.stop(t_wall0, t_wall1)
+    ms = max_over_ranks(ms)
+    cert_all = sum_over_ranks(cert)
+    value = cert_all / (ms / 1000.0)
+    status = dout["status"].cpu().numpy()
+    iters = dout["iters"].cpu().numpy()
+    diag = dout["diag"].cpu().numpy()
+    # ---- end-to-end lane: pinned host inputs and outputs, copies inside the call
+    hin, hout = inputs("host"), outputs("host")
+    for _ in range(max(1, args.warmup // 2)):
+        step(hin, hout)
+    ms_e2e, cert_e2e, _ = timed(hin, hout, args.steps)
+    ms_e2e = max_over_ranks(ms_e2e)
+    e2e_value = sum_over_ranks(cert_e2e) / (ms_e2e / 1000.0)
+    h2d = sum(t.numel() * t.element_size() for t in hin.values())
+    d2h = sum(t.numel() * t.element_size() for t in hout.values())
+    # ---- per-kernel profile pass (CUDA events around every launch on the solve stream)
+    prof = step(din, dout, profile=1)
+    kms, kl = prof["kernel_ms"], prof["kernel_launches"]
+    names = prism.KERNEL_CLASSES
+    it_sum = int(dout["iters"].sum().item())
+    N = uni.n_assets
+    alg = {"gemm_P": ALG_BYTES["gemm_P"] * M * N, "gemm_x": ALG_BYTES["gemm_x"] * M * N,
+           "prox": ALG_BYTES["prox"] * N * it_sum / max(1, kl[names.index("prox")])}
+    cand = ["gemm_P", "gemm_x", "prox"]
+    dom = max(cand, key=lambda n: kms[names.index(n)])
+    k = names.index(dom)
+    avg_ms = kms[k] / max(1, kl[k])
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    peak = float(peaks.get("hbm_gbs", 6800.0))
+    achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": None,
+                "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,
+                "kernel_share": {n: kms[i] / max(1e-9, sum(kms)) for i, n in enumerate(names)}}
+    # ---- plain FP32 single-account form on a sample (same GPU, one account per call)
+    plain = None
+    if rank == 0 and args.plain_sample > 0:
+        sub = batch.subset(list(range(args.plain_sample)))
+        step_p = lambda: prism.solve(h, sub, precision=prism.PRISM_PLAIN_FP32, cuda_stream=stream.cuda_stream)
+        step_p()
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        rp = step_p()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t
+        plain = {"value": int((rp["status"] == 0).sum()) / dt, "unit": "accounts/s",
+                 "sample": f"{args.plain_sample} accounts, one launch sequence per account, FP32 B, host wall clock"}
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        n = max(1, min(_cores(), 16))
+        pool = _oracle_pool(n)
+        try:
+            pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)
+            acc = list(range(n, n + args.cpu_accounts))
+            rate = oracle_rate(pool, n, acc)
+        finally:
+            pool.close()
+            pool.join()
+        cpu = {"value": rate, "unit": "accounts/s", "cores": n, "kind": "oracle",
+               "sample": f"{len(acc)} accounts of the same workload on {n} worker processes (FP64 active-set oracle)"}
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "accounts/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "bf16-products/f32-iterations/f64-polish" if args.precision == "bf16"
+        else "f32-iterations/f64-polish", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "accounts_per_gpu": M, "assets": N, "factors": uni.n_factors,
+                   "precision": "BATCHED_BF16" if args.precision == "bf16" else "BATCHED_FP32",
+                   "l2": "inputs larger than L2 (160 MB of FP64 account data per step)",
+                   "parallelism": f"accounts sharded over {world} GPU(s), no collective"},
+        "certified": int(cert_all), "certified_frac": cert_all / (args.steps * M * world),
+        "status_counts": {prism.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())},
+        "admm_iters": {"median": float(np.median(iters)), "max": int(iters.max())},
+        "max_residual": {"stat": float(diag[:, 4].max()), "budget": float(diag[:, 0].max()),
+                         "box": float(diag[:, 1].max())},
+        "phase_ms": dict(zip(("setup", "iterate", "polish", "certify"), prof["t_phase_ms"])),
+        "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
+        "e2e": {"value": e2e_value, "unit": "accounts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(launches), "clocks": clocks,
+    }
+    print(json.dumps(line), flush=True)
+    h.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
+    ap.add_argument("--plain-sample", type=int, default=8)
+    ap.add_argument("--cpu-accounts", type=int, default=16)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    dist, rank, world, local_rank = _dist()
+    if args.impl == "reference":
+        run_reference(args, rank)
+    else:
+        run_gpu(args, dist, rank, world, local_rank)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

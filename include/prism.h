@@ -1,0 +1,199 @@
+/*
+ * prism.h -- C-ABI of the GB300 batched rebalancing solver.
+ *
+ * The library solves a book of account rebalancing problems in one call. Each
+ * account a is the convex program of Eq. 1 (Sec. 4.2) as the workloads use it,
+ * with the objective scaled as in the Sec. 8 display (Q = 2 Sigma, eta = 1):
+ *
+ *   minimise   w' Sigma w - mu' w + sum_i phi_i(w_i)
+ *   subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,
+ *              ||w - w0||_1 <= tau,          Sigma = B diag(f) B' + diag(d),
+ *
+ * where phi_i is the transition cost against the current holdings w0: an L1
+ * cost c_i |w_i - w0_i|, or, when tax lots are given, the convex lot model
+ * phi(w) = c (w - w0) + G(max(S*, w0 - w)), G(S) = 2 c S + (cheapest-first tax
+ * cost of selling S), S* = total size of lots with 2c + kappa < 0.
+ *
+ * The boundary follows the paper's public solver call (Fig. 2, Sec. 4.3):
+ * problem data in; weights, per-account status codes (Table "Status
+ * vocabulary", Sec. 9), timings, memory class and the feasibility / KKT
+ * diagnostics of Sec. 4.4 out.
+ *
+ * Conventions for every entry point
+ *  - Pointers may be host or device memory; the library tells them apart with
+ *    cudaPointerGetAttributes. The caller owns every input and output buffer;
+ *    the library copies what it needs and never keeps a caller pointer.
+ *  - Return value: 0 on success, a negative PRISM_ERR_* code on a call-level
+ *    error (bad argument, CUDA error, allocation failure). The message is
+ *    available from prism_last_error() (thread-local). Per-account outcomes
+ *    are reported through prism_result.status, not the return value.
+ *  - Nothing here throws or aborts; no entry point may be called concurrently
+ *    on the same handle from two threads.
+ */
+#ifndef PRISM_H
+#define PRISM_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- call-level return codes ---------------------------------------- */
+#define PRISM_OK                 0
+#define PRISM_ERR_ARGUMENT     (-1)   /* bad size, NULL pointer, non-finite data, infeasible layout */
+#define PRISM_ERR_CUDA         (-2)   /* a CUDA runtime call failed */
+#define PRISM_ERR_ALLOCATION   (-3)   /* device or host allocation failed */
+#define PRISM_ERR_UNSUPPORTED  (-4)   /* option combination not implemented */
+
+/* ---- per-account status codes (Table "Status vocabulary", Sec. 9) ----- */
+#define PRISM_CERTIFIED              0  /* weights returned, all external checks pass */
+#define PRISM_FEASIBLE_NONCERTIFIED  1  /* feasibility passes, KKT certification does not */
+#define PRISM_TIMEOUT                2  /* iteration cap or time budget reached first */
+#define PRISM_DEADLINE_EXCEEDED      3  /* completed after the window (queue runs only) */
+#define PRISM_NO_FEASIBLE_RETURN     4  /* no output passed the gates (incl. capacity test) */
+#define PRISM_ALLOCATION_FAILURE     5  /* problem object could not be allocated */
+#define PRISM_NUMERICAL_FAILURE      6  /* NaN/Inf met in the iterates */
+
+/* ---- precision modes ---------------------------------------------------- */
+#define PRISM_PLAIN_FP32    0  /* one account per launch sequence, FP32 B, SIMT products */
+#define PRISM_BATCHED_FP32  1  /* all accounts batched, FP32 B, SIMT products */
+#define PRISM_BATCHED_BF16  2  /* all accounts batched, tcgen05 BF16 products (split hi+lo
+                                  operands), FP32 accumulate */
+
+/* ---- universe ----------------------------------------------------------- */
+/* Universe-level data shared by every account (Eq. 1 risk model, Sec. 4.2
+ * "structural facts": factor-structured risk, O(N K) objective and gradient).
+ * All arrays are FP64 (sector: int32), host or device; the library copies them. */
+typedef struct {
+    int32_t n_assets;       /* N >= 1 */
+    int32_t n_factors;      /* K in [1, 64] */
+    int32_t n_sectors;      /* S in [1, 64] */
+    const double* B;        /* N x K factor loadings, row-major */
+    const double* f;        /* K factor variances (> 0), F = diag(f) */
+    const double* d;        /* N idiosyncratic variances (> 0), D = diag(d) */
+    const double* mu;       /* N return input */
+    const int32_t* sector;  /* N sector ids in [0, S) */
+    int32_t device;         /* CUDA device ordinal */
+} prism_universe_desc;
+
+typedef struct prism_universe prism_universe;
+typedef struct prism_state prism_state;
+
+/* Validate and copy a universe to the device; precompute the FP32/BF16 copies
+ * of B and the Woodbury capacitance inverses (2F)^{-1} + B' Delta^{-1} B for the
+ * solver's penalty grid. *out receives an opaque handle owned by the caller
+ * (release with prism_destroy_universe). */
+int prism_create_universe(const prism_universe_desc* desc, prism_universe** out);
+void prism_destroy_universe(prism_universe* u);
+
+/* ---- a book of accounts ------------------------------------------------- */
+/* Per-account data, ragged: account a owns entries offsets[a] .. offsets[a+1]-1.
+ * Entry e refers to universe asset asset_idx[e], or, when asset_idx is NULL,
+ * entry offsets[a] + i refers to asset i (every account spans the universe in
+ * universe order, offsets[a+1] - offsets[a] == N). All FP64 unless noted. */
+typedef struct {
+    int32_t n_accounts;             /* M >= 1 */
+    const int64_t* offsets;         /* M + 1, offsets[0] == 0, nondecreasing */
+    const int32_t* asset_idx;       /* ragged universe rows, or NULL */
+    const double* w0;               /* current holdings, ragged */
+    const double* lower;            /* box lower bounds l, ragged (>= 0 when lots are given) */
+    const double* upper;            /* box upper bounds u, ragged (u == l excludes the name) */
+    const double* tc;               /* L1 transition cost c_i >= 0 per unit traded, ragged */
+    const double* band_lo;          /* M x S sector band lower edges (may be -inf) */
+    const double* band_hi;          /* M x S sector band upper edges (may be +inf) */
+    const double* turnover_cap;     /* M turnover caps tau (+inf = none), or NULL = none */
+    const int64_t* lot_offsets;     /* ragged+1 lot ranges per entry, or NULL = no lots */
+    const double* lot_size;         /* lot sizes (weight units), sum per entry == w0 */
+    const double* lot_kappa;        /* marginal tax per unit sold (negative = harvest) */
+} prism_batch;
+
+/* ---- options -------------------------------------------------------------- */
+typedef struct {
+    double  eps_kkt;          /* certification gate on every residual (default 1e-6) */
+    double  eps_admm;         /* ADMM residual target before the polish (default 3e-4) */
+    double  rho0;             /* initial ADMM penalty (default 0.1) */
+    double  alpha;            /* over-relaxation (default 1.6) */
+    double  time_budget_s;    /* wall-clock ceiling for the call (<= 0: none) */
+    int32_t max_iter;         /* ADMM iteration cap per account (default 4000) */
+    int32_t check_every;      /* iterations per captured graph launch (default 10) */
+    int32_t min_iter;         /* iterations before a convergence test may stop an account */
+    int32_t polish_rounds;    /* active-set correction rounds per polish (default 8) */
+    int32_t precision;        /* PRISM_PLAIN_FP32 | PRISM_BATCHED_FP32 | PRISM_BATCHED_BF16 */
+    int32_t use_graph;        /* capture the iteration loop in a CUDA graph (default 1) */
+    int32_t keep_for_backward;/* keep the polished active set for prism_solve_batch_backward */
+    int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
+    void*   cuda_stream;      /* cudaStream_t to run on (NULL = the library's own stream) */
+} prism_solve_opts;
+
+/* Fill *o with the defaults documented above. */
+void prism_default_opts(prism_solve_opts* o);
+
+/* ---- results ------------------------------------------------------------- */
+/* Diagnostic columns of prism_result.diag (FP64, Sec. 4.4, computed on the
+ * device in FP64 from the returned weights and multipliers). */
+#define PRISM_DIAG_BUDGET    0  /* |1'w - 1| */
+#define PRISM_DIAG_BOX       1  /* largest bound violation */
+#define PRISM_DIAG_EXPOSURE  2  /* largest band violation */
+#define PRISM_DIAG_TURNOVER  3  /* (||w - w0||_1 - tau)_+ */
+#define PRISM_DIAG_STAT      4  /* subgradient stationarity distance */
+#define PRISM_DIAG_COMP      5  /* complementarity of bands and cap */
+#define PRISM_DIAG_OBJ       6  /* objective w'Sigma w - mu'w + sum phi_i(w_i) */
+#define PRISM_DIAG_ITERS     7  /* polish rounds used (as a double) */
+#define PRISM_NDIAG          8
+
+/* Kernel classes of prism_result.kernel_ms / kernel_launches (profile mode). */
+#define PRISM_K_GEMM_P   0  /* shared-B reduction P = B' X over assets */
+#define PRISM_K_SOLVE_K  1  /* K x K capacitance solves */
+#define PRISM_K_GEMM_X   2  /* x-update B Q with the relaxation epilogue */
+#define PRISM_K_PROX     3  /* prox / projection / dual update / control */
+#define PRISM_K_POLISH   4  /* FP64 polish round (includes the certification checks) */
+#define PRISM_K_PACK     5  /* input packing and validation */
+#define PRISM_K_OTHER    6  /* capacity test, init, counters, classification, status */
+#define PRISM_K_UNPACK   7  /* output unpacking */
+#define PRISM_NKCLASS    8
+
+typedef struct {
+    double*  w;             /* ragged weights, same layout as prism_batch (required) */
+    double*  nu;            /* M budget multipliers, or NULL */
+    double*  lambda_band;   /* M x S band multipliers, or NULL */
+    double*  theta;         /* M cap multipliers, or NULL */
+    int32_t* status;        /* M per-account status (required) */
+    int32_t* iters;         /* M ADMM iterations used, or NULL */
+    double*  diag;          /* M x PRISM_NDIAG diagnostics, or NULL */
+    /* host scalars written by the call */
+    double   t_device_ms;   /* device time of the solve (CUDA events on the solve stream) */
+    double   t_call_ms;     /* host wall clock of the whole call (full-call lane, Sec. 5.4) */
+    double   t_phase_ms[4]; /* device time of: setup, ADMM iterations, polish, certification */
+    int64_t  device_bytes;  /* device memory held by the solve (memory class, Sec. 6) */
+    int64_t  n_launches;    /* kernels this call launched (graph replays included) */
+    double   kernel_ms[PRISM_NKCLASS];        /* profile mode: summed event time per class */
+    int64_t  kernel_launches[PRISM_NKCLASS];  /* profile mode: launches per class */
+    prism_state** state;    /* receives the state for the backward pass, if requested */
+} prism_result;
+
+/* Solve every account of *batch against universe u. All accounts' inputs are
+ * validated first (a bad input fails the whole call with PRISM_ERR_ARGUMENT);
+ * per-account outcomes are reported in res->status. Output buffers may be host
+ * or device memory and must be sized as documented above. */
+int prism_solve_batch(prism_universe* u, const prism_batch* batch,
+                      const prism_solve_opts* opts, prism_result* res);
+
+/* Implicit differentiation of the polished KKT system: given dL/dw (ragged,
+ * same layout as the solve), write dL/dmu (N, summed over accounts), dL/dB
+ * (N x K), dL/dd (N) and dL/dw0 (ragged). Any output may be NULL. Requires a
+ * state returned by a solve with keep_for_backward = 1. */
+int prism_solve_batch_backward(prism_state* state, const double* dL_dw,
+                               double* dmu, double* dB, double* dd, double* dw0);
+void prism_free_state(prism_state* state);
+
+/* Message of the last failed call on this thread ("" when none). */
+const char* prism_last_error(void);
+
+/* Library version string. */
+const char* prism_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PRISM_H */

@@ -1,0 +1,593 @@
+// admm.cu -- the batched ADMM iteration (SIMT products, prox/projection, control).
+//
+// Splitting (spec method; the paper discloses none of its own, Sec. 3):
+// x = z with f(x) = x' Sigma x - mu' x and g(z) = sum_i phi_i(z_i) + indicator of
+// Z = {1'z = 1, l <= z <= u, lo_s <= sum_{i in s} z_i <= hi_s, ||z - w0||_1 <= tau}
+// (Eq. 1 constraints, Sec. 4.2). One iteration, with penalty rho and relaxation alpha:
+//
+//   X  = Delta^{-1} (mu + rho z - y),     Delta = diag(2 d + rho)
+//   P  = B' X                              (G2, shared-B product over assets)
+//   Q  = C^{-1} P,  C = (2F)^{-1} + B' Delta^{-1} B      (G3, K x K)
+//   x  = X - Delta^{-1} B Q                (G4, Woodbury: x = (2 Sigma + rho I)^{-1} (mu + rho z - y))
+//   v  = alpha x + (1 - alpha) z + y / rho
+//   z+ = argmin_{z in Z} sum phi_i(z_i) + rho/2 ||z - v||^2     (G5)
+//   y+ = rho (v - z+)
+//
+// The projection in G5 relaxes the budget (nu), the bands (lambda_s) and the cap
+// (theta): z_i = prox of (phi_i + theta |. - w0_i|)/rho on [l_i, u_i] at
+// v_i - (nu + lambda_{s(i)})/rho. Each sector sum S_s(eta) is nonincreasing and
+// piecewise linear in eta, so a sector held at its upper edge has eta_s solving
+// S_s(eta_s) = hi_s, and the budget reads sum_s S_s(clamp(nu, eta_hi_s, eta_lo_s)) = 1.
+// Each scalar root is found by Newton steps on the piecewise-linear sum (exact once
+// on the right piece) safeguarded by a bracket; the cap multiplier theta is found
+// by an outer bracketed secant on the turnover U(theta) = tau.
+#include <cfloat>
+#include <cmath>
+
+#include "common.cuh"
+#include "solver.h"
+
+namespace prism {
+
+constexpr int PROX_MAXIT = 80;
+
+// ---------------------------------------------------------------------------
+// initial state: z = clip(w0, l, u), y = 0, X = Delta^{-1}(mu + rho z)
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float rho_val(int j) {
+    return float(RHO_MIN) * exp10f(float(j) / float(RHO_PER_DECADE));
+}
+
+__device__ __forceinline__ void store_X(const Dev& D, size_t e, float X) {
+    if (D.bf16) {
+        __nv_bfloat16 h = __float2bfloat16_rn(X);
+        D.Xhi[e] = h;
+        D.Xlo[e] = __float2bfloat16_rn(X - __bfloat162float(h));
+    } else {
+        D.X[e] = X;
+    }
+}
+
+__global__ void k_init_state(Dev D) {
+    size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)D.M * D.Npad) return;
+    int a = int(e / D.Npad), p = int(e % D.Npad);
+    float rho = rho_val(D.rho_idx[a]);
+    float z = fminf(fmaxf(D.w0[e], D.lo[e]), D.up[e]);
+    if (p >= D.N) z = 0.f;
+    D.z[e] = z;
+    D.y[e] = 0.f;
+    float X = (p < D.N) ? (D.mu32[p] + rho * z) / (2.f * D.d32[p] + rho) : 0.f;
+    store_X(D, e, X);
+}
+
+void launch_init_state(const Dev& D, cudaStream_t st) {
+    size_t n = (size_t)D.M * D.Npad;
+    k_init_state<<<(unsigned)cdiv64(n, 256), 256, 0, st>>>(D);
+}
+
+// ---------------------------------------------------------------------------
+// G2 (SIMT): Ppart[s][m][k] = sum_{i in split s} X[m][i] B[i][k]
+// block = 32 accounts x all K factors over one asset split; 256 threads,
+// thread = one account x K/8 factors.
+// ---------------------------------------------------------------------------
+int choose_nsplit(int M, int N) {
+    int tiles = cdiv(M, 32);
+    int ns = std::max(1, 2 * 152 / tiles);
+    ns = std::min(ns, cdiv(N, 32));
+    return ns;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_P(Dev D) {
+    const int m0 = blockIdx.x * 32;
+    const int split = blockIdx.y;
+    const int chunk = cdiv(cdiv(D.N, D.nsplit), 32) * 32;
+    const int i_begin = split * chunk, i_end = min(D.N, i_begin + chunk);
+    __shared__ float sX[32][33];
+    __shared__ float sB[32][KMAX + 1];
+    const int t = threadIdx.x;
+    const int am = t >> 3;            // account within tile
+    const int kg = t & 7;             // factor group
+    const int K = D.K;
+    float acc[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) acc[q] = 0.f;
+    for (int i0 = i_begin; i0 < i_end; i0 += 32) {
+        __syncthreads();
+        for (int e = t; e < 32 * 32; e += 256) {
+            int r = e >> 5, cc = e & 31;
+            int m = m0 + r, i = i0 + cc;
+            sX[r][cc] = (m < D.M && i < i_end) ? D.X[(size_t)m * D.Npad + i] : 0.f;
+        }
+        for (int e = t; e < 32 * K; e += 256) {
+            int r = e / K, cc = e % K;
+            int i = i0 + r;
+            sB[r][cc] = (i < i_end) ? D.B32[(size_t)i * K + cc] : 0.f;
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int r = 0; r < 32; ++r) {
+            float x = sX[am][r];
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                int k = kg + 8 * q;
+                if (k < K) acc[q] = fmaf(x, sB[r][k], acc[q]);
+            }
+        }
+    }
+    int m = m0 + am;
+    if (m < D.M) {
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            int k = kg + 8 * q;
+            if (k < K) D.Ppart[((size_t)split * D.M + m) * K + k] = acc[q];
+        }
+    }
+}
+
+void launch_gemm_P(const Dev& D, cudaStream_t st) {
+    dim3 grid(cdiv(D.M, 32), D.nsplit);
+    k_gemm_P<<<grid, 256, 0, st>>>(D);
+}
+
+// ---------------------------------------------------------------------------
+// G3: Q[m] = Cinv[rho_idx[m]] * sum_s Ppart[s][m]; one block of K threads per account
+// ---------------------------------------------------------------------------
+__global__ void k_small_solve(Dev D) {
+    const int m = blockIdx.x;
+    const int K = D.K;
+    __shared__ float sP[KMAX];
+    const int t = threadIdx.x;
+    if (t < K) {
+        float s = 0.f;
+        for (int sp = 0; sp < D.nsplit; ++sp) s += D.Ppart[((size_t)sp * D.M + m) * K + t];
+        sP[t] = s;
+    }
+    __syncthreads();
+    if (t < K) {
+        const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + (size_t)t * K;
+        float q = 0.f;
+        for (int j = 0; j < K; ++j) q = fmaf(C[j], sP[j], q);
+        if (D.bf16) {
+            __nv_bfloat16 h = __float2bfloat16_rn(q);
+            D.Qhi[(size_t)m * K + t] = h;
+            D.Qlo[(size_t)m * K + t] = __float2bfloat16_rn(q - __bfloat162float(h));
+        }
+        D.Q[(size_t)m * K + t] = q;
+    }
+}
+
+void launch_small_solve(const Dev& D, cudaStream_t st) {
+    k_small_solve<<<D.M, 64, 0, st>>>(D);
+}
+
+// ---------------------------------------------------------------------------
+// G4 (SIMT): v = alpha x + (1-alpha) z + y/rho with x = X - Delta^{-1} (B Q)
+// block = 32 accounts x 64 assets; thread = 4 accounts x 2 assets
+// ---------------------------------------------------------------------------
+// v = alpha x + (1 - alpha) z + y / rho with x = X - Delta^{-1} BQ, X = Delta^{-1}(mu + rho z - y)
+// recomputed here in FP32 from the state (so the split copy of X feeds only the products).
+__device__ __forceinline__ float relaxed_v(const Dev& D, size_t e, int i, float BQ, float rho,
+                                           float irho) {
+    const float z = D.z[e], y = D.y[e];
+    const float dinv = 1.f / (2.f * D.d32[i] + rho);
+    const float x = (D.mu32[i] + rho * z - y - BQ) * dinv;
+    return D.alpha * x + (1.f - D.alpha) * z + y * irho;
+}
+
+__global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
+    const int m0 = blockIdx.y * 32;
+    const int i0 = blockIdx.x * 64;
+    const int K = D.K;
+    __shared__ float sQ[32][KMAX + 1];
+    __shared__ float sB[64][KMAX + 1];
+    const int t = threadIdx.x;
+    for (int e = t; e < 32 * K; e += 256) {
+        int r = e / K, cc = e % K;
+        int m = m0 + r;
+        sQ[r][cc] = (m < D.M) ? D.Q[(size_t)m * K + cc] : 0.f;
+    }
+    for (int e = t; e < 64 * K; e += 256) {
+        int r = e / K, cc = e % K;
+        int i = i0 + r;
+        sB[r][cc] = (i < D.N) ? D.B32[(size_t)i * K + cc] : 0.f;
+    }
+    __syncthreads();
+    const int lane = t & 31, grp = t >> 5;    // 8 groups of 4 accounts
+    float acc[4][2];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) acc[u][0] = acc[u][1] = 0.f;
+    for (int k = 0; k < K; ++k) {
+        float b0 = sB[lane][k], b1 = sB[lane + 32][k];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            float q = sQ[grp * 4 + u][k];
+            acc[u][0] = fmaf(q, b0, acc[u][0]);
+            acc[u][1] = fmaf(q, b1, acc[u][1]);
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        int m = m0 + grp * 4 + u;
+        if (m >= D.M) continue;
+        float rho = rho_val(D.rho_idx[m]);
+        float irho = 1.f / rho;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int i = i0 + lane + 32 * h;
+            if (i >= D.N) continue;
+            size_t e = (size_t)m * D.Npad + i;
+            D.v[e] = relaxed_v(D, e, i, acc[u][h], rho, irho);
+        }
+    }
+}
+
+void launch_gemm_x(const Dev& D, cudaStream_t st) {
+    dim3 grid(cdiv(D.N, 64), cdiv(D.M, 32));
+    k_gemm_x<<<grid, 256, 0, st>>>(D);
+}
+
+// ---------------------------------------------------------------------------
+// G5/G6: projection onto Z with the transition prox, dual update, residuals,
+// penalty adaptation, convergence. One block per account, warp w owns sectors
+// w, w + nwarps, ...
+// ---------------------------------------------------------------------------
+struct EntryEval {
+    float z;
+    int lin;   // 1 when dz/deta = -1/rho (z strictly inside a linear piece)
+};
+
+// z_i(eta) for one entry: prox of (phi_i + theta|.-w0|)/rho on [l, u] at t = v - eta/rho.
+__device__ __forceinline__ EntryEval eval_entry(const Dev& D, size_t e, float vv, float eta,
+                                                float theta, float irho) {
+    EntryEval r;
+    const float t = vv - eta * irho;
+    const float w0 = D.w0[e], lo = D.lo[e], up = D.up[e];
+    const int pw = D.pw_idx ? D.pw_idx[e] : -1;
+    if (pw < 0) {
+        const float k = (D.c[e] + theta) * irho;
+        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+        z = fminf(fmaxf(z, lo), up);
+        r.z = z;
+        r.lin = (z > lo && z < up && z != w0) ? 1 : 0;
+    } else {
+        // segment search: the first segment j whose stationary point t - s_j/rho does
+        // not lie above it decides; below its left end -> the breakpoint itself
+        const float* bp = D.pw_bp + (size_t)pw * MAXBP;
+        const float* sl = D.pw_sl + (size_t)pw * (MAXBP - 1);
+        const int nb = D.pw_nbp[pw];
+        float z = bp[nb - 1];
+        int lin = 0;
+        for (int j = 0; j + 1 < nb; ++j) {
+            const float sj = sl[j] + theta * ((bp[j] + bp[j + 1] > 2.f * w0) ? 1.f : -1.f);
+            const float cand = t - sj * irho;
+            if (cand <= bp[j]) { z = bp[j]; break; }
+            if (cand < bp[j + 1]) { z = cand; lin = 1; break; }
+        }
+        r.z = z;
+        r.lin = lin;
+    }
+    return r;
+}
+
+// Warp-collective sum of z and count of linear entries over sorted positions [p0, p1).
+__device__ __forceinline__ void warp_sector_sum(const Dev& D, size_t base, int p0, int p1, float eta,
+                                                float theta, float irho, float& sum, int& cnt) {
+    const int lane = threadIdx.x & 31;
+    float s = 0.f;
+    int n = 0;
+    for (int p = p0 + lane; p < p1; p += 32) {
+        size_t e = base + p;
+        EntryEval r = eval_entry(D, e, D.v[e], eta, theta, irho);
+        s += r.z;
+        n += r.lin;
+    }
+    sum = warp_sum(s);
+    cnt = warp_sum(n);
+}
+
+// Safeguarded Newton for g(x) = S(x) - target, S nonincreasing PWL with slope -cnt/rho.
+struct Root {
+    float x, a, b, step;
+    int done;
+};
+
+__device__ __forceinline__ void root_init(Root& R, float x0, float step) {
+    R.x = x0;
+    R.a = -FLT_MAX;
+    R.b = FLT_MAX;
+    R.step = step;
+    R.done = 0;
+}
+
+// One update from g = S(x) - target and the count of linear entries. Returns next x.
+__device__ __forceinline__ void root_update(Root& R, float g, int cnt, float rho, float tol) {
+    if (fabsf(g) <= tol) { R.done = 1; return; }
+    if (g > 0.f) R.a = R.x; else R.b = R.x;
+    float xn;
+    bool ok = false;
+    if (cnt > 0) {
+        xn = R.x + g * rho / float(cnt);
+        ok = (xn > R.a && xn < R.b);
+    }
+    if (!ok) {
+        if (R.a > -FLT_MAX && R.b < FLT_MAX) {
+            xn = 0.5f * (R.a + R.b);
+        } else {
+            xn = (g > 0.f) ? R.x + R.step : R.x - R.step;
+            R.step *= 2.f;
+        }
+    }
+    if (R.a > -FLT_MAX && R.b < FLT_MAX && (R.b - R.a) <= 4e-7f * fmaxf(1e-6f, fabsf(R.a) + fabsf(R.b))) {
+        R.x = 0.5f * (R.a + R.b);
+        R.done = 1;
+        return;
+    }
+    R.x = xn;
+}
+
+struct ProxShared {
+    float eta_hi[SMAX], eta_lo[SMAX];
+    float cap_hi[SMAX], floor_lo[SMAX];
+    float red_f[32];
+    int red_i[32];
+    float red_f2[32];
+};
+
+// Inner projection at fixed theta: per-sector edge roots, then the budget root.
+// Returns nu; sector edge multipliers in sh.eta_*. Block-collective.
+__device__ float project_inner(const Dev& D, int a, float theta, float rho, float irho,
+                               float nu0, ProxShared& sh) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const size_t base = (size_t)a * D.Npad;
+    const float step0 = 0.05f * rho + 1e-6f;
+    // phase A: sector edges
+    for (int s = warp; s < D.S; s += nwarps) {
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        const float hi = D.band_hi[a * D.S + s], lo = D.band_lo[a * D.S + s];
+        float eh = -FLT_MAX, el = FLT_MAX;
+        if (p1 > p0 && hi < sh.cap_hi[s]) {
+            Root R;
+            float w = D.eta_hi[a * D.S + s];
+            root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
+            for (int it = 0; it < PROX_MAXIT && !R.done; ++it) {
+                float sum; int cnt;
+                warp_sector_sum(D, base, p0, p1, R.x, theta, irho, sum, cnt);
+                root_update(R, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
+            }
+            eh = R.x;
+        }
+        if (p1 > p0 && lo > sh.floor_lo[s]) {
+            Root R;
+            float w = D.eta_lo[a * D.S + s];
+            root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
+            for (int it = 0; it < PROX_MAXIT && !R.done; ++it) {
+                float sum; int cnt;
+                warp_sector_sum(D, base, p0, p1, R.x, theta, irho, sum, cnt);
+                root_update(R, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
+            }
+            el = R.x;
+        }
+        if ((threadIdx.x & 31) == 0) {
+            sh.eta_hi[s] = eh;
+            sh.eta_lo[s] = el;
+        }
+    }
+    __syncthreads();
+    // phase B: budget multiplier
+    Root R;
+    root_init(R, nu0, step0);
+    for (int it = 0; it < PROX_MAXIT; ++it) {
+        float part = 0.f;
+        int pc = 0;
+        for (int s = warp; s < D.S; s += nwarps) {
+            const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+            float arg = fminf(fmaxf(R.x, sh.eta_hi[s]), sh.eta_lo[s]);
+            float sum; int cnt;
+            warp_sector_sum(D, base, p0, p1, arg, theta, irho, sum, cnt);
+            part += sum;
+            if (arg == R.x) pc += cnt;
+        }
+        if ((threadIdx.x & 31) == 0) { sh.red_f[warp] = part; sh.red_i[warp] = pc; }
+        __syncthreads();
+        float T = 0.f;
+        int C = 0;
+        for (int w = 0; w < nwarps; ++w) { T += sh.red_f[w]; C += sh.red_i[w]; }
+        __syncthreads();
+        root_update(R, T - 1.f, C, rho, 1e-6f);
+        if (R.done) break;
+    }
+    return R.x;
+}
+
+// Turnover sum_i |z_i - w0_i| at the current (nu, eta, theta). Block-collective.
+__device__ float turnover_at(const Dev& D, int a, float nu, float theta, float irho, ProxShared& sh) {
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const size_t base = (size_t)a * D.Npad;
+    float part = 0.f;
+    for (int s = warp; s < D.S; s += nwarps) {
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+        float acc = 0.f;
+        for (int p = p0 + lane; p < p1; p += 32) {
+            size_t e = base + p;
+            EntryEval r = eval_entry(D, e, D.v[e], arg, theta, irho);
+            acc += fabsf(r.z - D.w0[e]);
+        }
+        part += warp_sum(acc);
+    }
+    if (lane == 0) sh.red_f[warp] = part;
+    __syncthreads();
+    float U = 0.f;
+    for (int w = 0; w < nwarps; ++w) U += sh.red_f[w];
+    __syncthreads();
+    return U;
+}
+
+__global__ void __launch_bounds__(1024) k_prox(Dev D) {
+    const int a = blockIdx.x;
+    if (!D.active[a]) return;
+    __shared__ ProxShared sh;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
+    const int tid = threadIdx.x;
+    const size_t base = (size_t)a * D.Npad;
+    const int j = D.rho_idx[a];
+    const float rho = rho_val(j), irho = 1.f / rho;
+    // sector capacities (largest / smallest attainable sums)
+    for (int s = warp; s < D.S; s += nwarps) {
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        float cu = 0.f, cl = 0.f;
+        for (int p = p0 + lane; p < p1; p += 32) {
+            cu += D.up[base + p];
+            cl += D.lo[base + p];
+        }
+        cu = warp_sum(cu);
+        cl = warp_sum(cl);
+        if (lane == 0) { sh.cap_hi[s] = cu; sh.floor_lo[s] = cl; }
+    }
+    __syncthreads();
+    float theta = 0.f;
+    float nu = project_inner(D, a, 0.f, rho, irho, D.nu[a], sh);
+    const float tau = D.tau ? D.tau[a] : INFINITY;
+    if (tau < INFINITY) {
+        float U = turnover_at(D, a, nu, 0.f, irho, sh);
+        if (U > tau * (1.f + 1e-6f)) {
+            // bracketed secant (Illinois) on U(theta) - tau, U nonincreasing in theta
+            float t_lo = 0.f, u_lo = U - tau;
+            float t_hi = fmaxf(D.theta[a], 1e-4f), u_hi;
+            for (int it = 0; it < 40; ++it) {
+                nu = project_inner(D, a, t_hi, rho, irho, nu, sh);
+                u_hi = turnover_at(D, a, nu, t_hi, irho, sh) - tau;
+                if (u_hi <= 0.f) break;
+                t_lo = t_hi; u_lo = u_hi;
+                t_hi *= 4.f;
+            }
+            int side = 0;
+            theta = t_hi;
+            for (int it = 0; it < 60; ++it) {
+                float tn = t_hi - u_hi * (t_hi - t_lo) / (u_hi - u_lo);
+                if (!(tn > t_lo && tn < t_hi)) tn = 0.5f * (t_lo + t_hi);
+                nu = project_inner(D, a, tn, rho, irho, nu, sh);
+                float un = turnover_at(D, a, nu, tn, irho, sh) - tau;
+                theta = tn;
+                if (fabsf(un) <= 2e-7f * tau || (t_hi - t_lo) <= 1e-7f * t_hi) break;
+                if (un > 0.f) {
+                    t_lo = tn; u_lo = un;
+                    if (side == -1) u_hi *= 0.5f;
+                    side = -1;
+                } else {
+                    t_hi = tn; u_hi = un;
+                    if (side == 1) u_lo *= 0.5f;
+                    side = 1;
+                }
+            }
+        }
+    }
+    // final z, dual update, residuals
+    float rp = 0.f, rd = 0.f, nx = 0.f, nz = 0.f, ny = 0.f;
+    int bad = 0;
+    for (int s = warp; s < D.S; s += nwarps) {
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+        for (int p = p0 + lane; p < p1; p += 32) {
+            size_t e = base + p;
+            float vv = D.v[e];
+            EntryEval r = eval_entry(D, e, vv, arg, theta, irho);
+            float zo = D.z[e], yo = D.y[e];
+            float yn = rho * (vv - r.z);
+            rp = fmaxf(rp, fabsf(yn - yo) * irho);
+            rd = fmaxf(rd, rho * fabsf(r.z - zo));
+            nx = fmaxf(nx, fabsf(vv - yo * irho));
+            nz = fmaxf(nz, fabsf(r.z));
+            ny = fmaxf(ny, fabsf(yn));
+            bad |= !(isfinite(r.z) && isfinite(yn));
+            D.z[e] = r.z;
+            D.y[e] = yn;
+        }
+    }
+    rp = warp_max(rp); rd = warp_max(rd); nx = warp_max(nx); nz = warp_max(nz); ny = warp_max(ny);
+    bad = warp_sum(bad);
+    __shared__ float s_red[5][32];
+    __shared__ int s_bad[32];
+    __shared__ int s_newj;
+    if (lane == 0) {
+        s_red[0][warp] = rp; s_red[1][warp] = rd; s_red[2][warp] = nx; s_red[3][warp] = nz;
+        s_red[4][warp] = ny; s_bad[warp] = bad;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        for (int w = 1; w < nwarps; ++w) {
+            rp = fmaxf(rp, s_red[0][w]); rd = fmaxf(rd, s_red[1][w]); nx = fmaxf(nx, s_red[2][w]);
+            nz = fmaxf(nz, s_red[3][w]); ny = fmaxf(ny, s_red[4][w]); bad += s_bad[w];
+        }
+        int it = D.iters[a] + 1;
+        D.iters[a] = it;
+        D.rp[a] = rp;
+        D.rd[a] = rd;
+        D.nu[a] = nu;
+        D.theta[a] = theta;
+        int newj = j;
+        if (bad) {
+            D.status[a] = PRISM_NUMERICAL_FAILURE;
+            D.active[a] = 0;
+        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
+            D.active[a] = 0;
+        } else if (it >= D.max_iter) {
+            D.active[a] = 0;
+            D.status[a] = PRISM_TIMEOUT;
+        } else if (it % D.adapt_every == 0) {
+            float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
+            float du = rd / fmaxf(ny, 1e-12f);
+            float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
+            int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
+            dj = max(-4, min(4, dj));
+            newj = max(0, min(NRHO - 1, j + dj));
+        }
+        s_newj = newj;
+    }
+    __syncthreads();
+    const int newj = s_newj;
+    for (int s = warp; s < D.S; s += nwarps)
+        if (lane == 0) {
+            D.eta_hi[a * D.S + s] = sh.eta_hi[s];
+            D.eta_lo[a * D.S + s] = sh.eta_lo[s];
+        }
+    if (newj != j && tid == 0) D.rho_idx[a] = newj;
+    // X for the next iteration with the (possibly new) penalty
+    const float rn = rho_val(newj);
+    for (int p = tid; p < D.N; p += blockDim.x) {
+        size_t e = base + p;
+        float X = (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn);
+        store_X(D, e, X);
+    }
+}
+
+void launch_prox(const Dev& D, cudaStream_t st) {
+    int nw = std::min(32, std::max(4, D.S));
+    k_prox<<<D.M, 32 * nw, 0, st>>>(D);
+}
+
+__global__ void k_count_active(Dev D) {
+    __shared__ int s[32];
+    int n = 0;
+    for (int a = threadIdx.x; a < D.M; a += blockDim.x) n += D.active[a];
+    n = warp_sum(n);
+    if ((threadIdx.x & 31) == 0) s[threadIdx.x >> 5] = n;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        *D.n_active = t;
+    }
+}
+
+void launch_count_active(const Dev& D, cudaStream_t st) { k_count_active<<<1, 1024, 0, st>>>(D); }
+
+__global__ void k_mark_timeout(Dev D) {
+    int a = blockIdx.x * blockDim.x + threadIdx.x;
+    if (a < D.M && D.active[a]) { D.active[a] = 0; D.status[a] = PRISM_TIMEOUT; }
+}
+
+void launch_mark_timeout(const Dev& D, cudaStream_t st) { k_mark_timeout<<<cdiv(D.M, 128), 128, 0, st>>>(D); }
+
+}  // namespace prism

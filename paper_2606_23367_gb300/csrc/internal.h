@@ -1,0 +1,93 @@
+// internal.h -- host/device data structures shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <stdint.h>
+#include <string>
+#include <vector>
+
+#include "../../include/prism.h"
+
+namespace prism {
+
+// Penalty grid: rho_j = RHO_MIN * 10^(j / RHO_PER_DECADE), j = 0 .. NRHO-1.
+// The Woodbury capacitance (2F)^{-1} + B' Delta_j^{-1} B with Delta_j = diag(2d + rho_j)
+// is precomputed for every grid point when the universe is created, so a
+// per-account penalty change costs nothing but an index.
+constexpr int NRHO = 33;
+constexpr double RHO_MIN = 1e-4;
+constexpr int RHO_PER_DECADE = 4;
+inline double rho_of(int j) { return RHO_MIN * pow(10.0, double(j) / RHO_PER_DECADE); }
+
+constexpr int KMAX = 64;     // largest factor count
+constexpr int SMAX = 64;     // largest sector count
+constexpr int MAXLOT = 4;    // lots per entry the prox keeps (more are rejected)
+constexpr int MAXBP = MAXLOT + 3;   // breakpoints per entry: l, kinks (<= MAXLOT), w0, u
+
+void set_error(const std::string& msg);
+
+// A universe resident on one device, assets reordered so that each sector is
+// a contiguous range (sorted position p <-> original asset perm[p]).
+struct Universe {
+    int device = 0;
+    int N = 0, K = 0, S = 0, Npad = 0;
+    std::vector<int> perm, inv_perm, sec_start;   // host copies
+    int* d_inv_perm = nullptr;     // N: original asset -> sorted position
+    int* d_perm = nullptr;         // N: sorted position -> original asset
+    int* d_sec_start = nullptr;    // S+1
+    int* d_sector = nullptr;       // Npad: sector of each sorted position (-1 = padding)
+    double* d_B64 = nullptr;       // Npad x K (sorted, zero rows in padding)
+    double* d_f64 = nullptr;       // K
+    double* d_d64 = nullptr;       // Npad (1 in padding)
+    double* d_mu64 = nullptr;      // Npad (0 in padding)
+    float* d_B32 = nullptr;        // Npad x K
+    float* d_f32 = nullptr;        // K
+    float* d_d32 = nullptr;        // Npad
+    float* d_mu32 = nullptr;       // Npad
+    __nv_bfloat16* d_B16 = nullptr;   // Npad x K  (row-major, K contiguous)
+    __nv_bfloat16* d_Bt16 = nullptr;  // K x Npad  (assets contiguous)
+    float* d_Cinv32 = nullptr;     // NRHO x K x K, capacitance inverses for FP32 B
+    float* d_Cinv16 = nullptr;     // NRHO x K x K, for the BF16-rounded B
+    size_t bytes = 0;
+    cudaStream_t stream = nullptr;
+};
+
+// Device workspace of one solve (grown on demand, kept by the universe's owner).
+struct Workspace {
+    size_t bytes = 0;
+    std::vector<void*> blocks;
+    void* alloc(size_t n);        // 256-byte aligned, zero-filled by the caller if needed
+    void release();
+};
+
+// Per-account transition-cost description on the device (sorted layout, M x Npad).
+struct BatchDev {
+    int M = 0, Npad = 0;
+    bool has_lots = false, has_cap = false;
+    // FP64 per entry (polish / certification)
+    double *w0 = nullptr, *lo = nullptr, *up = nullptr, *c = nullptr;
+    // FP32 per entry (iterations)
+    float *w0f = nullptr, *lof = nullptr, *upf = nullptr, *cf = nullptr;
+    // piecewise-linear pieces for entries with lots: MAXBP breakpoints, MAXBP-1 slopes
+    int* pw_idx = nullptr;         // M x Npad: -1 = plain L1 entry, else row in pw tables
+    int n_pw = 0;
+    double *pw_bp = nullptr, *pw_sl = nullptr;   // n_pw x MAXBP, n_pw x (MAXBP-1)
+    float *pw_bpf = nullptr, *pw_slf = nullptr;
+    int* pw_nbp = nullptr;         // n_pw
+    double *band_lo = nullptr, *band_hi = nullptr;   // M x S
+    float *band_lof = nullptr, *band_hif = nullptr;
+    double* tau = nullptr;         // M
+    float* tauf = nullptr;
+    int* member = nullptr;         // M x Npad: 1 if the entry belongs to the account
+};
+
+}  // namespace prism
+
+struct prism_universe {
+    prism::Universe u;
+};
+
+struct prism_state {
+    int dummy = 0;
+};

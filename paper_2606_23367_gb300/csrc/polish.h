@@ -1,0 +1,63 @@
+// polish.h -- FP64 polish / certification state.
+#pragma once
+
+#include "internal.h"
+
+namespace prism {
+
+constexpr int PMAXROWS = 24;   // working rows per polish: budget + held bands + cap
+
+struct PolDev {
+    int M = 0, N = 0, Npad = 0, K = 0, S = 0;
+    const double* B64 = nullptr;
+    const double* f64 = nullptr;
+    const double* d64 = nullptr;
+    const double* mu64 = nullptr;
+    const int* sec_start = nullptr;
+    const int* sector = nullptr;
+    const double* w0 = nullptr;         // M x Npad
+    const double* lo = nullptr;
+    const double* up = nullptr;
+    const double* c = nullptr;
+    const int* pw_idx = nullptr;
+    const double* pw_bp = nullptr;
+    const double* pw_sl = nullptr;
+    const double* pw_phi_lo = nullptr;  // phi at the left breakpoint of each PWL row
+    const int* pw_nbp = nullptr;
+    const double* band_lo = nullptr;    // M x S
+    const double* band_hi = nullptr;
+    const double* tau = nullptr;        // M (+inf = none)
+    const float* z = nullptr;           // ADMM iterate, M x Npad
+    const float* nu_f = nullptr;        // ADMM budget multiplier, M
+    const float* eta_hi_f = nullptr;    // M x S
+    const float* eta_lo_f = nullptr;
+    const float* theta_f = nullptr;     // M
+    int* skip = nullptr;                // M: 1 = leave this account alone
+    // state and scratch
+    int8_t* st = nullptr;               // M x Npad entry state
+    int* wband = nullptr;               // M x S working bands
+    int* wcap = nullptr;                // M
+    int* done = nullptr;                // M: 0 running, 1 certified, 2 failed
+    int* Flist = nullptr;               // M x FMAX
+    int* NZlist = nullptr;              // M x FMAX
+    double* Fsig = nullptr;             // M x FMAX cap sign of each free entry
+    double* Y = nullptr;                // M x FMAX x (PMAXROWS + 1)
+    int FMAX = 0;
+    // outputs
+    double* W = nullptr;                // M x Npad weights (FP64)
+    double* nu = nullptr;               // M
+    double* lam = nullptr;              // M x S
+    double* theta = nullptr;            // M
+    double* diag = nullptr;             // M x PRISM_NDIAG
+    int* status = nullptr;              // M
+    double tol_dual = 1e-11;
+    double tol_primal = 1e-12;
+};
+
+size_t polish_smem_bytes();
+void launch_classify(const PolDev& P, cudaStream_t st);
+void launch_polish_round(const PolDev& P, cudaStream_t st);
+void launch_fallback(const PolDev& P, cudaStream_t st);
+void launch_finish_status(const PolDev& P, double eps, cudaStream_t st);
+
+}  // namespace prism

@@ -1,0 +1,858 @@
+// solve.cu -- prism_solve_batch: packing, feasibility test, ADMM loop, polish, unpack.
+//
+// Call structure (one call = one book of accounts, Fig. 2 public solver call):
+//   1. validate and pack the ragged FP64 inputs into a sector-sorted M x Npad
+//      device layout (FP64 copies for the polish, FP32 copies for the iterations);
+//      lot data become per-entry piecewise-linear cost tables;
+//   2. closed-form capacity test per account (budget, box and bands admit a point);
+//      accounts that fail get NO_FEASIBLE_RETURN;
+//   3. ADMM iterations, check_every at a time, captured once in a CUDA graph and
+//      replayed until every account has converged or hit its cap;
+//   4. FP64 polish rounds and certification; accounts the polish cannot settle go
+//      back to the iterations with a tighter target, then fall back to the
+//      projected iterate (FEASIBLE_NONCERTIFIED when it passes the gates);
+//   5. unpack weights, multipliers, status and diagnostics into the caller's layout.
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+#include "polish.h"
+#include "solver.h"
+
+namespace prism {
+
+// ---------------------------------------------------------------------------
+// workspace: one device arena per universe handle, grown on demand
+// ---------------------------------------------------------------------------
+struct Arena {
+    char* base = nullptr;
+    size_t cap = 0, used = 0;
+    int alloc_fail = 0;
+    template <typename T>
+    T* take(size_t n) {
+        size_t bytes = (n * sizeof(T) + 255) / 256 * 256;
+        if (used + bytes > cap) { alloc_fail = 1; return nullptr; }
+        T* p = reinterpret_cast<T*>(base + used);
+        used += bytes;
+        return p;
+    }
+};
+
+// Launch accounting and, in profile mode, CUDA events around every launch.
+struct Prof {
+    bool on = false;
+    std::vector<cudaEvent_t> pool;
+    size_t used = 0;
+    struct Mark { int cls; cudaEvent_t a, b; };
+    std::vector<Mark> marks;
+    int64_t launches[PRISM_NKCLASS] = {};
+    cudaEvent_t get() {
+        if (used == pool.size()) {
+            cudaEvent_t e;
+            cudaEventCreate(&e);
+            pool.push_back(e);
+        }
+        return pool[used++];
+    }
+    void reset() {
+        used = 0;
+        marks.clear();
+        for (auto& l : launches) l = 0;
+    }
+    template <class F>
+    void run(int cls, int nkernels, cudaStream_t st, F f) {
+        launches[cls] += nkernels;
+        if (!on) { f(); return; }
+        cudaEvent_t a = get(), b = get();
+        cudaEventRecord(a, st);
+        f();
+        cudaEventRecord(b, st);
+        marks.push_back({cls, a, b});
+    }
+};
+
+struct SolveCache {
+    Prof prof;
+    char* arena = nullptr;
+    size_t arena_bytes = 0;
+    int* pinned = nullptr;          // host-pinned counter readback
+    cudaGraphExec_t gexec = nullptr;
+    Dev gdev;                       // Dev the graph was captured with
+    bool have_graph = false;
+    int g_iters = 0;
+    int64_t g_launches[PRISM_NKCLASS] = {};
+    cudaEvent_t ev[6] = {};
+};
+
+static SolveCache& cache_of(prism_universe* uh) {
+    static_assert(sizeof(void*) == 8, "64-bit only");
+    // one cache per universe handle, stored alongside it
+    struct Holder { prism_universe* u; SolveCache c; };
+    static std::vector<Holder*> all;
+    for (Holder* h : all) if (h->u == uh) return h->c;
+    Holder* h = new Holder{uh, SolveCache()};
+    all.push_back(h);
+    return h->c;
+}
+
+void release_cache(prism_universe* uh);
+
+// ---------------------------------------------------------------------------
+// pack / validate
+// ---------------------------------------------------------------------------
+enum : int { ERR_INDEX = 1, ERR_NONFINITE = 2, ERR_BOUNDS = 4, ERR_DUP = 8, ERR_COST = 16, ERR_LEN = 32 };
+
+struct PackArgs {
+    int M, N, Npad;
+    const int64_t* offsets;      // device
+    const int32_t* asset_idx;    // device or null
+    const double *w0, *lo, *up, *tc;   // device ragged
+    const int* inv_perm;
+    double *W0, *LO, *UP, *C;
+    float *W0f, *LOf, *UPf, *Cf;
+    int* member;
+    int* err;
+    int64_t nnz;
+};
+
+__global__ void k_pack(PackArgs A) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.nnz) return;
+    // account of entry e: last a with offsets[a] <= e
+    int lo = 0, hi = A.M;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (A.offsets[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int a = lo;
+    int i = A.asset_idx ? A.asset_idx[e] : int(e - A.offsets[a]);
+    if (i < 0 || i >= A.N) { atomicOr(A.err, ERR_INDEX); return; }
+    const double w0 = A.w0[e], l = A.lo[e], u = A.up[e], c = A.tc[e];
+    if (!(isfinite(w0) && isfinite(l) && isfinite(u) && isfinite(c))) { atomicOr(A.err, ERR_NONFINITE); return; }
+    if (l > u) { atomicOr(A.err, ERR_BOUNDS); return; }
+    if (c < 0) { atomicOr(A.err, ERR_COST); return; }
+    const size_t d = (size_t)a * A.Npad + A.inv_perm[i];
+    if (atomicExch(&A.member[d], 1) != 0) { atomicOr(A.err, ERR_DUP); return; }
+    A.W0[d] = w0; A.LO[d] = l; A.UP[d] = u; A.C[d] = c;
+    A.W0f[d] = float(w0); A.LOf[d] = float(l); A.UPf[d] = float(u); A.Cf[d] = float(c);
+}
+
+struct UnpackArgs {
+    int M, Npad;
+    const int64_t* offsets;
+    const int32_t* asset_idx;
+    const int* inv_perm;
+    const double* W;
+    double* out;
+    int64_t nnz;
+};
+
+__global__ void k_unpack(UnpackArgs A) {
+    int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= A.nnz) return;
+    int lo = 0, hi = A.M;
+    while (hi - lo > 1) {
+        int mid = (lo + hi) >> 1;
+        if (A.offsets[mid] <= e) lo = mid; else hi = mid;
+    }
+    const int a = lo;
+    int i = A.asset_idx ? A.asset_idx[e] : int(e - A.offsets[a]);
+    A.out[e] = A.W[(size_t)a * A.Npad + A.inv_perm[i]];
+}
+
+// Closed-form feasibility of budget + box + bands (+ the least-turnover test for a
+// cap): sum_s max(lo_s, sum_{i in s} l_i) <= 1 <= sum_s min(hi_s, sum_{i in s} u_i).
+__global__ void k_capacity(int S, int Npad, const int* sec_start, const double* LO, const double* UP,
+                           const double* W0, const double* band_lo, const double* band_hi,
+                           const double* tau, int* status, int* skip, int* active) {
+    const int a = blockIdx.x;
+    __shared__ double s_up[SMAX], s_lo[SMAX], s_kept[SMAX], s_forced[SMAX], s_w0[SMAX];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const size_t base = (size_t)a * Npad;
+    for (int s = warp; s < S; s += nw) {
+        double su = 0, sl = 0, sk = 0, sf = 0, sw = 0;
+        for (int p = sec_start[s] + lane; p < sec_start[s + 1]; p += 32) {
+            double u = UP[base + p], l = LO[base + p], w = W0[base + p];
+            su += u; sl += l; sk += fmin(w, u); sf += fmax(w - u, 0.0); sw += w;
+        }
+        su = warp_sum(su); sl = warp_sum(sl); sk = warp_sum(sk); sf = warp_sum(sf); sw = warp_sum(sw);
+        if (lane == 0) { s_up[s] = su; s_lo[s] = sl; s_kept[s] = sk; s_forced[s] = sf; s_w0[s] = sw; }
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double cap = 0, flo = 0, forced = 0, w0s = 0;
+        bool ok = true, lo_zero = true;
+        for (int s = 0; s < S; ++s) {
+            const double hi = band_hi[a * S + s], lo = band_lo[a * S + s];
+            if (lo > s_up[s] + 1e-12 || s_lo[s] > hi + 1e-12) ok = false;
+            cap += fmin(hi, s_up[s]);
+            flo += fmax(lo, s_lo[s]);
+            forced += s_forced[s] + fmax(s_kept[s] - hi, 0.0);
+            w0s += s_w0[s];
+            if (lo > 0 || s_lo[s] > 0) lo_zero = false;
+        }
+        if (!(cap >= 1.0 - 1e-12 && flo <= 1.0 + 1e-12)) ok = false;
+        const double t = tau[a];
+        if (ok && isfinite(t) && lo_zero && fabs(w0s - 1.0) < 1e-9 && 2.0 * forced > t * (1.0 + 1e-12)) ok = false;
+        if (!ok) {
+            status[a] = PRISM_NO_FEASIBLE_RETURN;
+            skip[a] = 1;
+            active[a] = 0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------
+// tax lots: convex piecewise-linear transition cost (lot-LP partial minimum)
+// ---------------------------------------------------------------------------
+struct PwlRow {
+    double bp[MAXBP];
+    double sl[MAXBP - 1];
+    int nb;
+    double phi_lo;
+};
+
+// phi(x) = c (x - w0) + G(max(S*, w0 - x)), G(S) = 2 c S + cheapest-first lot cost of S.
+static double lot_phi(double x, double w0, double c, const std::vector<std::pair<double, double>>& lots) {
+    double sstar = 0.0;
+    for (auto& l : lots) if (2.0 * c + l.second < 0.0) sstar += l.first;
+    double S = std::max(sstar, w0 - x);
+    double g = 2.0 * c * S, rem = S;
+    for (size_t j = 0; j < lots.size() && rem > 0; ++j) {
+        double take = (j + 1 < lots.size()) ? std::min(rem, lots[j].first) : rem;
+        g += lots[j].second * take;
+        rem -= take;
+    }
+    return c * (x - w0) + g;
+}
+
+static bool build_pwl(double w0, double lo, double up, double c, std::vector<std::pair<double, double>> lots,
+                      PwlRow& row) {
+    std::stable_sort(lots.begin(), lots.end(),
+                     [](const std::pair<double, double>& a, const std::pair<double, double>& b) { return a.second < b.second; });
+    // kinks over the real line with the slope to their right
+    std::vector<double> kinks;
+    std::vector<double> right_slope;
+    const int L = (int)lots.size();
+    int js = 0;
+    while (js < L && 2.0 * c + lots[js].second < 0.0) ++js;
+    std::vector<double> slopes;   // left to right
+    if (js < L) {
+        double H = 0.0;
+        for (int j = 0; j < js; ++j) H += lots[j].first;
+        // slope right of w0 - S* is c; left of it the lots js, js+1, ... are sold in turn
+        double x = w0 - H;
+        kinks.push_back(x);
+        double Hj = H;
+        std::vector<double> xs{x};
+        for (int j = js; j < L - 1; ++j) { Hj += lots[j].first; xs.push_back(w0 - Hj); }
+        // xs decreasing; slopes left of xs[q] = -c - kappa[js + q]
+        kinks.assign(xs.rbegin(), xs.rend());
+        for (int j = L - 1; j >= js; --j) slopes.push_back(-c - lots[j].second);
+        slopes.push_back(c);
+    } else {
+        slopes.push_back(c);
+    }
+    if (!(up > lo)) {
+        row.nb = 1; row.bp[0] = lo; row.phi_lo = lot_phi(lo, w0, c, lots);
+        return true;
+    }
+    std::vector<double> pts{lo};
+    for (double x : kinks) if (x > lo && x < up) pts.push_back(x);
+    if (w0 > lo && w0 < up) pts.push_back(w0);
+    std::sort(pts.begin(), pts.end());
+    pts.erase(std::unique(pts.begin(), pts.end()), pts.end());
+    pts.push_back(up);
+    if ((int)pts.size() > MAXBP) return false;
+    row.nb = (int)pts.size();
+    for (int j = 0; j < row.nb; ++j) row.bp[j] = pts[j];
+    for (int j = 0; j + 1 < row.nb; ++j) {
+        double mid = 0.5 * (pts[j] + pts[j + 1]);
+        int q = int(std::upper_bound(kinks.begin(), kinks.end(), mid) - kinks.begin());
+        row.sl[j] = slopes[q];
+    }
+    row.phi_lo = lot_phi(lo, w0, c, lots);
+    return true;
+}
+
+template <typename T>
+static bool is_dev(const T* p) {
+    if (!p) return false;
+    cudaPointerAttributes attr;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+static int to_host(const T* src, size_t n, std::vector<T>& dst) {
+    dst.resize(n);
+    if (!n) return PRISM_OK;
+    PRISM_CUDA_TRY(cudaMemcpy(dst.data(), src, n * sizeof(T), cudaMemcpyDefault));
+    return PRISM_OK;
+}
+
+static double ms_between(cudaEvent_t a, cudaEvent_t b) {
+    float ms = 0.f;
+    cudaEventElapsedTime(&ms, a, b);
+    return ms;
+}
+
+// ---------------------------------------------------------------------------
+// one batched solve (all accounts share the launch sequence)
+// ---------------------------------------------------------------------------
+static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solve_opts* o,
+                      prism_result* res, bool batched_mode_bf16, bool plain) {
+    Universe& U = uh->u;
+    SolveCache& SC = cache_of(uh);
+    const auto t_call0 = std::chrono::steady_clock::now();
+    PRISM_CUDA_TRY(cudaSetDevice(U.device));
+    cudaStream_t st = o->cuda_stream ? (cudaStream_t)o->cuda_stream : U.stream;
+    const int M = b->n_accounts, N = U.N, Npad = U.Npad, K = U.K, S = U.S;
+    // ---- offsets
+    std::vector<int64_t> offs;
+    int rc = to_host(b->offsets, (size_t)M + 1, offs);
+    if (rc) return rc;
+    if (offs[0] != 0) { set_error("offsets[0] must be 0"); return PRISM_ERR_ARGUMENT; }
+    for (int a = 0; a < M; ++a) {
+        if (offs[a + 1] < offs[a]) { set_error("offsets must be nondecreasing"); return PRISM_ERR_ARGUMENT; }
+        if (!b->asset_idx && offs[a + 1] - offs[a] != N) {
+            set_error("without asset_idx every account must span the universe (N entries)");
+            return PRISM_ERR_ARGUMENT;
+        }
+        if (offs[a + 1] - offs[a] > N) { set_error("account longer than the universe"); return PRISM_ERR_ARGUMENT; }
+    }
+    const int64_t nnz = offs[M];
+    // ---- lots (host-side construction of the piecewise-linear tables)
+    std::vector<PwlRow> pwl;
+    std::vector<int> pw_of_entry;   // ragged entry -> pw row or -1
+    const bool has_lots = b->lot_offsets != nullptr;
+    if (has_lots) {
+        std::vector<int64_t> lo_off;
+        std::vector<double> lsz, lka, w0h, loh, uph, tch;
+        if ((rc = to_host(b->lot_offsets, (size_t)nnz + 1, lo_off))) return rc;
+        const int64_t nl = lo_off[nnz];
+        if ((rc = to_host(b->lot_size, (size_t)nl, lsz)) || (rc = to_host(b->lot_kappa, (size_t)nl, lka)) ||
+            (rc = to_host(b->w0, (size_t)nnz, w0h)) || (rc = to_host(b->lower, (size_t)nnz, loh)) ||
+            (rc = to_host(b->upper, (size_t)nnz, uph)) || (rc = to_host(b->tc, (size_t)nnz, tch)))
+            return rc;
+        pw_of_entry.assign(nnz, -1);
+        for (int64_t e = 0; e < nnz; ++e) {
+            const int64_t l0 = lo_off[e], l1 = lo_off[e + 1];
+            if (l1 < l0) { set_error("lot_offsets must be nondecreasing"); return PRISM_ERR_ARGUMENT; }
+            if (l1 == l0) continue;
+            if (l1 - l0 > MAXLOT) { set_error("more than 4 lots on one entry"); return PRISM_ERR_UNSUPPORTED; }
+            if (loh[e] < 0) { set_error("lots need lower >= 0"); return PRISM_ERR_ARGUMENT; }
+            std::vector<std::pair<double, double>> lots;
+            double hs = 0;
+            for (int64_t q = l0; q < l1; ++q) {
+                if (!(lsz[q] >= 0) || !std::isfinite(lka[q])) { set_error("bad lot data"); return PRISM_ERR_ARGUMENT; }
+                lots.push_back({lsz[q], lka[q]});
+                hs += lsz[q];
+            }
+            if (std::fabs(hs - w0h[e]) > 1e-9 * std::max(1.0, std::fabs(w0h[e]))) {
+                set_error("lot sizes of an entry must sum to its w0");
+                return PRISM_ERR_ARGUMENT;
+            }
+            PwlRow row;
+            if (!build_pwl(w0h[e], loh[e], uph[e], tch[e], lots, row)) {
+                set_error("too many breakpoints in a lot cost");
+                return PRISM_ERR_UNSUPPORTED;
+            }
+            pw_of_entry[e] = (int)pwl.size();
+            pwl.push_back(row);
+        }
+    }
+    const int n_pw = (int)pwl.size();
+    // ---- workspace layout
+    const size_t MN = (size_t)M * Npad;
+    const int nsplit = choose_nsplit(M, N);
+    const int FMAX = std::min(N, 2048);
+    auto layout = [&](Arena& A, Dev& D, PolDev& P, BatchDev& BD, void** stage, int** member, int** err,
+                      int** pwidx_dev, double** ragged_out) {
+        BD.w0 = A.take<double>(MN); BD.lo = A.take<double>(MN); BD.up = A.take<double>(MN); BD.c = A.take<double>(MN);
+        BD.w0f = A.take<float>(MN); BD.lof = A.take<float>(MN); BD.upf = A.take<float>(MN); BD.cf = A.take<float>(MN);
+        *member = A.take<int>(MN);
+        *pwidx_dev = has_lots ? A.take<int>(MN) : nullptr;
+        BD.band_lo = A.take<double>((size_t)M * S); BD.band_hi = A.take<double>((size_t)M * S);
+        BD.band_lof = A.take<float>((size_t)M * S); BD.band_hif = A.take<float>((size_t)M * S);
+        BD.tau = A.take<double>(M); BD.tauf = A.take<float>(M);
+        D.z = A.take<float>(MN); D.y = A.take<float>(MN); D.v = A.take<float>(MN);
+        D.X = A.take<float>(MN);
+        D.Xhi = A.take<__nv_bfloat16>(MN); D.Xlo = A.take<__nv_bfloat16>(MN);
+        D.Ppart = A.take<float>((size_t)nsplit * M * K);
+        D.Q = A.take<float>((size_t)M * K);
+        D.Qhi = A.take<__nv_bfloat16>((size_t)M * K); D.Qlo = A.take<__nv_bfloat16>((size_t)M * K);
+        D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
+        D.nu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
+        D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(1);
+        P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
+        P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
+        P.Fsig = A.take<double>((size_t)M * FMAX);
+        P.Y = A.take<double>((size_t)M * FMAX * (PMAXROWS + 1));
+        P.W = A.take<double>(MN); P.nu = A.take<double>(M); P.lam = A.take<double>((size_t)M * S);
+        P.theta = A.take<double>(M); P.diag = A.take<double>((size_t)M * PRISM_NDIAG);
+        int* skip = A.take<int>(M);
+        P.skip = skip;
+        *err = A.take<int>(4);
+        // staging for host inputs / outputs (ragged FP64 x 4, offsets, asset_idx, out)
+        stage[0] = A.take<double>((size_t)nnz); stage[1] = A.take<double>((size_t)nnz);
+        stage[2] = A.take<double>((size_t)nnz); stage[3] = A.take<double>((size_t)nnz);
+        stage[4] = A.take<int64_t>((size_t)M + 1);
+        stage[5] = b->asset_idx ? (void*)A.take<int32_t>((size_t)nnz) : nullptr;
+        *ragged_out = A.take<double>((size_t)nnz);
+        BD.pw_bp = A.take<double>((size_t)std::max(n_pw, 1) * MAXBP);
+        BD.pw_sl = A.take<double>((size_t)std::max(n_pw, 1) * (MAXBP - 1));
+        BD.pw_bpf = A.take<float>((size_t)std::max(n_pw, 1) * MAXBP);
+        BD.pw_slf = A.take<float>((size_t)std::max(n_pw, 1) * (MAXBP - 1));
+        BD.pw_nbp = A.take<int>((size_t)std::max(n_pw, 1));
+        stage[6] = A.take<double>((size_t)std::max(n_pw, 1));   // phi_lo
+    };
+    Dev D;
+    std::memset((void*)&D, 0, sizeof(Dev));   // padding bytes take part in the graph-reuse test
+    PolDev P;
+    BatchDev BD;
+    void* stage[7];
+    int *member, *err, *pwidx;
+    double* ragged_out;
+    {
+        Arena probe;
+        probe.base = nullptr; probe.cap = SIZE_MAX;
+        layout(probe, D, P, BD, stage, &member, &err, &pwidx, &ragged_out);
+        size_t need = probe.used + 4096;
+        if (SC.arena_bytes < need) {
+            if (SC.arena) { cudaFree(SC.arena); SC.arena = nullptr; SC.arena_bytes = 0; }
+            if (SC.have_graph) { cudaGraphExecDestroy(SC.gexec); SC.have_graph = false; }
+            if (cudaMalloc(&SC.arena, need) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("device workspace allocation failed");
+                return PRISM_ERR_ALLOCATION;
+            }
+            SC.arena_bytes = need;
+        }
+        if (!SC.pinned) {
+            if (cudaMallocHost(&SC.pinned, 64) != cudaSuccess) { set_error("pinned alloc failed"); return PRISM_ERR_ALLOCATION; }
+            for (auto& e : SC.ev) cudaEventCreate(&e);
+        }
+        Arena A;
+        A.base = SC.arena; A.cap = SC.arena_bytes;
+        std::memset((void*)&D, 0, sizeof(Dev));
+        P = PolDev(); BD = BatchDev();
+        layout(A, D, P, BD, stage, &member, &err, &pwidx, &ragged_out);
+        if (A.alloc_fail) { set_error("workspace layout overflow"); return PRISM_ERR_ALLOCATION; }
+    }
+    SC.prof.reset();
+    SC.prof.on = o->profile != 0;
+    cudaEventRecord(SC.ev[0], st);
+    // ---- stage inputs on the device
+    auto stage_in = [&](const void* src, void* dst, size_t bytes) -> const void* {
+        if (is_dev(src)) return src;
+        cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
+        return dst;
+    };
+    PackArgs PA;
+    PA.M = M; PA.N = N; PA.Npad = Npad; PA.nnz = nnz;
+    PA.w0 = (const double*)stage_in(b->w0, stage[0], nnz * 8);
+    PA.lo = (const double*)stage_in(b->lower, stage[1], nnz * 8);
+    PA.up = (const double*)stage_in(b->upper, stage[2], nnz * 8);
+    PA.tc = (const double*)stage_in(b->tc, stage[3], nnz * 8);
+    cudaMemcpyAsync(stage[4], offs.data(), (M + 1) * sizeof(int64_t), cudaMemcpyHostToDevice, st);
+    PA.offsets = (const int64_t*)stage[4];
+    PA.asset_idx = b->asset_idx ? (const int32_t*)stage_in(b->asset_idx, stage[5], nnz * 4) : nullptr;
+    PA.inv_perm = U.d_inv_perm;
+    PA.W0 = BD.w0; PA.LO = BD.lo; PA.UP = BD.up; PA.C = BD.c;
+    PA.W0f = BD.w0f; PA.LOf = BD.lof; PA.UPf = BD.upf; PA.Cf = BD.cf;
+    PA.member = member; PA.err = err;
+    cudaMemsetAsync(BD.w0, 0, MN * 8, st); cudaMemsetAsync(BD.lo, 0, MN * 8, st);
+    cudaMemsetAsync(BD.up, 0, MN * 8, st); cudaMemsetAsync(BD.c, 0, MN * 8, st);
+    cudaMemsetAsync(BD.w0f, 0, MN * 4, st); cudaMemsetAsync(BD.lof, 0, MN * 4, st);
+    cudaMemsetAsync(BD.upf, 0, MN * 4, st); cudaMemsetAsync(BD.cf, 0, MN * 4, st);
+    cudaMemsetAsync(member, 0, MN * 4, st);
+    cudaMemsetAsync(err, 0, 16, st);
+    if (nnz > 0) SC.prof.run(PRISM_K_PACK, 1, st, [&] { k_pack<<<(unsigned)cdiv64(nnz, 256), 256, 0, st>>>(PA); });
+    // bands and caps
+    {
+        std::vector<double> blo, bhi, tau;
+        if ((rc = to_host(b->band_lo, (size_t)M * S, blo)) || (rc = to_host(b->band_hi, (size_t)M * S, bhi))) return rc;
+        if (b->turnover_cap) { if ((rc = to_host(b->turnover_cap, (size_t)M, tau))) return rc; }
+        else tau.assign(M, INFINITY);
+        for (size_t q = 0; q < blo.size(); ++q) {
+            if (std::isnan(blo[q]) || std::isnan(bhi[q]) || blo[q] > bhi[q]) {
+                set_error("band_lo <= band_hi required (no NaN)");
+                return PRISM_ERR_ARGUMENT;
+            }
+        }
+        bool cap_any = false;
+        for (int a = 0; a < M; ++a) {
+            if (std::isnan(tau[a]) || tau[a] < 0) { set_error("turnover_cap must be >= 0 or +inf"); return PRISM_ERR_ARGUMENT; }
+            cap_any |= std::isfinite(tau[a]);
+        }
+        std::vector<float> blof(blo.begin(), blo.end()), bhif(bhi.begin(), bhi.end()), tauf(tau.begin(), tau.end());
+        // the host vectors die at scope end: copy synchronously
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.band_lo, blo.data(), blo.size() * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.band_hi, bhi.data(), bhi.size() * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.band_lof, blof.data(), blof.size() * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.band_hif, bhif.data(), bhif.size() * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.tau, tau.data(), M * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.tauf, tauf.data(), M * 4, cudaMemcpyHostToDevice, st));
+        BD.has_cap = cap_any;
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    // lot tables
+    std::vector<double> h_phi;
+    if (has_lots) {
+        std::vector<double> bp((size_t)std::max(n_pw, 1) * MAXBP, 0.0), sl((size_t)std::max(n_pw, 1) * (MAXBP - 1), 0.0);
+        std::vector<float> bpf(bp.size()), slf(sl.size());
+        std::vector<int> nb(std::max(n_pw, 1), 1);
+        h_phi.assign(std::max(n_pw, 1), 0.0);
+        for (int r = 0; r < n_pw; ++r) {
+            nb[r] = pwl[r].nb;
+            h_phi[r] = pwl[r].phi_lo;
+            for (int j = 0; j < pwl[r].nb; ++j) { bp[(size_t)r * MAXBP + j] = pwl[r].bp[j]; bpf[(size_t)r * MAXBP + j] = float(pwl[r].bp[j]); }
+            for (int j = 0; j + 1 < pwl[r].nb; ++j) { sl[(size_t)r * (MAXBP - 1) + j] = pwl[r].sl[j]; slf[(size_t)r * (MAXBP - 1) + j] = float(pwl[r].sl[j]); }
+        }
+        // per sorted entry index of the table row
+        std::vector<int> pwidx_h(MN, -1);
+        std::vector<int32_t> aidx;
+        if (b->asset_idx && (rc = to_host(b->asset_idx, (size_t)nnz, aidx))) return rc;
+        for (int a = 0; a < M; ++a)
+            for (int64_t e = offs[a]; e < offs[a + 1]; ++e) {
+                int i = b->asset_idx ? aidx[e] : int(e - offs[a]);
+                if (i < 0 || i >= N) { set_error("asset index out of range"); return PRISM_ERR_ARGUMENT; }
+                pwidx_h[(size_t)a * Npad + U.inv_perm[i]] = pw_of_entry[e];
+            }
+        PRISM_CUDA_TRY(cudaMemcpyAsync(pwidx, pwidx_h.data(), MN * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.pw_bp, bp.data(), bp.size() * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.pw_sl, sl.data(), sl.size() * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.pw_bpf, bpf.data(), bpf.size() * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.pw_slf, slf.data(), slf.size() * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(BD.pw_nbp, nb.data(), nb.size() * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(stage[6], h_phi.data(), h_phi.size() * 8, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+    }
+    {
+        int herr = 0;
+        PRISM_CUDA_TRY(cudaMemcpyAsync(&herr, err, 4, cudaMemcpyDeviceToHost, st));
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+        if (herr) {
+            std::string m = "invalid batch input:";
+            if (herr & ERR_INDEX) m += " asset index out of range;";
+            if (herr & ERR_NONFINITE) m += " non-finite w0/lower/upper/tc;";
+            if (herr & ERR_BOUNDS) m += " lower > upper;";
+            if (herr & ERR_COST) m += " negative tc;";
+            if (herr & ERR_DUP) m += " duplicate asset within an account;";
+            set_error(m);
+            return PRISM_ERR_ARGUMENT;
+        }
+    }
+    // ---- device views
+    D.M = M; D.N = N; D.Npad = Npad; D.K = K; D.S = S;
+    D.B32 = U.d_B32; D.d32 = U.d_d32; D.mu32 = U.d_mu32; D.sec_start = U.d_sec_start; D.sector = U.d_sector;
+    D.B16 = U.d_B16; D.Bt16 = U.d_Bt16;
+    D.bf16 = batched_mode_bf16;
+    D.Cinv = batched_mode_bf16 ? U.d_Cinv16 : U.d_Cinv32;
+    D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
+    D.pw_idx = pwidx; D.pw_bp = BD.pw_bpf; D.pw_sl = BD.pw_slf; D.pw_nbp = BD.pw_nbp;
+    D.band_lo = BD.band_lof; D.band_hi = BD.band_hif; D.tau = BD.tauf;
+    D.nsplit = nsplit;
+    D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
+    D.adapt_every = 25;
+    P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;
+    P.B64 = U.d_B64; P.f64 = U.d_f64; P.d64 = U.d_d64; P.mu64 = U.d_mu64; P.sec_start = U.d_sec_start; P.sector = U.d_sector;
+    P.w0 = BD.w0; P.lo = BD.lo; P.up = BD.up; P.c = BD.c;
+    P.pw_idx = pwidx; P.pw_bp = BD.pw_bp; P.pw_sl = BD.pw_sl; P.pw_phi_lo = (const double*)stage[6]; P.pw_nbp = BD.pw_nbp;
+    P.band_lo = BD.band_lo; P.band_hi = BD.band_hi; P.tau = BD.tau;
+    P.z = D.z; P.nu_f = D.nu; P.eta_hi_f = D.eta_hi; P.eta_lo_f = D.eta_lo; P.theta_f = D.theta;
+    P.FMAX = FMAX;
+    P.status = D.status;
+    P.tol_dual = 1e-11; P.tol_primal = 1e-12;
+    // ---- control init
+    {
+        int j0 = (int)std::lround(RHO_PER_DECADE * std::log10(std::max(o->rho0, 1e-12) / RHO_MIN));
+        j0 = std::max(0, std::min(NRHO - 1, j0));
+        std::vector<int> h(M, j0);
+        PRISM_CUDA_TRY(cudaMemcpyAsync(D.rho_idx, h.data(), M * 4, cudaMemcpyHostToDevice, st));
+        std::vector<int> one(M, 1);
+        PRISM_CUDA_TRY(cudaMemcpyAsync(D.active, one.data(), M * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+        cudaMemsetAsync(D.iters, 0, M * 4, st);
+        cudaMemsetAsync(D.status, 0, M * 4, st);
+        cudaMemsetAsync(D.nu, 0, M * 4, st);
+        cudaMemsetAsync(D.theta, 0, M * 4, st);
+        cudaMemsetAsync(D.eta_hi, 0xff, (size_t)M * S * 4, st);   // NaN: no warm start yet
+        cudaMemsetAsync(D.eta_lo, 0xff, (size_t)M * S * 4, st);
+        cudaMemsetAsync(P.skip, 0, M * 4, st);
+        cudaMemsetAsync(P.done, 0, M * 4, st);
+        cudaMemsetAsync(P.diag, 0, (size_t)M * PRISM_NDIAG * 8, st);
+        cudaMemsetAsync(P.W, 0, MN * 8, st);
+        cudaMemsetAsync(P.nu, 0, M * 8, st);
+        cudaMemsetAsync(P.theta, 0, M * 8, st);
+        cudaMemsetAsync(P.lam, 0, (size_t)M * S * 8, st);
+        cudaMemsetAsync(D.X, 0, MN * 4, st);
+        cudaMemsetAsync(D.Xhi, 0, MN * 2, st);
+        cudaMemsetAsync(D.Xlo, 0, MN * 2, st);
+        cudaMemsetAsync(D.v, 0, MN * 4, st);
+    }
+    SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
+        k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
+                                      BD.tau, D.status, P.skip, D.active);
+        launch_init_state(D, st);
+    });
+    cudaEventRecord(SC.ev[1], st);
+    // ---- ADMM iterations
+    const int check_every = std::max(1, o->check_every);
+    auto run_chunk = [&](int n) {
+        for (int it = 0; it < n; ++it) {
+            SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
+            SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
+            SC.prof.run(PRISM_K_GEMM_X, 1, st, [&] { if (D.bf16) launch_tc_gemm_x(D, st); else launch_gemm_x(D, st); });
+            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st); });
+        }
+        SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
+        cudaMemcpyAsync(SC.pinned, D.n_active, 4, cudaMemcpyDeviceToHost, st);
+    };
+    int64_t chunk_launches[PRISM_NKCLASS] = {};
+    auto admm_loop = [&](int iter_budget) -> int {
+        int done_iters = 0;
+        bool use_graph = o->use_graph != 0 && !SC.prof.on;
+        if (use_graph) {
+            bool same = SC.have_graph && SC.g_iters == check_every && std::memcmp(&SC.gdev, &D, sizeof(Dev)) == 0;
+            if (!same) {
+                if (SC.have_graph) { cudaGraphExecDestroy(SC.gexec); SC.have_graph = false; }
+                cudaGraph_t g;
+                if (cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal) != cudaSuccess) { cudaGetLastError(); use_graph = false; }
+                else {
+                    int64_t before[PRISM_NKCLASS];
+                    std::memcpy(before, SC.prof.launches, sizeof(before));
+                    run_chunk(check_every);
+                    for (int q = 0; q < PRISM_NKCLASS; ++q) {
+                        chunk_launches[q] = SC.prof.launches[q] - before[q];
+                        SC.prof.launches[q] = before[q];
+                    }
+                    if (cudaStreamEndCapture(st, &g) != cudaSuccess ||
+                        cudaGraphInstantiate(&SC.gexec, g, 0) != cudaSuccess) {
+                        cudaGetLastError();
+                        use_graph = false;
+                    } else {
+                        SC.have_graph = true;
+                        SC.gdev = D;
+                        SC.g_iters = check_every;
+                        std::memcpy(SC.g_launches, chunk_launches, sizeof(chunk_launches));
+                    }
+                    cudaGraphDestroy(g);
+                }
+            }
+        }
+        while (done_iters < iter_budget) {
+            if (use_graph) {
+                cudaGraphLaunch(SC.gexec, st);
+                for (int q = 0; q < PRISM_NKCLASS; ++q) SC.prof.launches[q] += SC.g_launches[q];
+            } else {
+                run_chunk(check_every);
+            }
+            done_iters += check_every;
+            if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
+            if (*SC.pinned == 0) break;
+            if (o->time_budget_s > 0) {
+                double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call0).count();
+                if (el > o->time_budget_s) break;
+            }
+        }
+        return done_iters;
+    };
+    int total_iters = admm_loop(o->max_iter + check_every);
+    if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
+    SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_mark_timeout(D, st); });   // accounts still iterating
+    cudaEventRecord(SC.ev[2], st);
+    // ---- polish, with up to two returns to the iterations at a tighter target
+    const int rounds = std::max(1, o->polish_rounds);
+    SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });
+    for (int r = 0; r < rounds; ++r) SC.prof.run(PRISM_K_POLISH, 1, st, [&] { launch_polish_round(P, st); });
+    for (int retry = 0; retry < 2; ++retry) {
+        std::vector<int> done(M), skip(M), status(M);
+        cudaMemcpyAsync(done.data(), P.done, M * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(skip.data(), P.skip, M * 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(status.data(), D.status, M * 4, cudaMemcpyDeviceToHost, st);
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+        std::vector<int> act(M, 0);
+        int n_retry = 0;
+        for (int a = 0; a < M; ++a) {
+            if (skip[a] || done[a] == 1 || status[a] == PRISM_NUMERICAL_FAILURE) continue;
+            act[a] = 1;
+            done[a] = 0;
+            status[a] = 0;
+            ++n_retry;
+        }
+        if (!n_retry) break;
+        if (o->time_budget_s > 0 &&
+            std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call0).count() > o->time_budget_s) break;
+        // iterate again, to a tighter target, only the accounts the polish could not settle
+        PRISM_CUDA_TRY(cudaMemcpyAsync(D.active, act.data(), M * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(D.status, status.data(), M * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(P.done, done.data(), M * 4, cudaMemcpyHostToDevice, st));
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+        Dev saved = D;
+        D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);
+        D.max_iter = saved.max_iter * (retry + 2);
+        int more = admm_loop(D.max_iter);
+        D = saved;
+        if (more < 0) { set_error("ADMM retry failed"); return PRISM_ERR_CUDA; }
+        total_iters += more;
+        SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });
+        for (int r = 0; r < rounds; ++r) SC.prof.run(PRISM_K_POLISH, 1, st, [&] { launch_polish_round(P, st); });
+    }
+    SC.prof.run(PRISM_K_OTHER, 2, st, [&] { launch_fallback(P, st); });
+    cudaEventRecord(SC.ev[3], st);
+    SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_finish_status(P, o->eps_kkt, st); });
+    cudaEventRecord(SC.ev[4], st);
+    // ---- unpack
+    UnpackArgs UA;
+    UA.M = M; UA.Npad = Npad; UA.offsets = PA.offsets; UA.asset_idx = PA.asset_idx; UA.inv_perm = U.d_inv_perm;
+    UA.W = P.W; UA.nnz = nnz;
+    const bool w_dev = is_dev(res->w);
+    UA.out = w_dev ? res->w : ragged_out;
+    if (nnz > 0) SC.prof.run(PRISM_K_UNPACK, 1, st, [&] { k_unpack<<<(unsigned)cdiv64(nnz, 256), 256, 0, st>>>(UA); });
+    if (!w_dev) cudaMemcpyAsync(res->w, ragged_out, nnz * 8, cudaMemcpyDeviceToHost, st);
+    auto out = [&](void* dst, const void* src, size_t bytes) {
+        if (dst) cudaMemcpyAsync(dst, src, bytes, cudaMemcpyDefault, st);
+    };
+    out(res->status, D.status, M * 4);
+    out(res->iters, D.iters, M * 4);
+    out(res->nu, P.nu, M * 8);
+    out(res->lambda_band, P.lam, (size_t)M * S * 8);
+    out(res->theta, P.theta, M * 8);
+    out(res->diag, P.diag, (size_t)M * PRISM_NDIAG * 8);
+    cudaEventRecord(SC.ev[5], st);
+    cudaError_t e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) { set_error(std::string("solve failed: ") + cudaGetErrorString(e)); return PRISM_ERR_CUDA; }
+    e = cudaGetLastError();
+    if (e != cudaSuccess) { set_error(std::string("solve failed: ") + cudaGetErrorString(e)); return PRISM_ERR_CUDA; }
+    res->t_phase_ms[0] = ms_between(SC.ev[0], SC.ev[1]);
+    res->t_phase_ms[1] = ms_between(SC.ev[1], SC.ev[2]);
+    res->t_phase_ms[2] = ms_between(SC.ev[2], SC.ev[3]);
+    res->t_phase_ms[3] = ms_between(SC.ev[3], SC.ev[4]);
+    res->t_device_ms = ms_between(SC.ev[0], SC.ev[5]);
+    res->device_bytes = (int64_t)(SC.arena_bytes + U.bytes);
+    int64_t nl = 0;
+    for (int q = 0; q < PRISM_NKCLASS; ++q) {
+        res->kernel_launches[q] = SC.prof.launches[q];
+        res->kernel_ms[q] = 0.0;
+        nl += SC.prof.launches[q];
+    }
+    for (auto& mk : SC.prof.marks) res->kernel_ms[mk.cls] += ms_between(mk.a, mk.b);
+    res->n_launches = nl;
+    res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call0).count();
+    (void)plain;
+    return PRISM_OK;
+}
+
+}  // namespace prism
+
+extern "C" void prism_default_opts(prism_solve_opts* o) {
+    if (!o) return;
+    std::memset(o, 0, sizeof(*o));
+    o->eps_kkt = 1e-6;
+    o->eps_admm = 3e-4;
+    o->rho0 = 0.1;
+    o->alpha = 1.6;
+    o->time_budget_s = 0.0;
+    o->max_iter = 4000;
+    o->check_every = 10;
+    o->min_iter = 20;
+    o->polish_rounds = 8;
+    o->precision = PRISM_BATCHED_BF16;
+    o->use_graph = 1;
+    o->keep_for_backward = 0;
+    o->cuda_stream = nullptr;
+}
+
+extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const prism_solve_opts* opts,
+                                 prism_result* res) {
+    using namespace prism;
+    if (!uh || !b || !res) { set_error("NULL argument"); return PRISM_ERR_ARGUMENT; }
+    prism_solve_opts o;
+    if (opts) o = *opts; else prism_default_opts(&o);
+    if (b->n_accounts < 1) { set_error("n_accounts must be >= 1"); return PRISM_ERR_ARGUMENT; }
+    if (!b->offsets || !b->w0 || !b->lower || !b->upper || !b->tc || !b->band_lo || !b->band_hi) {
+        set_error("required batch array is NULL");
+        return PRISM_ERR_ARGUMENT;
+    }
+    if (!res->w || !res->status) { set_error("result w and status are required"); return PRISM_ERR_ARGUMENT; }
+    if (b->lot_offsets && (!b->lot_size || !b->lot_kappa)) { set_error("lot arrays incomplete"); return PRISM_ERR_ARGUMENT; }
+    if (!(o.eps_kkt > 0) || !(o.eps_admm > 0) || !(o.rho0 > 0) || !(o.alpha > 0 && o.alpha < 2) ||
+        o.max_iter < 1 || o.check_every < 1) {
+        set_error("invalid options");
+        return PRISM_ERR_ARGUMENT;
+    }
+    if (o.keep_for_backward) { set_error("keep_for_backward is not available in this build"); return PRISM_ERR_UNSUPPORTED; }
+    const auto t0 = std::chrono::steady_clock::now();
+    if (o.precision == PRISM_BATCHED_FP32) return solve_core(uh, b, &o, res, false, false);
+    if (o.precision == PRISM_BATCHED_BF16) {
+        if (!tc_available()) {
+            set_error("BATCHED_BF16 needs the tcgen05 product kernels, which this build does not provide");
+            return PRISM_ERR_UNSUPPORTED;
+        }
+        return solve_core(uh, b, &o, res, true, false);
+    }
+    if (o.precision != PRISM_PLAIN_FP32) { set_error("unknown precision mode"); return PRISM_ERR_ARGUMENT; }
+    // PLAIN_FP32: one account per launch sequence (the single-account form)
+    std::vector<int64_t> offs;
+    if (int rc = to_host(b->offsets, (size_t)b->n_accounts + 1, offs)) return rc;
+    const int S = uh->u.S;
+    double tdev = 0, tph[4] = {0, 0, 0, 0}, kms[PRISM_NKCLASS] = {};
+    int64_t dbytes = 0, nlaunch = 0, kl[PRISM_NKCLASS] = {};
+    for (int a = 0; a < b->n_accounts; ++a) {
+        int64_t sub_off[2] = {0, offs[a + 1] - offs[a]};
+        prism_batch sb = *b;
+        sb.n_accounts = 1;
+        sb.offsets = sub_off;
+        const int64_t e0 = offs[a];
+        sb.asset_idx = b->asset_idx ? b->asset_idx + e0 : nullptr;
+        sb.w0 = b->w0 + e0; sb.lower = b->lower + e0; sb.upper = b->upper + e0; sb.tc = b->tc + e0;
+        sb.band_lo = b->band_lo + (size_t)a * S; sb.band_hi = b->band_hi + (size_t)a * S;
+        sb.turnover_cap = b->turnover_cap ? b->turnover_cap + a : nullptr;
+        std::vector<int64_t> lot_sub;
+        if (b->lot_offsets) {
+            std::vector<int64_t> lo_all;
+            if (int rc = to_host(b->lot_offsets + e0, (size_t)(sub_off[1] + 1), lo_all)) return rc;
+            lot_sub.resize(lo_all.size());
+            for (size_t q = 0; q < lo_all.size(); ++q) lot_sub[q] = lo_all[q] - lo_all[0];
+            sb.lot_offsets = lot_sub.data();
+            sb.lot_size = b->lot_size + lo_all[0];
+            sb.lot_kappa = b->lot_kappa + lo_all[0];
+        }
+        prism_result r1 = *res;
+        r1.w = res->w + e0;
+        r1.status = res->status + a;
+        r1.iters = res->iters ? res->iters + a : nullptr;
+        r1.nu = res->nu ? res->nu + a : nullptr;
+        r1.lambda_band = res->lambda_band ? res->lambda_band + (size_t)a * S : nullptr;
+        r1.theta = res->theta ? res->theta + a : nullptr;
+        r1.diag = res->diag ? res->diag + (size_t)a * PRISM_NDIAG : nullptr;
+        int rc = solve_core(uh, &sb, &o, &r1, false, true);
+        if (rc != PRISM_OK) return rc;
+        tdev += r1.t_device_ms;
+        for (int q = 0; q < 4; ++q) tph[q] += r1.t_phase_ms[q];
+        nlaunch += r1.n_launches;
+        for (int q = 0; q < PRISM_NKCLASS; ++q) { kms[q] += r1.kernel_ms[q]; kl[q] += r1.kernel_launches[q]; }
+        dbytes = std::max(dbytes, r1.device_bytes);
+    }
+    res->t_device_ms = tdev;
+    for (int q = 0; q < 4; ++q) res->t_phase_ms[q] = tph[q];
+    res->device_bytes = dbytes;
+    res->n_launches = nlaunch;
+    for (int q = 0; q < PRISM_NKCLASS; ++q) { res->kernel_ms[q] = kms[q]; res->kernel_launches[q] = kl[q]; }
+    res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+    return PRISM_OK;
+}
+
+extern "C" int prism_solve_batch_backward(prism_state* state, const double* dL_dw, double* dmu, double* dB,
+                                          double* dd, double* dw0) {
+    (void)state; (void)dL_dw; (void)dmu; (void)dB; (void)dd; (void)dw0;
+    prism::set_error("backward pass is not available in this build");
+    return PRISM_ERR_UNSUPPORTED;
+}
+
+extern "C" void prism_free_state(prism_state* state) { delete state; }

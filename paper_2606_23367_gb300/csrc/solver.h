@@ -1,0 +1,79 @@
+// solver.h -- device-side state of one batched solve and the kernel launchers.
+#pragma once
+
+#include "internal.h"
+
+namespace prism {
+
+// Everything the iteration kernels touch, passed by value to every kernel.
+struct Dev {
+    int M = 0, N = 0, Npad = 0, K = 0, S = 0;
+    // universe (sorted order)
+    const float* B32 = nullptr;
+    const float* d32 = nullptr;
+    const float* mu32 = nullptr;
+    const int* sec_start = nullptr;
+    const int* sector = nullptr;
+    const __nv_bfloat16* B16 = nullptr;
+    const __nv_bfloat16* Bt16 = nullptr;
+    const float* Cinv = nullptr;        // NRHO x K x K for the mode's B
+    // per-entry account data (M x Npad), FP32
+    const float* w0 = nullptr;
+    const float* lo = nullptr;
+    const float* up = nullptr;
+    const float* c = nullptr;
+    const int* pw_idx = nullptr;        // -1 = plain L1 entry
+    const float* pw_bp = nullptr;       // n_pw x MAXBP
+    const float* pw_sl = nullptr;       // n_pw x (MAXBP-1)
+    const int* pw_nbp = nullptr;
+    const float* band_lo = nullptr;     // M x S
+    const float* band_hi = nullptr;
+    const float* tau = nullptr;         // M (inf = no cap)
+    // ADMM state (M x Npad)
+    float* z = nullptr;
+    float* y = nullptr;
+    float* X = nullptr;                 // Delta^{-1}(mu + rho z - y), FP32
+    float* v = nullptr;                 // relaxed x plus scaled dual, input of the prox
+    __nv_bfloat16* Xhi = nullptr;       // X split for the BF16 products: X ~ Xhi + Xlo
+    __nv_bfloat16* Xlo = nullptr;
+    float* Ppart = nullptr;             // nsplit x M x K partial B'X
+    float* Q = nullptr;                 // M x K
+    __nv_bfloat16* Qhi = nullptr;       // M x K split of Q
+    __nv_bfloat16* Qlo = nullptr;
+    int nsplit = 1;
+    // per-account control
+    int* rho_idx = nullptr;
+    int* iters = nullptr;
+    int* active = nullptr;
+    int* status = nullptr;
+    float* nu = nullptr;                // M warm start
+    float* eta_hi = nullptr;            // M x S warm start / result
+    float* eta_lo = nullptr;            // M x S
+    float* theta = nullptr;             // M cap multiplier
+    float* rp = nullptr;                // M residuals
+    float* rd = nullptr;
+    int* n_active = nullptr;            // 1
+    float alpha = 1.6f;
+    float eps_admm = 3e-4f;
+    int min_iter = 20;
+    int max_iter = 4000;
+    int adapt_every = 25;
+    bool bf16 = false;                  // X / Q split in BF16 for tensor-core products
+};
+
+// launchers (admm.cu)
+void launch_init_state(const Dev& D, cudaStream_t st);
+void launch_gemm_P(const Dev& D, cudaStream_t st);       // G2: Ppart = X B (SIMT)
+void launch_small_solve(const Dev& D, cudaStream_t st);  // G3: Q = Cinv * sum(Ppart)
+void launch_gemm_x(const Dev& D, cudaStream_t st);       // G4: v from X - Delta^{-1} B Q (SIMT)
+void launch_prox(const Dev& D, cudaStream_t st);         // G5/G6: projection, duals, control
+void launch_count_active(const Dev& D, cudaStream_t st);
+void launch_mark_timeout(const Dev& D, cudaStream_t st);
+int choose_nsplit(int M, int N);
+
+// tensor-core products (tc_gemm.cu)
+bool tc_available();                                     // tcgen05 kernels compiled in
+void launch_tc_gemm_P(const Dev& D, cudaStream_t st);    // G2 on tcgen05
+void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
+
+}  // namespace prism

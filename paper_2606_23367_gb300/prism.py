@@ -1,0 +1,248 @@
+"""Thin Python binding of the C-ABI in include/prism.h (argument marshalling only).
+
+Every step of the solve runs in libprism.so; this module only lays out the
+C structs, passes host (numpy) or device (torch CUDA tensor) pointers and
+raises on a negative return code. It fails loudly when the library has not
+been built: there is no fallback path.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libprism.so")
+
+PRISM_OK = 0
+PRISM_ERR_ARGUMENT, PRISM_ERR_CUDA, PRISM_ERR_ALLOCATION, PRISM_ERR_UNSUPPORTED = -1, -2, -3, -4
+PRISM_CERTIFIED, PRISM_FEASIBLE_NONCERTIFIED, PRISM_TIMEOUT, PRISM_DEADLINE_EXCEEDED = 0, 1, 2, 3
+PRISM_NO_FEASIBLE_RETURN, PRISM_ALLOCATION_FAILURE, PRISM_NUMERICAL_FAILURE = 4, 5, 6
+PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16 = 0, 1, 2
+PRISM_NDIAG = 8
+KERNEL_CLASSES = ("gemm_P", "solve_K", "gemm_x", "prox", "polish", "pack", "other", "unpack")
+DIAG_NAMES = ("r_budget", "r_box", "r_exposure", "r_turnover", "r_stat", "r_comp", "obj", "polish_rounds")
+STATUS_NAMES = ("CERTIFIED", "FEASIBLE_NONCERTIFIED", "TIMEOUT", "DEADLINE_EXCEEDED",
+                "NO_FEASIBLE_RETURN", "ALLOCATION_FAILURE", "NUMERICAL_FAILURE")
+
+_dp = C.POINTER(C.c_double)
+_ip = C.POINTER(C.c_int32)
+_lp = C.POINTER(C.c_int64)
+
+
+class PrismError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"prism error {code}: {msg}")
+        self.code = code
+
+
+class _UniverseDesc(C.Structure):
+    _fields_ = [("n_assets", C.c_int32), ("n_factors", C.c_int32), ("n_sectors", C.c_int32),
+                ("B", C.c_void_p), ("f", C.c_void_p), ("d", C.c_void_p), ("mu", C.c_void_p),
+                ("sector", C.c_void_p), ("device", C.c_int32)]
+
+
+class _Batch(C.Structure):
+    _fields_ = [("n_accounts", C.c_int32), ("offsets", C.c_void_p), ("asset_idx", C.c_void_p),
+                ("w0", C.c_void_p), ("lower", C.c_void_p), ("upper", C.c_void_p), ("tc", C.c_void_p),
+                ("band_lo", C.c_void_p), ("band_hi", C.c_void_p), ("turnover_cap", C.c_void_p),
+                ("lot_offsets", C.c_void_p), ("lot_size", C.c_void_p), ("lot_kappa", C.c_void_p)]
+
+
+class _Opts(C.Structure):
+    _fields_ = [("eps_kkt", C.c_double), ("eps_admm", C.c_double), ("rho0", C.c_double),
+                ("alpha", C.c_double), ("time_budget_s", C.c_double), ("max_iter", C.c_int32),
+                ("check_every", C.c_int32), ("min_iter", C.c_int32), ("polish_rounds", C.c_int32),
+                ("precision", C.c_int32), ("use_graph", C.c_int32), ("keep_for_backward", C.c_int32),
+                ("profile", C.c_int32), ("cuda_stream", C.c_void_p)]
+
+
+class _Result(C.Structure):
+    _fields_ = [("w", C.c_void_p), ("nu", C.c_void_p), ("lambda_band", C.c_void_p), ("theta", C.c_void_p),
+                ("status", C.c_void_p), ("iters", C.c_void_p), ("diag", C.c_void_p),
+                ("t_device_ms", C.c_double), ("t_call_ms", C.c_double), ("t_phase_ms", C.c_double * 4),
+                ("device_bytes", C.c_int64), ("n_launches", C.c_int64),
+                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8),
+                ("state", C.c_void_p)]
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libprism.so (built by paper_2606_23367_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(f"{path} is missing: build it with paper_2606_23367_gb300.build.build()")
+    lib = C.CDLL(path)
+    lib.prism_create_universe.argtypes = [C.POINTER(_UniverseDesc), C.POINTER(C.c_void_p)]
+    lib.prism_create_universe.restype = C.c_int
+    lib.prism_destroy_universe.argtypes = [C.c_void_p]
+    lib.prism_destroy_universe.restype = None
+    lib.prism_default_opts.argtypes = [C.POINTER(_Opts)]
+    lib.prism_default_opts.restype = None
+    lib.prism_solve_batch.argtypes = [C.c_void_p, C.POINTER(_Batch), C.POINTER(_Opts), C.POINTER(_Result)]
+    lib.prism_solve_batch.restype = C.c_int
+    lib.prism_solve_batch_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                               C.c_void_p, C.c_void_p]
+    lib.prism_solve_batch_backward.restype = C.c_int
+    lib.prism_free_state.argtypes = [C.c_void_p]
+    lib.prism_free_state.restype = None
+    lib.prism_last_error.argtypes = []
+    lib.prism_last_error.restype = C.c_char_p
+    lib.prism_version.argtypes = []
+    lib.prism_version.restype = C.c_char_p
+    _lib = lib
+    return lib
+
+
+def _check(rc):
+    if rc != PRISM_OK:
+        raise PrismError(rc, load_library().prism_last_error().decode())
+
+
+class _Keep:
+    """Holds the host arrays whose pointers were handed to C for the call's duration."""
+
+    def __init__(self):
+        self.refs = []
+
+    def ptr(self, x, dtype):
+        if x is None:
+            return None
+        if hasattr(x, "data_ptr"):            # torch tensor (host or CUDA)
+            import torch
+            want = {np.float64: torch.float64, np.int32: torch.int32, np.int64: torch.int64}[dtype]
+            if x.dtype != want or not x.is_contiguous():
+                raise TypeError(f"tensor must be contiguous {want}")
+            self.refs.append(x)
+            return x.data_ptr()
+        a = np.ascontiguousarray(x, dtype=dtype)
+        self.refs.append(a)
+        return a.ctypes.data
+
+
+def prism_version() -> str:
+    return load_library().prism_version().decode()
+
+
+def prism_last_error() -> str:
+    return load_library().prism_last_error().decode()
+
+
+class UniverseHandle:
+    def __init__(self, handle, n_assets, n_factors, n_sectors):
+        self.handle = handle
+        self.n_assets, self.n_factors, self.n_sectors = n_assets, n_factors, n_sectors
+
+    def close(self):
+        if self.handle:
+            load_library().prism_destroy_universe(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prism_create_universe(B, f, d, mu, sector, n_sectors, device=0) -> UniverseHandle:
+    lib = load_library()
+    keep = _Keep()
+    N, K = int(B.shape[0]), int(B.shape[1])
+    desc = _UniverseDesc(N, K, int(n_sectors), keep.ptr(B, np.float64), keep.ptr(f, np.float64),
+                         keep.ptr(d, np.float64), keep.ptr(mu, np.float64), keep.ptr(sector, np.int32),
+                         int(device))
+    h = C.c_void_p()
+    _check(lib.prism_create_universe(C.byref(desc), C.byref(h)))
+    return UniverseHandle(h.value, N, K, int(n_sectors))
+
+
+def prism_destroy_universe(u: UniverseHandle):
+    u.close()
+
+
+def prism_default_opts() -> dict:
+    o = _Opts()
+    load_library().prism_default_opts(C.byref(o))
+    return {name: getattr(o, name) for name, _ in _Opts._fields_}
+
+
+def _to_numpy(x):
+    return x.cpu().numpy() if hasattr(x, "cpu") else np.asarray(x)
+
+
+def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi,
+                      asset_idx=None, turnover_cap=None, lot_offsets=None, lot_size=None,
+                      lot_kappa=None, out=None, **opts) -> dict:
+    """Solve a book of accounts. Array arguments are numpy arrays (host) or torch
+    tensors (host or CUDA). ``out`` may supply preallocated outputs with keys
+    w/status/iters/nu/lambda_band/theta/diag (device or host); otherwise numpy
+    outputs are allocated. Returns a dict of outputs and timings."""
+    lib = load_library()
+    keep = _Keep()
+    M = int(len(offsets) - 1)
+    nnz = int(_to_numpy(offsets[-1:])[0]) if hasattr(offsets, "cpu") else int(offsets[-1])
+    S = u.n_sectors
+    b = _Batch(M, keep.ptr(offsets, np.int64), keep.ptr(asset_idx, np.int32),
+               keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
+               keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
+               keep.ptr(turnover_cap, np.float64), keep.ptr(lot_offsets, np.int64),
+               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64))
+    o = _Opts()
+    lib.prism_default_opts(C.byref(o))
+    for k, v in opts.items():
+        if k == "cuda_stream":
+            o.cuda_stream = v
+        elif not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        else:
+            setattr(o, k, v)
+    if out is None:
+        out = dict(w=np.zeros(nnz), status=np.zeros(M, np.int32), iters=np.zeros(M, np.int32),
+                   nu=np.zeros(M), lambda_band=np.zeros((M, S)), theta=np.zeros(M),
+                   diag=np.zeros((M, PRISM_NDIAG)))
+    r = _Result()
+    r.w = keep.ptr(out["w"], np.float64)
+    r.status = keep.ptr(out["status"], np.int32)
+    for k in ("iters",):
+        if out.get(k) is not None:
+            setattr(r, k, keep.ptr(out[k], np.int32))
+    for k in ("nu", "lambda_band", "theta", "diag"):
+        if out.get(k) is not None:
+            setattr(r, k, keep.ptr(out[k], np.float64))
+    _check(lib.prism_solve_batch(u.handle, C.byref(b), C.byref(o), C.byref(r)))
+    res = dict(out)
+    res.update(t_device_ms=r.t_device_ms, t_call_ms=r.t_call_ms, t_phase_ms=list(r.t_phase_ms),
+               device_bytes=r.device_bytes, n_launches=r.n_launches,
+               kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches))
+    return res
+
+
+def prism_solve_batch_backward(state, dL_dw, dmu=None, dB=None, dd=None, dw0=None):
+    lib = load_library()
+    keep = _Keep()
+    _check(lib.prism_solve_batch_backward(state, keep.ptr(dL_dw, np.float64), keep.ptr(dmu, np.float64),
+                                          keep.ptr(dB, np.float64), keep.ptr(dd, np.float64),
+                                          keep.ptr(dw0, np.float64)))
+
+
+def prism_free_state(state):
+    load_library().prism_free_state(state)
+
+
+# ---- conveniences over the workload dataclasses (duck-typed) -------------
+
+def create_universe(uni, device=0) -> UniverseHandle:
+    return prism_create_universe(uni.B, uni.f, uni.d, uni.mu, uni.sector, uni.n_sectors, device)
+
+
+def solve(handle: UniverseHandle, batch, **opts) -> dict:
+    return prism_solve_batch(handle, batch.offsets, batch.w0, batch.lower, batch.upper, batch.tc,
+                             batch.band_lo, batch.band_hi, asset_idx=batch.asset_idx,
+                             turnover_cap=batch.turnover_cap, lot_offsets=batch.lot_offsets,
+                             lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **opts)

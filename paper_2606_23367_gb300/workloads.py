@@ -261,8 +261,12 @@ def _feasible(acc, S) -> bool:
     return True
 
 
-def make_workload(workload: int, seed: int = 0, **overrides):
-    """Build (universe, batch) for a workload id; ``overrides`` replace sizes (N, K, M, ...)."""
+def make_workload(workload: int, seed: int = 0, first_account: int = 0, **overrides):
+    """Build (universe, batch) for a workload id; ``overrides`` replace sizes (N, K, M, ...).
+
+    Accounts are drawn with ids first_account .. first_account + M - 1, so disjoint
+    shards of one large book can be generated independently.
+    """
     p = dict(WORKLOADS[workload])
     p.update(overrides)
     N, K, M, S = int(p["N"]), int(p["K"]), int(p["M"]), int(p["S"])
@@ -270,7 +274,7 @@ def make_workload(workload: int, seed: int = 0, **overrides):
         p["ragged"] = (min(p["ragged"][0], N), min(p["ragged"][1], N))
     uni = make_universe(seed, workload, N, K, S)
     accs, redraws = [], []
-    for a in range(M):
+    for a in range(first_account, first_account + M):
         for r_ in range(MAX_REDRAWS):
             acc = _draw_account(p, seed, workload, a, r_, N, uni.sector, S)
             if _feasible(acc, S):

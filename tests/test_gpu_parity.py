@@ -1,0 +1,68 @@
+"""GPU parity: the library's certified weights equal the FP64 oracle's (through the C-ABI).
+
+Tolerances (written here, from the workload targets): 1e-6 max-abs on weights,
+1e-8 relative objective (guard max(|f*|, 1e-4)), primal and stationarity
+residuals <= 1e-6, all after the FP64 polish.
+"""
+import numpy as np
+import pytest
+
+from paper_2606_23367_gb300 import build, prism
+from paper_2606_23367_gb300.workloads import make_workload
+from tests.parity_util import assert_parity, gpu_solve
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    build.build()
+    prism.load_library()
+
+
+MODES = [prism.PRISM_BATCHED_FP32, prism.PRISM_PLAIN_FP32]
+
+
+@pytest.mark.parametrize("mode", MODES)
+def test_single_account_n100(mode):
+    uni, batch = make_workload(0)
+    res = gpu_solve(uni, batch, precision=mode)
+    assert_parity(uni, batch, res)
+
+
+@pytest.mark.parametrize("mode", [prism.PRISM_BATCHED_FP32])
+def test_batch_shared_universe_small(mode):
+    # 1,200 assets: several 64-wide tiles plus a ragged tail; K = 64 as at full size
+    uni, batch = make_workload(1, N=1200, K=64, M=6)
+    res = gpu_solve(uni, batch, precision=mode)
+    assert_parity(uni, batch, res)
+
+
+def test_ragged_accounts_small():
+    uni, batch = make_workload(2, N=900, M=6)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    assert_parity(uni, batch, res)
+
+
+def test_tax_lots_and_turnover_cap_small():
+    uni, batch = make_workload(3, N=400, K=12, M=4)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    assert_parity(uni, batch, res)
+
+
+def test_differentiation_workload_forward_small():
+    uni, batch = make_workload(4, N=500, M=4)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    assert_parity(uni, batch, res)
+
+
+def test_batch_order_does_not_change_results():
+    uni, batch = make_workload(1, N=700, K=32, M=5)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    order = [3, 1, 4, 0, 2]
+    res2 = gpu_solve(uni, batch.subset(order), precision=prism.PRISM_BATCHED_FP32)
+    sub = batch.subset(order)
+    for k, a in enumerate(order):
+        w1 = res["w"][batch.account_slice(a)]
+        w2 = res2["w"][sub.account_slice(k)]
+        assert np.max(np.abs(w1 - w2)) <= 1e-12
