@@ -187,6 +187,34 @@ int prism_solve_batch_backward(prism_state* state, const double* dL_dw,
                                double* dmu, double* dB, double* dd, double* dw0);
 void prism_free_state(prism_state* state);
 
+/* Allocation-free polish and certification of weights the caller already holds.
+ *
+ * The paper has no counterpart to this entry point. It exists for callers that
+ * cannot allocate device memory when they need an answer: a process that has
+ * reserved the whole GPU for its own memory pool, a latency-bound thread that
+ * must not wait on the allocator, or code recording a CUDA graph (where
+ * cudaMalloc is not allowed). Given weights w_in (ragged, the prism_batch
+ * layout; for example an earlier solve's result or a warm start) it runs the
+ * same FP64 active-set polish and Sec. 4.4 certification kernels as
+ * prism_solve_batch and fills res (w, status, nu, lambda_band, theta, diag;
+ * iters is set to 0; timings other than t_call_ms are 0).
+ *
+ * It calls no cudaMalloc / cudaFree and no allocating library routine: all
+ * device scratch comes from one static __device__ array of about 16 MB that
+ * every GPU loading the library holds until the process exits. Limits
+ * (PRISM_ERR_ARGUMENT beyond them): n_accounts <= 32, n_accounts x (universe
+ * width rounded up to 64) <= 131072, no tax lots (PRISM_ERR_UNSUPPORTED); an
+ * account with more than 512 free weights falls back to the given weights
+ * (status FEASIBLE_NONCERTIFIED at best).
+ *
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture. Every
+ * call reuses the same array and clears what it reads, so calls that overlap on
+ * the GPU (two streams, two threads) race and must be serialised by the caller.
+ * Only opts->eps_kkt, opts->polish_rounds and opts->cuda_stream are used. */
+int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const double* w_in,
+                         const prism_solve_opts* opts, prism_result* res);
+
 /* Message of the last failed call on this thread ("" when none). */
 const char* prism_last_error(void);
 

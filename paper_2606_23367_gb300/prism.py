@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH):
     lib.prism_solve_batch_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p]
     lib.prism_solve_batch_backward.restype = C.c_int
+    lib.prism_polish_noalloc.argtypes = [C.c_void_p, C.POINTER(_Batch), C.c_void_p, C.POINTER(_Opts),
+                                         C.POINTER(_Result)]
+    lib.prism_polish_noalloc.restype = C.c_int
     lib.prism_free_state.argtypes = [C.c_void_p]
     lib.prism_free_state.restype = None
     lib.prism_last_error.argtypes = []
@@ -220,6 +223,40 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
     res.update(t_device_ms=r.t_device_ms, t_call_ms=r.t_call_ms, t_phase_ms=list(r.t_phase_ms),
                device_bytes=r.device_bytes, n_launches=r.n_launches,
                kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches))
+    return res
+
+
+def prism_polish_noalloc(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi, w_in,
+                         asset_idx=None, turnover_cap=None, out=None, **opts) -> dict:
+    """Polish and certify the weights w_in without any device allocation (see prism.h)."""
+    lib = load_library()
+    keep = _Keep()
+    M = int(len(offsets) - 1)
+    nnz = int(_to_numpy(offsets[-1:])[0]) if hasattr(offsets, "cpu") else int(offsets[-1])
+    S = u.n_sectors
+    b = _Batch(M, keep.ptr(offsets, np.int64), keep.ptr(asset_idx, np.int32),
+               keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
+               keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
+               keep.ptr(turnover_cap, np.float64), None, None, None)
+    o = _Opts()
+    lib.prism_default_opts(C.byref(o))
+    for k, v in opts.items():
+        setattr(o, k, v)
+    if out is None:
+        out = dict(w=np.zeros(nnz), status=np.zeros(M, np.int32), iters=np.zeros(M, np.int32),
+                   nu=np.zeros(M), lambda_band=np.zeros((M, S)), theta=np.zeros(M),
+                   diag=np.zeros((M, PRISM_NDIAG)))
+    r = _Result()
+    r.w = keep.ptr(out["w"], np.float64)
+    r.status = keep.ptr(out["status"], np.int32)
+    if out.get("iters") is not None:
+        r.iters = keep.ptr(out["iters"], np.int32)
+    for k in ("nu", "lambda_band", "theta", "diag"):
+        if out.get(k) is not None:
+            setattr(r, k, keep.ptr(out[k], np.float64))
+    _check(lib.prism_polish_noalloc(u.handle, C.byref(b), keep.ptr(w_in, np.float64), C.byref(o), C.byref(r)))
+    res = dict(out)
+    res.update(t_call_ms=r.t_call_ms, device_bytes=r.device_bytes, n_launches=r.n_launches)
     return res
 
 
