@@ -187,6 +187,16 @@ int prism_solve_batch_backward(prism_state* state, const double* dL_dw,
                                double* dmu, double* dB, double* dd, double* dw0);
 void prism_free_state(prism_state* state);
 
+/* Diagnostic: the two shared-B products of one ADMM x-update, run on the solver's
+ * own kernels for the given precision (spec method; the paper discloses no
+ * solver internals, Sec. 3):
+ *   P  = X B   (M x K, FP64 out)   and   BQ = Q B'  (M x N, FP64 out),
+ * with X (M x N) and Q (M x K) row-major FP64 in universe asset order, host or
+ * device. In BATCHED_BF16 mode B is used rounded to BF16 and X, Q are split into
+ * two BF16 terms each, exactly as in the solve. Allocates its own temporaries. */
+int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double* X, const double* Q,
+                            int32_t precision, double* P, double* BQ);
+
 /* Allocation-free polish and certification of weights the caller already holds.
  *
  * The paper has no counterpart to this entry point. It exists for callers that

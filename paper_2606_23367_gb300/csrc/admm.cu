@@ -150,8 +150,8 @@ __global__ void k_small_solve(Dev D) {
         for (int j = 0; j < K; ++j) q = fmaf(C[j], sP[j], q);
         if (D.bf16) {
             __nv_bfloat16 h = __float2bfloat16_rn(q);
-            D.Qhi[(size_t)m * K + t] = h;
-            D.Qlo[(size_t)m * K + t] = __float2bfloat16_rn(q - __bfloat162float(h));
+            D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
+            D.Qlo[(size_t)m * KMAX + t] = __float2bfloat16_rn(q - __bfloat162float(h));
         }
         D.Q[(size_t)m * K + t] = q;
     }
@@ -217,7 +217,7 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
             int i = i0 + lane + 32 * h;
             if (i >= D.N) continue;
             size_t e = (size_t)m * D.Npad + i;
-            D.v[e] = relaxed_v(D, e, i, acc[u][h], rho, irho);
+            D.v[e] = D.raw_out ? acc[u][h] : relaxed_v(D, e, i, acc[u][h], rho, irho);
         }
     }
 }

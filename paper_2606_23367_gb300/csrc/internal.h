@@ -47,6 +47,8 @@ struct Universe {
     float* d_mu32 = nullptr;       // Npad
     __nv_bfloat16* d_B16 = nullptr;   // Npad x K  (row-major, K contiguous)
     __nv_bfloat16* d_Bt16 = nullptr;  // K x Npad  (assets contiguous)
+    __nv_bfloat16* d_B16p = nullptr;  // Npad x 64 (factors zero-padded to 64)
+    __nv_bfloat16* d_Bt16p = nullptr; // 64 x Npad
     float* d_Cinv32 = nullptr;     // NRHO x K x K, capacitance inverses for FP32 B
     float* d_Cinv16 = nullptr;     // NRHO x K x K, for the BF16-rounded B
     size_t bytes = 0;

@@ -368,7 +368,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     const int n_pw = (int)pwl.size();
     // ---- workspace layout
     const size_t MN = (size_t)M * Npad;
-    const int nsplit = choose_nsplit(M, N);
+    int tc_chunk = 0;
+    const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk) : choose_nsplit(M, N);
     const int FMAX = std::min(N, 2048);
     auto layout = [&](Arena& A, Dev& D, PolDev& P, BatchDev& BD, void** stage, int** member, int** err,
                       int** pwidx_dev, double** ragged_out) {
@@ -384,10 +385,10 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.Xhi = A.take<__nv_bfloat16>(MN); D.Xlo = A.take<__nv_bfloat16>(MN);
         D.Ppart = A.take<float>((size_t)nsplit * M * K);
         D.Q = A.take<float>((size_t)M * K);
-        D.Qhi = A.take<__nv_bfloat16>((size_t)M * K); D.Qlo = A.take<__nv_bfloat16>((size_t)M * K);
+        D.Qhi = A.take<__nv_bfloat16>((size_t)M * KMAX); D.Qlo = A.take<__nv_bfloat16>((size_t)M * KMAX);
         D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
         D.nu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
-        D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(1);
+        D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(2);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
@@ -550,7 +551,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     // ---- device views
     D.M = M; D.N = N; D.Npad = Npad; D.K = K; D.S = S;
     D.B32 = U.d_B32; D.d32 = U.d_d32; D.mu32 = U.d_mu32; D.sec_start = U.d_sec_start; D.sector = U.d_sector;
-    D.B16 = U.d_B16; D.Bt16 = U.d_Bt16;
+    D.B16 = U.d_B16; D.Bt16 = U.d_Bt16; D.B16p = U.d_B16p; D.Bt16p = U.d_Bt16p;
+    D.err = D.n_active + 1;
     D.bf16 = batched_mode_bf16;
     D.Cinv = batched_mode_bf16 ? U.d_Cinv16 : U.d_Cinv32;
     D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
@@ -594,6 +596,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.Xhi, 0, MN * 2, st);
         cudaMemsetAsync(D.Xlo, 0, MN * 2, st);
         cudaMemsetAsync(D.v, 0, MN * 4, st);
+        cudaMemsetAsync(D.Qhi, 0, (size_t)M * KMAX * 2, st);
+        cudaMemsetAsync(D.Qlo, 0, (size_t)M * KMAX * 2, st);
+        cudaMemsetAsync(D.n_active, 0, 8, st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
         k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
@@ -611,7 +616,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st); });
         }
         SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
-        cudaMemcpyAsync(SC.pinned, D.n_active, 4, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(SC.pinned, D.n_active, 8, cudaMemcpyDeviceToHost, st);
     };
     int64_t chunk_launches[PRISM_NKCLASS] = {};
     auto admm_loop = [&](int iter_budget) -> int {
@@ -654,7 +659,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             }
             done_iters += check_every;
             if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
-            if (*SC.pinned == 0) break;
+            if (SC.pinned[1] != 0) return -2;      // a bounded tensor-core wait expired
+            if (SC.pinned[0] == 0) break;
             if (o->time_budget_s > 0) {
                 double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call0).count();
                 if (el > o->time_budget_s) break;
@@ -663,6 +669,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         return done_iters;
     };
     int total_iters = admm_loop(o->max_iter + check_every);
+    if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_mark_timeout(D, st); });   // accounts still iterating
     cudaEventRecord(SC.ev[2], st);
@@ -698,6 +705,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.max_iter = saved.max_iter * (retry + 2);
         int more = admm_loop(D.max_iter);
         D = saved;
+        if (more == -2) { set_error("tensor-core pipeline wait timed out"); return PRISM_ERR_CUDA; }
         if (more < 0) { set_error("ADMM retry failed"); return PRISM_ERR_CUDA; }
         total_iters += more;
         SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });

@@ -16,6 +16,8 @@ struct Dev {
     const int* sector = nullptr;
     const __nv_bfloat16* B16 = nullptr;
     const __nv_bfloat16* Bt16 = nullptr;
+    const __nv_bfloat16* B16p = nullptr;    // Npad x 64, factors zero-padded (tensor-core operand)
+    const __nv_bfloat16* Bt16p = nullptr;   // 64 x Npad
     const float* Cinv = nullptr;        // NRHO x K x K for the mode's B
     // per-entry account data (M x Npad), FP32
     const float* w0 = nullptr;
@@ -38,7 +40,7 @@ struct Dev {
     __nv_bfloat16* Xlo = nullptr;
     float* Ppart = nullptr;             // nsplit x M x K partial B'X
     float* Q = nullptr;                 // M x K
-    __nv_bfloat16* Qhi = nullptr;       // M x K split of Q
+    __nv_bfloat16* Qhi = nullptr;       // M x 64 split of Q (factors zero-padded)
     __nv_bfloat16* Qlo = nullptr;
     int nsplit = 1;
     // per-account control
@@ -52,13 +54,15 @@ struct Dev {
     float* theta = nullptr;             // M cap multiplier
     float* rp = nullptr;                // M residuals
     float* rd = nullptr;
-    int* n_active = nullptr;            // 1
+    int* n_active = nullptr;            // [0] accounts still iterating, [1] pipeline error flags
+    int* err = nullptr;                 // = n_active + 1
     float alpha = 1.6f;
     float eps_admm = 3e-4f;
     int min_iter = 20;
     int max_iter = 4000;
     int adapt_every = 25;
     bool bf16 = false;                  // X / Q split in BF16 for tensor-core products
+    int raw_out = 0;                    // diagnostics: G4 writes B Q itself into v
 };
 
 // launchers (admm.cu)
@@ -72,7 +76,8 @@ void launch_mark_timeout(const Dev& D, cudaStream_t st);
 int choose_nsplit(int M, int N);
 
 // tensor-core products (tc_gemm.cu)
-bool tc_available();                                     // tcgen05 kernels compiled in
+bool tc_available();                                     // tensor-map encoder reachable
+int tc_nsplit(int M, int N, int* chunk);                 // asset splits of the tensor-core G2
 void launch_tc_gemm_P(const Dev& D, cudaStream_t st);    // G2 on tcgen05
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
 

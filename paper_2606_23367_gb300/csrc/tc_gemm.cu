@@ -1,9 +1,435 @@
-// tc_gemm.cu -- tcgen05 tensor-core products (placeholder until the kernels land).
+// tc_gemm.cu -- the two shared-B products of the ADMM x-update on tcgen05 tensor cores.
+//
+//   G2:  P[m][k]  = sum_i X[m][i] B[i][k]          (B' X, contraction over assets)
+//   G4:  BQ[i][m] = sum_k B[i][k] Q[m][k]          (B Q, contraction over factors)
+//        + fused epilogue v = alpha x + (1 - alpha) z + y / rho,
+//          x = (mu + rho z - y - BQ) / (2 d + rho)
+//
+// Both run BF16 operands with FP32 accumulation in tensor memory (kind::f16,
+// cta_group::1). B is held in BF16 (the capacitance inverses of the BF16 mode
+// are built from the same rounded B, so the x-update stays an exact solve of a
+// consistent operator); the iterate-side operands are split into two BF16 terms
+// (X = Xhi + Xlo, Q = Qhi + Qlo, 16 significant bits) and both are fed to the
+// MMA, so the products keep near-FP32 accuracy while reading 4 bytes per X entry.
+//
+// Operands are staged by TMA (cp.async.bulk.tensor.2d) into 128-byte-swizzled
+// shared memory, consumed by one elected thread issuing tcgen05.mma, and the
+// accumulator is read back with tcgen05.ld (warp w reads TMEM lanes 32w..32w+31).
+// Every mbarrier wait is bounded by a %globaltimer limit; on expiry the kernel
+// records an error flag, skips the remaining work, releases its tensor memory
+// and returns, and the host reports the failure.
+#include <cuda.h>
+
 #include "common.cuh"
 #include "solver.h"
 
 namespace prism {
-bool tc_available() { return false; }
-void launch_tc_gemm_P(const Dev&, cudaStream_t) {}
-void launch_tc_gemm_x(const Dev&, cudaStream_t) {}
+namespace tc {
+
+constexpr int TM = 128;            // MMA M (accounts in G2, assets in G4)
+constexpr int TK = 64;             // BF16 elements per 128-byte swizzled row
+constexpr int KP = 64;             // factors, zero-padded, in the BF16 copies of B and Q
+constexpr int G2_STAGES = 2;
+constexpr uint32_t G2_A_BYTES = TM * TK * 2;      // 16 KB
+constexpr uint32_t G2_B_BYTES = KP * TK * 2;      // 8 KB
+constexpr int G4_TN = 128;                        // MMA N in G4 (accounts per tile)
+constexpr uint32_t G4_TILE_BYTES = 128 * KP * 2;  // 16 KB
+constexpr uint64_t WAIT_LIMIT_NS = 1000000000ull; // 1 s
+
+// instruction descriptor, kind::f16: D = F32 (bit 4), A = B = BF16 (bits 7, 10),
+// both K-major, N >> 3 at bit 17, M >> 4 at bit 24
+__host__ __device__ constexpr uint32_t idesc_bf16(int m, int n) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(n >> 3) << 17) | (uint32_t(m >> 4) << 24);
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ uint64_t gtimer() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_barrier_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(smem_u32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+
+// Wait for the phase of parity `parity` to complete, for at most WAIT_LIMIT_NS.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = gtimer();
+    while (!mbar_try_wait(bar, parity)) {
+        if (gtimer() - t0 > WAIT_LIMIT_NS) {
+            atomicOr(err, code);
+            return false;
+        }
+    }
+    return true;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+            smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+
+__device__ __forceinline__ void tmem_alloc(uint32_t* dst, uint32_t ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(dst)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+
+__device__ __forceinline__ void fence_before_sync() {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void fence_after_sync() {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sw128_desc(const void* smem) {
+    const uint32_t a = smem_u32(smem);
+    uint64_t d = 0;
+    d |= uint64_t((a & 0x3FFFF) >> 4);       // start address (16-byte units)
+    d |= uint64_t(1) << 16;                  // leading byte offset (unused for this layout)
+    d |= uint64_t(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
+    d |= uint64_t(1) << 46;                  // descriptor version for tcgen05
+    d |= uint64_t(2) << 61;                  // swizzle: 128 B
+    return d;
+}
+
+__device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+            d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "r"(acc)
+        : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint64_t* bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+// 16 consecutive FP32 columns of this thread's TMEM lane
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
+    uint32_t r[16];
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+__device__ __forceinline__ float rho_of_idx(int j) {
+    return float(RHO_MIN) * exp10f(float(j) / float(RHO_PER_DECADE));
+}
+
+// ---------------------------------------------------------------------------
+// G2: Ppart[split][m][k] = sum over the split's assets of (Xhi + Xlo)[m][i] B[i][k]
+// grid (account tiles, splits); 128 threads; thread 0 drives TMA and the MMAs.
+// ---------------------------------------------------------------------------
+struct __align__(1024) G2Smem {
+    __nv_bfloat16 ahi[G2_STAGES][TM * TK];
+    __nv_bfloat16 alo[G2_STAGES][TM * TK];
+    __nv_bfloat16 b[G2_STAGES][KP * TK];
+    uint64_t full[G2_STAGES];
+    uint64_t empty[G2_STAGES];
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+};
+
+__global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUtensorMap mXhi,
+                                                    const __grid_constant__ CUtensorMap mXlo,
+                                                    const __grid_constant__ CUtensorMap mBt, Dev D, int chunk) {
+    extern __shared__ unsigned char raw[];
+    G2Smem& s = *reinterpret_cast<G2Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int mt = blockIdx.x, split = blockIdx.y;
+    const int i0 = split * chunk, i1 = min(D.N, i0 + chunk);
+    const int nk = (i1 > i0) ? (i1 - i0 + TK - 1) / TK : 0;
+    constexpr uint32_t IDESC = idesc_bf16(TM, KP);
+    if (warp == 0) tmem_alloc(&s.tmem, 64);
+    if (tid == 0) {
+        for (int q = 0; q < G2_STAGES; ++q) {
+            mbar_init(&s.full[q], 1);
+            mbar_init(&s.empty[q], 1);
+        }
+        mbar_init(&s.done, 1);
+        s.fail = 0;
+        fence_barrier_init();
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s.tmem;
+    if (tid == 0 && nk > 0) {
+        auto load = [&](int kt) {
+            const int q = kt % G2_STAGES;
+            mbar_expect_tx(&s.full[q], 2 * G2_A_BYTES + G2_B_BYTES);
+            tma_load_2d(s.ahi[q], &mXhi, &s.full[q], i0 + kt * TK, mt * TM);
+            tma_load_2d(s.alo[q], &mXlo, &s.full[q], i0 + kt * TK, mt * TM);
+            tma_load_2d(s.b[q], &mBt, &s.full[q], i0 + kt * TK, 0);
+        };
+        int issued = 0;
+        for (; issued < G2_STAGES && issued < nk; ++issued) load(issued);
+        bool ok = true;
+        int consumed = 0;
+        for (int kt = 0; kt < nk && ok; ++kt) {
+            const int q = kt % G2_STAGES;
+            const uint32_t par = (kt / G2_STAGES) & 1;
+            if (!mbar_wait(&s.full[q], par, D.err, 1)) { ok = false; break; }
+            consumed = kt + 1;
+            fence_after_sync();
+            const uint64_t dhi = sw128_desc(s.ahi[q]), dlo = sw128_desc(s.alo[q]), db = sw128_desc(s.b[q]);
+#pragma unroll
+            for (int kk = 0; kk < TK / 16; ++kk) {
+                // +32 bytes per 16-element K step inside the 128-byte swizzled row
+                umma_bf16(tmem, dhi + 2 * kk, db + 2 * kk, IDESC, (kt > 0 || kk > 0) ? 1u : 0u);
+                umma_bf16(tmem, dlo + 2 * kk, db + 2 * kk, IDESC, 1u);
+            }
+            umma_commit(&s.empty[q]);
+            if (kt + G2_STAGES < nk) {
+                if (!mbar_wait(&s.empty[q], par, D.err, 2)) { ok = false; break; }
+                load(kt + G2_STAGES);
+                ++issued;
+            }
+        }
+        if (ok) {
+            umma_commit(&s.done);
+        } else {
+            s.fail = 1;
+            // drain the loads still in flight before the shared memory goes away
+            for (int kt = consumed; kt < issued; ++kt)
+                mbar_wait(&s.full[kt % G2_STAGES], (kt / G2_STAGES) & 1, D.err, 4);
+        }
+    }
+    __syncthreads();
+    bool have = (nk > 0) && !s.fail;
+    if (have && !mbar_wait(&s.done, 0, D.err, 8)) have = false;
+    have = __syncthreads_and(have);        // tcgen05.ld below is warp-collective: decide uniformly
+    fence_after_sync();
+    const int m = mt * TM + warp * 32 + lane;
+    const uint32_t lane_addr = tmem + (uint32_t(warp * 32) << 16);
+    float acc[16];
+#pragma unroll 1
+    for (int c = 0; c < KP / 16; ++c) {
+        if (have) tmem_ld16(lane_addr + c * 16, acc);
+        else
+#pragma unroll
+            for (int j = 0; j < 16; ++j) acc[j] = 0.f;
+        if (m < D.M) {
+            float* out = D.Ppart + ((size_t)split * D.M + m) * D.K;
+#pragma unroll
+            for (int j = 0; j < 16; ++j)
+                if (c * 16 + j < D.K) out[c * 16 + j] = acc[j];
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, 64);
+}
+
+// ---------------------------------------------------------------------------
+// G4: one 128-asset x 128-account tile per block. TMEM lane = asset row, column =
+// account, so the epilogue reads z, y and writes v coalesced along assets.
+// ---------------------------------------------------------------------------
+struct __align__(1024) G4Smem {
+    __nv_bfloat16 a[TM * KP];        // B tile: 128 assets x 64 factors
+    __nv_bfloat16 bhi[G4_TN * KP];   // Qhi tile: 128 accounts x 64 factors
+    __nv_bfloat16 blo[G4_TN * KP];
+    uint64_t full;
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+    float rho[G4_TN];
+    float irho[G4_TN];
+};
+
+__global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUtensorMap mB,
+                                                    const __grid_constant__ CUtensorMap mQhi,
+                                                    const __grid_constant__ CUtensorMap mQlo, Dev D) {
+    extern __shared__ unsigned char raw[];
+    G4Smem& s = *reinterpret_cast<G4Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int at = blockIdx.x, mt = blockIdx.y;
+    constexpr uint32_t IDESC = idesc_bf16(TM, G4_TN);
+    if (warp == 0) tmem_alloc(&s.tmem, G4_TN);
+    if (tid == 0) {
+        mbar_init(&s.full, 1);
+        mbar_init(&s.done, 1);
+        s.fail = 0;
+        fence_barrier_init();
+    }
+    {
+        const int m = mt * G4_TN + tid;
+        const float r = (m < D.M) ? rho_of_idx(D.rho_idx[m]) : 1.f;
+        s.rho[tid] = r;
+        s.irho[tid] = 1.f / r;
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s.tmem;
+    if (tid == 0) {
+        mbar_expect_tx(&s.full, 3 * G4_TILE_BYTES);
+        tma_load_2d(s.a, &mB, &s.full, 0, at * TM);
+        tma_load_2d(s.bhi, &mQhi, &s.full, 0, mt * G4_TN);
+        tma_load_2d(s.blo, &mQlo, &s.full, 0, mt * G4_TN);
+        if (mbar_wait(&s.full, 0, D.err, 16)) {
+            fence_after_sync();
+            const uint64_t da = sw128_desc(s.a), dh = sw128_desc(s.bhi), dl = sw128_desc(s.blo);
+#pragma unroll
+            for (int kk = 0; kk < KP / 16; ++kk) {
+                umma_bf16(tmem, da + 2 * kk, dh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
+                umma_bf16(tmem, da + 2 * kk, dl + 2 * kk, IDESC, 1u);
+            }
+            umma_commit(&s.done);
+        } else {
+            s.fail = 1;
+        }
+    }
+    __syncthreads();
+    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
+    have = __syncthreads_and(have);
+    fence_after_sync();
+    const int i = at * TM + warp * 32 + lane;          // asset of this TMEM lane
+    const bool row_ok = have && i < D.N;
+    float mu = 0.f, dd = 1.f;
+    if (i < D.N) {
+        mu = D.mu32[i];
+        dd = 2.f * D.d32[i];
+    }
+    const uint32_t lane_addr = tmem + (uint32_t(warp * 32) << 16);
+    float bq[16];
+#pragma unroll 1
+    for (int c = 0; c < G4_TN / 16; ++c) {
+        if (have) tmem_ld16(lane_addr + c * 16, bq);
+        if (!row_ok) continue;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            const int col = c * 16 + j;
+            const int m = mt * G4_TN + col;
+            if (m >= D.M) break;
+            const size_t e = (size_t)m * D.Npad + i;
+            if (D.raw_out) { D.v[e] = bq[j]; continue; }
+            const float rho = s.rho[col];
+            const float z = D.z[e], y = D.y[e];
+            const float x = (mu + rho * z - y - bq[j]) / (dd + rho);
+            D.v[e] = D.alpha * x + (1.f - D.alpha) * z + y * s.irho[col];
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, G4_TN);
+}
+
+// ---------------------------------------------------------------------------
+// host side: tensor maps and launches
+// ---------------------------------------------------------------------------
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                 const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                 CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiled encoder() {
+    static EncodeTiled fn = nullptr;
+    static bool tried = false;
+    if (!tried) {
+        tried = true;
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+        else
+            cudaGetLastError();
+    }
+    return fn;
+}
+
+// 2-D BF16 map: inner dimension dim0 (contiguous), rows dim1 with the given byte stride.
+static bool map2d(CUtensorMap* m, const void* base, uint64_t dim0, uint64_t dim1, uint64_t row_bytes, uint32_t box0,
+                  uint32_t box1) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {dim0, dim1};
+    cuuint64_t strides[1] = {row_bytes};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+}  // namespace tc
+
+bool tc_available() { return tc::encoder() != nullptr; }
+
+int tc_nsplit(int M, int N, int* chunk_out) {
+    const int mtiles = cdiv(M, tc::TM);
+    const int target = std::max(1, 2 * 152 / mtiles);
+    int chunk = cdiv(cdiv(N, target), tc::TK) * tc::TK;
+    chunk = std::max(chunk, tc::TK);
+    *chunk_out = chunk;
+    return cdiv(N, chunk);
+}
+
+void launch_tc_gemm_P(const Dev& D, cudaStream_t st) {
+    CUtensorMap mXhi, mXlo, mBt;
+    bool ok = tc::map2d(&mXhi, D.Xhi, D.Npad, D.M, (uint64_t)D.Npad * 2, tc::TK, tc::TM) &&
+              tc::map2d(&mXlo, D.Xlo, D.Npad, D.M, (uint64_t)D.Npad * 2, tc::TK, tc::TM) &&
+              tc::map2d(&mBt, D.Bt16p, D.Npad, tc::KP, (uint64_t)D.Npad * 2, tc::TK, tc::KP);
+    if (!ok) { set_error("tensor map encoding failed (G2)"); return; }
+    int chunk = 0;
+    const int ns = tc_nsplit(D.M, D.N, &chunk);
+    const size_t smem = sizeof(tc::G2Smem) + 1024;
+    cudaFuncSetAttribute(tc::k_tc_gemm_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(cdiv(D.M, tc::TM), ns);
+    tc::k_tc_gemm_P<<<grid, 128, smem, st>>>(mXhi, mXlo, mBt, D, chunk);
+}
+
+void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
+    CUtensorMap mB, mQhi, mQlo;
+    bool ok = tc::map2d(&mB, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
+              tc::map2d(&mQhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::G4_TN) &&
+              tc::map2d(&mQlo, D.Qlo, tc::KP, D.M, tc::KP * 2, tc::KP, tc::G4_TN);
+    if (!ok) { set_error("tensor map encoding failed (G4)"); return; }
+    const size_t smem = sizeof(tc::G4Smem) + 1024;
+    cudaFuncSetAttribute(tc::k_tc_gemm_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::G4_TN));
+    tc::k_tc_gemm_x<<<grid, 128, smem, st>>>(mB, mQhi, mQlo, D);
+}
+
 }  // namespace prism

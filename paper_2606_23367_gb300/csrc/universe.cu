@@ -109,7 +109,8 @@ __global__ void k_cinv(const double* __restrict__ G, const double* __restrict__ 
 }
 
 __global__ void k_convert_B(const double* __restrict__ B64, int Npad, int K, float* __restrict__ B32,
-                            __nv_bfloat16* __restrict__ B16, __nv_bfloat16* __restrict__ Bt16) {
+                            __nv_bfloat16* __restrict__ B16, __nv_bfloat16* __restrict__ Bt16,
+                            __nv_bfloat16* __restrict__ B16p, __nv_bfloat16* __restrict__ Bt16p) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)Npad * K) return;
     int i = int(e / K), k = int(e % K);
@@ -118,6 +119,8 @@ __global__ void k_convert_B(const double* __restrict__ B64, int Npad, int K, flo
     __nv_bfloat16 h = __float2bfloat16_rn(float(b));
     B16[e] = h;
     Bt16[(size_t)k * Npad + i] = h;
+    B16p[(size_t)i * KMAX + k] = h;
+    Bt16p[(size_t)k * Npad + i] = h;
 }
 
 __global__ void k_bf16_to_float(const __nv_bfloat16* __restrict__ a, float* __restrict__ b, size_t n) {
@@ -149,7 +152,7 @@ static int fetch(const T* src, size_t n, std::vector<T>& dst) {
 
 static void free_universe(Universe& U) {
     void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64,
-                    U.d_mu64, U.d_B32, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16,
+                    U.d_mu64, U.d_B32, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
                     U.d_Cinv32, U.d_Cinv16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -250,6 +253,8 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     TRY(dalloc(U, &U.d_mu32, Npad));
     TRY(dalloc(U, &U.d_B16, (size_t)Npad * K));
     TRY(dalloc(U, &U.d_Bt16, (size_t)K * Npad));
+    TRY(dalloc(U, &U.d_B16p, (size_t)Npad * KMAX));
+    TRY(dalloc(U, &U.d_Bt16p, (size_t)KMAX * Npad));
     TRY(dalloc(U, &U.d_Cinv32, (size_t)NRHO * K * K));
     TRY(dalloc(U, &U.d_Cinv16, (size_t)NRHO * K * K));
     auto H2D = [&](void* dst, const void* src, size_t n) {
@@ -272,7 +277,10 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     }
     {
         size_t n = (size_t)Npad * K;
-        k_convert_B<<<(unsigned)cdiv64(n, 256), 256, 0, U.stream>>>(U.d_B64, Npad, K, U.d_B32, U.d_B16, U.d_Bt16);
+        cudaMemsetAsync(U.d_B16p, 0, (size_t)Npad * KMAX * 2, U.stream);
+        cudaMemsetAsync(U.d_Bt16p, 0, (size_t)KMAX * Npad * 2, U.stream);
+        k_convert_B<<<(unsigned)cdiv64(n, 256), 256, 0, U.stream>>>(U.d_B64, Npad, K, U.d_B32, U.d_B16, U.d_Bt16,
+                                                                      U.d_B16p, U.d_Bt16p);
         double* G = nullptr;
         if (cudaMalloc(&G, (size_t)NRHO * K * K * sizeof(double)) != cudaSuccess) {
             set_error("cudaMalloc (Gram scratch) failed");

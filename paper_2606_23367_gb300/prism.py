@@ -89,6 +89,9 @@ def load_library(path: str = LIB_PATH):
     lib.prism_solve_batch_backward.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                                C.c_void_p, C.c_void_p]
     lib.prism_solve_batch_backward.restype = C.c_int
+    lib.prism_shared_b_products.argtypes = [C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p, C.c_int32,
+                                            C.c_void_p, C.c_void_p]
+    lib.prism_shared_b_products.restype = C.c_int
     lib.prism_polish_noalloc.argtypes = [C.c_void_p, C.POINTER(_Batch), C.c_void_p, C.POINTER(_Opts),
                                          C.POINTER(_Result)]
     lib.prism_polish_noalloc.restype = C.c_int
@@ -224,6 +227,20 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
                device_bytes=r.device_bytes, n_launches=r.n_launches,
                kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches))
     return res
+
+
+def prism_shared_b_products(u: UniverseHandle, X, Q, precision=PRISM_BATCHED_BF16):
+    """P = X B and BQ = Q B' on the solver's kernels (diagnostic; see prism.h)."""
+    lib = load_library()
+    keep = _Keep()
+    X = np.ascontiguousarray(X, np.float64)
+    Q = np.ascontiguousarray(Q, np.float64)
+    M = X.shape[0]
+    P = np.zeros((M, u.n_factors))
+    BQ = np.zeros((M, u.n_assets))
+    _check(lib.prism_shared_b_products(u.handle, M, keep.ptr(X, np.float64), keep.ptr(Q, np.float64),
+                                       int(precision), P.ctypes.data, BQ.ctypes.data))
+    return P, BQ
 
 
 def prism_polish_noalloc(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi, w_in,

@@ -20,7 +20,8 @@ def _lib():
     prism.load_library()
 
 
-MODES = [prism.PRISM_BATCHED_FP32, prism.PRISM_PLAIN_FP32]
+MODES = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16, prism.PRISM_PLAIN_FP32]
+BATCHED = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16]
 
 
 @pytest.mark.parametrize("mode", MODES)
@@ -30,7 +31,7 @@ def test_single_account_n100(mode):
     assert_parity(uni, batch, res)
 
 
-@pytest.mark.parametrize("mode", [prism.PRISM_BATCHED_FP32])
+@pytest.mark.parametrize("mode", BATCHED)
 def test_batch_shared_universe_small(mode):
     # 1,200 assets: several 64-wide tiles plus a ragged tail; K = 64 as at full size
     uni, batch = make_workload(1, N=1200, K=64, M=6)
@@ -38,21 +39,24 @@ def test_batch_shared_universe_small(mode):
     assert_parity(uni, batch, res)
 
 
-def test_ragged_accounts_small():
+@pytest.mark.parametrize("mode", BATCHED)
+def test_ragged_accounts_small(mode):
     uni, batch = make_workload(2, N=900, M=6)
-    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    res = gpu_solve(uni, batch, precision=mode)
     assert_parity(uni, batch, res)
 
 
-def test_tax_lots_and_turnover_cap_small():
+@pytest.mark.parametrize("mode", BATCHED)
+def test_tax_lots_and_turnover_cap_small(mode):
     uni, batch = make_workload(3, N=400, K=12, M=4)
-    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    res = gpu_solve(uni, batch, precision=mode)
     assert_parity(uni, batch, res)
 
 
-def test_differentiation_workload_forward_small():
+@pytest.mark.parametrize("mode", BATCHED)
+def test_differentiation_workload_forward_small(mode):
     uni, batch = make_workload(4, N=500, M=4)
-    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32)
+    res = gpu_solve(uni, batch, precision=mode)
     assert_parity(uni, batch, res)
 
 
