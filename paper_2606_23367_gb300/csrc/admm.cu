@@ -165,16 +165,7 @@ void launch_small_solve(const Dev& D, cudaStream_t st) {
 // G4 (SIMT): v = alpha x + (1-alpha) z + y/rho with x = X - Delta^{-1} (B Q)
 // block = 32 accounts x 64 assets; thread = 4 accounts x 2 assets
 // ---------------------------------------------------------------------------
-// v = alpha x + (1 - alpha) z + y / rho with x = X - Delta^{-1} BQ, X = Delta^{-1}(mu + rho z - y)
-// recomputed here in FP32 from the state (so the split copy of X feeds only the products).
-__device__ __forceinline__ float relaxed_v(const Dev& D, size_t e, int i, float BQ, float rho,
-                                           float irho) {
-    const float z = D.z[e], y = D.y[e];
-    const float dinv = 1.f / (2.f * D.d32[i] + rho);
-    const float x = (D.mu32[i] + rho * z - y - BQ) * dinv;
-    return D.alpha * x + (1.f - D.alpha) * z + y * irho;
-}
-
+// (x is recomputed from z and y in the epilogue, so the split copy of X feeds only the products)
 __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
     const int m0 = blockIdx.y * 32;
     const int i0 = blockIdx.x * 64;
@@ -206,18 +197,34 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
             acc[u][1] = fmaf(q, b1, acc[u][1]);
         }
     }
+    // epilogue: all loads of the thread's 8 outputs first, then the stores
+    float zz[4][2], yy[4][2];
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-        int m = m0 + grp * 4 + u;
-        if (m >= D.M) continue;
-        float rho = rho_val(D.rho_idx[m]);
-        float irho = 1.f / rho;
+        const int m = m0 + grp * 4 + u;
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
-            int i = i0 + lane + 32 * h;
+            const int i = i0 + lane + 32 * h;
+            const bool ok = m < D.M && i < D.N;
+            const size_t e = (size_t)m * D.Npad + i;
+            zz[u][h] = ok ? __ldg(D.z + e) : 0.f;
+            yy[u][h] = ok ? __ldg(D.y + e) : 0.f;
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int m = m0 + grp * 4 + u;
+        if (m >= D.M) continue;
+        const float rho = rho_val(D.rho_idx[m]);
+        const float irho = 1.f / rho;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int i = i0 + lane + 32 * h;
             if (i >= D.N) continue;
-            size_t e = (size_t)m * D.Npad + i;
-            D.v[e] = D.raw_out ? acc[u][h] : relaxed_v(D, e, i, acc[u][h], rho, irho);
+            const size_t e = (size_t)m * D.Npad + i;
+            if (D.raw_out) { D.v[e] = acc[u][h]; continue; }
+            const float x = (D.mu32[i] + rho * zz[u][h] - yy[u][h] - acc[u][h]) / (2.f * D.d32[i] + rho);
+            D.v[e] = D.alpha * x + (1.f - D.alpha) * zz[u][h] + yy[u][h] * irho;
         }
     }
 }
@@ -230,22 +237,33 @@ void launch_gemm_x(const Dev& D, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // G5/G6: projection onto Z with the transition prox, dual update, residuals,
 // penalty adaptation, convergence. One block per account, warp w owns sectors
-// w, w + nwarps, ...
+// w, w + nwarps, ... The account's per-entry data are read through a source:
+// shared memory (staged once per launch) when the account fits, else global.
 // ---------------------------------------------------------------------------
 struct EntryEval {
     float z;
     int lin;   // 1 when dz/deta = -1/rho (z strictly inside a linear piece)
 };
 
+// per-entry data of one account, from global memory
+struct GlobalSrc {
+    const float *v, *w0, *lo, *up, *c;
+    const int* pw;
+    __device__ __forceinline__ GlobalSrc(const Dev& D, size_t base)
+        : v(D.v + base), w0(D.w0 + base), lo(D.lo + base), up(D.up + base), c(D.c + base),
+          pw(D.pw_idx ? D.pw_idx + base : nullptr) {}
+};
+
 // z_i(eta) for one entry: prox of (phi_i + theta|.-w0|)/rho on [l, u] at t = v - eta/rho.
-__device__ __forceinline__ EntryEval eval_entry(const Dev& D, size_t e, float vv, float eta,
-                                                float theta, float irho) {
+template <class Src>
+__device__ __forceinline__ EntryEval eval_entry(const Dev& D, const Src& S, int p, float eta, float theta,
+                                                float irho) {
     EntryEval r;
-    const float t = vv - eta * irho;
-    const float w0 = D.w0[e], lo = D.lo[e], up = D.up[e];
-    const int pw = D.pw_idx ? D.pw_idx[e] : -1;
+    const float t = S.v[p] - eta * irho;
+    const float w0 = S.w0[p], lo = S.lo[p], up = S.up[p];
+    const int pw = S.pw ? S.pw[p] : -1;
     if (pw < 0) {
-        const float k = (D.c[e] + theta) * irho;
+        const float k = (S.c[p] + theta) * irho;
         float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
         z = fminf(fmaxf(z, lo), up);
         r.z = z;
@@ -271,14 +289,14 @@ __device__ __forceinline__ EntryEval eval_entry(const Dev& D, size_t e, float vv
 }
 
 // Warp-collective sum of z and count of linear entries over sorted positions [p0, p1).
-__device__ __forceinline__ void warp_sector_sum(const Dev& D, size_t base, int p0, int p1, float eta,
+template <class Src>
+__device__ __forceinline__ void warp_sector_sum(const Dev& D, const Src& S, int p0, int p1, float eta,
                                                 float theta, float irho, float& sum, int& cnt) {
     const int lane = threadIdx.x & 31;
     float s = 0.f;
     int n = 0;
     for (int p = p0 + lane; p < p1; p += 32) {
-        size_t e = base + p;
-        EntryEval r = eval_entry(D, e, D.v[e], eta, theta, irho);
+        const EntryEval r = eval_entry(D, S, p, eta, theta, irho);
         s += r.z;
         n += r.lin;
     }
@@ -300,7 +318,7 @@ __device__ __forceinline__ void root_init(Root& R, float x0, float step) {
     R.done = 0;
 }
 
-// One update from g = S(x) - target and the count of linear entries. Returns next x.
+// One update from g = S(x) - target and the count of linear entries.
 __device__ __forceinline__ void root_update(Root& R, float g, int cnt, float rho, float tol) {
     if (fabsf(g) <= tol) { R.done = 1; return; }
     if (g > 0.f) R.a = R.x; else R.b = R.x;
@@ -331,39 +349,43 @@ struct ProxShared {
     float cap_hi[SMAX], floor_lo[SMAX];
     float red_f[32];
     int red_i[32];
-    float red_f2[32];
+    float red5[5][32];
+    int red_bad[32];
+    int newj;
 };
 
 // Inner projection at fixed theta: per-sector edge roots, then the budget root.
 // Returns nu; sector edge multipliers in sh.eta_*. Block-collective.
-__device__ float project_inner(const Dev& D, int a, float theta, float rho, float irho,
-                               float nu0, ProxShared& sh) {
+template <class Src>
+__device__ float project_inner(const Dev& D, const Src& S, int a, float theta, float rho, float irho, float nu0,
+                               ProxShared& sh) {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
-    const size_t base = (size_t)a * D.Npad;
     const float step0 = 0.05f * rho + 1e-6f;
-    // phase A: sector edges
+    // phase A: sector edges (one warp per sector, no block synchronisation)
     for (int s = warp; s < D.S; s += nwarps) {
         const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
         const float hi = D.band_hi[a * D.S + s], lo = D.band_lo[a * D.S + s];
         float eh = -FLT_MAX, el = FLT_MAX;
         if (p1 > p0 && hi < sh.cap_hi[s]) {
             Root R;
-            float w = D.eta_hi[a * D.S + s];
+            const float w = D.eta_hi[a * D.S + s];
             root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
-            for (int it = 0; it < PROX_MAXIT && !R.done; ++it) {
+            int it = 0;
+            for (; it < PROX_MAXIT && !R.done; ++it) {
                 float sum; int cnt;
-                warp_sector_sum(D, base, p0, p1, R.x, theta, irho, sum, cnt);
+                warp_sector_sum(D, S, p0, p1, R.x, theta, irho, sum, cnt);
                 root_update(R, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
             }
+            if (D.stats && (threadIdx.x & 31) == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
             eh = R.x;
         }
         if (p1 > p0 && lo > sh.floor_lo[s]) {
             Root R;
-            float w = D.eta_lo[a * D.S + s];
+            const float w = D.eta_lo[a * D.S + s];
             root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
             for (int it = 0; it < PROX_MAXIT && !R.done; ++it) {
                 float sum; int cnt;
-                warp_sector_sum(D, base, p0, p1, R.x, theta, irho, sum, cnt);
+                warp_sector_sum(D, S, p0, p1, R.x, theta, irho, sum, cnt);
                 root_update(R, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
             }
             el = R.x;
@@ -382,9 +404,9 @@ __device__ float project_inner(const Dev& D, int a, float theta, float rho, floa
         int pc = 0;
         for (int s = warp; s < D.S; s += nwarps) {
             const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-            float arg = fminf(fmaxf(R.x, sh.eta_hi[s]), sh.eta_lo[s]);
+            const float arg = fminf(fmaxf(R.x, sh.eta_hi[s]), sh.eta_lo[s]);
             float sum; int cnt;
-            warp_sector_sum(D, base, p0, p1, arg, theta, irho, sum, cnt);
+            warp_sector_sum(D, S, p0, p1, arg, theta, irho, sum, cnt);
             part += sum;
             if (arg == R.x) pc += cnt;
         }
@@ -395,24 +417,24 @@ __device__ float project_inner(const Dev& D, int a, float theta, float rho, floa
         for (int w = 0; w < nwarps; ++w) { T += sh.red_f[w]; C += sh.red_i[w]; }
         __syncthreads();
         root_update(R, T - 1.f, C, rho, 1e-6f);
+        if (D.stats && threadIdx.x == 0) atomicAdd(D.stats + 2, 1ull);
         if (R.done) break;
     }
     return R.x;
 }
 
 // Turnover sum_i |z_i - w0_i| at the current (nu, eta, theta). Block-collective.
-__device__ float turnover_at(const Dev& D, int a, float nu, float theta, float irho, ProxShared& sh) {
+template <class Src>
+__device__ float turnover_at(const Dev& D, const Src& S, float nu, float theta, float irho, ProxShared& sh) {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
-    const size_t base = (size_t)a * D.Npad;
     float part = 0.f;
     for (int s = warp; s < D.S; s += nwarps) {
         const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-        float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+        const float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
         float acc = 0.f;
         for (int p = p0 + lane; p < p1; p += 32) {
-            size_t e = base + p;
-            EntryEval r = eval_entry(D, e, D.v[e], arg, theta, irho);
-            acc += fabsf(r.z - D.w0[e]);
+            const EntryEval r = eval_entry(D, S, p, arg, theta, irho);
+            acc += fabsf(r.z - S.w0[p]);
         }
         part += warp_sum(acc);
     }
@@ -424,10 +446,9 @@ __device__ float turnover_at(const Dev& D, int a, float nu, float theta, float i
     return U;
 }
 
-__global__ void __launch_bounds__(1024) k_prox(Dev D) {
-    const int a = blockIdx.x;
-    if (!D.active[a]) return;
-    __shared__ ProxShared sh;
+// The whole per-account step once the source is ready.
+template <class Src>
+__device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) {
     const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
     const int tid = threadIdx.x;
     const size_t base = (size_t)a * D.Npad;
@@ -438,8 +459,8 @@ __global__ void __launch_bounds__(1024) k_prox(Dev D) {
         const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
         float cu = 0.f, cl = 0.f;
         for (int p = p0 + lane; p < p1; p += 32) {
-            cu += D.up[base + p];
-            cl += D.lo[base + p];
+            cu += S.up[p];
+            cl += S.lo[p];
         }
         cu = warp_sum(cu);
         cl = warp_sum(cl);
@@ -447,17 +468,17 @@ __global__ void __launch_bounds__(1024) k_prox(Dev D) {
     }
     __syncthreads();
     float theta = 0.f;
-    float nu = project_inner(D, a, 0.f, rho, irho, D.nu[a], sh);
+    float nu = project_inner(D, S, a, 0.f, rho, irho, D.nu[a], sh);
     const float tau = D.tau ? D.tau[a] : INFINITY;
     if (tau < INFINITY) {
-        float U = turnover_at(D, a, nu, 0.f, irho, sh);
+        const float U = turnover_at(D, S, nu, 0.f, irho, sh);
         if (U > tau * (1.f + 1e-6f)) {
             // bracketed secant (Illinois) on U(theta) - tau, U nonincreasing in theta
             float t_lo = 0.f, u_lo = U - tau;
-            float t_hi = fmaxf(D.theta[a], 1e-4f), u_hi;
+            float t_hi = fmaxf(D.theta[a], 1e-4f), u_hi = 0.f;
             for (int it = 0; it < 40; ++it) {
-                nu = project_inner(D, a, t_hi, rho, irho, nu, sh);
-                u_hi = turnover_at(D, a, nu, t_hi, irho, sh) - tau;
+                nu = project_inner(D, S, a, t_hi, rho, irho, nu, sh);
+                u_hi = turnover_at(D, S, nu, t_hi, irho, sh) - tau;
                 if (u_hi <= 0.f) break;
                 t_lo = t_hi; u_lo = u_hi;
                 t_hi *= 4.f;
@@ -467,8 +488,8 @@ __global__ void __launch_bounds__(1024) k_prox(Dev D) {
             for (int it = 0; it < 60; ++it) {
                 float tn = t_hi - u_hi * (t_hi - t_lo) / (u_hi - u_lo);
                 if (!(tn > t_lo && tn < t_hi)) tn = 0.5f * (t_lo + t_hi);
-                nu = project_inner(D, a, tn, rho, irho, nu, sh);
-                float un = turnover_at(D, a, nu, tn, irho, sh) - tau;
+                nu = project_inner(D, S, a, tn, rho, irho, nu, sh);
+                const float un = turnover_at(D, S, nu, tn, irho, sh) - tau;
                 theta = tn;
                 if (fabsf(un) <= 2e-7f * tau || (t_hi - t_lo) <= 1e-7f * t_hi) break;
                 if (un > 0.f) {
@@ -483,45 +504,60 @@ __global__ void __launch_bounds__(1024) k_prox(Dev D) {
             }
         }
     }
-    // final z, dual update, residuals
+    // final z, dual update, residuals, and X for the next iteration at the current
+    // penalty; each lane's loads for a chunk of CH entries are issued before its stores
+    constexpr int CH = 8;
     float rp = 0.f, rd = 0.f, nx = 0.f, nz = 0.f, ny = 0.f;
     int bad = 0;
     for (int s = warp; s < D.S; s += nwarps) {
         const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-        float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
-        for (int p = p0 + lane; p < p1; p += 32) {
-            size_t e = base + p;
-            float vv = D.v[e];
-            EntryEval r = eval_entry(D, e, vv, arg, theta, irho);
-            float zo = D.z[e], yo = D.y[e];
-            float yn = rho * (vv - r.z);
-            rp = fmaxf(rp, fabsf(yn - yo) * irho);
-            rd = fmaxf(rd, rho * fabsf(r.z - zo));
-            nx = fmaxf(nx, fabsf(vv - yo * irho));
-            nz = fmaxf(nz, fabsf(r.z));
-            ny = fmaxf(ny, fabsf(yn));
-            bad |= !(isfinite(r.z) && isfinite(yn));
-            D.z[e] = r.z;
-            D.y[e] = yn;
+        const float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+        for (int pb = p0 + lane; pb < p1; pb += 32 * CH) {
+            float zo[CH], yo[CH], mu[CH], dd[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int p = pb + 32 * c;
+                const bool in = p < p1;
+                zo[c] = in ? D.z[base + p] : 0.f;
+                yo[c] = in ? D.y[base + p] : 0.f;
+                mu[c] = in ? D.mu32[p] : 0.f;
+                dd[c] = in ? D.d32[p] : 1.f;
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int p = pb + 32 * c;
+                if (p >= p1) break;
+                const size_t e = base + p;
+                const float vv = S.v[p];
+                const EntryEval r = eval_entry(D, S, p, arg, theta, irho);
+                const float yn = rho * (vv - r.z);
+                rp = fmaxf(rp, fabsf(yn - yo[c]) * irho);
+                rd = fmaxf(rd, rho * fabsf(r.z - zo[c]));
+                nx = fmaxf(nx, fabsf(vv - yo[c] * irho));
+                nz = fmaxf(nz, fabsf(r.z));
+                ny = fmaxf(ny, fabsf(yn));
+                bad |= !(isfinite(r.z) && isfinite(yn));
+                D.z[e] = r.z;
+                D.y[e] = yn;
+                store_X(D, e, (mu[c] + rho * r.z - yn) / (2.f * dd[c] + rho));
+            }
         }
     }
     rp = warp_max(rp); rd = warp_max(rd); nx = warp_max(nx); nz = warp_max(nz); ny = warp_max(ny);
     bad = warp_sum(bad);
-    __shared__ float s_red[5][32];
-    __shared__ int s_bad[32];
-    __shared__ int s_newj;
     if (lane == 0) {
-        s_red[0][warp] = rp; s_red[1][warp] = rd; s_red[2][warp] = nx; s_red[3][warp] = nz;
-        s_red[4][warp] = ny; s_bad[warp] = bad;
+        sh.red5[0][warp] = rp; sh.red5[1][warp] = rd; sh.red5[2][warp] = nx; sh.red5[3][warp] = nz;
+        sh.red5[4][warp] = ny; sh.red_bad[warp] = bad;
     }
     __syncthreads();
     if (tid == 0) {
         for (int w = 1; w < nwarps; ++w) {
-            rp = fmaxf(rp, s_red[0][w]); rd = fmaxf(rd, s_red[1][w]); nx = fmaxf(nx, s_red[2][w]);
-            nz = fmaxf(nz, s_red[3][w]); ny = fmaxf(ny, s_red[4][w]); bad += s_bad[w];
+            rp = fmaxf(rp, sh.red5[0][w]); rd = fmaxf(rd, sh.red5[1][w]); nx = fmaxf(nx, sh.red5[2][w]);
+            nz = fmaxf(nz, sh.red5[3][w]); ny = fmaxf(ny, sh.red5[4][w]); bad += sh.red_bad[w];
         }
-        int it = D.iters[a] + 1;
+        const int it = D.iters[a] + 1;
         D.iters[a] = it;
+        if (D.stats) atomicAdd(D.stats, 1ull);
         D.rp[a] = rp;
         D.rd[a] = rd;
         D.nu[a] = nu;
@@ -536,35 +572,109 @@ __global__ void __launch_bounds__(1024) k_prox(Dev D) {
             D.active[a] = 0;
             D.status[a] = PRISM_TIMEOUT;
         } else if (it % D.adapt_every == 0) {
-            float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
-            float du = rd / fmaxf(ny, 1e-12f);
-            float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
+            const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
+            const float du = rd / fmaxf(ny, 1e-12f);
+            const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
             int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
             dj = max(-4, min(4, dj));
             newj = max(0, min(NRHO - 1, j + dj));
         }
-        s_newj = newj;
+        sh.newj = newj;
     }
     __syncthreads();
-    const int newj = s_newj;
+    const int newj = sh.newj;
     for (int s = warp; s < D.S; s += nwarps)
         if (lane == 0) {
             D.eta_hi[a * D.S + s] = sh.eta_hi[s];
             D.eta_lo[a * D.S + s] = sh.eta_lo[s];
         }
-    if (newj != j && tid == 0) D.rho_idx[a] = newj;
-    // X for the next iteration with the (possibly new) penalty
-    const float rn = rho_val(newj);
-    for (int p = tid; p < D.N; p += blockDim.x) {
-        size_t e = base + p;
-        float X = (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn);
-        store_X(D, e, X);
+    if (newj != j) {
+        // the penalty changed: X again at the new penalty (this block wrote z and y above)
+        if (tid == 0) D.rho_idx[a] = newj;
+        const float rn = rho_val(newj);
+        for (int p = tid; p < D.N; p += blockDim.x) {
+            const size_t e = base + p;
+            store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+        }
     }
 }
 
+__global__ void __launch_bounds__(640, 1) k_prox(Dev D) {
+    const int a = blockIdx.x;
+    if (!D.active[a]) return;
+    __shared__ ProxShared sh;
+    const GlobalSrc S(D, (size_t)a * D.Npad);
+    prox_account(D, S, a, sh);
+}
+
+// per-entry data of one account staged in shared memory
+struct SmemSrc {
+    const float *v, *w0, *lo, *up, *c;
+    const int* pw;
+};
+
+__global__ void __launch_bounds__(640, 1) k_prox_smem(Dev D) {
+    const int a = blockIdx.x;
+    if (!D.active[a]) return;
+    __shared__ ProxShared sh;
+    extern __shared__ float4 dyn4[];
+    float* dyn = reinterpret_cast<float*>(dyn4);
+    const int NP = D.Npad;
+    float* sv = dyn;
+    float* sw0 = sv + NP;
+    float* slo = sw0 + NP;
+    float* sup = slo + NP;
+    float* sc = sup + NP;
+    int* spw = D.pw_idx ? reinterpret_cast<int*>(sc + NP) : nullptr;
+    const size_t base = (size_t)a * NP;
+    // one coalesced pass from global memory (Npad is a multiple of 64: float4-aligned)
+    const float4* gv = reinterpret_cast<const float4*>(D.v + base);
+    const float4* gw0 = reinterpret_cast<const float4*>(D.w0 + base);
+    const float4* glo = reinterpret_cast<const float4*>(D.lo + base);
+    const float4* gup = reinterpret_cast<const float4*>(D.up + base);
+    const float4* gc = reinterpret_cast<const float4*>(D.c + base);
+    for (int q0 = threadIdx.x; q0 < NP / 4; q0 += 2 * blockDim.x) {
+        const int q1 = q0 + blockDim.x;
+        const bool has1 = q1 < NP / 4;
+        const float4 a0 = gv[q0], b0 = gw0[q0], c0 = glo[q0], d0 = gup[q0], e0 = gc[q0];
+        float4 a1, b1, c1, d1, e1;
+        if (has1) { a1 = gv[q1]; b1 = gw0[q1]; c1 = glo[q1]; d1 = gup[q1]; e1 = gc[q1]; }
+        reinterpret_cast<float4*>(sv)[q0] = a0;
+        reinterpret_cast<float4*>(sw0)[q0] = b0;
+        reinterpret_cast<float4*>(slo)[q0] = c0;
+        reinterpret_cast<float4*>(sup)[q0] = d0;
+        reinterpret_cast<float4*>(sc)[q0] = e0;
+        if (has1) {
+            reinterpret_cast<float4*>(sv)[q1] = a1;
+            reinterpret_cast<float4*>(sw0)[q1] = b1;
+            reinterpret_cast<float4*>(slo)[q1] = c1;
+            reinterpret_cast<float4*>(sup)[q1] = d1;
+            reinterpret_cast<float4*>(sc)[q1] = e1;
+        }
+        if (spw) {
+            reinterpret_cast<int4*>(spw)[q0] = reinterpret_cast<const int4*>(D.pw_idx + base)[q0];
+            if (has1) reinterpret_cast<int4*>(spw)[q1] = reinterpret_cast<const int4*>(D.pw_idx + base)[q1];
+        }
+    }
+    __syncthreads();
+    const SmemSrc S{sv, sw0, slo, sup, sc, spw};
+    prox_account(D, S, a, sh);
+}
+
+size_t prox_smem_bytes(const Dev& D) {
+    return (size_t)D.Npad * 4 * (5 + (D.pw_idx ? 1 : 0));
+}
+
 void launch_prox(const Dev& D, cudaStream_t st) {
-    int nw = std::min(32, std::max(4, D.S));
-    k_prox<<<D.M, 32 * nw, 0, st>>>(D);
+    const int nw = std::min(20, std::max(4, D.S));      // at most 640 threads: warps loop over sectors
+    const size_t smem = prox_smem_bytes(D);
+    const size_t limit = 227 * 1024 - sizeof(ProxShared) - 1024;
+    if (smem <= limit) {
+        cudaFuncSetAttribute(k_prox_smem, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_prox_smem<<<D.M, 32 * nw, smem, st>>>(D);
+    } else {
+        k_prox<<<D.M, 32 * nw, 0, st>>>(D);
+    }
 }
 
 __global__ void k_count_active(Dev D) {

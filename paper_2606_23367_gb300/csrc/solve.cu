@@ -15,6 +15,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -389,6 +391,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
         D.nu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
         D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(2);
+        D.stats = A.take<unsigned long long>(4);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
@@ -599,6 +602,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.Qhi, 0, (size_t)M * KMAX * 2, st);
         cudaMemsetAsync(D.Qlo, 0, (size_t)M * KMAX * 2, st);
         cudaMemsetAsync(D.n_active, 0, 8, st);
+        cudaMemsetAsync(D.stats, 0, 32, st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
         k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
@@ -673,6 +677,14 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_mark_timeout(D, st); });   // accounts still iterating
     cudaEventRecord(SC.ev[2], st);
+    if (std::getenv("PRISM_DEBUG_STATS")) {
+        unsigned long long h[4] = {0, 0, 0, 0};
+        cudaMemcpyAsync(h, D.stats, 32, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        std::fprintf(stderr, "prism stats: ADMM iterations %d, prox account-calls %llu, sector-edge evals/call %.2f, "
+                     "budget evals/call %.2f\n", total_iters, h[0], h[0] ? double(h[1]) / h[0] : 0.0,
+                     h[0] ? double(h[2]) / h[0] : 0.0);
+    }
     // ---- polish, with up to two returns to the iterations at a tighter target
     const int rounds = std::max(1, o->polish_rounds);
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });

@@ -63,6 +63,7 @@ struct Dev {
     int adapt_every = 25;
     bool bf16 = false;                  // X / Q split in BF16 for tensor-core products
     int raw_out = 0;                    // diagnostics: G4 writes B Q itself into v
+    unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
 };
 
 // launchers (admm.cu)

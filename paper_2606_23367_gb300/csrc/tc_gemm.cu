@@ -337,17 +337,27 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
     for (int c = 0; c < G4_TN / 16; ++c) {
         if (have) tmem_ld16(lane_addr + c * 16, bq);
         if (!row_ok) continue;
+        const int m0 = mt * G4_TN + c * 16;
+        const int ncol = min(16, D.M - m0);
+        if (ncol <= 0) continue;
+        // issue the chunk's loads before any store (z, y and v never alias, but the
+        // compiler cannot know): 32 independent loads in flight per thread
+        float zz[16], yy[16];
 #pragma unroll
         for (int j = 0; j < 16; ++j) {
-            const int col = c * 16 + j;
-            const int m = mt * G4_TN + col;
-            if (m >= D.M) break;
-            const size_t e = (size_t)m * D.Npad + i;
+            const size_t e = (size_t)(m0 + j) * D.Npad + i;
+            zz[j] = (j < ncol) ? __ldg(D.z + e) : 0.f;
+            yy[j] = (j < ncol) ? __ldg(D.y + e) : 0.f;
+        }
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (j >= ncol) break;
+            const size_t e = (size_t)(m0 + j) * D.Npad + i;
             if (D.raw_out) { D.v[e] = bq[j]; continue; }
+            const int col = c * 16 + j;
             const float rho = s.rho[col];
-            const float z = D.z[e], y = D.y[e];
-            const float x = (mu + rho * z - y - bq[j]) / (dd + rho);
-            D.v[e] = D.alpha * x + (1.f - D.alpha) * z + y * s.irho[col];
+            const float x = (mu + rho * zz[j] - yy[j] - bq[j]) / (dd + rho);
+            D.v[e] = D.alpha * x + (1.f - D.alpha) * zz[j] + yy[j] * s.irho[col];
         }
     }
     fence_before_sync();
