@@ -39,6 +39,21 @@ M_ACCOUNTS = 500
 ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40}
 
 
+def shard_first_account(rank: int, per_rank: int = M_ACCOUNTS) -> int:
+    """First account id of a rank's book: ranks solve disjoint blocks of accounts."""
+    return rank * per_rank
+
+
+def reduce_over_ranks(dist, value: float, op: str, device) -> float:
+    """max or sum of a per-rank scalar (host logic of the weak-scaling report)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws > 1:
@@ -176,7 +191,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     build.build()
     prism.load_library()
     precision = {"bf16": prism.PRISM_BATCHED_BF16, "fp32": prism.PRISM_BATCHED_FP32}[args.precision]
-    uni, batch = make_workload(1, first_account=rank * M_ACCOUNTS, M=M_ACCOUNTS)
+    uni, batch = make_workload(1, first_account=shard_first_account(rank), M=M_ACCOUNTS)
     M, S = batch.n_accounts, uni.n_sectors
     nnz = int(batch.offsets[-1])
     dev = torch.device("cuda", local_rank)
@@ -236,18 +251,10 @@ def run_gpu(args, dist, rank, world, local_rank):
         return e0.elapsed_time(e1), cert, launches
 
     def max_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "max", dev)
 
     def sum_over_ranks(x):
-        if dist is None:
-            return x
-        t = torch.tensor([x], dtype=torch.float64, device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.SUM)
-        return float(t.item())
+        return reduce_over_ranks(dist, x, "sum", dev)
 
     # ---- device-resident lane (the clock sampler starts before the warm-up so that
     # its start-up does not overlap the timed region)

@@ -3,7 +3,7 @@
  *
  * The library solves a book of account rebalancing problems in one call. Each
  * account a is the convex program of Eq. 1 (Sec. 4.2) as the workloads use it,
- * with the objective scaled as in the Sec. 8 display (Q = 2 Sigma, eta = 1):
+ * with the objective scaled as in the Sec. 9 display (Q = 2 Sigma, eta = 1):
  *
  *   minimise   w' Sigma w - mu' w + sum_i phi_i(w_i)
  *   subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,
@@ -16,7 +16,7 @@
  *
  * The boundary follows the paper's public solver call (Fig. 2, Sec. 4.3):
  * problem data in; weights, per-account status codes (Table "Status
- * vocabulary", Sec. 9), timings, memory class and the feasibility / KKT
+ * vocabulary", Sec. 10.2), timings, memory class and the feasibility / KKT
  * diagnostics of Sec. 4.4 out.
  *
  * Conventions for every entry point
@@ -46,7 +46,7 @@ extern "C" {
 #define PRISM_ERR_ALLOCATION   (-3)   /* device or host allocation failed */
 #define PRISM_ERR_UNSUPPORTED  (-4)   /* option combination not implemented */
 
-/* ---- per-account status codes (Table "Status vocabulary", Sec. 9) ----- */
+/* ---- per-account status codes (Table "Status vocabulary", Sec. 10.2) ----- */
 #define PRISM_CERTIFIED              0  /* weights returned, all external checks pass */
 #define PRISM_FEASIBLE_NONCERTIFIED  1  /* feasibility passes, KKT certification does not */
 #define PRISM_TIMEOUT                2  /* iteration cap or time budget reached first */
@@ -210,8 +210,8 @@ int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double*
  * iters is set to 0; timings other than t_call_ms are 0).
  *
  * It calls no cudaMalloc / cudaFree and no allocating library routine: all
- * device scratch comes from one static __device__ array of about 16 MB that
- * every GPU loading the library holds until the process exits. Limits
+ * device scratch comes from one static __device__ array that
+ * every GPU loading the library holds until the process exits (about 17 MB). Limits
  * (PRISM_ERR_ARGUMENT beyond them): n_accounts <= 32, n_accounts x (universe
  * width rounded up to 64) <= 131072, no tax lots (PRISM_ERR_UNSUPPORTED); an
  * account with more than 512 free weights falls back to the given weights

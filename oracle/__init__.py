@@ -17,7 +17,7 @@ Contents
                returns the unique minimiser of each account's problem
 
 Problem (Eq. 1, Sec. 4.2, with Q = 2 Sigma, w_b = 0, eta = 1, R = 0, no G rows,
-D_a = I, A = sector incidence; objective scaling as in the Sec. 8 display):
+D_a = I, A = sector incidence; objective scaling as in the Sec. 9 display):
 
     minimise   w' Sigma w - mu' w + sum_i phi_i(w_i)
     subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,

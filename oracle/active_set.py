@@ -1,7 +1,7 @@
 """The FP64 oracle: a primal active-set method for one account (CPU, numpy).
 
 Each account of a book is the convex program of Eq. 1 (Sec. 4.2) as the
-workloads instantiate it (objective scaled as in the Sec. 8 display):
+workloads instantiate it (objective scaled as in the Sec. 9 display):
 
     minimise   f(w) = w' Sigma w - mu' w + sum_i phi_i(w_i)
     subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,

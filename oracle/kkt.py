@@ -22,7 +22,7 @@ with the bound multipliers implicit in the normal cone N. A weight within
     r_comp = max over bands and the cap of |multiplier| * |slack|, plus any
              multiplier of the wrong sign.
 
-Objective (Sec. 8 display, Eq. 1 with Q = 2 Sigma): f(w) = w'Sigma w - mu'w + sum_i phi_i(w_i).
+Objective (Sec. 9 display, Eq. 1 with Q = 2 Sigma): f(w) = w'Sigma w - mu'w + sum_i phi_i(w_i).
 Quality gates (Sec. 5.5): budget <= 1e-4 and bound <= 1e-6 in the paper; the
 workloads here hold every residual to 1e-6.
 """

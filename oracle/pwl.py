@@ -3,9 +3,9 @@
 Eq. 1 (Sec. 4.2) charges a transaction-cost term C(dw) and a tax-aware
 transition term T_tax(dw; D_a). The workloads use
 
-  * an L1 cost c_i |w - w0_i| (Sec. 8 display, gamma ||w - w0||_1), and
+  * an L1 cost c_i |w - w0_i| (Sec. 9 display, gamma ||w - w0||_1), and
   * for tax-aware accounts a convex lot model. The paper leaves discrete lot
-    logic out of its benchmark (Sec. 4.2 scope notes, Sec. 8); the convex
+    logic out of its benchmark (Sec. 4.2 scope notes, Sec. 9); the convex
     reading used here is the partial minimum of the lot LP: selling S units
     cheapest-first costs K(S) = sum of kappa over the units sold, every unit
     traded costs c, and the sale may exceed the net reduction (sell and buy

@@ -24,7 +24,10 @@
 #include <cfloat>
 #include <cmath>
 
+#include <cstring>
+
 #include "common.cuh"
+#include "polish.h"
 #include "solver.h"
 
 namespace prism {
@@ -78,9 +81,19 @@ int choose_nsplit(int M, int N) {
     return ns;
 }
 
+__device__ __forceinline__ bool tile_active(const Dev& D, int m0, int count) {
+    int act = 0;
+    if (threadIdx.x < count) {
+        const int m = m0 + threadIdx.x;
+        act = (D.active == nullptr) || (m < D.M && D.active[m]);
+    }
+    return __syncthreads_or(act) != 0;
+}
+
 __global__ void __launch_bounds__(256) k_gemm_P(Dev D) {
     const int m0 = blockIdx.x * 32;
     const int split = blockIdx.y;
+    if (!tile_active(D, m0, 32)) return;
     const int chunk = cdiv(cdiv(D.N, D.nsplit), 32) * 32;
     const int i_begin = split * chunk, i_end = min(D.N, i_begin + chunk);
     __shared__ float sX[32][33];
@@ -135,19 +148,27 @@ void launch_gemm_P(const Dev& D, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 __global__ void k_small_solve(Dev D) {
     const int m = blockIdx.x;
+    if (D.active && !D.active[m]) return;
     const int K = D.K;
     __shared__ float sP[KMAX];
     const int t = threadIdx.x;
     if (t < K) {
-        float s = 0.f;
-        for (int sp = 0; sp < D.nsplit; ++sp) s += D.Ppart[((size_t)sp * D.M + m) * K + t];
-        sP[t] = s;
+        float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+        const float* pp = D.Ppart + (size_t)m * K + t;
+        const size_t stride = (size_t)D.M * K;
+        int sp = 0;
+        for (; sp + 8 <= D.nsplit; sp += 8)
+#pragma unroll
+            for (int u = 0; u < 8; ++u) acc[u] += pp[(size_t)(sp + u) * stride];
+        for (; sp < D.nsplit; ++sp) acc[0] += pp[(size_t)sp * stride];
+        sP[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
     }
     __syncthreads();
     if (t < K) {
-        const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + (size_t)t * K;
+        // C^{-1} is symmetric: read column t so that the block's loads are contiguous
+        const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;
         float q = 0.f;
-        for (int j = 0; j < K; ++j) q = fmaf(C[j], sP[j], q);
+        for (int j = 0; j < K; ++j) q = fmaf(C[(size_t)j * K], sP[j], q);
         if (D.bf16) {
             __nv_bfloat16 h = __float2bfloat16_rn(q);
             D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
@@ -170,6 +191,7 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
     const int m0 = blockIdx.y * 32;
     const int i0 = blockIdx.x * 64;
     const int K = D.K;
+    if (!tile_active(D, m0, 32)) return;
     __shared__ float sQ[32][KMAX + 1];
     __shared__ float sB[64][KMAX + 1];
     const int t = threadIdx.x;
@@ -197,6 +219,18 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
             acc[u][1] = fmaf(q, b1, acc[u][1]);
         }
     }
+    if (D.raw_out) {          // the plain product (diagnostics, polish gradient)
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int m = m0 + grp * 4 + u;
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int i = i0 + lane + 32 * h;
+                if (m < D.M && i < D.N) D.v[(size_t)m * D.Npad + i] = acc[u][h];
+            }
+        }
+        return;
+    }
     // epilogue: all loads of the thread's 8 outputs first, then the stores
     float zz[4][2], yy[4][2];
 #pragma unroll
@@ -222,7 +256,6 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
             const int i = i0 + lane + 32 * h;
             if (i >= D.N) continue;
             const size_t e = (size_t)m * D.Npad + i;
-            if (D.raw_out) { D.v[e] = acc[u][h]; continue; }
             const float x = (D.mu32[i] + rho * zz[u][h] - yy[u][h] - acc[u][h]) / (2.f * D.d32[i] + rho);
             D.v[e] = D.alpha * x + (1.f - D.alpha) * zz[u][h] + yy[u][h] * irho;
         }
@@ -232,6 +265,19 @@ __global__ void __launch_bounds__(256) k_gemm_x(Dev D) {
 void launch_gemm_x(const Dev& D, cudaStream_t st) {
     dim3 grid(cdiv(D.N, 64), cdiv(D.M, 32));
     k_gemm_x<<<grid, 256, 0, st>>>(D);
+}
+
+// G[m][i] = sum_k B[i][k] fh[m][k] in FP32 for every account: the polish's gradient
+// filter, on the SIMT x-update product kernel in its plain-output form.
+void launch_gradient_product(const PolDev& P, cudaStream_t st) {
+    Dev D;
+    std::memset((void*)&D, 0, sizeof(Dev));
+    D.M = P.M; D.N = P.N; D.Npad = P.Npad; D.K = P.K; D.S = P.S;
+    D.B32 = P.B32;
+    D.Q = P.fh32;
+    D.v = P.G32;
+    D.raw_out = 1;
+    launch_gemm_x(D, st);
 }
 
 // ---------------------------------------------------------------------------

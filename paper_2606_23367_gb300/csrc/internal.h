@@ -41,6 +41,7 @@ struct Universe {
     double* d_f64 = nullptr;       // K
     double* d_d64 = nullptr;       // Npad (1 in padding)
     double* d_mu64 = nullptr;      // Npad (0 in padding)
+    double* d_Bn1 = nullptr;       // Npad: sum_k |B_ik|
     float* d_B32 = nullptr;        // Npad x K
     float* d_f32 = nullptr;        // K
     float* d_d32 = nullptr;        // Npad

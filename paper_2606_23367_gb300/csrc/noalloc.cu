@@ -45,6 +45,12 @@ constexpr size_t NA_BYTES =
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * 4) * 2 +    // free / nonzero lists
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * 8) +        // cap signs of free entries
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * (PMAXROWS + 1) * 8) +   // Woodbury columns
+    na_round(NA_MAX_ENTRIES * 4) +                           // FP32 gradient product
+    na_round((size_t)NA_MAX_ACCOUNTS * KMAX * 8) +           // f .* h (FP64)
+    na_round((size_t)NA_MAX_ACCOUNTS * KMAX * 4) +           // f .* h (FP32)
+    na_round(NA_MAX_ACCOUNTS * 8) * 2 +                      // quad, fhmax
+    na_round(NA_MAX_ACCOUNTS * 4) +                          // ndep
+    na_round(16) +                                           // pending counter
     na_round(16);                                            // error flags
 
 // The scratch: resident on every GPU that loads the library, until the process exits.
@@ -247,6 +253,13 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     int* Fl = cv.take<int>((size_t)M * FMAX); int* NZl = cv.take<int>((size_t)M * FMAX);
     double* Fsig = cv.take<double>((size_t)M * FMAX);
     double* Y = cv.take<double>((size_t)M * FMAX * (PMAXROWS + 1));
+    float* G32 = cv.take<float>(MN);
+    double* fh64 = cv.take<double>((size_t)M * KMAX);
+    float* fh32 = cv.take<float>((size_t)M * K);
+    double* quad = cv.take<double>(M);
+    double* fhmax = cv.take<double>(M);
+    int* ndep = cv.take<int>(M);
+    int* pending = cv.take<int>(4);
     int* err = cv.take<int>(4);
     if (cv.overflow) return na_fail(PRISM_ERR_ARGUMENT, "prism_polish_noalloc: request exceeds the static scratch");
     // stage the inputs (host pointers are copied into the scratch, device pointers used in place)
@@ -291,6 +304,8 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     PolDev P;
     P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;
     P.B64 = U.d_B64; P.f64 = U.d_f64; P.d64 = U.d_d64; P.mu64 = U.d_mu64;
+    P.B32 = U.d_B32; P.Bn1 = U.d_Bn1;
+    P.G32 = G32; P.fh64 = fh64; P.fh32 = fh32; P.quad = quad; P.fhmax = fhmax; P.ndep = ndep; P.pending = pending;
     P.sec_start = U.d_sec_start; P.sector = U.d_sector;
     P.w0 = W0; P.lo = LO; P.up = UP; P.c = Cc;
     P.band_lo = blo; P.band_hi = bhi; P.tau = tau;
@@ -327,8 +342,8 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     for (double& x : res->t_phase_ms) x = 0.0;
     for (double& x : res->kernel_ms) x = 0.0;
     for (int64_t& x : res->kernel_launches) x = 0;
-    // fill (no cap given), pack, rows, classify, rounds, fallback (2), status, unpack
-    res->n_launches = (b->turnover_cap ? 0 : 1) + (nnz > 0 ? 2 : 0) + 1 + 1 + rounds + 2 + 1;
+    // fill (no cap given), pack, rows, classify, 3 kernels per round, fallback (2), status, unpack
+    res->n_launches = (b->turnover_cap ? 0 : 1) + (nnz > 0 ? 2 : 0) + 1 + 1 + 3 * rounds + 2 + 1;
     res->device_bytes = (int64_t)NA_BYTES;
     res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     set_error("");

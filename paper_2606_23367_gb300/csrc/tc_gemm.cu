@@ -180,6 +180,12 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     const int i0 = split * chunk, i1 = min(D.N, i0 + chunk);
     const int nk = (i1 > i0) ? (i1 - i0 + TK - 1) / TK : 0;
     constexpr uint32_t IDESC = idesc_bf16(TM, KP);
+    {
+        // a tile whose accounts have all stopped iterating has nothing to compute
+        const int m = mt * TM + tid;
+        const int act = (D.active == nullptr) || (m < D.M && D.active[m]);
+        if (!__syncthreads_or(act)) return;
+    }
     if (warp == 0) tmem_alloc(&s.tmem, 64);
     if (tid == 0) {
         for (int q = 0; q < G2_STAGES; ++q) {
@@ -285,6 +291,11 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int at = blockIdx.x, mt = blockIdx.y;
     constexpr uint32_t IDESC = idesc_bf16(TM, G4_TN);
+    {
+        const int m = mt * G4_TN + tid;
+        const int act = (D.active == nullptr) || (m < D.M && D.active[m]);
+        if (!__syncthreads_or(act)) return;
+    }
     if (warp == 0) tmem_alloc(&s.tmem, G4_TN);
     if (tid == 0) {
         mbar_init(&s.full, 1);

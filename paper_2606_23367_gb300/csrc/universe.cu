@@ -151,7 +151,7 @@ static int fetch(const T* src, size_t n, std::vector<T>& dst) {
 }
 
 static void free_universe(Universe& U) {
-    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64,
+    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1,
                     U.d_mu64, U.d_B32, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
                     U.d_Cinv32, U.d_Cinv16};
     for (void* p : ptrs)
@@ -237,6 +237,9 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         secs[p] = sec[i];
     }
     std::vector<float> f32(f.begin(), f.end()), d32(ds.begin(), ds.end()), mu32(mus.begin(), mus.end());
+    std::vector<double> bn1(Npad, 0.0);
+    for (int p = 0; p < N; ++p)
+        for (int k = 0; k < K; ++k) bn1[p] += std::fabs(Bs[(size_t)p * K + k]);
     cudaError_t se = cudaStreamCreateWithFlags(&U.stream, cudaStreamNonBlocking);
     if (se != cudaSuccess) { set_error(cudaGetErrorString(se)); return PRISM_ERR_CUDA; }
     TRY(dalloc(U, &U.d_inv_perm, N));
@@ -247,6 +250,7 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     TRY(dalloc(U, &U.d_f64, K));
     TRY(dalloc(U, &U.d_d64, Npad));
     TRY(dalloc(U, &U.d_mu64, Npad));
+    TRY(dalloc(U, &U.d_Bn1, Npad));
     TRY(dalloc(U, &U.d_B32, (size_t)Npad * K));
     TRY(dalloc(U, &U.d_f32, K));
     TRY(dalloc(U, &U.d_d32, Npad));
@@ -268,6 +272,7 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         H2D(U.d_f64, f.data(), K * sizeof(double)) ||
         H2D(U.d_d64, ds.data(), Npad * sizeof(double)) ||
         H2D(U.d_mu64, mus.data(), Npad * sizeof(double)) ||
+        H2D(U.d_Bn1, bn1.data(), Npad * sizeof(double)) ||
         H2D(U.d_f32, f32.data(), K * sizeof(float)) ||
         H2D(U.d_d32, d32.data(), Npad * sizeof(float)) ||
         H2D(U.d_mu32, mu32.data(), Npad * sizeof(float))) {

@@ -12,7 +12,7 @@ w0, optionally convex tax-lot transition penalties, restriction caps
 (u <= w0) and a turnover cap ||w - w0||_1 <= tau.
 
 The paper's own instances (S&P 500 prices, its real-calibrated extension
-and the E5 queue accounts, Sec. 6.5 and Sec. 8) are not available; these
+and the E5 queue accounts; Sec. 9 and Sec. 8) are not available; these
 seeded draws stand in for them with the shapes the workloads name:
 
   id  workload                                   N       K   M

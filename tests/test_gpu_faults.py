@@ -1,6 +1,6 @@
 """Failure vocabulary on the GPU without any device fault: bad inputs are rejected on the
 host, infeasible accounts and iteration caps map to the paper's statuses (Table
-"Status vocabulary", Sec. 9)."""
+"Status vocabulary", Sec. 10.2)."""
 import numpy as np
 import pytest
 
