@@ -27,7 +27,6 @@
 #include <cstring>
 
 #include "common.cuh"
-#include "polish.h"
 #include "solver.h"
 
 namespace prism {
@@ -267,18 +266,7 @@ void launch_gemm_x(const Dev& D, cudaStream_t st) {
     k_gemm_x<<<grid, 256, 0, st>>>(D);
 }
 
-// G[m][i] = sum_k B[i][k] fh[m][k] in FP32 for every account: the polish's gradient
-// filter, on the SIMT x-update product kernel in its plain-output form.
-void launch_gradient_product(const PolDev& P, cudaStream_t st) {
-    Dev D;
-    std::memset((void*)&D, 0, sizeof(Dev));
-    D.M = P.M; D.N = P.N; D.Npad = P.Npad; D.K = P.K; D.S = P.S;
-    D.B32 = P.B32;
-    D.Q = P.fh32;
-    D.v = P.G32;
-    D.raw_out = 1;
-    launch_gemm_x(D, st);
-}
+
 
 // ---------------------------------------------------------------------------
 // G5/G6: projection onto Z with the transition prox, dual update, residuals,

@@ -42,7 +42,9 @@ struct Universe {
     double* d_d64 = nullptr;       // Npad (1 in padding)
     double* d_mu64 = nullptr;      // Npad (0 in padding)
     double* d_Bn1 = nullptr;       // Npad: sum_k |B_ik|
+    float* d_Bn1f = nullptr;       // Npad: its FP32 copy
     float* d_B32 = nullptr;        // Npad x K
+    float* d_B32p = nullptr;       // Npad x 64 (factors zero-padded to 64, rows 256-byte aligned)
     float* d_f32 = nullptr;        // K
     float* d_d32 = nullptr;        // Npad
     float* d_mu32 = nullptr;       // Npad

@@ -33,6 +33,7 @@ constexpr size_t na_round(size_t n) { return (n + 255) / 256 * 256; }
 constexpr size_t NA_BYTES =
     na_round(NA_MAX_ENTRIES * 8) * 5 +                       // w0, lo, up, c, W (FP64, sorted layout)
     na_round(NA_MAX_ENTRIES * 4) * 2 +                       // z (FP32), member flags
+    na_round(NA_MAX_ENTRIES * 4) * 4 +                       // FP32 copies of w0, lo, up, c
     na_round(NA_MAX_ENTRIES) +                               // entry states
     na_round(NA_MAX_ENTRIES * 8) * 6 +                       // staged ragged w0, lo, up, tc, w_in, w_out
     na_round(NA_MAX_ENTRIES * 4) +                           // staged asset_idx
@@ -45,7 +46,7 @@ constexpr size_t NA_BYTES =
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * 4) * 2 +    // free / nonzero lists
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * 8) +        // cap signs of free entries
     na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * (PMAXROWS + 1) * 8) +   // Woodbury columns
-    na_round(NA_MAX_ENTRIES * 4) +                           // FP32 gradient product
+    na_round((size_t)NA_MAX_ACCOUNTS * NA_FMAX * 8) +        // 1/d of free entries
     na_round((size_t)NA_MAX_ACCOUNTS * KMAX * 8) +           // f .* h (FP64)
     na_round((size_t)NA_MAX_ACCOUNTS * KMAX * 4) +           // f .* h (FP32)
     na_round(NA_MAX_ACCOUNTS * 8) * 2 +                      // quad, fhmax
@@ -67,6 +68,7 @@ struct NaPack {
     const double *w0, *lo, *up, *tc, *w_in;
     const int* inv_perm;
     double *W0, *LO, *UP, *C;
+    float *W0f, *LOf, *UPf, *Cf;
     float* Z;
     int* member;
     int* err;
@@ -91,6 +93,7 @@ __global__ void k_na_pack(NaPack A) {
     const size_t d = (size_t)a * A.Npad + A.inv_perm[i];
     if (atomicExch(&A.member[d], 1) != 0) { atomicOr(A.err, 4); return; }
     A.W0[d] = w0; A.LO[d] = l; A.UP[d] = u; A.C[d] = c;
+    A.W0f[d] = float(w0); A.LOf[d] = float(l); A.UPf[d] = float(u); A.Cf[d] = float(c);
     A.Z[d] = float(w);
 }
 
@@ -233,6 +236,8 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     double* UP = cv.take<double>(MN); double* Cc = cv.take<double>(MN);
     double* W = cv.take<double>(MN);
     float* Z = cv.take<float>(MN);
+    float* W0f = cv.take<float>(MN); float* LOf = cv.take<float>(MN);
+    float* UPf = cv.take<float>(MN); float* Cf = cv.take<float>(MN);
     int* member = cv.take<int>(MN);
     int8_t* stt = cv.take<int8_t>(MN);
     double* s_w0 = cv.take<double>(nnz); double* s_lo = cv.take<double>(nnz);
@@ -253,7 +258,7 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     int* Fl = cv.take<int>((size_t)M * FMAX); int* NZl = cv.take<int>((size_t)M * FMAX);
     double* Fsig = cv.take<double>((size_t)M * FMAX);
     double* Y = cv.take<double>((size_t)M * FMAX * (PMAXROWS + 1));
-    float* G32 = cv.take<float>(MN);
+    double* Fdinv = cv.take<double>((size_t)M * FMAX);
     double* fh64 = cv.take<double>((size_t)M * KMAX);
     float* fh32 = cv.take<float>((size_t)M * K);
     double* quad = cv.take<double>(M);
@@ -280,10 +285,13 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     A.w_in = (const double*)stage(w_in, s_win, nnz * 8);
     A.inv_perm = U.d_inv_perm;
     A.W0 = W0; A.LO = LO; A.UP = UP; A.C = Cc; A.Z = Z; A.member = member; A.err = err;
+    A.W0f = W0f; A.LOf = LOf; A.UPf = UPf; A.Cf = Cf;
     // the array keeps the previous call's contents: clear everything read before written
     cudaMemsetAsync(W0, 0, MN * 8, st); cudaMemsetAsync(LO, 0, MN * 8, st);
     cudaMemsetAsync(UP, 0, MN * 8, st); cudaMemsetAsync(Cc, 0, MN * 8, st);
     cudaMemsetAsync(W, 0, MN * 8, st); cudaMemsetAsync(Z, 0, MN * 4, st);
+    cudaMemsetAsync(W0f, 0, MN * 4, st); cudaMemsetAsync(LOf, 0, MN * 4, st);
+    cudaMemsetAsync(UPf, 0, MN * 4, st); cudaMemsetAsync(Cf, 0, MN * 4, st);
     cudaMemsetAsync(member, 0, MN * 4, st); cudaMemsetAsync(err, 0, 16, st);
     cudaMemsetAsync(done, 0, M * 4, st); cudaMemsetAsync(skip, 0, M * 4, st);
     cudaMemsetAsync(status, 0, M * 4, st); cudaMemsetAsync(iters, 0, M * 4, st);
@@ -304,8 +312,9 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     PolDev P;
     P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;
     P.B64 = U.d_B64; P.f64 = U.d_f64; P.d64 = U.d_d64; P.mu64 = U.d_mu64;
-    P.B32 = U.d_B32; P.Bn1 = U.d_Bn1;
-    P.G32 = G32; P.fh64 = fh64; P.fh32 = fh32; P.quad = quad; P.fhmax = fhmax; P.ndep = ndep; P.pending = pending;
+    P.B32 = U.d_B32; P.B32p = U.d_B32p; P.Bn1 = U.d_Bn1; P.Bn1f = U.d_Bn1f; P.mu32 = U.d_mu32;
+    P.w0f = W0f; P.lof = LOf; P.upf = UPf; P.cf = Cf;
+    P.Fdinv = Fdinv; P.fh64 = fh64; P.fh32 = fh32; P.quad = quad; P.fhmax = fhmax; P.ndep = ndep; P.pending = pending;
     P.sec_start = U.d_sec_start; P.sector = U.d_sector;
     P.w0 = W0; P.lo = LO; P.up = UP; P.c = Cc;
     P.band_lo = blo; P.band_hi = bhi; P.tau = tau;
@@ -315,7 +324,7 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     P.W = W; P.nu = nu; P.lam = lam; P.theta = theta; P.diag = diag; P.status = status;
     launch_classify(P, st);
     const int rounds = std::max(1, o.polish_rounds);
-    for (int r = 0; r < rounds; ++r) launch_polish_round(P, st);
+    launch_polish(P, rounds, st);
     launch_fallback(P, st);
     launch_finish_status(P, o.eps_kkt, st);
     const bool w_dev = na_is_dev(res->w);
@@ -342,8 +351,8 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     for (double& x : res->t_phase_ms) x = 0.0;
     for (double& x : res->kernel_ms) x = 0.0;
     for (int64_t& x : res->kernel_launches) x = 0;
-    // fill (no cap given), pack, rows, classify, 3 kernels per round, fallback (2), status, unpack
-    res->n_launches = (b->turnover_cap ? 0 : 1) + (nnz > 0 ? 2 : 0) + 1 + 1 + 3 * rounds + 2 + 1;
+    // fill (no cap given), pack, rows, classify, polish, fallback (2), status, unpack
+    res->n_launches = (b->turnover_cap ? 0 : 1) + (nnz > 0 ? 2 : 0) + 1 + 1 + 1 + 2 + 1;
     res->device_bytes = (int64_t)NA_BYTES;
     res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     set_error("");

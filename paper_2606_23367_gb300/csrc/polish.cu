@@ -68,7 +68,6 @@ __device__ __forceinline__ void entry_pieces(const PolDev& P, size_t e, Pieces& 
 // independent loads in flight (the int8 state stores would otherwise order them).
 struct EntryRaw {
     double w0, lo, up, c, W, d, mu, bn1;
-    float g32;
     int code, sec, pw;
 };
 
@@ -76,7 +75,6 @@ __device__ __forceinline__ void load_raw(const PolDev& P, size_t base, int p, En
     const size_t e = base + p;
     r.w0 = P.w0[e]; r.lo = P.lo[e]; r.up = P.up[e]; r.c = P.c[e];
     r.W = P.W[e]; r.d = P.d64[p]; r.mu = P.mu64[p]; r.bn1 = P.Bn1[p];
-    r.g32 = P.G32[e];
     r.code = P.st[e];
     r.sec = P.sector[p];
     r.pw = P.pw_idx ? P.pw_idx[e] : -1;
@@ -153,23 +151,60 @@ __global__ void __launch_bounds__(PB) k_classify(PolDev P) {
 }
 
 // ---------------------------------------------------------------------------
-// P1: the FP64 equality-constrained solve on the current working set
-// (one block per account still running)
+// The polish: one block per account runs all of its active-set rounds.
+//
+// Each round (a) compacts the free set, (b) solves the equality-constrained QP on it,
+// (c) checks every KKT condition and switches the violators. The solve factors the
+// Woodbury capacitance and the Schur complement in FP32 and then applies FP64
+// iterative refinement to the full reduced KKT system
+//     [2 Sigma_FF  E_F'] [w_F]   [g0]
+//     [E_F         0   ] [lam] = [e ]
+// (FP64 residuals, FP32 corrections), which converges to FP64 accuracy because the
+// system's condition number times the FP32 unit roundoff is far below one. GB300
+// runs FP64 at 1/64 of its FP32 rate, so this keeps the O(|F| K^2 + K^3) work in
+// FP32 and only O(|F| K) per refinement step in FP64.
 // ---------------------------------------------------------------------------
-constexpr int BCH = 64;   // rows of B_F staged in shared memory at a time
+constexpr int FS = 64;                    // free entries whose data live in shared memory
+constexpr int COL_W = PMAXROWS - 1;       // column of Y holding w_F (FP64)
+constexpr int COL_R = PMAXROWS;           // column of Y holding the refinement workspace
+constexpr int MAXWROWS = PMAXROWS - 2;    // working rows this kernel accepts
+constexpr int IR_STEPS = 6;
+constexpr int YS = PMAXROWS + 1;          // row stride of Y
+constexpr int AU = 4;                     // entries per lane whose loads are batched in the scans
 
-struct SolveShared {
-    double C[KMAX][KMAX + 1];          // capacitance, then its Cholesky factor (lower)
-    double Bc[BCH][KMAX + 1];          // staged rows of B_F
-    double dinv[BCH];
-    double T[KMAX][PMAXROWS + 1];
-    double hA[KMAX], fhA[KMAX];
-    double Sm[PMAXROWS][PMAXROWS + 1];
-    double erhs[PMAXROWS], lam[PMAXROWS];
+struct PolishShared {
+    float C[KMAX][KMAX + 1];              // FP32 capacitance, then its Cholesky factor
+    float Bc[FS][KMAX + 1];               // FP32 rows of B of the first FS free entries
+    double Bd[FS][KMAX + 1];              // FP64 rows of B of the first FS free entries
+    double Ys[FS][YS];                    // Y rows of the first FS free entries
+    double dinv_s[FS], sig_s[FS];
+    float dinvf_s[FS];
+    int Fl_s[FS];
+    float Ldinv[KMAX];                    // reciprocal of the Cholesky diagonal
+    float T[KMAX][PMAXROWS + 1];          // FP32 Woodbury workspace
+    double Sf[PMAXROWS][PMAXROWS + 1];    // Schur matrix after pivoted elimination
+    double hA[KMAX], fhA[KMAX], fh[KMAX], t64[KMAX];
+    alignas(16) float fh32[KMAX];
+    double erhs[PMAXROWS], lam[PMAXROWS], rr2[PMAXROWS], dlam[PMAXROWS];
+    int order[PMAXROWS], used[PMAXROWS];
     int rows[PMAXROWS];
-    int nrows, nF, nNZ, fail, ndep;
-    int cntF[PB], cntN[PB];
-    double sumA[PB], capA[PB];
+    int nrows, nF, nNZ, fail, nc, go;
+    int cntF[PB / 32], cntN[PB / 32];
+    double sumA[PB / 32], capA[PB / 32];
+    double lam_s[SMAX];
+    double red[PB / 32][8];
+    double secsum[SMAX];
+    double mmin[PB / 32];
+    int mwho[PB / 32];
+};
+
+// the free-set data of one account: shared memory when |F| <= FS, else global scratch
+struct FreeSet {
+    int* Fl;            // entry of each free index
+    double* Y;          // rows of YS doubles
+    double* dinv;
+    double* sig;
+    bool in_smem;
 };
 
 // coefficient of free entry p (cap sign sig) in working row ``row``
@@ -179,502 +214,615 @@ __device__ __forceinline__ double row_coef(const PolDev& P, int row, int p, doub
     return sig;                                               // cap
 }
 
-__global__ void __launch_bounds__(PB) k_pol_solve(PolDev P) {
+__device__ __forceinline__ float brow32(const PolDev& P, const PolishShared& sh, const FreeSet& F, int q, int k) {
+    return q < FS ? sh.Bc[q][k] : P.B32[(size_t)F.Fl[q] * P.K + k];
+}
+__device__ __forceinline__ double brow64(const PolDev& P, const PolishShared& sh, const FreeSet& F, int q, int k) {
+    return q < FS ? sh.Bd[q][k] : P.B64[(size_t)F.Fl[q] * P.K + k];
+}
+
+// FP32 Woodbury solve of Sigma_FF x = r for the columns c0..c1 of Y (in: D^{-1} r;
+// out: x). Block-collective.
+__device__ void woodbury32(const PolDev& P, PolishShared& sh, const FreeSet& F, int nF, int c0, int c1) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = P.K, nc = c1 - c0;
+    for (int e2 = tid; e2 < K * nc; e2 += PB) {
+        const int k = e2 / nc, c = c0 + e2 % nc;
+        float acc = 0.f;
+        for (int q = 0; q < nF; ++q) acc = fmaf(brow32(P, sh, F, q, k), float(F.Y[(size_t)q * YS + c]), acc);
+        sh.T[k][c - c0] = acc;
+    }
+    __syncthreads();
+    // L L' t = T column by column, one warp per column, rows lane and lane + 32 in registers
+    for (int c = warp; c < nc; c += PB / 32) {
+        float v0 = lane < K ? sh.T[lane][c] : 0.f, v1 = lane + 32 < K ? sh.T[lane + 32][c] : 0.f;
+        for (int r = 0; r < K; ++r) {
+            const float x = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) * sh.Ldinv[r];
+            if (lane > r) v0 = fmaf(-sh.C[lane][r], x, v0);
+            if (lane + 32 > r && lane + 32 < K) v1 = fmaf(-sh.C[lane + 32][r], x, v1);
+            if (lane == (r & 31)) { if (r < 32) v0 = x; else v1 = x; }
+        }
+        for (int r = K - 1; r >= 0; --r) {
+            const float x = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) * sh.Ldinv[r];
+            if (lane < r) v0 = fmaf(-sh.C[r][lane], x, v0);
+            if (lane + 32 < r) v1 = fmaf(-sh.C[r][lane + 32], x, v1);
+            if (lane == (r & 31)) { if (r < 32) v0 = x; else v1 = x; }
+        }
+        if (lane < K) sh.T[lane][c] = v0;
+        if (lane + 32 < K) sh.T[lane + 32][c] = v1;
+    }
+    __syncthreads();
+    for (int e2 = tid; e2 < nF * nc; e2 += PB) {
+        const int q = e2 / nc, c = c0 + e2 % nc;
+        float acc = 0.f;
+        for (int k = 0; k < K; ++k) acc = fmaf(brow32(P, sh, F, q, k), sh.T[k][c - c0], acc);
+        F.Y[(size_t)q * YS + c] -= double(acc) * F.dinv[q];
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
     const int a = blockIdx.x;
     if ((P.skip && P.skip[a]) || P.done[a]) return;
     extern __shared__ unsigned char smem_raw[];
-    SolveShared& sh = *reinterpret_cast<SolveShared*>(smem_raw);
+    PolishShared& sh = *reinterpret_cast<PolishShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = P.K, S = P.S, N = P.N;
     const size_t base = (size_t)a * P.Npad;
-    int* Fl = P.Flist + (size_t)a * P.FMAX;
+    int* Flg = P.Flist + (size_t)a * P.FMAX;
     int* NZl = P.NZlist + (size_t)a * P.FMAX;
-    double* Fsig = P.Fsig + (size_t)a * P.FMAX;
-    double* Y = P.Y + (size_t)a * P.FMAX * (PMAXROWS + 1);
     double* W = P.W + base;
-    // ---- 1. ordered compaction: warp w owns a contiguous range of entries, read in
-    // coalesced tiles of 32; pass 1 counts (and fixes W of fixed entries), pass 2 writes
-    const int Lw = cdiv(cdiv(N, PB / 32), 32) * 32;
-    const int w0r = min(N, warp * Lw), w1r = min(N, w0r + Lw);
-    int nf = 0, nn = 0;
-    double sa = 0.0, ca = 0.0;
-    for (int p = w0r + lane; p < w1r + lane; p += 32) {
-        int isF = 0, isNZ = 0;
-        if (p < w1r) {
+    const double tol_d = P.tol_dual, tol_p = P.tol_primal;
+    for (int round = 0; round < rounds; ++round) {
+        // ---- (a) ordered compaction in coalesced warp tiles; W of the fixed entries
+        const int Lw = cdiv(cdiv(N, PB / 32), 32) * 32;
+        const int w0r = min(N, warp * Lw), w1r = min(N, w0r + Lw);
+        int nf = 0, nn = 0;
+        double sa = 0.0, ca = 0.0;
+        for (int p0 = w0r; p0 < w1r; p0 += 32 * AU) {
+            int code[AU], pwv[AU];
+            float w0v[AU], lov[AU];
+#pragma unroll
+            for (int u = 0; u < AU; ++u) {              // all loads of the batch first
+                const int p = p0 + 32 * u + lane;
+                const size_t e = base + (p < w1r ? p : 0);
+                code[u] = P.st[e];
+                w0v[u] = P.w0f[e];
+                lov[u] = P.lof[e];
+                pwv[u] = P.pw_idx ? P.pw_idx[e] : -1;
+            }
+#pragma unroll
+            for (int u = 0; u < AU; ++u) {
+                const int p = p0 + 32 * u + lane;
+                int isF = 0, isNZ = 0;
+                if (p < w1r) {
+                    if (code[u] == 0 && w0v[u] == 0.f && lov[u] == 0.f && pwv[u] < 0) {
+                        W[p] = 0.0;
+                    } else {
+                        Pieces pc;
+                        entry_pieces(P, base + p, pc);
+                        if (code[u] >= ST_FREE) {
+                            isF = 1;
+                            ca -= seg_sign(pc, code[u] - ST_FREE) * pc.w0;
+                        } else {
+                            const double wv = pc.bp[code[u]];
+                            W[p] = wv;
+                            sa += wv;
+                            ca += fabs(wv - pc.w0);
+                            isNZ = (wv != 0.0);
+                        }
+                    }
+                }
+                nf += __popc(__ballot_sync(0xffffffffu, isF));
+                nn += __popc(__ballot_sync(0xffffffffu, isNZ));
+            }
+        }
+        sa = warp_sum(sa);
+        ca = warp_sum(ca);
+        if (lane == 0) { sh.cntF[warp] = nf; sh.cntN[warp] = nn; sh.sumA[warp] = sa; sh.capA[warp] = ca; }
+        __syncthreads();
+        if (tid == 0) {
+            int of = 0, on = 0;
+            double ss = 0.0, cc = 0.0;
+            for (int t = 0; t < PB / 32; ++t) {
+                const int f = sh.cntF[t], n = sh.cntN[t];
+                sh.cntF[t] = of; sh.cntN[t] = on;
+                of += f; on += n;
+                ss += sh.sumA[t]; cc += sh.capA[t];
+            }
+            sh.nF = of; sh.nNZ = on;
+            sh.sumA[0] = ss; sh.capA[0] = cc;
+            int r = 0;
+            sh.rows[r++] = -1;
+            for (int q = 0; q < S; ++q)
+                if (P.wband[a * S + q] != 0) { if (r < PMAXROWS) sh.rows[r] = q; ++r; }
+            if (P.wcap[a]) { if (r < PMAXROWS) sh.rows[r] = S; ++r; }
+            sh.nrows = r;
+            sh.fail = (of > P.FMAX || on > P.FMAX || of == 0 || r > MAXWROWS);
+        }
+        __syncthreads();
+        if (sh.fail) {
+            if (tid == 0) P.done[a] = 2;
+            return;
+        }
+        {
+            int of = sh.cntF[warp], on = sh.cntN[warp];
+            const unsigned lt = (1u << lane) - 1u;
+            for (int p0 = w0r; p0 < w1r; p0 += 32 * AU) {
+                int code[AU];
+                double wv[AU];
+#pragma unroll
+                for (int u = 0; u < AU; ++u) {
+                    const int p = p0 + 32 * u + lane, pp = p < w1r ? p : 0;
+                    code[u] = P.st[base + pp];
+                    wv[u] = W[pp];
+                }
+#pragma unroll
+                for (int u = 0; u < AU; ++u) {
+                    const int p = p0 + 32 * u + lane;
+                    const int isF = p < w1r && code[u] >= ST_FREE;
+                    const int isNZ = p < w1r && !isF && wv[u] != 0.0;
+                    const unsigned bF = __ballot_sync(0xffffffffu, isF), bN = __ballot_sync(0xffffffffu, isNZ);
+                    if (isF) Flg[of + __popc(bF & lt)] = p;
+                    if (isNZ) NZl[on + __popc(bN & lt)] = p;
+                    of += __popc(bF);
+                    on += __popc(bN);
+                }
+            }
+        }
+        __syncthreads();
+        const int nF = sh.nF, nNZ = sh.nNZ, m = sh.nrows;
+        const double sumA = sh.sumA[0], capA = sh.capA[0];
+        // ---- (b1) h_A = B' w_A (FP64) over the nonzero fixed entries
+        for (int k = tid; k < K; k += PB) {
+            double acc = 0.0;
+            for (int q = 0; q < nNZ; ++q) {
+                const int p = NZl[q];
+                acc += W[p] * P.B64[(size_t)p * K + k];
+            }
+            sh.hA[k] = acc;
+            sh.fhA[k] = P.f64[k] * acc;
+        }
+        __syncthreads();
+        // ---- (b2) the free set: shared memory when small; rows of B in FP32 and FP64
+        FreeSet F;
+        F.in_smem = nF <= FS;
+        if (F.in_smem) {
+            F.Fl = sh.Fl_s; F.Y = &sh.Ys[0][0]; F.dinv = sh.dinv_s; F.sig = sh.sig_s;
+            for (int q = tid; q < nF; q += PB) sh.Fl_s[q] = Flg[q];
+        } else {
+            F.Fl = Flg;
+            F.Y = P.Y + (size_t)a * P.FMAX * YS;
+            F.dinv = P.Fdinv + (size_t)a * P.FMAX;
+            F.sig = P.Fsig + (size_t)a * P.FMAX;
+        }
+        for (int e2 = tid; e2 < min(nF, FS) * K; e2 += PB) {
+            const int q = e2 / K, k = e2 % K;
+            const double b = P.B64[(size_t)Flg[q] * K + k];
+            sh.Bd[q][k] = b;
+            sh.Bc[q][k] = P.B32[(size_t)Flg[q] * K + k];
+        }
+        __syncthreads();
+        // g0 (FP64), 1/d, cap signs
+        for (int q = tid; q < nF; q += PB) {
+            const int p = F.Fl[q];
             const size_t e = base + p;
-            const int code = P.st[e];
             Pieces pc;
             entry_pieces(P, e, pc);
-            if (code >= ST_FREE) {
-                isF = 1;
-                ca -= seg_sign(pc, code - ST_FREE) * pc.w0;
-            } else {
-                const double wv = pc.bp[code];
-                W[p] = wv;
-                sa += wv;
-                ca += fabs(wv - pc.w0);
-                isNZ = (wv != 0.0);
+            const int seg = P.st[e] - ST_FREE;
+            double b0 = 0.0, b1 = 0.0;
+            for (int k = 0; k + 1 < K; k += 2) {
+                b0 += brow64(P, sh, F, q, k) * sh.fhA[k];
+                b1 += brow64(P, sh, F, q, k + 1) * sh.fhA[k + 1];
             }
+            if (K & 1) b0 += brow64(P, sh, F, q, K - 1) * sh.fhA[K - 1];
+            double* Yq = F.Y + (size_t)q * YS;
+            Yq[0] = P.mu64[p] - pc.sl[seg] - 2.0 * (b0 + b1);
+            Yq[COL_W] = 0.0;
+            F.dinv[q] = 1.0 / P.d64[p];
+            if (q < FS) sh.dinvf_s[q] = float(F.dinv[q]);
+            F.sig[q] = seg_sign(pc, seg);
         }
-        nf += __popc(__ballot_sync(0xffffffffu, isF));
-        nn += __popc(__ballot_sync(0xffffffffu, isNZ));
-    }
-    sa = warp_sum(sa);
-    ca = warp_sum(ca);
-    if (lane == 0) {
-        sh.cntF[warp] = nf;
-        sh.cntN[warp] = nn;
-        sh.sumA[warp] = sa;
-        sh.capA[warp] = ca;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int of = 0, on = 0;
-        double ss = 0.0, cc = 0.0;
-        for (int t = 0; t < PB / 32; ++t) {
-            const int f = sh.cntF[t], n = sh.cntN[t];
-            sh.cntF[t] = of; sh.cntN[t] = on;
-            of += f; on += n;
-            ss += sh.sumA[t]; cc += sh.capA[t];
-        }
-        sh.nF = of; sh.nNZ = on;
-        sh.sumA[0] = ss; sh.capA[0] = cc;
-        sh.fail = (of > P.FMAX || on > P.FMAX || of == 0);
-        // working rows
-        int r = 0;
-        sh.rows[r++] = -1;
-        for (int q = 0; q < S; ++q)
-            if (P.wband[a * S + q] != 0) { if (r < PMAXROWS) sh.rows[r] = q; ++r; }
-        if (P.wcap[a]) { if (r < PMAXROWS) sh.rows[r] = S; ++r; }
-        sh.nrows = r;
-        if (r > PMAXROWS) sh.fail = 1;
-    }
-    __syncthreads();
-    if (sh.fail) {
-        if (tid == 0) P.done[a] = 2;
-        return;
-    }
-    {
-        int of = sh.cntF[warp], on = sh.cntN[warp];
-        const unsigned lt = (1u << lane) - 1u;
-        for (int p = w0r + lane; p < w1r + lane; p += 32) {
-            int isF = 0, isNZ = 0;
-            if (p < w1r) {
-                isF = P.st[base + p] >= ST_FREE;
-                isNZ = !isF && W[p] != 0.0;
-            }
-            const unsigned bF = __ballot_sync(0xffffffffu, isF), bN = __ballot_sync(0xffffffffu, isNZ);
-            if (isF) Fl[of + __popc(bF & lt)] = p;
-            if (isNZ) NZl[on + __popc(bN & lt)] = p;
-            of += __popc(bF);
-            on += __popc(bN);
-        }
-    }
-    __syncthreads();
-    const int nF = sh.nF, nNZ = sh.nNZ, m = sh.nrows;
-    const double sumA = sh.sumA[0], capA = sh.capA[0];
-    // ---- 2. h_A = B' w_A over the nonzero fixed entries
-    for (int k = tid; k < K; k += PB) {
-        double acc = 0.0;
-        for (int q = 0; q < nNZ; ++q) {
-            const int p = NZl[q];
-            acc += W[p] * P.B64[(size_t)p * K + k];
-        }
-        sh.hA[k] = acc;
-        sh.fhA[k] = P.f64[k] * acc;
-    }
-    __syncthreads();
-    // ---- 3. scaled right-hand sides D^{-1} [g0, E_F'] of the free entries
-    for (int q = tid; q < nF; q += PB) {
-        const int p = Fl[q];
-        const size_t e = base + p;
-        Pieces pc;
-        entry_pieces(P, e, pc);
-        const int seg = P.st[e] - ST_FREE;
-        const double* Bp = P.B64 + (size_t)p * K;
-        double bfh = 0.0;
-        for (int k = 0; k < K; ++k) bfh += Bp[k] * sh.fhA[k];
-        const double dinv = 1.0 / P.d64[p];
-        const double sig = seg_sign(pc, seg);
-        Fsig[q] = sig;
-        double* Yq = Y + (size_t)q * (PMAXROWS + 1);
-        Yq[0] = (P.mu64[p] - pc.sl[seg] - 2.0 * bfh) * dinv;
-        for (int r = 0; r < m; ++r) Yq[1 + r] = row_coef(P, sh.rows[r], p, sig) * dinv;
-    }
-    // ---- 4. C = F^{-1} + B_F' D_F^{-1} B_F and T = B_F' Y, over staged chunks of B_F
-    for (int e2 = tid; e2 < K * K; e2 += PB) {
-        const int r = e2 / K, c = e2 % K;
-        sh.C[r][c] = (r == c) ? 1.0 / P.f64[r] : 0.0;
-    }
-    for (int e2 = tid; e2 < K * (PMAXROWS + 1); e2 += PB) sh.T[e2 / (PMAXROWS + 1)][e2 % (PMAXROWS + 1)] = 0.0;
-    for (int q0 = 0; q0 < nF; q0 += BCH) {
-        const int nb = min(BCH, nF - q0);
         __syncthreads();
-        for (int e2 = tid; e2 < nb * K; e2 += PB) {
-            const int j = e2 / K, k = e2 % K;
-            sh.Bc[j][k] = P.B64[(size_t)Fl[q0 + j] * K + k];
-        }
-        for (int j = tid; j < nb; j += PB) sh.dinv[j] = 1.0 / P.d64[Fl[q0 + j]];
-        __syncthreads();
+        // ---- (b3) FP32 capacitance C = F^{-1} + B_F' D_F^{-1} B_F and its Cholesky factor
         for (int e2 = tid; e2 < K * K; e2 += PB) {
             const int r = e2 / K, c = e2 % K;
             if (c > r) continue;
-            double acc = 0.0;
-            for (int j = 0; j < nb; ++j) acc += sh.Bc[j][r] * sh.Bc[j][c] * sh.dinv[j];
-            sh.C[r][c] += acc;
+            float acc = (r == c) ? float(1.0 / P.f64[r]) : 0.f;
+            const int q1 = min(nF, FS);
+            for (int q = 0; q < q1; ++q) acc = fmaf(sh.Bc[q][r] * sh.dinvf_s[q], sh.Bc[q][c], acc);
+            for (int q = q1; q < nF; ++q)
+                acc = fmaf(brow32(P, sh, F, q, r) * float(F.dinv[q]), brow32(P, sh, F, q, c), acc);
+            sh.C[r][c] = acc;
         }
-        for (int e2 = tid; e2 < K * (m + 1); e2 += PB) {
-            const int k = e2 / (m + 1), c = e2 % (m + 1);
-            double acc = 0.0;
-            for (int j = 0; j < nb; ++j) acc += sh.Bc[j][k] * Y[(size_t)(q0 + j) * (PMAXROWS + 1) + c];
-            sh.T[k][c] += acc;
-        }
-    }
-    __syncthreads();
-    // ---- 5. Cholesky of C by warp 0 (lower triangle, in place)
-    if (warp == 0) {
+        __syncthreads();
+        // Cholesky in the L D L' form (column c of the trailing update reads only column c),
+        // then L = L D^{1/2}
         for (int c = 0; c < K; ++c) {
-            const double piv = sh.C[c][c];
-            if (!(piv > 0.0)) { if (lane == 0) sh.fail = 1; break; }
-            const double lc = sqrt(piv);
-            __syncwarp();
-            if (lane == 0) sh.C[c][c] = lc;
-            for (int r = c + 1 + lane; r < K; r += 32) sh.C[r][c] /= lc;
-            __syncwarp();
-            const int w = K - c - 1;
-            for (int idx = lane; idx < w * w; idx += 32) {
-                const int r = c + 1 + idx / w, q = c + 1 + idx % w;
-                if (q <= r) sh.C[r][q] -= sh.C[r][c] * sh.C[q][c];
+            const float piv = sh.C[c][c];
+            if (!(piv > 0.f)) { if (tid == 0) sh.fail = 1; break; }
+            const float ip = 1.f / piv;
+            for (int r = c + 1 + warp; r < K; r += PB / 32) {
+                const float lr = sh.C[r][c] * ip;
+                for (int q = c + 1 + lane; q <= r; q += 32) sh.C[r][q] = fmaf(-lr, sh.C[q][c], sh.C[r][q]);
             }
-            __syncwarp();
+            __syncthreads();
         }
-    }
-    __syncthreads();
-    if (sh.fail) {
-        if (tid == 0) P.done[a] = 2;
-        return;
-    }
-    // ---- 6. T <- C^{-1} T, one column per warp at a time (substitution with lanes over rows)
-    for (int c = warp; c < m + 1; c += PB / 32) {
-        for (int r = 0; r < K; ++r) {
-            const double x = sh.T[r][c] / sh.C[r][r];
-            __syncwarp();
-            for (int q = r + 1 + lane; q < K; q += 32) sh.T[q][c] -= sh.C[q][r] * x;
-            if (lane == 0) sh.T[r][c] = x;
-            __syncwarp();
+        if (!sh.fail) {
+            for (int c = tid; c < K; c += PB) sh.Ldinv[c] = sqrtf(sh.C[c][c]);
+            __syncthreads();
+            for (int e2 = tid; e2 < K * K; e2 += PB) {
+                const int r = e2 / K, c = e2 % K;
+                if (c < r) sh.C[r][c] /= sh.Ldinv[c];
+            }
+            __syncthreads();
+            for (int c = tid; c < K; c += PB) { sh.C[c][c] = sh.Ldinv[c]; sh.Ldinv[c] = 1.f / sh.Ldinv[c]; }
         }
-        for (int r = K - 1; r >= 0; --r) {
-            const double x = sh.T[r][c] / sh.C[r][r];
-            __syncwarp();
-            for (int q = lane; q < r; q += 32) sh.T[q][c] -= sh.C[r][q] * x;
-            if (lane == 0) sh.T[r][c] = x;
-            __syncwarp();
-        }
-    }
-    __syncthreads();
-    // ---- 7. Y <- D^{-1} (X - B_F T): now Y = Sigma_FF^{-1} [g0, E_F']
-    for (int q0 = 0; q0 < nF; q0 += BCH) {
-        const int nb = min(BCH, nF - q0);
         __syncthreads();
-        for (int e2 = tid; e2 < nb * K; e2 += PB) {
-            const int j = e2 / K, k = e2 % K;
-            sh.Bc[j][k] = P.B64[(size_t)Fl[q0 + j] * K + k];
+        if (sh.fail) {
+            if (tid == 0) P.done[a] = 2;
+            return;
         }
-        for (int j = tid; j < nb; j += PB) sh.dinv[j] = 1.0 / P.d64[Fl[q0 + j]];
+        // ---- (b4) Y_E = Sigma_FF^{-1} E_F' (FP32, stored in Y columns 1..m)
+        for (int e2 = tid; e2 < nF * m; e2 += PB) {
+            const int q = e2 / m, r = e2 % m;
+            F.Y[(size_t)q * YS + 1 + r] = row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.dinv[q];
+        }
         __syncthreads();
-        for (int e2 = tid; e2 < nb * (m + 1); e2 += PB) {
-            const int j = e2 / (m + 1), c = e2 % (m + 1);
+        woodbury32(P, sh, F, nF, 1, 1 + m);
+        // Schur matrix S = 1/2 E Y_E, and row edges e = edge - fixed part
+        for (int e2 = tid; e2 < m * m; e2 += PB) {
+            const int r = e2 / m, c = e2 % m;
             double acc = 0.0;
-            for (int k = 0; k < K; ++k) acc += sh.Bc[j][k] * sh.T[k][c];
-            Y[(size_t)(q0 + j) * (PMAXROWS + 1) + c] -= acc * sh.dinv[j];
+            for (int q = 0; q < nF; ++q)
+                acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + 1 + c];
+            sh.Sf[r][c] = 0.5 * acc;
         }
-    }
-    __syncthreads();
-    // ---- 8. Schur system (1/2) E Y_E lambda = (1/2) E Y_g - e
-    for (int e2 = tid; e2 < m * (m + 1); e2 += PB) {
-        const int r = e2 / (m + 1), c = e2 % (m + 1);
-        double acc = 0.0;
-        for (int q = 0; q < nF; ++q)
-            acc += row_coef(P, sh.rows[r], Fl[q], Fsig[q]) * Y[(size_t)q * (PMAXROWS + 1) + c];
-        if (c == 0) sh.erhs[r] = 0.5 * acc;
-        else sh.Sm[r][c - 1] = 0.5 * acc;
-    }
-    __syncthreads();
-    // edges of the working rows minus what the fixed entries already contribute
-    for (int r = tid; r < m; r += PB) {
-        const int row = sh.rows[r];
-        double e_r;
-        if (row < 0) {
-            e_r = 1.0 - sumA;
-        } else if (row < S) {
-            double fixed_s = 0.0;
-            for (int q = 0; q < nNZ; ++q)
-                if (P.sector[NZl[q]] == row) fixed_s += W[NZl[q]];
-            const double edge = (P.wband[a * S + row] > 0) ? P.band_hi[a * S + row] : P.band_lo[a * S + row];
-            e_r = edge - fixed_s;
-        } else {
-            e_r = P.tau[a] - capA;
-        }
-        sh.erhs[r] -= e_r;
-    }
-    __syncthreads();
-    // symmetric elimination with diagonal pivoting (budget row first); rows whose pivot
-    // vanishes are dependent on the free set and get multiplier 0
-    if (tid == 0) {
-        double A[PMAXROWS][PMAXROWS + 1];
-        int chosen[PMAXROWS], used[PMAXROWS];
-        double scale = 0.0;
-        for (int r = 0; r < m; ++r) {
-            for (int c = 0; c < m; ++c) A[r][c] = sh.Sm[r][c];
-            A[r][m] = sh.erhs[r];
-            used[r] = 0;
-            scale = fmax(scale, fabs(A[r][r]));
-        }
-        int nc = 0;
-        for (int k = 0; k < m; ++k) {
-            int p = -1;
-            if (k == 0) p = 0;
-            else {
-                double best = 0.0;
-                for (int j = 0; j < m; ++j)
-                    if (!used[j] && fabs(A[j][j]) > best) { best = fabs(A[j][j]); p = j; }
+        for (int r = tid; r < m; r += PB) {
+            const int row = sh.rows[r];
+            double e_r;
+            if (row < 0) {
+                e_r = 1.0 - sumA;
+            } else if (row < S) {
+                double fixed_s = 0.0;
+                for (int q = 0; q < nNZ; ++q)
+                    if (P.sector[NZl[q]] == row) fixed_s += W[NZl[q]];
+                const double edge = (P.wband[a * S + row] > 0) ? P.band_hi[a * S + row] : P.band_lo[a * S + row];
+                e_r = edge - fixed_s;
+            } else {
+                e_r = P.tau[a] - capA;
             }
-            if (p < 0 || !(fabs(A[p][p]) > 1e-11 * scale)) break;
-            used[p] = 1;
-            chosen[nc++] = p;
-            for (int j = 0; j < m; ++j) {
-                if (used[j]) continue;
-                const double f = A[j][p] / A[p][p];
-                for (int q = 0; q <= m; ++q) A[j][q] -= f * A[p][q];
+            sh.erhs[r] = e_r;
+            sh.lam[r] = 0.0;
+        }
+        __syncthreads();
+        // pivoted symmetric elimination of S (budget row first); vanishing pivots mark
+        // rows that depend on the free set: their multipliers stay 0
+        if (tid == 0) {
+            double scale = 0.0;
+            for (int r = 0; r < m; ++r) { sh.used[r] = 0; scale = fmax(scale, fabs(sh.Sf[r][r])); }
+            int nc = 0;
+            for (int k = 0; k < m; ++k) {
+                int p = -1;
+                if (k == 0) p = 0;
+                else {
+                    double best = 0.0;
+                    for (int j = 0; j < m; ++j)
+                        if (!sh.used[j] && fabs(sh.Sf[j][j]) > best) { best = fabs(sh.Sf[j][j]); p = j; }
+                }
+                if (p < 0 || !(fabs(sh.Sf[p][p]) > 1e-9 * scale)) break;
+                sh.used[p] = 1;
+                sh.order[nc++] = p;
+                for (int j = 0; j < m; ++j) {
+                    if (sh.used[j]) continue;
+                    const double f = sh.Sf[j][p] / sh.Sf[p][p];
+                    // only columns not yet pivoted: pivoted ones of row j hold its multipliers
+                    for (int q = 0; q < m; ++q) if (!sh.used[q]) sh.Sf[j][q] -= f * sh.Sf[p][q];
+                    sh.Sf[j][p] = f;                       // multiplier of row j against pivot p
+                }
             }
+            sh.nc = nc;
+            sh.fail = (nc == 0);
         }
-        for (int r = 0; r < m; ++r) sh.lam[r] = 0.0;
-        for (int k = nc - 1; k >= 0; --k) {
-            const int p = chosen[k];
-            double v = A[p][m];
-            for (int q = 0; q < m; ++q) if (q != p && used[q]) v -= A[p][q] * sh.lam[q];
-            sh.lam[p] = v / A[p][p];
+        __syncthreads();
+        if (sh.fail) {
+            if (tid == 0) P.done[a] = 2;
+            return;
         }
-        sh.fail = (nc == 0);
-        sh.ndep = m - nc;
-    }
-    __syncthreads();
-    if (sh.fail) {
-        if (tid == 0) P.done[a] = 2;
-        return;
-    }
-    // ---- 9. w_F = 1/2 (Y_g - Y_E lambda); h = h_A + B_F' w_F; multipliers
-    for (int q = tid; q < nF; q += PB) {
-        const double* Yq = Y + (size_t)q * (PMAXROWS + 1);
-        double acc = Yq[0];
-        for (int r = 0; r < m; ++r) acc -= Yq[1 + r] * sh.lam[r];
-        W[Fl[q]] = 0.5 * acc;
-    }
-    __syncthreads();
-    for (int k = tid; k < K; k += PB) {
-        double acc = sh.hA[k];
-        for (int q = 0; q < nF; ++q) acc += W[Fl[q]] * P.B64[(size_t)Fl[q] * K + k];
-        const double fh = P.f64[k] * acc;
-        P.fh64[(size_t)a * KMAX + k] = fh;
-        P.fh32[(size_t)a * K + k] = float(fh);
-        sh.hA[k] = acc;        // reuse: full h
-        sh.fhA[k] = fh;
-    }
-    __syncthreads();
-    if (tid == 0) {
-        double quad = 0.0, fmax_ = 0.0;
-        for (int k = 0; k < K; ++k) { quad += sh.hA[k] * sh.fhA[k]; fmax_ = fmax(fmax_, fabs(sh.fhA[k])); }
-        P.quad[a] = quad;
-        P.fhmax[a] = fmax_;
-        P.nu[a] = sh.lam[0];
+        const int ndep = m - sh.nc;
+        // ---- (b5) iterative refinement: FP64 residuals, FP32 corrections
+        for (int it = 0; it < IR_STEPS; ++it) {
+            // t = B_F' w_F (FP64)
+            for (int k = tid; k < K; k += PB) {
+                double acc = 0.0;
+                for (int q = 0; q < nF; ++q) acc += F.Y[(size_t)q * YS + COL_W] * brow64(P, sh, F, q, k);
+                sh.t64[k] = P.f64[k] * acc;
+            }
+            __syncthreads();
+            // r1 = g0 - 2 Sigma_FF w - E' lam ; stored scaled by D^{-1} in COL_R
+            double rmax = 0.0;
+            for (int q = tid; q < nF; q += PB) {
+                const int p = F.Fl[q];
+                double b0 = 0.0, b1 = 0.0;
+                for (int k = 0; k + 1 < K; k += 2) {
+                    b0 += brow64(P, sh, F, q, k) * sh.t64[k];
+                    b1 += brow64(P, sh, F, q, k + 1) * sh.t64[k + 1];
+                }
+                if (K & 1) b0 += brow64(P, sh, F, q, K - 1) * sh.t64[K - 1];
+                double* Yq = F.Y + (size_t)q * YS;
+                double r1 = Yq[0] - 2.0 * ((b0 + b1) + P.d64[p] * Yq[COL_W]);
+                for (int r = 0; r < m; ++r) r1 -= row_coef(P, sh.rows[r], p, F.sig[q]) * sh.lam[r];
+                rmax = fmax(rmax, fabs(r1));
+                Yq[COL_R] = r1 * F.dinv[q];
+            }
+            // r2 = e - E w
+            for (int r = tid; r < m; r += PB) {
+                double acc = 0.0;
+                for (int q = 0; q < nF; ++q)
+                    acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + COL_W];
+                sh.rr2[r] = sh.erhs[r] - acc;
+            }
+            rmax = warp_max(rmax);
+            if (lane == 0) sh.red[warp][0] = rmax;
+            __syncthreads();
+            double rm = 0.0, r2m = 0.0;
+            for (int w = 0; w < PB / 32; ++w) rm = fmax(rm, sh.red[w][0]);
+            for (int r = 0; r < m; ++r) r2m = fmax(r2m, fabs(sh.rr2[r]));
+            if (it > 0 && rm <= 1e-15 && r2m <= 1e-16) break;
+            // Yr = Sigma_FF^{-1} r1 (FP32)
+            woodbury32(P, sh, F, nF, COL_R, COL_R + 1);
+            // dlam = S^{-1} (1/2 E Yr - r2) with the eliminated S
+            for (int r = tid; r < m; r += PB) {
+                double acc = 0.0;
+                for (int q = 0; q < nF; ++q)
+                    acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + COL_R];
+                sh.dlam[r] = 0.5 * acc - sh.rr2[r];
+            }
+            __syncthreads();
+            if (tid == 0) {
+                // forward: apply the recorded eliminations in pivot order
+                for (int k = 0; k < sh.nc; ++k) {
+                    const int p = sh.order[k];
+                    for (int j = 0; j < m; ++j) {
+                        bool later = !sh.used[j];
+                        for (int kk = k + 1; kk < sh.nc; ++kk) if (sh.order[kk] == j) later = true;
+                        if (later && j != p) sh.dlam[j] -= sh.Sf[j][p] * sh.dlam[p];
+                    }
+                }
+                double x[PMAXROWS];
+                for (int r = 0; r < m; ++r) x[r] = 0.0;
+                for (int k = sh.nc - 1; k >= 0; --k) {
+                    const int p = sh.order[k];
+                    double v = sh.dlam[p];
+                    for (int kk = k + 1; kk < sh.nc; ++kk) { const int q = sh.order[kk]; v -= sh.Sf[p][q] * x[q]; }
+                    x[p] = v / sh.Sf[p][p];
+                }
+                for (int r = 0; r < m; ++r) { sh.dlam[r] = x[r]; sh.lam[r] += x[r]; }
+            }
+            __syncthreads();
+            // dw = 1/2 (Yr - Y_E dlam)
+            for (int q = tid; q < nF; q += PB) {
+                double* Yq = F.Y + (size_t)q * YS;
+                double acc = Yq[COL_R];
+                for (int r = 0; r < m; ++r) acc -= Yq[1 + r] * sh.dlam[r];
+                Yq[COL_W] += 0.5 * acc;
+            }
+            __syncthreads();
+        }
+        // ---- (b6) the solved point: W_F, h = h_A + B_F' w_F, multipliers
+        for (int q = tid; q < nF; q += PB) W[F.Fl[q]] = F.Y[(size_t)q * YS + COL_W];
+        for (int k = tid; k < K; k += PB) {
+            double acc = sh.hA[k];
+            for (int q = 0; q < nF; ++q) acc += F.Y[(size_t)q * YS + COL_W] * brow64(P, sh, F, q, k);
+            const double fhk = P.f64[k] * acc;
+            sh.t64[k] = acc;
+            sh.fh[k] = fhk;
+            sh.fh32[k] = float(fhk);
+        }
+        for (int k = K + tid; k < KMAX; k += PB) sh.fh32[k] = 0.f;
+        for (int s2 = tid; s2 < S; s2 += PB) sh.lam_s[s2] = 0.0;
+        __syncthreads();
         double theta = 0.0;
-        for (int s = 0; s < S; ++s) P.lam[a * S + s] = 0.0;
-        for (int r = 1; r < m; ++r) {
-            if (sh.rows[r] < S) P.lam[a * S + sh.rows[r]] = sh.lam[r];
-            else theta = sh.lam[r];
-        }
-        P.theta[a] = theta;
-        P.ndep[a] = sh.ndep;
-    }
-}
-
-// ---------------------------------------------------------------------------
-// P3: KKT / feasibility checks of the solved point (Sec. 4.4), state switches,
-// diagnostics. The batched FP32 product G32 = B (F h) filters the entries: an
-// entry whose FP32 margin exceeds a bound on the FP32 error is decided by it;
-// every other entry, and every free entry, is recomputed in FP64.
-// ---------------------------------------------------------------------------
-struct CheckShared {
-    double lam[SMAX];
-    double fh[KMAX];
-    double red[PB / 32][6];
-    double secsum[SMAX];
-    double mmin[PB / 32];
-    int mwho[PB / 32];
-};
-
-__global__ void __launch_bounds__(PB) k_pol_check(PolDev P) {
-    const int a = blockIdx.x;
-    if ((P.skip && P.skip[a]) || P.done[a]) return;
-    __shared__ CheckShared sh;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int K = P.K, S = P.S, N = P.N;
-    const size_t base = (size_t)a * P.Npad;
-    double* W = P.W + base;
-    for (int s = tid; s < S; s += PB) sh.lam[s] = P.lam[a * S + s];
-    for (int k = tid; k < K; k += PB) sh.fh[k] = P.fh64[(size_t)a * KMAX + k];
-    __syncthreads();
-    const double nu = P.nu[a], theta = P.theta[a], fhmax = P.fhmax[a];
-    const double tol_d = P.tol_dual, tol_p = P.tol_primal;
-    double r_stat = 0.0, r_box = 0.0, obj_lin = 0.0, sum_w = 0.0, turn = 0.0;
-    int nviol = 0;
-    double my_margin = INFINITY;
-    int my_who = 0;
-    constexpr int CH = 4;
-    for (int p0 = tid; p0 < N; p0 += PB * CH) {
-        EntryRaw raw[CH];
+        for (int r = 1; r < m; ++r) if (sh.rows[r] == S) theta = sh.lam[r];
+        if (tid == 0) for (int r = 1; r < m; ++r) if (sh.rows[r] < S) sh.lam_s[sh.rows[r]] = sh.lam[r];
+        __syncthreads();
+        const double nu = sh.lam[0];
+        double fhmax = 0.0, quad = 0.0;
+        for (int k = 0; k < K; ++k) { fhmax = fmax(fhmax, fabs(sh.fh[k])); quad += sh.t64[k] * sh.fh[k]; }
+        // ---- (c) checks of every entry (Sec. 4.4): FP32 gradient as a filter, FP64 where it
+        // cannot decide; violators switch state for the next round
+        const float nu_f = float(nu), theta_f = float(theta), fhmax_f = float(fhmax);
+        double r_stat = 0.0, r_box = 0.0, obj_lin = 0.0, sum_w = 0.0, turn = 0.0;
+        int nviol = 0;
+        double my_margin = INFINITY;
+        int my_who = 0;
+        // lane (4 r + j) holds columns 16 i + 4 j .. + 3 (i < 4) of fh in FP32
+        float4 fr[4];
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-            const int p = p0 + PB * c;
-            if (p < N) load_raw(P, base, p, raw[c]);
-        }
+        for (int i = 0; i < 4; ++i) fr[i] = *reinterpret_cast<const float4*>(&sh.fh32[16 * i + 4 * (lane & 3)]);
+        const int ntiles = cdiv(N, 32);
+        for (int ti = warp; ti < ntiles; ti += PB / 32) {
+            const int p = ti * 32 + lane;                 // entries of padding (p >= N) are skipped below
+            const size_t e = base + p;
+            const int code = P.st[e];
+            const int pwv = P.pw_idx ? P.pw_idx[e] : -1;
+            const int sec = P.sector[p];
+            const float w0v = P.w0f[e], lov = P.lof[e], upv = P.upf[e], cv = P.cf[e];
+            const float muf = P.mu32[p], bn1f = P.Bn1f[p];
+            // g32 = B_p . fh for the tile's 32 rows: four rows of 64 floats per group of 8 lanes x 4
+            // float4, coalesced over the tile's contiguous 8 KB; lane p ends with its own row
+            float g32 = 0.f;
+            const float* Bt = P.B32p + (size_t)ti * 32 * KMAX;
 #pragma unroll
-        for (int c = 0; c < CH; ++c) {
-        const int p = p0 + PB * c;
-        if (p >= N) break;
-        const size_t e = base + p;
-        const EntryRaw& rw = raw[c];
-        Pieces pc;
-        pieces_from(P, rw, pc);
-        const int code = rw.code;
-        const double wv = rw.W;
-        const double dd = rw.d, mu = rw.mu;
-        const double lam_s = sh.lam[rw.sec];
-        sum_w += wv;
-        turn += fabs(wv - pc.w0);
-        obj_lin += dd * wv * wv - mu * wv + phi_value(pc, wv);
-        r_box = fmax(r_box, fmax(rw.lo - wv, wv - rw.up));
-        // FP32 gradient and its error bound
-        const double g_a = 2.0 * (double(rw.g32) + dd * wv) - mu;
-        const double delta = 1e-5 * (2.0 * rw.bn1 * fhmax + 2.0 * fabs(dd * wv) + fabs(mu) + fabs(nu) + fabs(lam_s));
-        auto exact_rr = [&]() {
-            const double* Bp = P.B64 + (size_t)p * K;
-            double bfh = 0.0;
-            for (int k = 0; k < K; ++k) bfh += Bp[k] * sh.fh[k];
-            return 2.0 * (bfh + dd * wv) - mu + nu + lam_s;
-        };
-        if (code >= ST_FREE) {
-            const int seg = code - ST_FREE;
-            const double rr = exact_rr();
-            r_stat = fmax(r_stat, fabs(rr + pc.sl[seg] + theta * seg_sign(pc, seg)));
-            if (wv > pc.bp[seg + 1] + tol_p) { ++nviol; P.st[e] = (int8_t)(seg + 1); }
-            else if (wv < pc.bp[seg] - tol_p) { ++nviol; P.st[e] = (int8_t)seg; }
-        } else {
-            const int j = code;
-            const double left = (j > 0) ? pc.sl[j - 1] + theta * seg_sign(pc, j - 1) : -INFINITY;
-            const double right = (j + 1 < pc.nb) ? pc.sl[j] + theta * seg_sign(pc, j) : INFINITY;
-            double rr = g_a + nu + lam_s;
-            double up = -rr - right, dn = left + rr;
-            if (fmax(up, dn) > -delta) {            // too close to call in FP32
-                rr = exact_rr();
-                up = -rr - right;
-                dn = left + rr;
+            for (int grp = 0; grp < 4; ++grp) {
+                const float4* Br = reinterpret_cast<const float4*>(Bt + (size_t)(grp * 8 + (lane >> 2)) * KMAX) + (lane & 3);
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 b = __ldg(Br + 4 * i);
+                    acc = fmaf(b.x, fr[i].x, acc);
+                    acc = fmaf(b.y, fr[i].y, acc);
+                    acc = fmaf(b.z, fr[i].z, acc);
+                    acc = fmaf(b.w, fr[i].w, acc);
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                const float v = __shfl_sync(0xffffffffu, acc, 4 * (lane & 7));
+                if ((lane >> 3) == grp) g32 = v;
             }
-            r_stat = fmax(r_stat, fmax(fmax(up, dn), 0.0));
-            if (pc.nb > 1) {
-                if (isfinite(right) && -up < my_margin) { my_margin = -up; my_who = p + 1; }
-                if (isfinite(left) && -dn < my_margin) { my_margin = -dn; my_who = -(p + 1); }
+            if (p >= N) continue;
+            if (pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv > 0.f) {
+                const float lam_f = float(sh.lam_s[sec]);
+                const float rr = 2.f * g32 - muf + nu_f + lam_f;
+                const float up = -rr - (cv + theta_f);
+                const float delta = 1e-5f * (2.f * bn1f * fhmax_f + fabsf(muf) + fabsf(nu_f) + fabsf(lam_f)) + 1e-9f;
+                if (up < -delta) {
+                    if (double(-up) < my_margin) { my_margin = double(-up); my_who = p + 1; }
+                    continue;
+                }
             }
-            if (up > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j); }
-            else if (dn > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j - 1); }
+            EntryRaw rw;
+            load_raw(P, base, p, rw);
+            Pieces pc;
+            pieces_from(P, rw, pc);
+            const double wv = rw.W;
+            const double dd = rw.d, mu = rw.mu;
+            const double lam_s = sh.lam_s[sec];
+            sum_w += wv;
+            turn += fabs(wv - pc.w0);
+            obj_lin += dd * wv * wv - mu * wv + phi_value(pc, wv);
+            r_box = fmax(r_box, fmax(rw.lo - wv, wv - rw.up));
+            const double g_a = 2.0 * (double(g32) + dd * wv) - mu;
+            const double delta = 1e-5 * (2.0 * rw.bn1 * fhmax + 2.0 * fabs(dd * wv) + fabs(mu) + fabs(nu) + fabs(lam_s));
+            auto exact_rr = [&]() {
+                const double* Bp = P.B64 + (size_t)p * K;
+                double b0 = 0.0, b1 = 0.0, b2 = 0.0, b3 = 0.0;
+                int k = 0;
+                for (; k + 4 <= K; k += 4) {
+                    b0 += Bp[k] * sh.fh[k]; b1 += Bp[k + 1] * sh.fh[k + 1];
+                    b2 += Bp[k + 2] * sh.fh[k + 2]; b3 += Bp[k + 3] * sh.fh[k + 3];
+                }
+                for (; k < K; ++k) b0 += Bp[k] * sh.fh[k];
+                return 2.0 * (((b0 + b1) + (b2 + b3)) + dd * wv) - mu + nu + lam_s;
+            };
+            if (code >= ST_FREE) {
+                const int seg = code - ST_FREE;
+                const double rr = exact_rr();
+                r_stat = fmax(r_stat, fabs(rr + pc.sl[seg] + theta * seg_sign(pc, seg)));
+                if (wv > pc.bp[seg + 1] + tol_p) { ++nviol; P.st[e] = (int8_t)(seg + 1); }
+                else if (wv < pc.bp[seg] - tol_p) { ++nviol; P.st[e] = (int8_t)seg; }
+            } else {
+                const int j = code;
+                const double left = (j > 0) ? pc.sl[j - 1] + theta * seg_sign(pc, j - 1) : -INFINITY;
+                const double right = (j + 1 < pc.nb) ? pc.sl[j] + theta * seg_sign(pc, j) : INFINITY;
+                double rr = g_a + nu + lam_s;
+                double up = -rr - right, dn = left + rr;
+                if (fmax(up, dn) > -delta) {            // too close to call in FP32
+                    rr = exact_rr();
+                    up = -rr - right;
+                    dn = left + rr;
+                }
+                r_stat = fmax(r_stat, fmax(fmax(up, dn), 0.0));
+                if (pc.nb > 1) {
+                    if (isfinite(right) && -up < my_margin) { my_margin = -up; my_who = p + 1; }
+                    if (isfinite(left) && -dn < my_margin) { my_margin = -dn; my_who = -(p + 1); }
+                }
+                if (up > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j); }
+                else if (dn > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j - 1); }
+            }
         }
+        r_stat = warp_max(r_stat); r_box = warp_max(r_box);
+        obj_lin = warp_sum(obj_lin); sum_w = warp_sum(sum_w); turn = warp_sum(turn);
+        nviol = warp_sum(nviol);
+        for (int o = 16; o > 0; o >>= 1) {
+            const double om = __shfl_xor_sync(0xffffffffu, my_margin, o);
+            const int ow = __shfl_xor_sync(0xffffffffu, my_who, o);
+            if (om < my_margin || (om == my_margin && abs(ow) < abs(my_who))) { my_margin = om; my_who = ow; }
         }
-    }
-    r_stat = warp_max(r_stat); r_box = warp_max(r_box);
-    obj_lin = warp_sum(obj_lin); sum_w = warp_sum(sum_w); turn = warp_sum(turn);
-    nviol = warp_sum(nviol);
-    for (int o = 16; o > 0; o >>= 1) {
-        const double om = __shfl_xor_sync(0xffffffffu, my_margin, o);
-        const int ow = __shfl_xor_sync(0xffffffffu, my_who, o);
-        if (om < my_margin || (om == my_margin && abs(ow) < abs(my_who))) { my_margin = om; my_who = ow; }
-    }
-    if (lane == 0) {
-        sh.red[warp][0] = r_stat; sh.red[warp][1] = r_box; sh.red[warp][2] = obj_lin;
-        sh.red[warp][3] = sum_w; sh.red[warp][4] = turn; sh.red[warp][5] = double(nviol);
-        sh.mmin[warp] = my_margin; sh.mwho[warp] = my_who;
-    }
-    for (int s = warp; s < S; s += PB / 32) {
-        double acc = 0.0;
-        for (int p = P.sec_start[s] + lane; p < P.sec_start[s + 1]; p += 32) acc += W[p];
-        acc = warp_sum(acc);
-        if (lane == 0) sh.secsum[s] = acc;
-    }
-    __syncthreads();
-    if (tid != 0) return;
-    double rs = 0, rb = 0, ol = 0, sw = 0, tu = 0, nv = 0;
-    for (int w = 0; w < PB / 32; ++w) {
-        rs = fmax(rs, sh.red[w][0]); rb = fmax(rb, sh.red[w][1]); ol += sh.red[w][2];
-        sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5];
-    }
-    double r_exp = 0.0, r_comp = 0.0;
-    int bviol = 0;
-    for (int s = 0; s < S; ++s) {
-        const double ssum = sh.secsum[s];
-        const double hi = P.band_hi[a * S + s], lo = P.band_lo[a * S + s];
-        r_exp = fmax(r_exp, fmax(lo - ssum, ssum - hi));
-        const int wb = P.wband[a * S + s];
-        const double ls = sh.lam[s];
-        if (wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p) ++bviol;   // dropped dependent row
-        if (wb == 0) {
-            if (ssum > hi + tol_p) { ++bviol; P.wband[a * S + s] = 1; }
-            else if (ssum < lo - tol_p) { ++bviol; P.wband[a * S + s] = -1; }
-        } else if (wb > 0) {
-            r_comp = fmax(r_comp, fabs(ls) * fabs(hi - ssum));
-            if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); P.wband[a * S + s] = 0; }
-        } else {
-            r_comp = fmax(r_comp, fabs(ls) * fabs(ssum - lo));
-            if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); P.wband[a * S + s] = 0; }
+        if (lane == 0) {
+            sh.red[warp][0] = r_stat; sh.red[warp][1] = r_box; sh.red[warp][2] = obj_lin;
+            sh.red[warp][3] = sum_w; sh.red[warp][4] = turn; sh.red[warp][5] = double(nviol);
+            sh.mmin[warp] = my_margin; sh.mwho[warp] = my_who;
         }
-    }
-    double r_turn = 0.0;
-    const double tau = P.tau[a];
-    if (isfinite(tau)) {
-        r_turn = fmax(tu - tau, 0.0);
-        if (!P.wcap[a]) {
-            if (tu > tau + tol_p) { ++bviol; P.wcap[a] = 1; }
-        } else {
-            if (fabs(tu - tau) > tol_p) ++bviol;                            // dropped dependent row
-            r_comp = fmax(r_comp, fabs(theta) * fabs(tau - tu));
-            if (theta < -tol_d) { ++bviol; r_comp = fmax(r_comp, -theta); P.wcap[a] = 0; }
+        for (int s2 = warp; s2 < S; s2 += PB / 32) {
+            double acc = 0.0;
+            for (int p = P.sec_start[s2] + lane; p < P.sec_start[s2 + 1]; p += 32) acc += W[p];
+            acc = warp_sum(acc);
+            if (lane == 0) sh.secsum[s2] = acc;
         }
-    }
-    const double r_budget = fabs(sw - 1.0);
-    if (r_budget > tol_p) ++bviol;
-    const int total = int(nv) + bviol;
-    if (total > 0 && P.ndep[a] > 0) {
-        // the working rows were dependent on the free set: free the fixed entry
-        // closest to leaving its breakpoint, in the direction of least resistance
-        double bm = INFINITY;
-        int who = 0;
-        for (int w = 0; w < PB / 32; ++w)
-            if (sh.mmin[w] < bm || (sh.mmin[w] == bm && abs(sh.mwho[w]) < abs(who))) { bm = sh.mmin[w]; who = sh.mwho[w]; }
-        if (who != 0) {
-            const size_t e = base + (abs(who) - 1);
-            const int j = P.st[e];
-            if (j < ST_FREE) P.st[e] = (int8_t)(who > 0 ? ST_FREE + j : ST_FREE + j - 1);
+        __syncthreads();
+        if (tid == 0) {
+            double rs = 0, rb = 0, ol = 0, sw = 0, tu = 0, nv = 0;
+            for (int w = 0; w < PB / 32; ++w) {
+                rs = fmax(rs, sh.red[w][0]); rb = fmax(rb, sh.red[w][1]); ol += sh.red[w][2];
+                sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5];
+            }
+            double r_exp = 0.0, r_comp = 0.0;
+            int bviol = 0;
+            for (int s2 = 0; s2 < S; ++s2) {
+                const double ssum = sh.secsum[s2];
+                const double hi = P.band_hi[a * S + s2], lo = P.band_lo[a * S + s2];
+                r_exp = fmax(r_exp, fmax(lo - ssum, ssum - hi));
+                const int wb = P.wband[a * S + s2];
+                const double ls = sh.lam_s[s2];
+                if (wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p) ++bviol;   // dropped dependent row
+                if (wb == 0) {
+                    if (ssum > hi + tol_p) { ++bviol; P.wband[a * S + s2] = 1; }
+                    else if (ssum < lo - tol_p) { ++bviol; P.wband[a * S + s2] = -1; }
+                } else if (wb > 0) {
+                    r_comp = fmax(r_comp, fabs(ls) * fabs(hi - ssum));
+                    if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); P.wband[a * S + s2] = 0; }
+                } else {
+                    r_comp = fmax(r_comp, fabs(ls) * fabs(ssum - lo));
+                    if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); P.wband[a * S + s2] = 0; }
+                }
+            }
+            double r_turn = 0.0;
+            const double tau = P.tau[a];
+            if (isfinite(tau)) {
+                r_turn = fmax(tu - tau, 0.0);
+                if (!P.wcap[a]) {
+                    if (tu > tau + tol_p) { ++bviol; P.wcap[a] = 1; }
+                } else {
+                    if (fabs(tu - tau) > tol_p) ++bviol;                        // dropped dependent row
+                    r_comp = fmax(r_comp, fabs(theta) * fabs(tau - tu));
+                    if (theta < -tol_d) { ++bviol; r_comp = fmax(r_comp, -theta); P.wcap[a] = 0; }
+                }
+            }
+            const double r_budget = fabs(sw - 1.0);
+            if (r_budget > tol_p) ++bviol;
+            const int total = int(nv) + bviol;
+            if (total > 0 && ndep > 0) {
+                // the working rows were dependent on the free set: free the fixed entry
+                // closest to leaving its breakpoint, in the direction of least resistance
+                double bm = INFINITY;
+                int who = 0;
+                for (int w = 0; w < PB / 32; ++w)
+                    if (sh.mmin[w] < bm || (sh.mmin[w] == bm && abs(sh.mwho[w]) < abs(who))) { bm = sh.mmin[w]; who = sh.mwho[w]; }
+                if (who != 0) {
+                    const size_t e = base + (abs(who) - 1);
+                    const int j = P.st[e];
+                    if (j < ST_FREE) P.st[e] = (int8_t)(who > 0 ? ST_FREE + j : ST_FREE + j - 1);
+                }
+            }
+            double* dg = P.diag + (size_t)a * PRISM_NDIAG;
+            dg[PRISM_DIAG_BUDGET] = r_budget;
+            dg[PRISM_DIAG_BOX] = fmax(rb, 0.0);
+            dg[PRISM_DIAG_EXPOSURE] = fmax(r_exp, 0.0);
+            dg[PRISM_DIAG_TURNOVER] = r_turn;
+            dg[PRISM_DIAG_STAT] = rs;
+            dg[PRISM_DIAG_COMP] = r_comp;
+            dg[PRISM_DIAG_OBJ] = quad + ol;
+            dg[PRISM_DIAG_ITERS] = dg[PRISM_DIAG_ITERS] + 1.0;
+            P.nu[a] = nu;
+            P.theta[a] = theta;
+            for (int s2 = 0; s2 < S; ++s2) P.lam[a * S + s2] = sh.lam_s[s2];
+            if (total == 0) P.done[a] = 1;
+            sh.go = (total > 0);
         }
+        __syncthreads();
+        if (!sh.go) break;
     }
-    double* dg = P.diag + (size_t)a * PRISM_NDIAG;
-    dg[PRISM_DIAG_BUDGET] = r_budget;
-    dg[PRISM_DIAG_BOX] = fmax(rb, 0.0);
-    dg[PRISM_DIAG_EXPOSURE] = fmax(r_exp, 0.0);
-    dg[PRISM_DIAG_TURNOVER] = r_turn;
-    dg[PRISM_DIAG_STAT] = rs;
-    dg[PRISM_DIAG_COMP] = r_comp;
-    dg[PRISM_DIAG_OBJ] = P.quad[a] + ol;
-    dg[PRISM_DIAG_ITERS] = dg[PRISM_DIAG_ITERS] + 1.0;
-    if (total == 0) P.done[a] = 1;
-    else atomicAdd(P.pending, 1);
 }
 
 // Diagnostics of the fallback weights (no multipliers: stationarity is not certified).
@@ -767,18 +915,14 @@ __global__ void k_fallback_weights(PolDev P) {
     for (int p = threadIdx.x; p < P.N; p += blockDim.x) P.W[base + p] = double(P.z[base + p]);
 }
 
-size_t polish_smem_bytes() { return sizeof(SolveShared); }
+size_t polish_smem_bytes() { return sizeof(PolishShared); }
 
 void launch_classify(const PolDev& P, cudaStream_t st) { k_classify<<<P.M, PB, 0, st>>>(P); }
 
-// One polish round: FP64 solve, batched FP32 gradient product, checks. Accounts that
-// still need work add themselves to *P.pending.
-void launch_polish_round(const PolDev& P, cudaStream_t st) {
-    cudaFuncSetAttribute(k_pol_solve, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(SolveShared));
-    cudaMemsetAsync(P.pending, 0, sizeof(int), st);
-    k_pol_solve<<<P.M, PB, sizeof(SolveShared), st>>>(P);
-    launch_gradient_product(P, st);
-    k_pol_check<<<P.M, PB, 0, st>>>(P);
+// Up to `rounds` active-set rounds for every account not yet settled, in one launch.
+void launch_polish(const PolDev& P, int rounds, cudaStream_t st) {
+    cudaFuncSetAttribute(k_polish, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(PolishShared));
+    k_polish<<<P.M, PB, sizeof(PolishShared), st>>>(P, rounds);
 }
 
 void launch_fallback(const PolDev& P, cudaStream_t st) {

@@ -13,8 +13,15 @@ struct PolDev {
     const double* f64 = nullptr;
     const double* d64 = nullptr;
     const double* mu64 = nullptr;
-    const float* B32 = nullptr;         // FP32 B for the batched gradient product
+    const float* B32 = nullptr;         // FP32 B (Npad x K)
+    const float* B32p = nullptr;        // FP32 B zero-padded to 64 factors (Npad x 64)
     const double* Bn1 = nullptr;        // sum_k |B_ik| per asset (error bound of that product)
+    const float* Bn1f = nullptr;        // its FP32 copy
+    const float* mu32 = nullptr;
+    const float* w0f = nullptr;         // FP32 copies of the per-entry data (M x Npad)
+    const float* lof = nullptr;
+    const float* upf = nullptr;
+    const float* cf = nullptr;
     const int* sec_start = nullptr;
     const int* sector = nullptr;
     const double* w0 = nullptr;         // M x Npad
@@ -43,15 +50,15 @@ struct PolDev {
     int* Flist = nullptr;               // M x FMAX
     int* NZlist = nullptr;              // M x FMAX
     double* Fsig = nullptr;             // M x FMAX cap sign of each free entry
+    double* Fdinv = nullptr;            // M x FMAX 1/d of each free entry
     double* Y = nullptr;                // M x FMAX x (PMAXROWS + 1)
     int FMAX = 0;
     double* fh64 = nullptr;             // M x 64: f .* (B' w) of the solved point
     float* fh32 = nullptr;              // M x K, its FP32 copy (operand of the product)
-    float* G32 = nullptr;               // M x Npad: B (f .* h) in FP32
     double* quad = nullptr;             // M: w' B F B' w
     double* fhmax = nullptr;            // M: max_k |f_k h_k|
     int* ndep = nullptr;                // M: working rows dependent on the free set
-    int* pending = nullptr;             // 1: accounts that need another round
+    int* pending = nullptr;             // unused
     // outputs
     double* W = nullptr;                // M x Npad weights (FP64)
     double* nu = nullptr;               // M
@@ -65,9 +72,8 @@ struct PolDev {
 
 size_t polish_smem_bytes();
 void launch_classify(const PolDev& P, cudaStream_t st);
-void launch_polish_round(const PolDev& P, cudaStream_t st);
+void launch_polish(const PolDev& P, int rounds, cudaStream_t st);
 void launch_fallback(const PolDev& P, cudaStream_t st);
 void launch_finish_status(const PolDev& P, double eps, cudaStream_t st);
-void launch_gradient_product(const PolDev& P, cudaStream_t st);   // admm.cu
 
 }  // namespace prism

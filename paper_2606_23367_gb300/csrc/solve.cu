@@ -396,8 +396,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
         P.Y = A.take<double>((size_t)M * FMAX * (PMAXROWS + 1));
+        P.Fdinv = A.take<double>((size_t)M * FMAX);
         P.fh64 = A.take<double>((size_t)M * KMAX); P.fh32 = A.take<float>((size_t)M * K);
-        P.G32 = A.take<float>(MN); P.quad = A.take<double>(M); P.fhmax = A.take<double>(M);
+        P.quad = A.take<double>(M); P.fhmax = A.take<double>(M);
         P.ndep = A.take<int>(M); P.pending = A.take<int>(1);
         P.W = A.take<double>(MN); P.nu = A.take<double>(M); P.lam = A.take<double>((size_t)M * S);
         P.theta = A.take<double>(M); P.diag = A.take<double>((size_t)M * PRISM_NDIAG);
@@ -569,7 +570,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.adapt_every = 25;
     P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;
     P.B64 = U.d_B64; P.f64 = U.d_f64; P.d64 = U.d_d64; P.mu64 = U.d_mu64; P.sec_start = U.d_sec_start; P.sector = U.d_sector;
-    P.B32 = U.d_B32; P.Bn1 = U.d_Bn1;
+    P.B32 = U.d_B32; P.B32p = U.d_B32p; P.Bn1 = U.d_Bn1; P.Bn1f = U.d_Bn1f; P.mu32 = U.d_mu32;
+    P.w0f = BD.w0f; P.lof = BD.lof; P.upf = BD.upf; P.cf = BD.cf;
     P.w0 = BD.w0; P.lo = BD.lo; P.up = BD.up; P.c = BD.c;
     P.pw_idx = pwidx; P.pw_bp = BD.pw_bp; P.pw_sl = BD.pw_sl; P.pw_phi_lo = (const double*)stage[6]; P.pw_nbp = BD.pw_nbp;
     P.band_lo = BD.band_lo; P.band_hi = BD.band_hi; P.tau = BD.tau;
@@ -693,15 +695,10 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     const int rounds = std::max(1, o->polish_rounds);
     // polish rounds until no account needs another (checked after each round)
     int n_rounds_run = 0, n_retried = 0;
+    // all active-set rounds of every account in one launch; each block stops when settled
     auto polish_rounds = [&]() -> int {
-        for (int r = 0; r < rounds; ++r) {
-            ++n_rounds_run;
-            SC.prof.run(PRISM_K_POLISH, 3, st, [&] { launch_polish_round(P, st); });
-            cudaMemcpyAsync(SC.pinned + 2, P.pending, 4, cudaMemcpyDeviceToHost, st);
-            if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
-            if (std::getenv("PRISM_DEBUG_STATS")) std::fprintf(stderr, "prism stats: polish round %d pending %d\n", r, SC.pinned[2]);
-            if (SC.pinned[2] == 0) break;
-        }
+        ++n_rounds_run;
+        SC.prof.run(PRISM_K_POLISH, 1, st, [&] { launch_polish(P, rounds, st); });
         return 0;
     };
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });

@@ -109,13 +109,14 @@ __global__ void k_cinv(const double* __restrict__ G, const double* __restrict__ 
 }
 
 __global__ void k_convert_B(const double* __restrict__ B64, int Npad, int K, float* __restrict__ B32,
-                            __nv_bfloat16* __restrict__ B16, __nv_bfloat16* __restrict__ Bt16,
+                            float* __restrict__ B32p, __nv_bfloat16* __restrict__ B16, __nv_bfloat16* __restrict__ Bt16,
                             __nv_bfloat16* __restrict__ B16p, __nv_bfloat16* __restrict__ Bt16p) {
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)Npad * K) return;
     int i = int(e / K), k = int(e % K);
     double b = B64[e];
     B32[e] = float(b);
+    B32p[(size_t)i * KMAX + k] = float(b);
     __nv_bfloat16 h = __float2bfloat16_rn(float(b));
     B16[e] = h;
     Bt16[(size_t)k * Npad + i] = h;
@@ -151,8 +152,8 @@ static int fetch(const T* src, size_t n, std::vector<T>& dst) {
 }
 
 static void free_universe(Universe& U) {
-    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1,
-                    U.d_mu64, U.d_B32, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
+    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1, U.d_Bn1f,
+                    U.d_mu64, U.d_B32, U.d_B32p, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
                     U.d_Cinv32, U.d_Cinv16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
@@ -240,6 +241,7 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     std::vector<double> bn1(Npad, 0.0);
     for (int p = 0; p < N; ++p)
         for (int k = 0; k < K; ++k) bn1[p] += std::fabs(Bs[(size_t)p * K + k]);
+    std::vector<float> bn1f(bn1.begin(), bn1.end());
     cudaError_t se = cudaStreamCreateWithFlags(&U.stream, cudaStreamNonBlocking);
     if (se != cudaSuccess) { set_error(cudaGetErrorString(se)); return PRISM_ERR_CUDA; }
     TRY(dalloc(U, &U.d_inv_perm, N));
@@ -251,7 +253,9 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     TRY(dalloc(U, &U.d_d64, Npad));
     TRY(dalloc(U, &U.d_mu64, Npad));
     TRY(dalloc(U, &U.d_Bn1, Npad));
+    TRY(dalloc(U, &U.d_Bn1f, Npad));
     TRY(dalloc(U, &U.d_B32, (size_t)Npad * K));
+    TRY(dalloc(U, &U.d_B32p, (size_t)Npad * KMAX));
     TRY(dalloc(U, &U.d_f32, K));
     TRY(dalloc(U, &U.d_d32, Npad));
     TRY(dalloc(U, &U.d_mu32, Npad));
@@ -273,6 +277,7 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         H2D(U.d_d64, ds.data(), Npad * sizeof(double)) ||
         H2D(U.d_mu64, mus.data(), Npad * sizeof(double)) ||
         H2D(U.d_Bn1, bn1.data(), Npad * sizeof(double)) ||
+        H2D(U.d_Bn1f, bn1f.data(), Npad * sizeof(float)) ||
         H2D(U.d_f32, f32.data(), K * sizeof(float)) ||
         H2D(U.d_d32, d32.data(), Npad * sizeof(float)) ||
         H2D(U.d_mu32, mu32.data(), Npad * sizeof(float))) {
@@ -282,9 +287,10 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     }
     {
         size_t n = (size_t)Npad * K;
+        cudaMemsetAsync(U.d_B32p, 0, (size_t)Npad * KMAX * 4, U.stream);
         cudaMemsetAsync(U.d_B16p, 0, (size_t)Npad * KMAX * 2, U.stream);
         cudaMemsetAsync(U.d_Bt16p, 0, (size_t)KMAX * Npad * 2, U.stream);
-        k_convert_B<<<(unsigned)cdiv64(n, 256), 256, 0, U.stream>>>(U.d_B64, Npad, K, U.d_B32, U.d_B16, U.d_Bt16,
+        k_convert_B<<<(unsigned)cdiv64(n, 256), 256, 0, U.stream>>>(U.d_B64, Npad, K, U.d_B32, U.d_B32p, U.d_B16, U.d_Bt16,
                                                                       U.d_B16p, U.d_Bt16p);
         double* G = nullptr;
         if (cudaMalloc(&G, (size_t)NRHO * K * K * sizeof(double)) != cudaSuccess) {
