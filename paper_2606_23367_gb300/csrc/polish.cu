@@ -190,6 +190,8 @@ struct PolishShared {
     int rows[PMAXROWS];
     int nrows, nF, nNZ, fail, nc, go;
     int cntF[PB / 32], cntN[PB / 32];
+    int qp[PB / 32][64];                  // per-warp queue of entries that need FP64 work
+    float qg[PB / 32][64];
     double sumA[PB / 32], capA[PB / 32];
     double lam_s[SMAX];
     double red[PB / 32][8];
@@ -205,6 +207,40 @@ struct FreeSet {
     double* dinv;
     double* sig;
     bool in_smem;
+};
+
+// Per-warp queue: entries whose checks need FP64 arithmetic are gathered so that the
+// (slow on this part) FP64 pipe runs them 32 at a time instead of one lane per warp
+struct WarpQueue {
+    int* p;
+    float* g;
+    int n = 0;
+    __device__ void push(bool need, int q, float gv, int lane) {
+        const unsigned b = __ballot_sync(0xffffffffu, need);
+        if (need) {
+            const int pos = n + __popc(b & ((1u << lane) - 1u));
+            p[pos] = q;
+            g[pos] = gv;
+        }
+        n += __popc(b);
+        __syncwarp();
+    }
+    // run body(q, g) on 32 queued entries at a time (on all that remain when ``all``)
+    template <class Body>
+    __device__ void drain(bool all, int lane, Body&& body) {
+        while (n >= 32 || (all && n > 0)) {
+            const int take = min(n, 32), rest = n - take;
+            if (lane < take) body(p[lane], g[lane]);
+            __syncwarp();
+            int tq = 0;
+            float tg = 0.f;
+            if (lane < rest) { tq = p[32 + lane]; tg = g[32 + lane]; }
+            __syncwarp();
+            if (lane < rest) { p[lane] = tq; g[lane] = tg; }
+            __syncwarp();
+            n = rest;
+        }
+    }
 };
 
 // coefficient of free entry p (cap sign sig) in working row ``row``
@@ -279,6 +315,24 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         const int w0r = min(N, warp * Lw), w1r = min(N, w0r + Lw);
         int nf = 0, nn = 0;
         double sa = 0.0, ca = 0.0;
+        WarpQueue wq;
+        wq.p = sh.qp[warp];
+        wq.g = sh.qg[warp];
+        auto fixed_or_free = [&](int p, float) {
+            const int code = P.st[base + p];
+            Pieces pc;
+            entry_pieces(P, base + p, pc);
+            if (code >= ST_FREE) {
+                ++nf;
+                ca -= seg_sign(pc, code - ST_FREE) * pc.w0;
+            } else {
+                const double wv = pc.bp[code];
+                W[p] = wv;
+                sa += wv;
+                ca += fabs(wv - pc.w0);
+                nn += (wv != 0.0);
+            }
+        };
         for (int p0 = w0r; p0 < w1r; p0 += 32 * AU) {
             int code[AU], pwv[AU];
             float w0v[AU], lov[AU];
@@ -294,29 +348,15 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
 #pragma unroll
             for (int u = 0; u < AU; ++u) {
                 const int p = p0 + 32 * u + lane;
-                int isF = 0, isNZ = 0;
-                if (p < w1r) {
-                    if (code[u] == 0 && w0v[u] == 0.f && lov[u] == 0.f && pwv[u] < 0) {
-                        W[p] = 0.0;
-                    } else {
-                        Pieces pc;
-                        entry_pieces(P, base + p, pc);
-                        if (code[u] >= ST_FREE) {
-                            isF = 1;
-                            ca -= seg_sign(pc, code[u] - ST_FREE) * pc.w0;
-                        } else {
-                            const double wv = pc.bp[code[u]];
-                            W[p] = wv;
-                            sa += wv;
-                            ca += fabs(wv - pc.w0);
-                            isNZ = (wv != 0.0);
-                        }
-                    }
-                }
-                nf += __popc(__ballot_sync(0xffffffffu, isF));
-                nn += __popc(__ballot_sync(0xffffffffu, isNZ));
+                const bool zero_fixed = code[u] == 0 && w0v[u] == 0.f && lov[u] == 0.f && pwv[u] < 0;
+                if (p < w1r && zero_fixed) W[p] = 0.0;
+                wq.push(p < w1r && !zero_fixed, p, 0.f, lane);
             }
+            wq.drain(false, lane, fixed_or_free);
         }
+        wq.drain(true, lane, fixed_or_free);
+        nf = warp_sum(nf);
+        nn = warp_sum(nn);
         sa = warp_sum(sa);
         ca = warp_sum(ca);
         if (lane == 0) { sh.cntF[warp] = nf; sh.cntN[warp] = nn; sh.sumA[warp] = sa; sh.capA[warp] = ca; }
@@ -636,51 +676,11 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         int nviol = 0;
         double my_margin = INFINITY;
         int my_who = 0;
-        // lane (4 r + j) holds columns 16 i + 4 j .. + 3 (i < 4) of fh in FP32
-        float4 fr[4];
-#pragma unroll
-        for (int i = 0; i < 4; ++i) fr[i] = *reinterpret_cast<const float4*>(&sh.fh32[16 * i + 4 * (lane & 3)]);
-        const int ntiles = cdiv(N, 32);
-        for (int ti = warp; ti < ntiles; ti += PB / 32) {
-            const int p = ti * 32 + lane;                 // entries of padding (p >= N) are skipped below
+        // FP64 checks of one entry (run 32 entries at a time from the warp's queue)
+        auto check_entry = [&](int p, float g32) {
             const size_t e = base + p;
             const int code = P.st[e];
-            const int pwv = P.pw_idx ? P.pw_idx[e] : -1;
             const int sec = P.sector[p];
-            const float w0v = P.w0f[e], lov = P.lof[e], upv = P.upf[e], cv = P.cf[e];
-            const float muf = P.mu32[p], bn1f = P.Bn1f[p];
-            // g32 = B_p . fh for the tile's 32 rows: four rows of 64 floats per group of 8 lanes x 4
-            // float4, coalesced over the tile's contiguous 8 KB; lane p ends with its own row
-            float g32 = 0.f;
-            const float* Bt = P.B32p + (size_t)ti * 32 * KMAX;
-#pragma unroll
-            for (int grp = 0; grp < 4; ++grp) {
-                const float4* Br = reinterpret_cast<const float4*>(Bt + (size_t)(grp * 8 + (lane >> 2)) * KMAX) + (lane & 3);
-                float acc = 0.f;
-#pragma unroll
-                for (int i = 0; i < 4; ++i) {
-                    const float4 b = __ldg(Br + 4 * i);
-                    acc = fmaf(b.x, fr[i].x, acc);
-                    acc = fmaf(b.y, fr[i].y, acc);
-                    acc = fmaf(b.z, fr[i].z, acc);
-                    acc = fmaf(b.w, fr[i].w, acc);
-                }
-                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
-                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
-                const float v = __shfl_sync(0xffffffffu, acc, 4 * (lane & 7));
-                if ((lane >> 3) == grp) g32 = v;
-            }
-            if (p >= N) continue;
-            if (pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv > 0.f) {
-                const float lam_f = float(sh.lam_s[sec]);
-                const float rr = 2.f * g32 - muf + nu_f + lam_f;
-                const float up = -rr - (cv + theta_f);
-                const float delta = 1e-5f * (2.f * bn1f * fhmax_f + fabsf(muf) + fabsf(nu_f) + fabsf(lam_f)) + 1e-9f;
-                if (up < -delta) {
-                    if (double(-up) < my_margin) { my_margin = double(-up); my_who = p + 1; }
-                    continue;
-                }
-            }
             EntryRaw rw;
             load_raw(P, base, p, rw);
             Pieces pc;
@@ -730,7 +730,59 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 if (up > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j); }
                 else if (dn > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j - 1); }
             }
+        };
+        float fmargin = INFINITY;
+        int fwho = 0;
+        // lane (4 r + j) holds columns 16 i + 4 j .. + 3 (i < 4) of fh in FP32
+        float4 fr[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) fr[i] = *reinterpret_cast<const float4*>(&sh.fh32[16 * i + 4 * (lane & 3)]);
+        const int ntiles = cdiv(N, 32);
+        for (int ti = warp; ti < ntiles; ti += PB / 32) {
+            const int p = ti * 32 + lane;                 // entries of padding (p >= N) are skipped below
+            const size_t e = base + p;
+            const int code = P.st[e];
+            const int pwv = P.pw_idx ? P.pw_idx[e] : -1;
+            const int sec = P.sector[p];
+            const float w0v = P.w0f[e], lov = P.lof[e], upv = P.upf[e], cv = P.cf[e];
+            const float muf = P.mu32[p], bn1f = P.Bn1f[p];
+            // g32 = B_p . fh for the tile's 32 rows: four rows of 64 floats per group of 8 lanes x 4
+            // float4, coalesced over the tile's contiguous 8 KB; lane p ends with its own row
+            float g32 = 0.f;
+            const float* Bt = P.B32p + (size_t)ti * 32 * KMAX;
+#pragma unroll
+            for (int grp = 0; grp < 4; ++grp) {
+                const float4* Br = reinterpret_cast<const float4*>(Bt + (size_t)(grp * 8 + (lane >> 2)) * KMAX) + (lane & 3);
+                float acc = 0.f;
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                    const float4 b = __ldg(Br + 4 * i);
+                    acc = fmaf(b.x, fr[i].x, acc);
+                    acc = fmaf(b.y, fr[i].y, acc);
+                    acc = fmaf(b.z, fr[i].z, acc);
+                    acc = fmaf(b.w, fr[i].w, acc);
+                }
+                acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+                acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+                const float v = __shfl_sync(0xffffffffu, acc, 4 * (lane & 7));
+                if ((lane >> 3) == grp) g32 = v;
+            }
+            bool need = p < N;
+            if (need && pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv > 0.f) {
+                const float lam_f = float(sh.lam_s[sec]);
+                const float rr = 2.f * g32 - muf + nu_f + lam_f;
+                const float up = -rr - (cv + theta_f);
+                const float delta = 1e-5f * (2.f * bn1f * fhmax_f + fabsf(muf) + fabsf(nu_f) + fabsf(lam_f)) + 1e-9f;
+                if (up < -delta) {
+                    if (-up < fmargin) { fmargin = -up; fwho = p + 1; }
+                    need = false;
+                }
+            }
+            wq.push(need, p, g32, lane);
+            wq.drain(false, lane, check_entry);
         }
+        wq.drain(true, lane, check_entry);
+        if (double(fmargin) < my_margin) { my_margin = double(fmargin); my_who = fwho; }
         r_stat = warp_max(r_stat); r_box = warp_max(r_box);
         obj_lin = warp_sum(obj_lin); sum_w = warp_sum(sum_w); turn = warp_sum(turn);
         nviol = warp_sum(nviol);
