@@ -214,7 +214,7 @@ struct FreeSet {
 struct WarpQueue {
     int* p;
     float* g;
-    int n = 0;
+    int n = 0;                            // queued entries (at most 63: one push onto at most 31)
     __device__ void push(bool need, int q, float gv, int lane) {
         const unsigned b = __ballot_sync(0xffffffffu, need);
         if (need) {
@@ -351,8 +351,8 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 const bool zero_fixed = code[u] == 0 && w0v[u] == 0.f && lov[u] == 0.f && pwv[u] < 0;
                 if (p < w1r && zero_fixed) W[p] = 0.0;
                 wq.push(p < w1r && !zero_fixed, p, 0.f, lane);
+                wq.drain(false, lane, fixed_or_free);     // keeps at most 31 queued before a push
             }
-            wq.drain(false, lane, fixed_or_free);
         }
         wq.drain(true, lane, fixed_or_free);
         nf = warp_sum(nf);
