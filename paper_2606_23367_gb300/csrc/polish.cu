@@ -810,15 +810,20 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5];
             }
             double r_exp = 0.0, r_comp = 0.0;
-            int bviol = 0;
+            int bviol = 0, dep_in = 0, dep_out = 0;
             for (int s2 = 0; s2 < S; ++s2) {
                 const double ssum = sh.secsum[s2];
                 const double hi = P.band_hi[a * S + s2], lo = P.band_lo[a * S + s2];
                 r_exp = fmax(r_exp, fmax(lo - ssum, ssum - hi));
                 const int wb = P.wband[a * S + s2];
                 const double ls = sh.lam_s[s2];
-                if (wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p) ++bviol;   // dropped dependent row
-                if (wb == 0) {
+                if (wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p) {
+                    // a dependent working row (dropped from the solve): inside the band it is
+                    // inactive and leaves the working set; outside, a fixed entry is released
+                    ++bviol;
+                    if (wb > 0 ? ssum < hi : ssum > lo) { P.wband[a * S + s2] = 0; ++dep_in; }
+                    else ++dep_out;
+                } else if (wb == 0) {
                     if (ssum > hi + tol_p) { ++bviol; P.wband[a * S + s2] = 1; }
                     else if (ssum < lo - tol_p) { ++bviol; P.wband[a * S + s2] = -1; }
                 } else if (wb > 0) {
@@ -836,7 +841,11 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 if (!P.wcap[a]) {
                     if (tu > tau + tol_p) { ++bviol; P.wcap[a] = 1; }
                 } else {
-                    if (fabs(tu - tau) > tol_p) ++bviol;                        // dropped dependent row
+                    if (fabs(tu - tau) > tol_p) {                               // dependent row
+                        ++bviol;
+                        if (tu < tau) { P.wcap[a] = 0; ++dep_in; }
+                        else ++dep_out;
+                    }
                     r_comp = fmax(r_comp, fabs(theta) * fabs(tau - tu));
                     if (theta < -tol_d) { ++bviol; r_comp = fmax(r_comp, -theta); P.wcap[a] = 0; }
                 }
@@ -844,9 +853,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             const double r_budget = fabs(sw - 1.0);
             if (r_budget > tol_p) ++bviol;
             const int total = int(nv) + bviol;
-            if (total > 0 && ndep > 0) {
-                // the working rows were dependent on the free set: free the fixed entry
-                // closest to leaving its breakpoint, in the direction of least resistance
+            if (dep_out > 0 || (total > 0 && ndep > 0 && dep_in == 0)) {
+                // a working row is dependent on the free set and cannot be met by it: free the
+                // fixed entry closest to leaving its breakpoint, in the direction of least resistance
                 double bm = INFINITY;
                 int who = 0;
                 for (int w = 0; w < PB / 32; ++w)
