@@ -695,11 +695,366 @@ __global__ void __launch_bounds__(640, 1) k_prox_smem(Dev D) {
     prox_account(D, S, a, sh);
 }
 
+// ---------------------------------------------------------------------------
+// G5/G6, streaming form (accounts with the L1 cost only and no turnover cap).
+//
+// z_i(eta) is nonincreasing in eta and equals l_i for every eta at or above the
+// point where it first reaches l_i. With L = nu_prev - margin, an entry with
+// z_i(L) == l_i takes z = l_i at every eta >= L: its new z, y and X are written
+// during the single streaming pass. The other entries (held positions and names
+// near activation, typically around 1% of the universe) are kept in shared
+// memory for the root searches and written at the end. The budget equation is
+// solved directly as
+//     sum_s clamp(S_s(nu), lo_s, hi_s) = 1,
+// which equals sum_s S_s(clamp(nu, eta_hi_s, eta_lo_s)) with the sector-edge
+// roots (S_s nonincreasing); edge roots are found only for sectors that bind.
+// A sector whose kept entries overflow their slots evaluates the rest of its
+// range from global memory. If a root lies below L (the budget root when
+// T(L) < 1, or a lower band edge), the sectors concerned are recomputed from
+// global memory and this call reports infinite residuals (their old z and y
+// are gone), so the account simply does not stop on this call.
+// Global traffic per entry: one read of (v, w0, l, u, c, z, y) and one write of
+// (z, y, X), the algorithmic minimum of the step.
+// ---------------------------------------------------------------------------
+constexpr int SP_WARPS = 10;            // warps per block; warp w owns sectors w, w + 10, ...
+constexpr int SP_CW = 128;              // kept-entry slots per warp
+
+struct StreamShared {
+    float blo[SMAX], bhi[SMAX];
+    float SL[SMAX], sumlo[SMAX], Sx[SMAX];
+    int CL[SMAX], Cx[SMAX];
+    int cb[SMAX], ce[SMAX];             // slot range of each sector
+    int gs[SMAX];                       // positions [gs, end) of the sector are read from global memory
+    float eta_hi[SMAX], eta_lo[SMAX];
+    float red5[5][SP_WARPS];
+    int red_bad[SP_WARPS];
+    int newj;
+    // kept entries
+    float v[SP_WARPS * SP_CW], w0[SP_WARPS * SP_CW], lo[SP_WARPS * SP_CW], up[SP_WARPS * SP_CW];
+    float k[SP_WARPS * SP_CW], zo[SP_WARPS * SP_CW], yo[SP_WARPS * SP_CW];
+    int pos[SP_WARPS * SP_CW];
+};
+
+// prox of c|.-w0|/rho on [l, u] at t = v - eta/rho with k = c/rho precomputed (the L1
+// branch of eval_entry at theta = 0, bit for bit)
+__device__ __forceinline__ EntryEval eval_l1(float v, float w0, float lo, float up, float k, float eta, float irho) {
+    EntryEval r;
+    const float t = v - eta * irho;
+    float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+    z = fminf(fmaxf(z, lo), up);
+    r.z = z;
+    r.lin = (z > lo && z < up && z != w0) ? 1 : 0;
+    return r;
+}
+
+// Warp-collective S_s(eta) and the count of entries on a linear piece, for sector s.
+__device__ __forceinline__ void stream_sector_eval(const Dev& D, const StreamShared& sh, const GlobalSrc& G, int s,
+                                                   float eta, float irho, float& sum, int& cnt) {
+    const int lane = threadIdx.x & 31;
+    float acc = 0.f;
+    int n = 0;
+    for (int q = sh.cb[s] + lane; q < sh.ce[s]; q += 32) {
+        const EntryEval r = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], eta, irho);
+        acc += r.z;
+        n += r.lin;
+    }
+    for (int p = sh.gs[s] + lane; p < D.sec_start[s + 1]; p += 32) {
+        const EntryEval r = eval_entry(D, G, p, eta, 0.f, irho);
+        acc += r.z;
+        n += r.lin;
+    }
+    sum = warp_sum(acc) + sh.sumlo[s];
+    cnt = warp_sum(n);
+}
+
+// Residual maxima of one entry's update, then the writes of z, y, X.
+struct StreamRes {
+    float rp = 0.f, rd = 0.f, nx = 0.f, nz = 0.f, ny = 0.f;
+    int bad = 0;
+    __device__ __forceinline__ void put(const Dev& D, size_t e, float z, float v, float zo, float yo, float mu,
+                                        float dd, float rho, float irho) {
+        const float yn = rho * (v - z);
+        rp = fmaxf(rp, fabsf(yn - yo) * irho);
+        rd = fmaxf(rd, rho * fabsf(z - zo));
+        nx = fmaxf(nx, fabsf(v - yo * irho));
+        nz = fmaxf(nz, fabsf(z));
+        ny = fmaxf(ny, fabsf(yn));
+        bad |= !(isfinite(z) && isfinite(yn));
+        D.z[e] = z;
+        D.y[e] = yn;
+        store_X(D, e, (mu + rho * z - yn) / (2.f * dd + rho));
+    }
+};
+
+__global__ void __launch_bounds__(32 * SP_WARPS, 3) k_prox_stream(Dev D) {
+    const int a = blockIdx.x;
+    if (!D.active[a]) return;
+    extern __shared__ float4 dyn4[];
+    StreamShared& sh = *reinterpret_cast<StreamShared*>(dyn4);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int NS = D.S;
+    const unsigned lt = (1u << lane) - 1u;
+    for (int s = tid; s < NS; s += blockDim.x) {
+        sh.blo[s] = D.band_lo[a * NS + s];
+        sh.bhi[s] = D.band_hi[a * NS + s];
+    }
+    const size_t base = (size_t)a * D.Npad;
+    const GlobalSrc G(D, base);
+    const int j = D.rho_idx[a];
+    const float rho = rho_val(j), irho = 1.f / rho;
+    const float nu0 = D.nu[a];
+    const float margin = fmaxf(4.f * D.dnu[a], 2e-3f);  // in units of nu (a price), not of weights
+    const float L = nu0 - margin;
+    StreamRes res;
+    // ---- the streaming pass: every entry is evaluated at L; entries pinned at l are final
+    constexpr int CH = 4;
+    int wcnt = 0;                                   // slots used by this warp (uniform)
+    for (int s = warp; s < NS; s += SP_WARPS) {
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        const int start = wcnt;
+        int gs = p1;
+        float sL = 0.f, slo = 0.f;
+        int cL = 0;
+        for (int pb = p0 + lane; pb - lane < p1; pb += 32 * CH) {
+            float vv[CH], w0v[CH], lov[CH], upv[CH], cv[CH], zo[CH], yo[CH], mu[CH], dd[CH];
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int p = pb + 32 * c;
+                const bool in = p < p1;
+                vv[c] = in ? G.v[p] : 0.f;
+                w0v[c] = in ? G.w0[p] : 0.f;
+                lov[c] = in ? G.lo[p] : 0.f;
+                upv[c] = in ? G.up[p] : 0.f;
+                cv[c] = in ? G.c[p] : 0.f;
+                zo[c] = in ? D.z[base + p] : 0.f;
+                yo[c] = in ? D.y[base + p] : 0.f;
+                mu[c] = in ? D.mu32[p] : 0.f;
+                dd[c] = in ? D.d32[p] : 1.f;
+            }
+#pragma unroll
+            for (int c = 0; c < CH; ++c) {
+                const int p = pb + 32 * c;
+                const bool in = p < p1;
+                const float k = cv[c] * irho;
+                const EntryEval r = eval_l1(vv[c], w0v[c], lov[c], upv[c], k, L, irho);
+                const bool pinned = in && r.z == lov[c];
+                if (in) { sL += r.z; cL += r.lin; }
+                const int batch0 = pb - lane + 32 * c;   // first position of this row of the batch
+                if (batch0 >= gs) continue;             // the rest of the sector reads global memory later
+                const bool keep = in && !pinned;
+                const unsigned b = __ballot_sync(0xffffffffu, keep);
+                if (wcnt + __popc(b) > SP_CW) {
+                    gs = batch0;                        // overflow: from here on, global memory
+                    continue;
+                }
+                if (keep) {
+                    const int q = warp * SP_CW + wcnt + __popc(b & lt);
+                    sh.v[q] = vv[c]; sh.w0[q] = w0v[c]; sh.lo[q] = lov[c]; sh.up[q] = upv[c]; sh.k[q] = k;
+                    sh.zo[q] = zo[c]; sh.yo[q] = yo[c]; sh.pos[q] = p;
+                }
+                wcnt += __popc(b);
+                if (pinned) {
+                    slo += lov[c];
+                    res.put(D, base + p, lov[c], vv[c], zo[c], yo[c], mu[c], dd[c], rho, irho);
+                }
+            }
+        }
+        sL = warp_sum(sL);
+        slo = warp_sum(slo);
+        cL = warp_sum(cL);
+        if (lane == 0) {
+            sh.SL[s] = sL; sh.CL[s] = cL; sh.sumlo[s] = slo; sh.gs[s] = gs;
+            sh.cb[s] = warp * SP_CW + start;
+            sh.ce[s] = warp * SP_CW + wcnt;
+        }
+    }
+    __syncthreads();
+    // ---- budget multiplier
+    float TL = 0.f;
+    for (int s = 0; s < NS; ++s) TL += fminf(fmaxf(sh.SL[s], sh.blo[s]), sh.bhi[s]);
+    const bool below = !(TL >= 1.f - 1e-6f);           // the root lies below L (or T is not finite)
+    bool redo_all = below;
+    if (below) {
+        // every sector from global memory; the entries written above are redone
+        __syncthreads();
+        for (int s = tid; s < NS; s += blockDim.x) {
+            sh.gs[s] = D.sec_start[s];
+            sh.ce[s] = sh.cb[s];
+            sh.sumlo[s] = 0.f;
+        }
+        __syncthreads();
+    }
+    Root R;
+    root_init(R, nu0, 0.05f * rho + 1e-6f);
+    if (!below) R.a = L;
+    float x_eval = NAN;
+    if (!below && L > -INFINITY && TL <= 1.f + 1e-6f) {
+        R.x = L;                                         // L itself solves the budget equation
+        x_eval = L;
+        for (int s = tid; s < NS; s += blockDim.x) { sh.Sx[s] = sh.SL[s]; sh.Cx[s] = sh.CL[s]; }
+        __syncthreads();
+    } else {
+        for (int it = 0; it < PROX_MAXIT; ++it) {
+            for (int s = warp; s < NS; s += SP_WARPS) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
+                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
+            }
+            __syncthreads();
+            float T = 0.f;
+            int Cn = 0;
+            for (int s = 0; s < NS; ++s) {
+                const float v = sh.Sx[s];
+                T += fminf(fmaxf(v, sh.blo[s]), sh.bhi[s]);
+                if (v > sh.blo[s] && v < sh.bhi[s]) Cn += sh.Cx[s];
+            }
+            __syncthreads();
+            x_eval = R.x;
+            root_update(R, T - 1.f, Cn, rho, 1e-6f);
+            if (D.stats && tid == 0) atomicAdd(D.stats + 2, 1ull);
+            if (R.done) break;
+        }
+        if (R.x != x_eval) {
+            for (int s = warp; s < NS; s += SP_WARPS) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
+                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
+            }
+            __syncthreads();
+        }
+    }
+    const float nu = R.x;
+    // ---- edge roots of the sectors that bind (warp per sector), then the kept and
+    // global-memory entries of the sector
+    int redo_mine = 0;
+    for (int s = warp; s < NS; s += SP_WARPS) {
+        float eh = -FLT_MAX, el = FLT_MAX;
+        const float Sv = sh.Sx[s];
+        const float hi = sh.bhi[s], lo = sh.blo[s];
+        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
+            Root E;
+            const float w = D.eta_hi[a * NS + s];
+            root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.a = nu;
+            int it = 0;
+            for (; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
+            }
+            if (D.stats && lane == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
+            eh = E.x;
+        } else if (Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
+            if (!redo_all && sh.SL[s] < lo) {
+                // this sector's root lies below L: all of it from global memory
+                __syncwarp();
+                if (lane == 0) { sh.gs[s] = p0; sh.ce[s] = sh.cb[s]; sh.sumlo[s] = 0.f; }
+                __syncwarp();
+                redo_mine = 1;
+            }
+            Root E;
+            const float w = D.eta_lo[a * NS + s];
+            root_init(E, (w < nu && w > -FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.b = nu;
+            for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
+            }
+            el = E.x;
+        }
+        if (lane == 0) { sh.eta_hi[s] = eh; sh.eta_lo[s] = el; }
+        if (D.stats && lane == 0 && sh.gs[s] < p1) atomicAdd(D.stats + 3, 1ull);
+        const float arg = fminf(fmaxf(nu, eh), el);
+        for (int q = sh.cb[s] + lane; q < sh.ce[s]; q += 32) {
+            const int p = sh.pos[q];
+            const float z = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], arg, irho).z;
+            res.put(D, base + p, z, sh.v[q], sh.zo[q], sh.yo[q], D.mu32[p], D.d32[p], rho, irho);
+        }
+        for (int p = sh.gs[s] + lane; p < p1; p += 32) {
+            const float z = eval_entry(D, G, p, arg, 0.f, irho).z;
+            const size_t e = base + p;
+            res.put(D, e, z, G.v[p], D.z[e], D.y[e], D.mu32[p], D.d32[p], rho, irho);
+        }
+    }
+    float rp = warp_max(res.rp), rd = warp_max(res.rd), nx = warp_max(res.nx), nz = warp_max(res.nz),
+          ny = warp_max(res.ny);
+    int bad = warp_sum(res.bad) > 0 ? 1 : 0;
+    redo_mine = warp_sum(redo_mine);
+    if (lane == 0) {
+        sh.red5[0][warp] = rp; sh.red5[1][warp] = rd; sh.red5[2][warp] = nx; sh.red5[3][warp] = nz;
+        sh.red5[4][warp] = ny; sh.red_bad[warp] = bad | (redo_mine ? 2 : 0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int redo = redo_all ? 1 : 0;
+        bad = bad & 1;
+        redo |= sh.red_bad[0] >> 1;
+        for (int w = 1; w < SP_WARPS; ++w) {
+            rp = fmaxf(rp, sh.red5[0][w]); rd = fmaxf(rd, sh.red5[1][w]); nx = fmaxf(nx, sh.red5[2][w]);
+            nz = fmaxf(nz, sh.red5[3][w]); ny = fmaxf(ny, sh.red5[4][w]);
+            bad |= sh.red_bad[w] & 1;
+            redo |= sh.red_bad[w] >> 1;
+        }
+        if (redo) { rp = INFINITY; rd = INFINITY; }    // entries were rewritten: no residual this call
+        const int it = D.iters[a] + 1;
+        D.iters[a] = it;
+        if (D.stats) atomicAdd(D.stats, 1ull);
+        D.rp[a] = rp;
+        D.rd[a] = rd;
+        D.nu[a] = nu;
+        D.theta[a] = 0.f;
+        // the next call's margin: four times the last move of nu, or more after a miss
+        D.dnu[a] = redo ? fmaxf(fabsf(nu - nu0), margin) : fabsf(nu - nu0);
+        int newj = j;
+        if (bad) {
+            D.status[a] = PRISM_NUMERICAL_FAILURE;
+            D.active[a] = 0;
+        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
+            D.active[a] = 0;
+        } else if (it >= D.max_iter) {
+            D.active[a] = 0;
+            D.status[a] = PRISM_TIMEOUT;
+        } else if (!redo && it % D.adapt_every == 0) {
+            const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
+            const float du = rd / fmaxf(ny, 1e-12f);
+            const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
+            int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
+            dj = max(-4, min(4, dj));
+            newj = max(0, min(NRHO - 1, j + dj));
+        }
+        sh.newj = newj;
+    }
+    __syncthreads();
+    const int newj = sh.newj;
+    for (int s = tid; s < NS; s += blockDim.x) {
+        D.eta_hi[a * NS + s] = sh.eta_hi[s];
+        D.eta_lo[a * NS + s] = sh.eta_lo[s];
+    }
+    if (newj != j) {
+        if (tid == 0) D.rho_idx[a] = newj;
+        const float rn = rho_val(newj);
+        for (int p = tid; p < D.N; p += blockDim.x) {
+            const size_t e = base + p;
+            store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+        }
+    }
+}
+
+size_t prox_stream_smem_bytes(const Dev&) { return sizeof(StreamShared); }
+
 size_t prox_smem_bytes(const Dev& D) {
     return (size_t)D.Npad * 4 * (5 + (D.pw_idx ? 1 : 0));
 }
 
 void launch_prox(const Dev& D, cudaStream_t st) {
+    if (D.stream_prox) {
+        const size_t smem = prox_stream_smem_bytes(D);
+        cudaFuncSetAttribute(k_prox_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        k_prox_stream<<<D.M, 32 * SP_WARPS, smem, st>>>(D);
+        return;
+    }
     const int nw = std::min(20, std::max(4, D.S));      // at most 640 threads: warps loop over sectors
     const size_t smem = prox_smem_bytes(D);
     const size_t limit = 227 * 1024 - sizeof(ProxShared) - 1024;

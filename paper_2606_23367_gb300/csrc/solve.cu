@@ -389,7 +389,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.Q = A.take<float>((size_t)M * K);
         D.Qhi = A.take<__nv_bfloat16>((size_t)M * KMAX); D.Qlo = A.take<__nv_bfloat16>((size_t)M * KMAX);
         D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
-        D.nu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
+        D.nu = A.take<float>(M); D.dnu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
         D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(2);
         D.stats = A.take<unsigned long long>(4);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
@@ -565,6 +565,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
     D.pw_idx = pwidx; D.pw_bp = BD.pw_bpf; D.pw_sl = BD.pw_slf; D.pw_nbp = BD.pw_nbp;
     D.band_lo = BD.band_lof; D.band_hi = BD.band_hif; D.tau = BD.tauf;
+    D.stream_prox = (pwidx == nullptr && !BD.has_cap) ? 1 : 0;
     D.nsplit = nsplit;
     D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
     D.adapt_every = 25;
@@ -591,6 +592,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.iters, 0, M * 4, st);
         cudaMemsetAsync(D.status, 0, M * 4, st);
         cudaMemsetAsync(D.nu, 0, M * 4, st);
+        cudaMemsetAsync(D.dnu, 0x7f, M * 4, st);                    // 3.4e38: no margin yet
         cudaMemsetAsync(D.theta, 0, M * 4, st);
         cudaMemsetAsync(D.eta_hi, 0xff, (size_t)M * S * 4, st);   // NaN: no warm start yet
         cudaMemsetAsync(D.eta_lo, 0xff, (size_t)M * S * 4, st);
@@ -688,8 +690,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemcpyAsync(h, D.stats, 32, cudaMemcpyDeviceToHost, st);
         cudaStreamSynchronize(st);
         std::fprintf(stderr, "prism stats: ADMM iterations %d, prox account-calls %llu, sector-edge evals/call %.2f, "
-                     "budget evals/call %.2f\n", total_iters, h[0], h[0] ? double(h[1]) / h[0] : 0.0,
-                     h[0] ? double(h[2]) / h[0] : 0.0);
+                     "budget evals/call %.2f, sectors from global memory/call %.2f\n", total_iters, h[0],
+                     h[0] ? double(h[1]) / h[0] : 0.0, h[0] ? double(h[2]) / h[0] : 0.0,
+                     h[0] ? double(h[3]) / h[0] : 0.0);
     }
     // ---- polish, with up to two returns to the iterations at a tighter target
     const int rounds = std::max(1, o->polish_rounds);

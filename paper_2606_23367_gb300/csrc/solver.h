@@ -49,6 +49,7 @@ struct Dev {
     int* active = nullptr;
     int* status = nullptr;
     float* nu = nullptr;                // M warm start
+    float* dnu = nullptr;               // M last change of nu (margin of the streaming prox)
     float* eta_hi = nullptr;            // M x S warm start / result
     float* eta_lo = nullptr;            // M x S
     float* theta = nullptr;             // M cap multiplier
@@ -63,6 +64,7 @@ struct Dev {
     int adapt_every = 25;
     bool bf16 = false;                  // X / Q split in BF16 for tensor-core products
     int raw_out = 0;                    // diagnostics: G4 writes B Q itself into v
+    int stream_prox = 0;                // prox in the streaming form (no lots, no turnover cap)
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
 };
 
