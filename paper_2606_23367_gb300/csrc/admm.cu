@@ -132,7 +132,7 @@ __global__ void __launch_bounds__(256) k_gemm_P(Dev D) {
 #pragma unroll
         for (int q = 0; q < 8; ++q) {
             int k = kg + 8 * q;
-            if (k < K) D.Ppart[((size_t)split * D.M + m) * K + k] = acc[q];
+            if (k < K) D.Ppart[((size_t)split * D.M + m) * D.pstride + k] = acc[q];
         }
     }
 }
@@ -153,8 +153,8 @@ __global__ void k_small_solve(Dev D) {
     const int t = threadIdx.x;
     if (t < K) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
-        const float* pp = D.Ppart + (size_t)m * K + t;
-        const size_t stride = (size_t)D.M * K;
+        const float* pp = D.Ppart + (size_t)m * D.pstride + t;
+        const size_t stride = (size_t)D.M * D.pstride;
         int sp = 0;
         for (; sp + 8 <= D.nsplit; sp += 8)
 #pragma unroll
@@ -716,7 +716,7 @@ __global__ void __launch_bounds__(640, 1) k_prox_smem(Dev D) {
 // Global traffic per entry: one read of (v, w0, l, u, c, z, y) and one write of
 // (z, y, X), the algorithmic minimum of the step.
 // ---------------------------------------------------------------------------
-constexpr int SP_WARPS = 10;            // warps per block; warp w owns sectors w, w + 10, ...
+constexpr int SP_WARPS = 8;             // warps per block; warp w owns sectors w, w + 8, ...
 constexpr int SP_CW = 128;              // kept-entry slots per warp
 
 struct StreamShared {
@@ -729,6 +729,7 @@ struct StreamShared {
     float red5[5][SP_WARPS];
     int red_bad[SP_WARPS];
     int newj;
+    float nu;
     // kept entries
     float v[SP_WARPS * SP_CW], w0[SP_WARPS * SP_CW], lo[SP_WARPS * SP_CW], up[SP_WARPS * SP_CW];
     float k[SP_WARPS * SP_CW], zo[SP_WARPS * SP_CW], yo[SP_WARPS * SP_CW];
@@ -786,7 +787,114 @@ struct StreamRes {
     }
 };
 
-__global__ void __launch_bounds__(32 * SP_WARPS, 3) k_prox_stream(Dev D) {
+// S_s(eta) and its linear count by one lane: the sector's kept entries, then its
+// global-memory range (empty unless the sector was moved there)
+__device__ __forceinline__ void lane_sector_eval(const Dev& D, const StreamShared& sh, const GlobalSrc& G, int s,
+                                                 float eta, float irho, float& sum, int& cnt) {
+    float acc = sh.sumlo[s];
+    int n = 0;
+    for (int q = sh.cb[s]; q < sh.ce[s]; ++q) {
+        const EntryEval r = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], eta, irho);
+        acc += r.z;
+        n += r.lin;
+    }
+    for (int p = sh.gs[s]; p < D.sec_start[s + 1]; ++p) {
+        const EntryEval r = eval_entry(D, G, p, eta, 0.f, irho);
+        acc += r.z;
+        n += r.lin;
+    }
+    sum = acc;
+    cnt = n;
+}
+
+// Budget root and the edge roots of the binding sectors by warp 0 alone, lane s owning
+// sectors s and s + 32. Writes sh.nu, sh.eta_hi, sh.eta_lo (and moves a sector whose lower
+// edge lies below L to global memory).
+__device__ void lane_solve(const Dev& D, StreamShared& sh, const GlobalSrc& G, int a, float L, float TL, float nu0,
+                           float rho, float irho) {
+    const int lane = threadIdx.x & 31, NS = D.S;
+    const int s0 = lane, s1 = lane + 32;
+    float S0 = s0 < NS ? sh.SL[s0] : 0.f, S1 = s1 < NS ? sh.SL[s1] : 0.f;
+    Root R;
+    root_init(R, nu0, 0.05f * rho + 1e-6f);
+    R.a = L;
+    if (L > -INFINITY && TL <= 1.f + 1e-6f) {
+        R.x = L;                                         // L itself solves the budget equation
+    } else {
+        for (int it = 0; it < PROX_MAXIT; ++it) {
+            float T = 0.f;
+            int Cn = 0;
+            if (s0 < NS) {
+                int c;
+                lane_sector_eval(D, sh, G, s0, R.x, irho, S0, c);
+                T += fminf(fmaxf(S0, sh.blo[s0]), sh.bhi[s0]);
+                if (S0 > sh.blo[s0] && S0 < sh.bhi[s0]) Cn += c;
+            }
+            if (s1 < NS) {
+                int c;
+                lane_sector_eval(D, sh, G, s1, R.x, irho, S1, c);
+                T += fminf(fmaxf(S1, sh.blo[s1]), sh.bhi[s1]);
+                if (S1 > sh.blo[s1] && S1 < sh.bhi[s1]) Cn += c;
+            }
+            T = warp_sum(T);
+            Cn = warp_sum(Cn);
+            const float x_eval = R.x;
+            root_update(R, T - 1.f, Cn, rho, 1e-6f);
+            if (D.stats && lane == 0) atomicAdd(D.stats + 2, 1ull);
+            if (R.done && R.x == x_eval) break;
+            if (R.done) {                                // bracket collapsed to a new point
+                int c;
+                if (s0 < NS) lane_sector_eval(D, sh, G, s0, R.x, irho, S0, c);
+                if (s1 < NS) lane_sector_eval(D, sh, G, s1, R.x, irho, S1, c);
+                break;
+            }
+        }
+    }
+    const float nu = R.x;
+    for (int h = 0; h < 2; ++h) {
+        const int s = h ? s1 : s0;
+        if (s >= NS) continue;
+        const float Sv = h ? S1 : S0;
+        const float hi = sh.bhi[s], lo = sh.blo[s];
+        float eh = -FLT_MAX, el = FLT_MAX;
+        if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
+            Root E;
+            const float w = D.eta_hi[a * NS + s];
+            root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.a = nu;
+            int it = 0;
+            for (; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                lane_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
+            }
+            if (D.stats) atomicAdd(D.stats + 1, (unsigned long long)it);
+            eh = E.x;
+        } else if (Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
+            if (sh.SL[s] < lo) {
+                // the root lies below L: this sector from global memory
+                sh.gs[s] = D.sec_start[s];
+                sh.ce[s] = sh.cb[s];
+                sh.sumlo[s] = 0.f;
+            }
+            Root E;
+            const float w = D.eta_lo[a * NS + s];
+            root_init(E, (w < nu && w > -FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.b = nu;
+            for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                lane_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
+            }
+            el = E.x;
+        }
+        sh.eta_hi[s] = eh;
+        sh.eta_lo[s] = el;
+    }
+    if (lane == 0) sh.nu = nu;
+}
+
+__global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_stream(Dev D) {
     const int a = blockIdx.x;
     if (!D.active[a]) return;
     extern __shared__ float4 dyn4[];
@@ -884,10 +992,21 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 3) k_prox_stream(Dev D) {
         }
         __syncthreads();
     }
+    bool compact = !below;
+    for (int s = 0; s < NS; ++s) compact &= (sh.gs[s] == D.sec_start[s + 1]);
+    if (compact) {
+        // every sector's entries are in shared memory: warp 0 solves the budget and the
+        // edge equations with lane s owning sector s (and s + 32), no block barriers
+        if (warp == 0) lane_solve(D, sh, G, a, L, TL, nu0, rho, irho);
+        __syncthreads();
+    }
     Root R;
     root_init(R, nu0, 0.05f * rho + 1e-6f);
     if (!below) R.a = L;
     float x_eval = NAN;
+    if (compact) {
+        R.x = sh.nu;
+    } else
     if (!below && L > -INFINITY && TL <= 1.f + 1e-6f) {
         R.x = L;                                         // L itself solves the budget equation
         x_eval = L;
@@ -929,10 +1048,14 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 3) k_prox_stream(Dev D) {
     int redo_mine = 0;
     for (int s = warp; s < NS; s += SP_WARPS) {
         float eh = -FLT_MAX, el = FLT_MAX;
-        const float Sv = sh.Sx[s];
+        const float Sv = compact ? 0.f : sh.Sx[s];
         const float hi = sh.bhi[s], lo = sh.blo[s];
         const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-        if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
+        if (compact) {
+            eh = sh.eta_hi[s];
+            el = sh.eta_lo[s];
+            if (sh.gs[s] == p0 && p1 > p0) redo_mine = 1;   // a lower edge below L, redone in global memory
+        } else if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
             Root E;
             const float w = D.eta_hi[a * NS + s];
             root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);

@@ -78,7 +78,7 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
     D.v = (float*)take(MN * 4);
     D.z = (float*)take(MN * 4);
     D.y = (float*)take(MN * 4);
-    D.Ppart = (float*)take((size_t)nsplit * M * K * 4);
+    D.Ppart = (float*)take((size_t)nsplit * M * KMAX * 4);
     D.Q = (float*)take((size_t)M * K * 4);
     D.Qhi = (__nv_bfloat16*)take((size_t)M * KMAX * 2);
     D.Qlo = (__nv_bfloat16*)take((size_t)M * KMAX * 2);
@@ -86,6 +86,7 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
     D.n_active = (int*)take(8);
     D.err = D.n_active + 1;
     D.nsplit = nsplit;
+    D.pstride = bf16 ? KMAX : K;
     D.bf16 = bf16;
     D.raw_out = 1;
     D.alpha = 1.f;
@@ -104,12 +105,14 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
     int err = 0;
     cudaMemcpy(&err, D.err, 4, cudaMemcpyDeviceToHost);
     if (err) { cleanup(); set_error("tensor-core pipeline wait timed out"); return PRISM_ERR_CUDA; }
-    std::vector<float> part((size_t)nsplit * M * K), v(MN);
+    std::vector<float> part((size_t)nsplit * M * D.pstride), v(MN);
     cudaMemcpy(part.data(), D.Ppart, part.size() * 4, cudaMemcpyDeviceToHost);
     cudaMemcpy(v.data(), D.v, MN * 4, cudaMemcpyDeviceToHost);
     std::vector<double> hP((size_t)M * K, 0.0), hBQ((size_t)M * N);
     for (int sp = 0; sp < nsplit; ++sp)
-        for (size_t q = 0; q < (size_t)M * K; ++q) hP[q] += part[(size_t)sp * M * K + q];
+        for (int m = 0; m < M; ++m)
+            for (int k = 0; k < K; ++k)
+                hP[(size_t)m * K + k] += part[((size_t)sp * M + m) * D.pstride + k];
     for (int m = 0; m < M; ++m)
         for (int i = 0; i < N; ++i) hBQ[(size_t)m * N + i] = v[(size_t)m * Npad + U.inv_perm[i]];
     cudaMemcpy(P, hP.data(), hP.size() * 8, cudaMemcpyDefault);

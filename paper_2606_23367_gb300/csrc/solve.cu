@@ -385,7 +385,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.z = A.take<float>(MN); D.y = A.take<float>(MN); D.v = A.take<float>(MN);
         D.X = A.take<float>(MN);
         D.Xhi = A.take<__nv_bfloat16>(MN); D.Xlo = A.take<__nv_bfloat16>(MN);
-        D.Ppart = A.take<float>((size_t)nsplit * M * K);
+        D.Ppart = A.take<float>((size_t)nsplit * M * KMAX);
         D.Q = A.take<float>((size_t)M * K);
         D.Qhi = A.take<__nv_bfloat16>((size_t)M * KMAX); D.Qlo = A.take<__nv_bfloat16>((size_t)M * KMAX);
         D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
@@ -567,6 +567,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.band_lo = BD.band_lof; D.band_hi = BD.band_hif; D.tau = BD.tauf;
     D.stream_prox = (pwidx == nullptr && !BD.has_cap) ? 1 : 0;
     D.nsplit = nsplit;
+    D.pstride = batched_mode_bf16 ? KMAX : K;
     D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
     D.adapt_every = 25;
     P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;

@@ -38,7 +38,8 @@ struct Dev {
     float* v = nullptr;                 // relaxed x plus scaled dual, input of the prox
     __nv_bfloat16* Xhi = nullptr;       // X split for the BF16 products: X ~ Xhi + Xlo
     __nv_bfloat16* Xlo = nullptr;
-    float* Ppart = nullptr;             // nsplit x M x K partial B'X
+    float* Ppart = nullptr;             // nsplit x M x pstride partial B'X
+    int pstride = 0;                    // row stride of Ppart: K (SIMT G2) or 64 (tensor-core G2)
     float* Q = nullptr;                 // M x K
     __nv_bfloat16* Qhi = nullptr;       // M x 64 split of Q (factors zero-padded)
     __nv_bfloat16* Qlo = nullptr;
@@ -80,7 +81,7 @@ int choose_nsplit(int M, int N);
 
 // tensor-core products (tc_gemm.cu)
 bool tc_available();                                     // tensor-map encoder reachable
-int tc_nsplit(int M, int N, int* chunk);                 // asset splits of the tensor-core G2
+int tc_nsplit(int M, int N, int* chunk);                 // partial sets of the tensor-core G2 (its asset chunk)
 void launch_tc_gemm_P(const Dev& D, cudaStream_t st);    // G2 on tcgen05
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
 

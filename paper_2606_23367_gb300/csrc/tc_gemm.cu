@@ -30,6 +30,8 @@ constexpr int TM = 128;            // MMA M (accounts in G2, assets in G4)
 constexpr int TK = 64;             // BF16 elements per 128-byte swizzled row
 constexpr int KP = 64;             // factors, zero-padded, in the BF16 copies of B and Q
 constexpr int G2_STAGES = 2;
+constexpr int G2_CL = 8;           // CTAs per cluster along the asset splits (reduced over DSMEM)
+constexpr int G2_PR = KP + 4;      // row stride (floats) of a CTA's partial in shared memory
 constexpr uint32_t G2_A_BYTES = TM * TK * 2;      // 16 KB
 constexpr uint32_t G2_B_BYTES = KP * TK * 2;      // 8 KB
 constexpr int G4_TN = 128;                        // MMA N in G4 (accounts per tile)
@@ -151,13 +153,41 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
     for (int j = 0; j < 16; ++j) v[j] = __uint_as_float(r[j]);
 }
 
+__device__ __forceinline__ uint32_t cluster_ctarank() {
+    uint32_t r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+
+// every thread of every CTA of the cluster; orders this CTA's shared-memory writes before
+// the other CTAs' reads after the barrier
+__device__ __forceinline__ void cluster_sync_all() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+
+// 16 bytes of CTA `rank`'s shared memory at the address this CTA uses for the same object
+__device__ __forceinline__ float4 ld_dsmem_f4(uint32_t local_addr, uint32_t rank) {
+    uint32_t ra;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(ra) : "r"(local_addr), "r"(rank));
+    float4 v;
+    asm volatile("ld.shared::cluster.v4.f32 {%0, %1, %2, %3}, [%4];"
+                 : "=f"(v.x), "=f"(v.y), "=f"(v.z), "=f"(v.w)
+                 : "r"(ra)
+                 : "memory");
+    return v;
+}
+
 __device__ __forceinline__ float rho_of_idx(int j) {
     return float(RHO_MIN) * exp10f(float(j) / float(RHO_PER_DECADE));
 }
 
 // ---------------------------------------------------------------------------
-// G2: Ppart[split][m][k] = sum over the split's assets of (Xhi + Xlo)[m][i] B[i][k]
-// grid (account tiles, splits); 128 threads; thread 0 drives TMA and the MMAs.
+// G2: P[m][k] = sum_i (Xhi + Xlo)[m][i] B[i][k], split over assets.
+// grid (account tiles, splits), clusters of G2_CL consecutive splits; 128 threads;
+// thread 0 drives TMA and the MMAs. Each CTA stages its 128 x 64 FP32 partial in
+// shared memory; CTA rank r of the cluster then sums rows 16r..16r+15 over the
+// cluster's CTAs (fixed order, over DSMEM) and writes them as one partial set:
+// Ppart[set][m][0..63], set = split / G2_CL.
 // ---------------------------------------------------------------------------
 struct __align__(1024) G2Smem {
     __nv_bfloat16 ahi[G2_STAGES][TM * TK];
@@ -246,24 +276,43 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     if (have && !mbar_wait(&s.done, 0, D.err, 8)) have = false;
     have = __syncthreads_and(have);        // tcgen05.ld below is warp-collective: decide uniformly
     fence_after_sync();
-    const int m = mt * TM + warp * 32 + lane;
     const uint32_t lane_addr = tmem + (uint32_t(warp * 32) << 16);
-    float acc[16];
+    // the stage buffers are free once the MMAs are done (or the loads drained on failure)
+    float* part = reinterpret_cast<float*>(&s.ahi[0][0]);
+    const int row = warp * 32 + lane;
 #pragma unroll 1
     for (int c = 0; c < KP / 16; ++c) {
+        float acc[16];
         if (have) tmem_ld16(lane_addr + c * 16, acc);
         else
 #pragma unroll
             for (int j = 0; j < 16; ++j) acc[j] = 0.f;
-        if (m < D.M) {
-            float* out = D.Ppart + ((size_t)split * D.M + m) * D.K;
+        float4* dst = reinterpret_cast<float4*>(part + row * G2_PR + c * 16);
 #pragma unroll
-            for (int j = 0; j < 16; ++j)
-                if (c * 16 + j < D.K) out[c * 16 + j] = acc[j];
-        }
+        for (int j = 0; j < 4; ++j) dst[j] = make_float4(acc[4 * j], acc[4 * j + 1], acc[4 * j + 2], acc[4 * j + 3]);
     }
     fence_before_sync();
-    __syncthreads();
+    cluster_sync_all();
+    {
+        constexpr int ROWS = TM / G2_CL;           // rows this CTA reduces
+        const uint32_t rank = cluster_ctarank();
+        const int set = blockIdx.y / G2_CL;
+        const uint32_t base_addr = smem_u32(part);
+        for (int item = tid; item < ROWS * (KP / 4); item += blockDim.x) {
+            const int r = int(rank) * ROWS + item / (KP / 4), c4 = item % (KP / 4);
+            const uint32_t off = base_addr + uint32_t(r * G2_PR + c4 * 4) * 4u;
+            float4 sum = ld_dsmem_f4(off, 0);
+#pragma unroll
+            for (int q = 1; q < G2_CL; ++q) {
+                const float4 v = ld_dsmem_f4(off, uint32_t(q));
+                sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
+            }
+            const int m = mt * TM + r;
+            if (m < D.M) *reinterpret_cast<float4*>(D.Ppart + ((size_t)set * D.M + m) * KP + c4 * 4) = sum;
+        }
+    }
+    cluster_sync_all();                          // no CTA leaves while another reads its partial
+    fence_after_sync();
     if (warp == 0) tmem_dealloc(tmem, 64);
 }
 
@@ -419,12 +468,13 @@ static bool map2d(CUtensorMap* m, const void* base, uint64_t dim0, uint64_t dim1
 bool tc_available() { return tc::encoder() != nullptr; }
 
 int tc_nsplit(int M, int N, int* chunk_out) {
+    // about one CTA per SM: G2_CL splits per cluster, nsets clusters per account tile
     const int mtiles = cdiv(M, tc::TM);
-    const int target = std::max(1, 2 * 152 / mtiles);
-    int chunk = cdiv(cdiv(N, target), tc::TK) * tc::TK;
-    chunk = std::max(chunk, tc::TK);
-    *chunk_out = chunk;
-    return cdiv(N, chunk);
+    int nsets = std::max(1, int(std::lround(152.0 / double(mtiles * tc::G2_CL))));
+    nsets = std::min(nsets, std::max(1, cdiv(cdiv(N, tc::TK), tc::G2_CL)));
+    const int ns = nsets * tc::G2_CL;
+    *chunk_out = std::max(tc::TK, cdiv(cdiv(N, ns), tc::TK) * tc::TK);
+    return nsets;
 }
 
 void launch_tc_gemm_P(const Dev& D, cudaStream_t st) {
@@ -434,11 +484,22 @@ void launch_tc_gemm_P(const Dev& D, cudaStream_t st) {
               tc::map2d(&mBt, D.Bt16p, D.Npad, tc::KP, (uint64_t)D.Npad * 2, tc::TK, tc::KP);
     if (!ok) { set_error("tensor map encoding failed (G2)"); return; }
     int chunk = 0;
-    const int ns = tc_nsplit(D.M, D.N, &chunk);
+    const int nsets = tc_nsplit(D.M, D.N, &chunk);
     const size_t smem = sizeof(tc::G2Smem) + 1024;
     cudaFuncSetAttribute(tc::k_tc_gemm_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    dim3 grid(cdiv(D.M, tc::TM), ns);
-    tc::k_tc_gemm_P<<<grid, 128, smem, st>>>(mXhi, mXlo, mBt, D, chunk);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(cdiv(D.M, tc::TM), nsets * tc::G2_CL);
+    cfg.blockDim = dim3(128);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = tc::G2_CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, tc::k_tc_gemm_P, mXhi, mXlo, mBt, D, chunk);
 }
 
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
