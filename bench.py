@@ -181,6 +181,29 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def profiled_traffic(kernel_class):
+    """DRAM bytes per launch of a kernel class from the committed ncu summary of the default
+    workload, or None when the kernel's source file has changed since that capture."""
+    import hashlib
+    import re
+    path = os.path.join(ROOT, "profiles", "dram_traffic_500x10000.md")
+    try:
+        text = open(path).read()
+    except OSError:
+        return None
+    pat = re.compile(r"^\| (\w+) \| `[^`]+` \| \d+ \| [\d.]+ \| [\d.]+ \| (\d+) \| (\S+) \| ([0-9a-f]+) \|$")
+    for line in text.splitlines():
+        m = pat.match(line.strip())
+        if not m or m.group(1) != kernel_class:
+            continue
+        try:
+            cur = hashlib.sha256(open(os.path.join(ROOT, m.group(3)), "rb").read()).hexdigest()
+        except OSError:
+            return None
+        return int(m.group(2)) if cur.startswith(m.group(4)) else None
+    return None
+
+
 def run_gpu(args, dist, rank, world, local_rank):
     import numpy as np
     import torch
@@ -315,7 +338,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
     roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": None,
+                "frac": achieved / peak, "traffic": profiled_traffic(dom),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,
                 "kernel_share": {n: kms[i] / max(1e-9, sum(kms)) for i, n in enumerate(names)}}
