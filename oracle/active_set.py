@@ -53,6 +53,11 @@ class OracleResult:
     theta: float         # cap multiplier, 0 when the cap is slack
     iters: int
     n_free: int
+    # the identified active set at the solution
+    fixed: np.ndarray = None   # (n,) bool: weight at a breakpoint
+    pos: np.ndarray = None     # (n,) breakpoint index (fixed) or segment index (free)
+    wband: np.ndarray = None   # (S,) +1 band held at hi, -1 at lo, 0 not a working row
+    wcap: bool = False         # cap a working row
 
 
 class AccountProblem:
@@ -256,7 +261,8 @@ class AccountProblem:
                 best, what = -theta, ("cap", 0)
             if what is None:
                 return OracleResult(w=w, nu=float(nu), lam=lam, theta=float(theta),
-                                    iters=it, n_free=int(F.shape[0]))
+                                    iters=it, n_free=int(F.shape[0]), fixed=fixed.copy(),
+                                    pos=pos.copy(), wband=wband.copy(), wcap=bool(wcap))
             kind, j = what
             if kind == "up":
                 fixed[j] = False            # pos stays: segment p lies right of breakpoint p
