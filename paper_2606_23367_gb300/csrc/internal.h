@@ -93,6 +93,23 @@ struct prism_universe {
     prism::Universe u;
 };
 
+// What the backward pass needs of a polished solve: the identified active set and
+// the ragged layout. Device buffers are owned by the state; the universe must outlive it.
 struct prism_state {
-    int dummy = 0;
+    const prism_universe* uh = nullptr;
+    int device = 0, M = 0, N = 0, Npad = 0, K = 0, S = 0;
+    int64_t nnz = 0;
+    int64_t* offsets = nullptr;       // M + 1
+    int32_t* asset_idx = nullptr;     // nnz, or null for full-universe accounts
+    double* W = nullptr;              // M x Npad polished weights (sorted layout)
+    uint8_t* flags = nullptr;         // M x Npad active-set flags
+    int* wband = nullptr;             // M x S working bands
+    int* wcap = nullptr;              // M
+    int* status = nullptr;            // M
+    std::vector<void*> blocks;        // every device allocation above and the scratch below
+    // backward scratch (allocated on first use)
+    int fmax = 0;
+    double *G = nullptr, *U = nullptr, *DW0 = nullptr, *Fh = nullptr, *Ft = nullptr, *Y = nullptr;
+    int *Flist = nullptr, *NZlist = nullptr, *err = nullptr;
+    double *out_dmu = nullptr, *out_dd = nullptr, *out_dB = nullptr, *out_dw0 = nullptr, *in_g = nullptr;
 };

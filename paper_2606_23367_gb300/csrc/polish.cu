@@ -478,9 +478,10 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         __syncthreads();
         // Cholesky in the L D L' form (column c of the trailing update reads only column c),
         // then L = L D^{1/2}
+        bool chol_ok = true;
         for (int c = 0; c < K; ++c) {
             const float piv = sh.C[c][c];
-            if (!(piv > 0.f)) { if (tid == 0) sh.fail = 1; break; }
+            if (!(piv > 0.f)) { chol_ok = false; break; }          // every thread reads the same pivot
             const float ip = 1.f / piv;
             for (int r = c + 1 + warp; r < K; r += PB / 32) {
                 const float lr = sh.C[r][c] * ip;
@@ -488,7 +489,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             }
             __syncthreads();
         }
-        if (!sh.fail) {
+        if (chol_ok) {
             for (int c = tid; c < K; c += PB) sh.Ldinv[c] = sqrtf(sh.C[c][c]);
             __syncthreads();
             for (int e2 = tid; e2 < K * K; e2 += PB) {
@@ -499,7 +500,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             for (int c = tid; c < K; c += PB) { sh.C[c][c] = sh.Ldinv[c]; sh.Ldinv[c] = 1.f / sh.Ldinv[c]; }
         }
         __syncthreads();
-        if (sh.fail) {
+        if (!chol_ok) {
             if (tid == 0) P.done[a] = 2;
             return;
         }
@@ -993,6 +994,33 @@ void launch_fallback(const PolDev& P, cudaStream_t st) {
 
 void launch_finish_status(const PolDev& P, double eps, cudaStream_t st) {
     k_finish_status<<<cdiv(P.M, 128), 128, 0, st>>>(P, eps);
+}
+
+__global__ void k_adjoint_flags(PolDev P, uint8_t* flags) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)P.M * P.Npad) return;
+    const int p = int(e % P.Npad);
+    if (p >= P.N) { flags[e] = 0; return; }
+    Pieces pc;
+    entry_pieces(P, e, pc);
+    const int code = P.st[e];
+    int fl = 0;
+    double sg;
+    if (code >= ST_FREE) {
+        fl = 1;
+        sg = seg_sign(pc, code - ST_FREE);
+    } else {
+        if (code > 0 && code < pc.nb - 1) fl = 2;
+        const double dw = P.W[e] - pc.w0;
+        sg = dw > 0.0 ? 1.0 : (dw < 0.0 ? -1.0 : 0.0);
+    }
+    fl |= sg > 0.0 ? 4 : (sg < 0.0 ? 8 : 0);
+    flags[e] = (uint8_t)fl;
+}
+
+void launch_adjoint_flags(const PolDev& P, uint8_t* flags, cudaStream_t st) {
+    const size_t n = (size_t)P.M * P.Npad;
+    k_adjoint_flags<<<(unsigned)cdiv64((int64_t)n, 256), 256, 0, st>>>(P, flags);
 }
 
 }  // namespace prism

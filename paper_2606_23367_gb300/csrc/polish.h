@@ -75,5 +75,12 @@ void launch_classify(const PolDev& P, cudaStream_t st);
 void launch_polish(const PolDev& P, int rounds, cudaStream_t st);
 void launch_fallback(const PolDev& P, cudaStream_t st);
 void launch_finish_status(const PolDev& P, double eps, cudaStream_t st);
+// Per-entry active-set flags of the polished solution for the adjoint:
+// bit 0 free; bit 1 fixed at an interior breakpoint (a kink of phi, moving with w0);
+// bits 2-3 the cap row's coefficient (1: +1, 2: -1, 0: none).
+void launch_adjoint_flags(const PolDev& P, uint8_t* flags, cudaStream_t st);
+// The backward-pass state of a polished solve (adjoint.cu).
+int make_backward_state(const prism_universe* uh, const PolDev& P, const int* status_dev, const int64_t* offsets_dev,
+                        const int32_t* asset_idx_dev, int64_t nnz, cudaStream_t st, prism_state** out);
 
 }  // namespace prism

@@ -749,6 +749,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     cudaEventRecord(SC.ev[3], st);
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_finish_status(P, o->eps_kkt, st); });
     cudaEventRecord(SC.ev[4], st);
+    if (o->keep_for_backward) {
+        if (int rc2 = make_backward_state(uh, P, D.status, PA.offsets, PA.asset_idx, nnz, st, res->state)) return rc2;
+    }
     // ---- unpack
     UnpackArgs UA;
     UA.M = M; UA.Npad = Npad; UA.offsets = PA.offsets; UA.asset_idx = PA.asset_idx; UA.inv_perm = U.d_inv_perm;
@@ -828,7 +831,12 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         set_error("invalid options");
         return PRISM_ERR_ARGUMENT;
     }
-    if (o.keep_for_backward) { set_error("keep_for_backward is not available in this build"); return PRISM_ERR_UNSUPPORTED; }
+    if (o.keep_for_backward && !res->state) { set_error("keep_for_backward needs res->state"); return PRISM_ERR_ARGUMENT; }
+    if (o.keep_for_backward && o.precision == PRISM_PLAIN_FP32) {
+        set_error("keep_for_backward is available in the batched modes");
+        return PRISM_ERR_UNSUPPORTED;
+    }
+    if (o.keep_for_backward) *res->state = nullptr;
     const auto t0 = std::chrono::steady_clock::now();
     if (o.precision == PRISM_BATCHED_FP32) return solve_core(uh, b, &o, res, false, false);
     if (o.precision == PRISM_BATCHED_BF16) {
@@ -890,11 +898,4 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     return PRISM_OK;
 }
 
-extern "C" int prism_solve_batch_backward(prism_state* state, const double* dL_dw, double* dmu, double* dB,
-                                          double* dd, double* dw0) {
-    (void)state; (void)dL_dw; (void)dmu; (void)dB; (void)dd; (void)dw0;
-    prism::set_error("backward pass is not available in this build");
-    return PRISM_ERR_UNSUPPORTED;
-}
 
-extern "C" void prism_free_state(prism_state* state) { delete state; }

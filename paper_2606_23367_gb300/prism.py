@@ -221,11 +221,16 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
     for k in ("nu", "lambda_band", "theta", "diag"):
         if out.get(k) is not None:
             setattr(r, k, keep.ptr(out[k], np.float64))
+    holder = C.c_void_p(None)
+    if o.keep_for_backward:
+        r.state = C.addressof(holder)
     _check(lib.prism_solve_batch(u.handle, C.byref(b), C.byref(o), C.byref(r)))
     res = dict(out)
     res.update(t_device_ms=r.t_device_ms, t_call_ms=r.t_call_ms, t_phase_ms=list(r.t_phase_ms),
                device_bytes=r.device_bytes, n_launches=r.n_launches,
                kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches))
+    if o.keep_for_backward:
+        res["state"] = BackwardState(holder.value, u, nnz)
     return res
 
 
@@ -277,12 +282,43 @@ def prism_polish_noalloc(u: UniverseHandle, offsets, w0, lower, upper, tc, band_
     return res
 
 
-def prism_solve_batch_backward(state, dL_dw, dmu=None, dB=None, dd=None, dw0=None):
+class BackwardState:
+    """The active set kept by a solve with keep_for_backward=1 (owns the C state; keeps
+    its universe alive)."""
+
+    def __init__(self, ptr, universe, nnz):
+        self.ptr = ptr
+        self.universe = universe
+        self.nnz = nnz
+
+    def close(self):
+        if self.ptr:
+            prism_free_state(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def prism_solve_batch_backward(state, dL_dw, dmu=None, dB=None, dd=None, dw0=None) -> dict:
+    """Gradients of L (given dL/dw, ragged) with respect to mu (N), B (N x K), d (N) and w0
+    (ragged) through the polished KKT system. Outputs may be supplied (host or device);
+    missing ones are allocated as numpy arrays."""
     lib = load_library()
     keep = _Keep()
-    _check(lib.prism_solve_batch_backward(state, keep.ptr(dL_dw, np.float64), keep.ptr(dmu, np.float64),
+    u = state.universe
+    N, K = u.n_assets, u.n_factors
+    dmu = np.zeros(N) if dmu is None else dmu
+    dB = np.zeros((N, K)) if dB is None else dB
+    dd = np.zeros(N) if dd is None else dd
+    dw0 = np.zeros(state.nnz) if dw0 is None else dw0
+    _check(lib.prism_solve_batch_backward(state.ptr, keep.ptr(dL_dw, np.float64), keep.ptr(dmu, np.float64),
                                           keep.ptr(dB, np.float64), keep.ptr(dd, np.float64),
                                           keep.ptr(dw0, np.float64)))
+    return dict(dmu=dmu, dB=dB, dd=dd, dw0=dw0)
 
 
 def prism_free_state(state):
