@@ -121,7 +121,8 @@ typedef struct {
     int32_t polish_rounds;    /* active-set correction rounds per polish (default 8) */
     int32_t precision;        /* PRISM_PLAIN_FP32 | PRISM_BATCHED_FP32 | PRISM_BATCHED_BF16 */
     int32_t use_graph;        /* capture the iteration loop in a CUDA graph (default 1) */
-    int32_t keep_for_backward;/* keep the polished active set for prism_solve_batch_backward */
+    int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
+                                 prism_solve_batch_backward (batched modes only) */
     int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
     void*   cuda_stream;      /* cudaStream_t to run on (NULL = the library's own stream) */
 } prism_solve_opts;
@@ -179,12 +180,30 @@ typedef struct {
 int prism_solve_batch(prism_universe* u, const prism_batch* batch,
                       const prism_solve_opts* opts, prism_result* res);
 
-/* Implicit differentiation of the polished KKT system: given dL/dw (ragged,
- * same layout as the solve), write dL/dmu (N, summed over accounts), dL/dB
- * (N x K), dL/dd (N) and dL/dw0 (ragged). Any output may be NULL. Requires a
- * state returned by a solve with keep_for_backward = 1. */
+/* Implicit differentiation of the polished KKT system (Sec. 4.4 conditions on the
+ * active set the polish identified; the variables are those of Eq. 1).
+ *
+ * For L = sum_a g_a' w_a with g = dL/dw given ragged in the solve's layout (nnz
+ * doubles), writes dL/dmu (N), dL/dB (N x K row-major, universe asset order) and
+ * dL/dd (N), each summed over the book's accounts, and dL/dw0 (nnz, ragged). Every
+ * pointer may be host or device memory; an output pointer may be NULL. Per account
+ * one FP64 solve of [2 Sigma_FF, E_F'; E_F, 0] [u; kappa] = [g_F; 0] on the free
+ * weights F and working rows E gives all four gradients; the sums over accounts run
+ * in a fixed order, so repeated calls return identical numbers. Accounts whose status
+ * is not CERTIFIED contribute nothing (their active set is not identified). A weight
+ * held at a kink of phi_i (w0_i itself or a tax-lot kink) moves with w0_i; the
+ * derivative is that of the locally constant active set (one-sided at degenerate points).
+ *
+ * state: from prism_solve_batch with keep_for_backward = 1; owned by the caller, who
+ * frees it with prism_free_state; the universe it came from must outlive it. It may be
+ * used for any number of backward calls (not concurrently). Scratch device memory is
+ * allocated on the first call and kept by the state.
+ * Returns PRISM_OK; PRISM_ERR_ARGUMENT for NULL state or dL_dw; PRISM_ERR_UNSUPPORTED
+ * when an account has more than min(Npad, 2048) free weights or more than 24 working
+ * rows; PRISM_ERR_CUDA / PRISM_ERR_ALLOCATION on device failures. */
 int prism_solve_batch_backward(prism_state* state, const double* dL_dw,
                                double* dmu, double* dB, double* dd, double* dw0);
+/* Release a backward state and its device memory (NULL is a no-op). */
 void prism_free_state(prism_state* state);
 
 /* Diagnostic: the two shared-B products of one ADMM x-update, run on the solver's

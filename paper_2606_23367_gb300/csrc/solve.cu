@@ -560,6 +560,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.B32 = U.d_B32; D.d32 = U.d_d32; D.mu32 = U.d_mu32; D.sec_start = U.d_sec_start; D.sector = U.d_sector;
     D.B16 = U.d_B16; D.Bt16 = U.d_Bt16; D.B16p = U.d_B16p; D.Bt16p = U.d_Bt16p;
     D.err = D.n_active + 1;
+    if (!std::getenv("PRISM_DEBUG_STATS")) D.stats = nullptr;   // counters only when asked for
     D.bf16 = batched_mode_bf16;
     D.Cinv = batched_mode_bf16 ? U.d_Cinv16 : U.d_Cinv32;
     D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
@@ -611,7 +612,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.Qhi, 0, (size_t)M * KMAX * 2, st);
         cudaMemsetAsync(D.Qlo, 0, (size_t)M * KMAX * 2, st);
         cudaMemsetAsync(D.n_active, 0, 8, st);
-        cudaMemsetAsync(D.stats, 0, 32, st);
+        if (D.stats) cudaMemsetAsync(D.stats, 0, 32, st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
         k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
