@@ -502,7 +502,8 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
     }
     __syncthreads();
     float theta = 0.f;
-    float nu = project_inner(D, S, a, 0.f, rho, irho, D.nu[a], sh);
+    const float nu_in = D.nu[a];
+    float nu = project_inner(D, S, a, 0.f, rho, irho, nu_in, sh);
     const float tau = D.tau ? D.tau[a] : INFINITY;
     if (tau < INFINITY) {
         const float U = turnover_at(D, S, nu, 0.f, irho, sh);
@@ -595,6 +596,7 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
         D.rp[a] = rp;
         D.rd[a] = rd;
         D.nu[a] = nu;
+        if (D.dnu) D.dnu[a] = fabsf(nu - nu_in);          // the streaming form's margin
         D.theta[a] = theta;
         int newj = j;
         if (bad) {
@@ -1171,8 +1173,8 @@ size_t prox_smem_bytes(const Dev& D) {
     return (size_t)D.Npad * 4 * (5 + (D.pw_idx ? 1 : 0));
 }
 
-void launch_prox(const Dev& D, cudaStream_t st) {
-    if (D.stream_prox) {
+void launch_prox(const Dev& D, cudaStream_t st, bool cold) {
+    if (D.stream_prox && !cold) {
         const size_t smem = prox_stream_smem_bytes(D);
         cudaFuncSetAttribute(k_prox_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         k_prox_stream<<<D.M, 32 * SP_WARPS, smem, st>>>(D);

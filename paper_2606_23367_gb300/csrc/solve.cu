@@ -682,7 +682,17 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         }
         return done_iters;
     };
-    int total_iters = admm_loop(o->max_iter + check_every);
+    // the first iterations run the staged prox: the streaming form needs a warm start of the
+    // budget multiplier to keep its shared-memory candidate lists short
+    const int cold = D.stream_prox ? std::min(3, o->max_iter) : 0;
+    for (int it = 0; it < cold; ++it) {
+        SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
+        SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
+        SC.prof.run(PRISM_K_GEMM_X, 1, st, [&] { if (D.bf16) launch_tc_gemm_x(D, st); else launch_gemm_x(D, st); });
+        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st, true); });
+    }
+    int total_iters = admm_loop(o->max_iter + check_every - cold);
+    if (total_iters >= 0) total_iters += cold;
     if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
     SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_mark_timeout(D, st); });   // accounts still iterating

@@ -74,7 +74,9 @@ void launch_init_state(const Dev& D, cudaStream_t st);
 void launch_gemm_P(const Dev& D, cudaStream_t st);       // G2: Ppart = X B (SIMT)
 void launch_small_solve(const Dev& D, cudaStream_t st);  // G3: Q = Cinv * sum(Ppart)
 void launch_gemm_x(const Dev& D, cudaStream_t st);       // G4: v from X - Delta^{-1} B Q (SIMT)
-void launch_prox(const Dev& D, cudaStream_t st);         // G5/G6: projection, duals, control
+// G5/G6: projection, duals, control. cold: the staged form even for L1-only books (the first
+// calls of a solve, before the multipliers have warm starts for the streaming form's margin)
+void launch_prox(const Dev& D, cudaStream_t st, bool cold = false);
 void launch_count_active(const Dev& D, cudaStream_t st);
 void launch_mark_timeout(const Dev& D, cudaStream_t st);
 int choose_nsplit(int M, int N);
