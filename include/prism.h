@@ -112,7 +112,7 @@ typedef struct {
 typedef struct {
     double  eps_kkt;          /* certification gate on every residual (default 1e-6) */
     double  eps_admm;         /* ADMM residual target before the polish (default 3e-4) */
-    double  rho0;             /* initial ADMM penalty (default 0.1) */
+    double  rho0;             /* initial ADMM penalty (default 2.0) */
     double  alpha;            /* over-relaxation (default 1.6) */
     double  time_budget_s;    /* wall-clock ceiling for the call (<= 0: none) */
     int32_t max_iter;         /* ADMM iteration cap per account (default 4000) */

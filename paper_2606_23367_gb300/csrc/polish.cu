@@ -812,27 +812,39 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             }
             double r_exp = 0.0, r_comp = 0.0;
             int bviol = 0, dep_in = 0, dep_out = 0;
+            // a working row is dependent when the pivoted elimination left it unpivoted
+            auto row_dependent = [&](int row) {
+                for (int r = 1; r < m; ++r)
+                    if (sh.rows[r] == row) return sh.used[r] == 0;
+                return false;
+            };
             for (int s2 = 0; s2 < S; ++s2) {
                 const double ssum = sh.secsum[s2];
                 const double hi = P.band_hi[a * S + s2], lo = P.band_lo[a * S + s2];
                 r_exp = fmax(r_exp, fmax(lo - ssum, ssum - hi));
                 const int wb = P.wband[a * S + s2];
                 const double ls = sh.lam_s[s2];
-                if (wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p) {
-                    // a dependent working row (dropped from the solve): inside the band it is
-                    // inactive and leaves the working set; outside, a fixed entry is released
+                const bool off = wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p;
+                if (off && row_dependent(s2)) {
+                    // dropped from the solve: inside the band it is inactive and leaves the
+                    // working set; outside, a fixed entry is released
                     ++bviol;
                     if (wb > 0 ? ssum < hi : ssum > lo) { P.wband[a * S + s2] = 0; ++dep_in; }
                     else ++dep_out;
                 } else if (wb == 0) {
                     if (ssum > hi + tol_p) { ++bviol; P.wband[a * S + s2] = 1; }
                     else if (ssum < lo - tol_p) { ++bviol; P.wband[a * S + s2] = -1; }
-                } else if (wb > 0) {
-                    r_comp = fmax(r_comp, fabs(ls) * fabs(hi - ssum));
-                    if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); P.wband[a * S + s2] = 0; }
                 } else {
-                    r_comp = fmax(r_comp, fabs(ls) * fabs(ssum - lo));
-                    if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); P.wband[a * S + s2] = 0; }
+                    // an independent working row is off its bound only when free weights left
+                    // their segments (counted in nviol): the next round solves again
+                    if (off) ++bviol;
+                    if (wb > 0) {
+                        r_comp = fmax(r_comp, fabs(ls) * fabs(hi - ssum));
+                        if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); P.wband[a * S + s2] = 0; }
+                    } else {
+                        r_comp = fmax(r_comp, fabs(ls) * fabs(ssum - lo));
+                        if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); P.wband[a * S + s2] = 0; }
+                    }
                 }
             }
             double r_turn = 0.0;
@@ -842,10 +854,13 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 if (!P.wcap[a]) {
                     if (tu > tau + tol_p) { ++bviol; P.wcap[a] = 1; }
                 } else {
-                    if (fabs(tu - tau) > tol_p) {                               // dependent row
+                    const bool off = fabs(tu - tau) > tol_p;
+                    if (off && row_dependent(S)) {
                         ++bviol;
                         if (tu < tau) { P.wcap[a] = 0; ++dep_in; }
                         else ++dep_out;
+                    } else if (off) {
+                        ++bviol;
                     }
                     r_comp = fmax(r_comp, fabs(theta) * fabs(tau - tu));
                     if (theta < -tol_d) { ++bviol; r_comp = fmax(r_comp, -theta); P.wcap[a] = 0; }

@@ -811,7 +811,7 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     std::memset(o, 0, sizeof(*o));
     o->eps_kkt = 1e-6;
     o->eps_admm = 3e-4;
-    o->rho0 = 0.1;
+    o->rho0 = 2.0;
     o->alpha = 1.6;
     o->time_budget_s = 0.0;
     o->max_iter = 4000;
