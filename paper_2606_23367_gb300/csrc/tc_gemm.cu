@@ -332,9 +332,35 @@ struct __align__(1024) G4Smem {
     float irho[G4_TN];
 };
 
-__global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUtensorMap mB,
-                                                    const __grid_constant__ CUtensorMap mQhi,
-                                                    const __grid_constant__ CUtensorMap mQlo, Dev D) {
+// 32 lanes x 8 consecutive FP32 columns of this warp's TMEM lane quarter
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, float* v) {
+    uint32_t r[8];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 8; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+constexpr int G4_THREADS = 256;   // warp w: TMEM lane quarter w % 4 (32 assets), accounts 64 (w / 4) .. + 63
+constexpr int G4_CC = 8;          // accounts per epilogue chunk
+
+// z and y of one chunk of G4_CC accounts for this thread's asset (coalesced over the warp)
+__device__ __forceinline__ void g4_load_chunk(const Dev& D, int i, int m0, float* zz, float* yy) {
+#pragma unroll
+    for (int j = 0; j < G4_CC; ++j) {
+        const int m = m0 + j;
+        const size_t e = (size_t)m * D.Npad + i;
+        const bool ok = m < D.M;
+        zz[j] = ok ? __ldg(D.z + e) : 0.f;
+        yy[j] = ok ? __ldg(D.y + e) : 0.f;
+    }
+}
+
+__global__ void __launch_bounds__(G4_THREADS, 3) k_tc_gemm_x(const __grid_constant__ CUtensorMap mB,
+                                                            const __grid_constant__ CUtensorMap mQhi,
+                                                            const __grid_constant__ CUtensorMap mQlo, Dev D) {
     extern __shared__ unsigned char raw[];
     G4Smem& s = *reinterpret_cast<G4Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -342,7 +368,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
     constexpr uint32_t IDESC = idesc_bf16(TM, G4_TN);
     {
         const int m = mt * G4_TN + tid;
-        const int act = (D.active == nullptr) || (m < D.M && D.active[m]);
+        const int act = tid < G4_TN && ((D.active == nullptr) || (m < D.M && D.active[m]));
         if (!__syncthreads_or(act)) return;
     }
     if (warp == 0) tmem_alloc(&s.tmem, G4_TN);
@@ -352,7 +378,7 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
         s.fail = 0;
         fence_barrier_init();
     }
-    {
+    if (tid < G4_TN) {
         const int m = mt * G4_TN + tid;
         const float r = (m < D.M) ? rho_of_idx(D.rho_idx[m]) : 1.f;
         s.rho[tid] = r;
@@ -367,6 +393,18 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
         tma_load_2d(s.a, &mB, &s.full, 0, at * TM);
         tma_load_2d(s.bhi, &mQhi, &s.full, 0, mt * G4_TN);
         tma_load_2d(s.blo, &mQlo, &s.full, 0, mt * G4_TN);
+    }
+    // while the tile loads and multiplies: this thread's first two chunks of z and y
+    const int q = warp & 3, half = warp >> 2;
+    const int i = at * TM + q * 32 + lane;              // asset of this TMEM lane
+    const int ii = i < D.N ? i : 0;
+    const int col0 = half * (G4_TN / 2);                // first account column of this warp
+    const int m_base = mt * G4_TN + col0;
+    float za[G4_CC], ya[G4_CC], zb[G4_CC], yb[G4_CC];
+    g4_load_chunk(D, ii, m_base, za, ya);
+    g4_load_chunk(D, ii, m_base + G4_CC, zb, yb);
+    const float mu = D.mu32[ii], dd = 2.f * D.d32[ii];
+    if (tid == 0) {
         if (mbar_wait(&s.full, 0, D.err, 16)) {
             fence_after_sync();
             const uint64_t da = sw128_desc(s.a), dh = sw128_desc(s.bhi), dl = sw128_desc(s.blo);
@@ -384,41 +422,33 @@ __global__ void __launch_bounds__(128) k_tc_gemm_x(const __grid_constant__ CUten
     bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
     have = __syncthreads_and(have);
     fence_after_sync();
-    const int i = at * TM + warp * 32 + lane;          // asset of this TMEM lane
     const bool row_ok = have && i < D.N;
-    float mu = 0.f, dd = 1.f;
-    if (i < D.N) {
-        mu = D.mu32[i];
-        dd = 2.f * D.d32[i];
-    }
-    const uint32_t lane_addr = tmem + (uint32_t(warp * 32) << 16);
-    float bq[16];
-#pragma unroll 1
-    for (int c = 0; c < G4_TN / 16; ++c) {
-        if (have) tmem_ld16(lane_addr + c * 16, bq);
-        if (!row_ok) continue;
-        const int m0 = mt * G4_TN + c * 16;
-        const int ncol = min(16, D.M - m0);
-        if (ncol <= 0) continue;
-        // issue the chunk's loads before any store (z, y and v never alias, but the
-        // compiler cannot know): 32 independent loads in flight per thread
-        float zz[16], yy[16];
+    const uint32_t lane_addr = tmem + (uint32_t(q * 32) << 16) + col0;
+    // chunk c uses the buffer loaded two chunks earlier; the chunk after next is loaded
+    // into it once it is consumed
+    auto consume = [&](int c, float* zz, float* yy) {
+        float bq[G4_CC];
+        if (have) tmem_ld8(lane_addr + c * G4_CC, bq);
+        const int m0 = m_base + c * G4_CC;
+        if (row_ok) {
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            const size_t e = (size_t)(m0 + j) * D.Npad + i;
-            zz[j] = (j < ncol) ? __ldg(D.z + e) : 0.f;
-            yy[j] = (j < ncol) ? __ldg(D.y + e) : 0.f;
+            for (int j = 0; j < G4_CC; ++j) {
+                const int m = m0 + j;
+                if (m >= D.M) break;
+                const size_t e = (size_t)m * D.Npad + i;
+                if (D.raw_out) { D.v[e] = bq[j]; continue; }
+                const int col = col0 + c * G4_CC + j;
+                const float rho = s.rho[col];
+                const float x = (mu + rho * zz[j] - yy[j] - bq[j]) / (dd + rho);
+                D.v[e] = D.alpha * x + (1.f - D.alpha) * zz[j] + yy[j] * s.irho[col];
+            }
         }
+        if (c + 2 < (G4_TN / 2) / G4_CC) g4_load_chunk(D, ii, m0 + 2 * G4_CC, zz, yy);
+    };
 #pragma unroll
-        for (int j = 0; j < 16; ++j) {
-            if (j >= ncol) break;
-            const size_t e = (size_t)(m0 + j) * D.Npad + i;
-            if (D.raw_out) { D.v[e] = bq[j]; continue; }
-            const int col = c * 16 + j;
-            const float rho = s.rho[col];
-            const float x = (mu + rho * zz[j] - yy[j] - bq[j]) / (dd + rho);
-            D.v[e] = D.alpha * x + (1.f - D.alpha) * zz[j] + yy[j] * s.irho[col];
-        }
+    for (int c = 0; c < (G4_TN / 2) / G4_CC; c += 2) {
+        consume(c, za, ya);
+        consume(c + 1, zb, yb);
     }
     fence_before_sync();
     __syncthreads();
@@ -511,7 +541,7 @@ void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
     const size_t smem = sizeof(tc::G4Smem) + 1024;
     cudaFuncSetAttribute(tc::k_tc_gemm_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::G4_TN));
-    tc::k_tc_gemm_x<<<grid, 128, smem, st>>>(mB, mQhi, mQlo, D);
+    tc::k_tc_gemm_x<<<grid, tc::G4_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
 }
 
 }  // namespace prism
