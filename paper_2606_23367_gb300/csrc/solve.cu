@@ -682,9 +682,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         }
         return done_iters;
     };
-    // the first iterations run the staged prox: the streaming form needs a warm start of the
-    // budget multiplier to keep its shared-memory candidate lists short
-    const int cold = D.stream_prox ? std::min(3, o->max_iter) : 0;
+    // the first iterations run the staged prox: the streaming form needs the budget multiplier
+    // to have settled (its moves set the streaming form's margin) to keep its candidate lists short
+    const int cold = D.stream_prox ? std::min(6, o->max_iter) : 0;
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
         SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
