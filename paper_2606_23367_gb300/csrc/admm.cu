@@ -151,6 +151,7 @@ __global__ void k_small_solve(Dev D) {
     const int K = D.K;
     __shared__ float sP[KMAX];
     const int t = threadIdx.x;
+    const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;   // issued before the partial sums
     if (t < K) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float* pp = D.Ppart + (size_t)m * D.pstride + t;
@@ -164,10 +165,19 @@ __global__ void k_small_solve(Dev D) {
     }
     __syncthreads();
     if (t < K) {
-        // C^{-1} is symmetric: read column t so that the block's loads are contiguous
-        const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;
-        float q = 0.f;
-        for (int j = 0; j < K; ++j) q = fmaf(C[(size_t)j * K], sP[j], q);
+        // C^{-1} is symmetric: read column t so that the block's loads are contiguous; four
+        // accumulators and an unrolled loop keep 16 loads in flight
+        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+        int j = 0;
+#pragma unroll 4
+        for (; j + 4 <= K; j += 4) {
+            q0 = fmaf(C[(size_t)j * K], sP[j], q0);
+            q1 = fmaf(C[(size_t)(j + 1) * K], sP[j + 1], q1);
+            q2 = fmaf(C[(size_t)(j + 2) * K], sP[j + 2], q2);
+            q3 = fmaf(C[(size_t)(j + 3) * K], sP[j + 3], q3);
+        }
+        for (; j < K; ++j) q0 = fmaf(C[(size_t)j * K], sP[j], q0);
+        const float q = (q0 + q1) + (q2 + q3);
         if (D.bf16) {
             __nv_bfloat16 h = __float2bfloat16_rn(q);
             D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
