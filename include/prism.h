@@ -245,6 +245,19 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
                          const prism_solve_opts* opts, prism_result* res);
 
 /* Message of the last failed call on this thread ("" when none). */
+/* Autotuner (no counterpart in the paper, which discloses no solver internals, Sec. 3):
+ * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
+ * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
+ * (1.4 .. 1.8) and the iterations per captured graph (5, 10, 20), starting from *base (or
+ * the defaults when base is NULL); a candidate's score is certified accounts per second of
+ * device time, and one that certifies fewer accounts never wins. Writes the chosen options
+ * to *tuned (the other fields copied from base). Runs about 20 full solves, each allocated
+ * and timed like a normal call; the book's buffers may be host or device memory and are
+ * only read. PLAIN_FP32 is returned unchanged. Returns PRISM_OK or the first failing
+ * solve's error code. */
+int prism_autotune(prism_universe* u, const prism_batch* batch, const prism_solve_opts* base,
+                   prism_solve_opts* tuned);
+
 const char* prism_last_error(void);
 
 /* Library version string. */

@@ -1,0 +1,119 @@
+// autotune.cu -- prism_autotune: pick the solver schedule (initial penalty, over-relaxation,
+// iterations per captured graph) for a book by timing trial solves of that very book.
+//
+// The search is coordinate-wise over small grids: first the initial penalty rho0 (the
+// schedule's largest effect: it sets how many iterations the accounts need), then the
+// over-relaxation alpha, then the graph chunk length. A candidate's score is certified
+// accounts per second of device time; a candidate that certifies fewer accounts than the
+// best so far never wins. Each trial is a full prism_solve_batch with the caller's book, so
+// the result is specific to that book's shape and data (and to this GPU).
+#include <algorithm>
+#include <cstring>
+#include <vector>
+
+#include "common.cuh"
+
+namespace prism {
+namespace {
+
+struct Trial {
+    double score = -1.0;
+    int certified = -1;
+    double device_ms = 0.0;
+};
+
+Trial run_trial(prism_universe* u, const prism_batch* b, const prism_solve_opts& o, int64_t nnz, int M, int S,
+                int reps, int* rc) {
+    std::vector<double> w(std::max<int64_t>(nnz, 1)), nu(M), lam((size_t)M * S), theta(M), diag((size_t)M * PRISM_NDIAG);
+    std::vector<int32_t> status(M), iters(M);
+    Trial t;
+    std::vector<double> times;
+    for (int r = 0; r < reps; ++r) {
+        prism_result res;
+        std::memset(&res, 0, sizeof(res));
+        res.w = w.data(); res.nu = nu.data(); res.lambda_band = lam.data(); res.theta = theta.data();
+        res.status = status.data(); res.iters = iters.data(); res.diag = diag.data();
+        *rc = prism_solve_batch(u, b, &o, &res);
+        if (*rc != PRISM_OK) return t;
+        times.push_back(res.t_device_ms);
+    }
+    std::sort(times.begin(), times.end());
+    t.device_ms = times[times.size() / 2];
+    t.certified = (int)std::count(status.begin(), status.end(), PRISM_CERTIFIED);
+    t.score = t.device_ms > 0 ? t.certified / (t.device_ms * 1e-3) : 0.0;
+    return t;
+}
+
+bool better(const Trial& a, const Trial& b) {
+    if (a.certified != b.certified) return a.certified > b.certified;
+    return a.score > b.score;
+}
+
+}  // namespace
+}  // namespace prism
+
+extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const prism_solve_opts* base,
+                              prism_solve_opts* tuned) {
+    using namespace prism;
+    if (!u || !b || !tuned) { set_error("NULL argument"); return PRISM_ERR_ARGUMENT; }
+    prism_solve_opts o;
+    if (base) o = *base; else prism_default_opts(&o);
+    o.keep_for_backward = 0;
+    o.profile = 0;
+    if (o.precision == PRISM_PLAIN_FP32) { *tuned = o; return PRISM_OK; }   // nothing batched to tune
+    const int M = b->n_accounts;
+    if (M < 1 || !b->offsets) { set_error("empty book"); return PRISM_ERR_ARGUMENT; }
+    int64_t nnz = 0;
+    {
+        cudaPointerAttributes at;
+        const bool dev = cudaPointerGetAttributes(&at, b->offsets) == cudaSuccess &&
+                         (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged);
+        cudaGetLastError();
+        if (dev) {
+            if (cudaMemcpy(&nnz, b->offsets + M, 8, cudaMemcpyDeviceToHost) != cudaSuccess) {
+                set_error("reading offsets failed");
+                return PRISM_ERR_CUDA;
+            }
+        } else {
+            nnz = b->offsets[M];
+        }
+    }
+    const int S = u->u.S;
+    int rc = PRISM_OK;
+    constexpr int REPS = 3;
+    // warm the caches and graphs of the universe handle once
+    run_trial(u, b, o, nnz, M, S, 1, &rc);
+    if (rc != PRISM_OK) return rc;
+    prism_solve_opts best = o;
+    Trial tb = run_trial(u, b, best, nnz, M, S, REPS, &rc);
+    if (rc != PRISM_OK) return rc;
+    auto consider = [&](prism_solve_opts cand) -> int {
+        int r2 = PRISM_OK;
+        const Trial tc = run_trial(u, b, cand, nnz, M, S, REPS, &r2);
+        if (r2 != PRISM_OK) return r2;
+        if (better(tc, tb)) { tb = tc; best = cand; }
+        return PRISM_OK;
+    };
+    for (double rho0 : {0.5, 1.0, 2.0, 3.0, 5.0, 8.0}) {
+        if (rho0 == o.rho0) continue;
+        prism_solve_opts c = best;
+        c.rho0 = rho0;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    for (double alpha : {1.4, 1.5, 1.6, 1.7, 1.8}) {
+        if (alpha == best.alpha) continue;
+        prism_solve_opts c = best;
+        c.alpha = alpha;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    for (int ce : {5, 10, 20}) {
+        if (ce == best.check_every) continue;
+        prism_solve_opts c = best;
+        c.check_every = ce;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    *tuned = best;
+    tuned->keep_for_backward = base ? base->keep_for_backward : 0;
+    tuned->profile = base ? base->profile : 0;
+    return PRISM_OK;
+}

@@ -95,6 +95,8 @@ def load_library(path: str = LIB_PATH):
     lib.prism_polish_noalloc.argtypes = [C.c_void_p, C.POINTER(_Batch), C.c_void_p, C.POINTER(_Opts),
                                          C.POINTER(_Result)]
     lib.prism_polish_noalloc.restype = C.c_int
+    lib.prism_autotune.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+    lib.prism_autotune.restype = C.c_int
     lib.prism_free_state.argtypes = [C.c_void_p]
     lib.prism_free_state.restype = None
     lib.prism_last_error.argtypes = []
@@ -232,6 +234,41 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
     if o.keep_for_backward:
         res["state"] = BackwardState(holder.value, u, nnz)
     return res
+
+
+def prism_autotune(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi,
+                   asset_idx=None, turnover_cap=None, lot_offsets=None, lot_size=None, lot_kappa=None,
+                   **base) -> dict:
+    """Schedule chosen by the library's autotuner for this book (see prism.h): a dict of
+    solve options (rho0, alpha, check_every and the base options) to pass to a solve."""
+    lib = load_library()
+    keep = _Keep()
+    M = int(len(offsets) - 1)
+    b = _Batch(M, keep.ptr(offsets, np.int64), keep.ptr(asset_idx, np.int32),
+               keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
+               keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
+               keep.ptr(turnover_cap, np.float64), keep.ptr(lot_offsets, np.int64),
+               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64))
+    o = _Opts()
+    lib.prism_default_opts(C.byref(o))
+    for k, v in base.items():
+        if k == "cuda_stream":
+            o.cuda_stream = v
+        elif not hasattr(o, k):
+            raise TypeError(f"unknown option {k}")
+        else:
+            setattr(o, k, v)
+    t = _Opts()
+    _check(lib.prism_autotune(u.handle, C.byref(b), C.byref(o), C.byref(t)))
+    out = {name: getattr(t, name) for name, _ in _Opts._fields_ if name != "cuda_stream"}
+    return out
+
+
+def autotune(handle: UniverseHandle, batch, **base) -> dict:
+    return prism_autotune(handle, batch.offsets, batch.w0, batch.lower, batch.upper, batch.tc,
+                          batch.band_lo, batch.band_hi, asset_idx=batch.asset_idx,
+                          turnover_cap=batch.turnover_cap, lot_offsets=batch.lot_offsets,
+                          lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **base)
 
 
 def prism_shared_b_products(u: UniverseHandle, X, Q, precision=PRISM_BATCHED_BF16):
