@@ -778,6 +778,10 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                     if (-up < fmargin) { fmargin = -up; fwho = p + 1; }
                     need = false;
                 }
+            } else if (need && pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv == 0.f) {
+                // an excluded name that is not held: its box is the point 0 and w0 = 0, so it adds
+                // nothing to any sum and has no stationarity condition
+                need = false;
             }
             wq.push(need, p, g32, lane);
             wq.drain(false, lane, check_entry);
