@@ -70,3 +70,23 @@ def test_batch_order_does_not_change_results():
         w1 = res["w"][batch.account_slice(a)]
         w2 = res2["w"][sub.account_slice(k)]
         assert np.max(np.abs(w1 - w2)) <= 1e-12
+
+
+FULL_SAMPLES = {1: [0, 250, 499], 2: [0, 128, 255], 3: [0, 100, 199], 4: [0, 64, 127]}
+
+
+@pytest.mark.parametrize("workload", sorted(FULL_SAMPLES))
+def test_full_size_workloads_sampled_against_the_oracle(workload):
+    # each workload at its full size, in the launch configuration the benchmark times (batched
+    # BF16, default schedule); the oracle checks three accounts one by one, and the library's own
+    # FP64 certification must hold for every account
+    uni, batch = make_workload(workload)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
+    assert np.all(res["status"] == prism.PRISM_CERTIFIED), np.bincount(res["status"])
+    diag = res["diag"]
+    assert float(diag[:, prism.PRISM_DIAG_BUDGET].max()) <= 1e-6
+    assert float(diag[:, prism.PRISM_DIAG_BOX].max()) <= 1e-6
+    assert float(diag[:, prism.PRISM_DIAG_EXPOSURE].max()) <= 1e-6
+    assert float(diag[:, prism.PRISM_DIAG_TURNOVER].max()) <= 1e-6
+    assert float(diag[:, prism.PRISM_DIAG_STAT].max()) <= 1e-6
+    assert_parity(uni, batch, res, accounts=FULL_SAMPLES[workload])
