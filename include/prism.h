@@ -152,7 +152,9 @@ void prism_default_opts(prism_solve_opts* o);
 #define PRISM_K_PACK     5  /* input packing and validation */
 #define PRISM_K_OTHER    6  /* capacity test, init, counters, classification, status */
 #define PRISM_K_UNPACK   7  /* output unpacking */
-#define PRISM_NKCLASS    8
+#define PRISM_K_XPROX    8  /* x-update B Q fused with the streaming pass of the prox (L1-only books) */
+#define PRISM_K_ROOTS    9  /* per-account multipliers, candidates and control after PRISM_K_XPROX */
+#define PRISM_NKCLASS   10
 
 typedef struct {
     double*  w;             /* ragged weights, same layout as prism_batch (required) */

@@ -145,13 +145,18 @@ void launch_gemm_P(const Dev& D, cudaStream_t st) {
 // ---------------------------------------------------------------------------
 // G3: Q[m] = Cinv[rho_idx[m]] * sum_s Ppart[s][m]; one block of K threads per account
 // ---------------------------------------------------------------------------
-__global__ void k_small_solve(Dev D) {
+__global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
     const int m = blockIdx.x;
     if (D.active && !D.active[m]) return;
     const int K = D.K;
     __shared__ float sP[KMAX];
     const int t = threadIdx.x;
-    const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;   // issued before the partial sums
+    // C^{-1} is symmetric: thread t reads column t (the block's loads are contiguous). The whole
+    // column is loaded into registers first, so that it is in flight with the partial sums.
+    float c[KMAX];
+    const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;
+#pragma unroll
+    for (int j = 0; j < KMAX; ++j) c[j] = (t < K && j < K) ? C[(size_t)j * K] : 0.f;
     if (t < K) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float* pp = D.Ppart + (size_t)m * D.pstride + t;
@@ -162,21 +167,19 @@ __global__ void k_small_solve(Dev D) {
             for (int u = 0; u < 8; ++u) acc[u] += pp[(size_t)(sp + u) * stride];
         for (; sp < D.nsplit; ++sp) acc[0] += pp[(size_t)sp * stride];
         sP[t] = ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
+    } else {
+        sP[t] = 0.f;                       // factors beyond K (their column entries are zero too)
     }
     __syncthreads();
     if (t < K) {
-        // C^{-1} is symmetric: read column t so that the block's loads are contiguous; four
-        // accumulators and an unrolled loop keep 16 loads in flight
         float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-        int j = 0;
-#pragma unroll 4
-        for (; j + 4 <= K; j += 4) {
-            q0 = fmaf(C[(size_t)j * K], sP[j], q0);
-            q1 = fmaf(C[(size_t)(j + 1) * K], sP[j + 1], q1);
-            q2 = fmaf(C[(size_t)(j + 2) * K], sP[j + 2], q2);
-            q3 = fmaf(C[(size_t)(j + 3) * K], sP[j + 3], q3);
+#pragma unroll
+        for (int j = 0; j < KMAX; j += 4) {
+            q0 = fmaf(c[j], sP[j], q0);
+            q1 = fmaf(c[j + 1], sP[j + 1], q1);
+            q2 = fmaf(c[j + 2], sP[j + 2], q2);
+            q3 = fmaf(c[j + 3], sP[j + 3], q3);
         }
-        for (; j < K; ++j) q0 = fmaf(C[(size_t)j * K], sP[j], q0);
         const float q = (q0 + q1) + (q2 + q3);
         if (D.bf16) {
             __nv_bfloat16 h = __float2bfloat16_rn(q);
@@ -732,6 +735,9 @@ constexpr int SP_WARPS = 8;             // warps per block; warp w owns sectors 
 constexpr int SP_CW = 128;              // kept-entry slots per warp
 
 struct StreamShared {
+    int sec[SMAX + 1];                  // sector ranges (a copy of sec_start)
+    float wh[SMAX], wl[SMAX];           // warm starts of the sector-edge multipliers
+    int it0;                            // iterations before this call
     float blo[SMAX], bhi[SMAX];
     float SL[SMAX], sumlo[SMAX], Sx[SMAX];
     int CL[SMAX], Cx[SMAX];
@@ -771,7 +777,7 @@ __device__ __forceinline__ void stream_sector_eval(const Dev& D, const StreamSha
         acc += r.z;
         n += r.lin;
     }
-    for (int p = sh.gs[s] + lane; p < D.sec_start[s + 1]; p += 32) {
+    for (int p = sh.gs[s] + lane; p < sh.sec[s + 1]; p += 32) {
         const EntryEval r = eval_entry(D, G, p, eta, 0.f, irho);
         acc += r.z;
         n += r.lin;
@@ -810,7 +816,7 @@ __device__ __forceinline__ void lane_sector_eval(const Dev& D, const StreamShare
         acc += r.z;
         n += r.lin;
     }
-    for (int p = sh.gs[s]; p < D.sec_start[s + 1]; ++p) {
+    for (int p = sh.gs[s]; p < sh.sec[s + 1]; ++p) {
         const EntryEval r = eval_entry(D, G, p, eta, 0.f, irho);
         acc += r.z;
         n += r.lin;
@@ -871,7 +877,7 @@ __device__ void lane_solve(const Dev& D, StreamShared& sh, const GlobalSrc& G, i
         float eh = -FLT_MAX, el = FLT_MAX;
         if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
             Root E;
-            const float w = D.eta_hi[a * NS + s];
+            const float w = sh.wh[s];
             root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
             E.a = nu;
             int it = 0;
@@ -885,12 +891,12 @@ __device__ void lane_solve(const Dev& D, StreamShared& sh, const GlobalSrc& G, i
         } else if (Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
             if (sh.SL[s] < lo) {
                 // the root lies below L: this sector from global memory
-                sh.gs[s] = D.sec_start[s];
+                sh.gs[s] = sh.sec[s];
                 sh.ce[s] = sh.cb[s];
                 sh.sumlo[s] = 0.f;
             }
             Root E;
-            const float w = D.eta_lo[a * NS + s];
+            const float w = sh.wl[s];
             root_init(E, (w < nu && w > -FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
             E.b = nu;
             for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
@@ -906,6 +912,227 @@ __device__ void lane_solve(const Dev& D, StreamShared& sh, const GlobalSrc& G, i
     if (lane == 0) sh.nu = nu;
 }
 
+// Everything after the streaming pass: the budget root, the edge roots of the sectors that
+// bind, the writes of the kept and global-memory entries, the residuals and the control.
+// Block-collective. sh holds the pass's sector sums at L (SL, CL, sumlo) and slot ranges.
+// mask != null: the pass ran in the x-update's epilogue (k_tc_xprox), which already wrote
+// every entry pinned at L (mask bit clear) and put its residuals into res; such an entry of a
+// global-memory range is skipped here unless its sector is recomputed below L.
+// In that case the slots also carry mu_i, d_i and their sector (smu, sdd, ssec; nslots of
+// them, in sector order), and they are written by one block-wide pass.
+__device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, int a, int j, float rho, float irho,
+                            float nu0, float L, float margin, StreamRes& res, const unsigned* mask,
+                            const float* smu = nullptr, const float* sdd = nullptr, const uint8_t* ssec = nullptr,
+                            int nslots = 0) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int NS = D.S;
+    const size_t base = (size_t)a * D.Npad;
+    __syncthreads();
+    // ---- budget multiplier
+    float TL = 0.f;
+    for (int s = 0; s < NS; ++s) TL += fminf(fmaxf(sh.SL[s], sh.blo[s]), sh.bhi[s]);
+    const bool below = !(TL >= 1.f - 1e-6f);           // the root lies below L (or T is not finite)
+    bool redo_all = below;
+    if (below) {
+        // every sector from global memory; the entries written above are redone
+        __syncthreads();
+        for (int s = tid; s < NS; s += blockDim.x) {
+            sh.gs[s] = sh.sec[s];
+            sh.ce[s] = sh.cb[s];
+            sh.sumlo[s] = 0.f;
+        }
+        __syncthreads();
+    }
+    bool compact = !below;
+    for (int s = 0; s < NS; ++s) compact &= (sh.gs[s] == sh.sec[s + 1]);
+    if (compact) {
+        // every sector's entries are in shared memory: warp 0 solves the budget and the
+        // edge equations with lane s owning sector s (and s + 32), no block barriers
+        if (warp == 0) lane_solve(D, sh, G, a, L, TL, nu0, rho, irho);
+        __syncthreads();
+    }
+    Root R;
+    root_init(R, nu0, 0.05f * rho + 1e-6f);
+    if (!below) R.a = L;
+    float x_eval = NAN;
+    if (compact) {
+        R.x = sh.nu;
+    } else
+    if (!below && L > -INFINITY && TL <= 1.f + 1e-6f) {
+        R.x = L;                                         // L itself solves the budget equation
+        x_eval = L;
+        for (int s = tid; s < NS; s += blockDim.x) { sh.Sx[s] = sh.SL[s]; sh.Cx[s] = sh.CL[s]; }
+        __syncthreads();
+    } else {
+        for (int it = 0; it < PROX_MAXIT; ++it) {
+            for (int s = warp; s < NS; s += SP_WARPS) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
+                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
+            }
+            __syncthreads();
+            float T = 0.f;
+            int Cn = 0;
+            for (int s = 0; s < NS; ++s) {
+                const float v = sh.Sx[s];
+                T += fminf(fmaxf(v, sh.blo[s]), sh.bhi[s]);
+                if (v > sh.blo[s] && v < sh.bhi[s]) Cn += sh.Cx[s];
+            }
+            __syncthreads();
+            x_eval = R.x;
+            root_update(R, T - 1.f, Cn, rho, 1e-6f);
+            if (D.stats && tid == 0) atomicAdd(D.stats + 2, 1ull);
+            if (R.done) break;
+        }
+        if (R.x != x_eval) {
+            for (int s = warp; s < NS; s += SP_WARPS) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
+                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
+            }
+            __syncthreads();
+        }
+    }
+    const float nu = R.x;
+    // ---- edge roots of the sectors that bind (warp per sector), then the kept and
+    // global-memory entries of the sector
+    int redo_mine = 0;
+    for (int s = warp; s < NS; s += SP_WARPS) {
+        float eh = -FLT_MAX, el = FLT_MAX;
+        bool sec_redo = redo_all;           // every entry of the sector is recomputed below L
+        const float Sv = compact ? 0.f : sh.Sx[s];
+        const float hi = sh.bhi[s], lo = sh.blo[s];
+        const int p0 = sh.sec[s], p1 = sh.sec[s + 1];
+        if (compact) {
+            eh = sh.eta_hi[s];
+            el = sh.eta_lo[s];
+            if (sh.gs[s] == p0 && p1 > p0) { redo_mine = 1; sec_redo = true; }   // a lower edge below L, redone in global memory
+        } else if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
+            Root E;
+            const float w = sh.wh[s];
+            root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.a = nu;
+            int it = 0;
+            for (; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
+            }
+            if (D.stats && lane == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
+            eh = E.x;
+        } else if (Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
+            if (!redo_all && sh.SL[s] < lo) {
+                // this sector's root lies below L: all of it from global memory
+                __syncwarp();
+                if (lane == 0) { sh.gs[s] = p0; sh.ce[s] = sh.cb[s]; sh.sumlo[s] = 0.f; }
+                __syncwarp();
+                redo_mine = 1;
+                sec_redo = true;
+            }
+            Root E;
+            const float w = sh.wl[s];
+            root_init(E, (w < nu && w > -FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
+            E.b = nu;
+            for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
+                float sum; int cnt;
+                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
+                root_update(E, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
+            }
+            el = E.x;
+        }
+        if (lane == 0) { sh.eta_hi[s] = eh; sh.eta_lo[s] = el; }
+        if (D.stats && lane == 0 && sh.gs[s] < p1) atomicAdd(D.stats + 3, 1ull);
+        const float arg = fminf(fmaxf(nu, eh), el);
+        if (!mask) {
+            for (int q = sh.cb[s] + lane; q < sh.ce[s]; q += 32) {
+                const int p = sh.pos[q];
+                const float z = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], arg, irho).z;
+                res.put(D, base + p, z, sh.v[q], sh.zo[q], sh.yo[q], D.mu32[p], D.d32[p], rho, irho);
+            }
+        }
+        for (int p = sh.gs[s] + lane; p < p1; p += 32) {
+            if (mask && !sec_redo && !((mask[p >> 5] >> (p & 31)) & 1u)) continue;   // written by the pass
+            const float z = eval_entry(D, G, p, arg, 0.f, irho).z;
+            const size_t e = base + p;
+            res.put(D, e, z, G.v[p], D.z[e], D.y[e], D.mu32[p], D.d32[p], rho, irho);
+        }
+    }
+    if (mask) {
+        // the kept entries, every slot by its own thread (a slot of a sector that was moved
+        // to global memory above lies outside its sector's range and was written there)
+        __syncthreads();
+        for (int q = tid; q < nslots; q += blockDim.x) {
+            const int s = ssec[q];
+            if (q >= sh.ce[s]) continue;
+            const float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+            const float z = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], arg, irho).z;
+            res.put(D, base + sh.pos[q], z, sh.v[q], sh.zo[q], sh.yo[q], smu[q], sdd[q], rho, irho);
+        }
+    }
+    float rp = warp_max(res.rp), rd = warp_max(res.rd), nx = warp_max(res.nx), nz = warp_max(res.nz),
+          ny = warp_max(res.ny);
+    int bad = warp_sum(res.bad) > 0 ? 1 : 0;
+    redo_mine = warp_sum(redo_mine);
+    if (lane == 0) {
+        sh.red5[0][warp] = rp; sh.red5[1][warp] = rd; sh.red5[2][warp] = nx; sh.red5[3][warp] = nz;
+        sh.red5[4][warp] = ny; sh.red_bad[warp] = bad | (redo_mine ? 2 : 0);
+    }
+    __syncthreads();
+    if (tid == 0) {
+        int redo = redo_all ? 1 : 0;
+        bad = bad & 1;
+        redo |= sh.red_bad[0] >> 1;
+        for (int w = 1; w < SP_WARPS; ++w) {
+            rp = fmaxf(rp, sh.red5[0][w]); rd = fmaxf(rd, sh.red5[1][w]); nx = fmaxf(nx, sh.red5[2][w]);
+            nz = fmaxf(nz, sh.red5[3][w]); ny = fmaxf(ny, sh.red5[4][w]);
+            bad |= sh.red_bad[w] & 1;
+            redo |= sh.red_bad[w] >> 1;
+        }
+        if (redo) { rp = INFINITY; rd = INFINITY; }    // entries were rewritten: no residual this call
+        const int it = sh.it0 + 1;
+        D.iters[a] = it;
+        if (D.stats) atomicAdd(D.stats, 1ull);
+        D.rp[a] = rp;
+        D.rd[a] = rd;
+        D.nu[a] = nu;
+        D.theta[a] = 0.f;
+        // the next call's margin: four times the last move of nu, or more after a miss
+        D.dnu[a] = redo ? fmaxf(fabsf(nu - nu0), margin) : fabsf(nu - nu0);
+        int newj = j;
+        if (bad) {
+            D.status[a] = PRISM_NUMERICAL_FAILURE;
+            D.active[a] = 0;
+        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
+            D.active[a] = 0;
+        } else if (it >= D.max_iter) {
+            D.active[a] = 0;
+            D.status[a] = PRISM_TIMEOUT;
+        } else if (!redo && it % D.adapt_every == 0) {
+            const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
+            const float du = rd / fmaxf(ny, 1e-12f);
+            const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
+            int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
+            dj = max(-4, min(4, dj));
+            newj = max(0, min(NRHO - 1, j + dj));
+        }
+        sh.newj = newj;
+    }
+    __syncthreads();
+    const int newj = sh.newj;
+    for (int s = tid; s < NS; s += blockDim.x) {
+        D.eta_hi[a * NS + s] = sh.eta_hi[s];
+        D.eta_lo[a * NS + s] = sh.eta_lo[s];
+    }
+    if (newj != j) {
+        if (tid == 0) D.rho_idx[a] = newj;
+        const float rn = rho_val(newj);
+        for (int p = tid; p < D.N; p += blockDim.x) {
+            const size_t e = base + p;
+            store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+        }
+    }
+}
+
 __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_stream(Dev D) {
     const int a = blockIdx.x;
     if (!D.active[a]) return;
@@ -918,6 +1145,10 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_stream(Dev D) {
         sh.blo[s] = D.band_lo[a * NS + s];
         sh.bhi[s] = D.band_hi[a * NS + s];
     }
+    for (int s = tid; s <= NS; s += blockDim.x) sh.sec[s] = D.sec_start[s];
+    for (int s = tid; s < NS; s += blockDim.x) { sh.wh[s] = D.eta_hi[a * NS + s]; sh.wl[s] = D.eta_lo[a * NS + s]; }
+    if (tid == 0) sh.it0 = D.iters[a];
+    __syncthreads();
     const size_t base = (size_t)a * D.Npad;
     const GlobalSrc G(D, base);
     const int j = D.rho_idx[a];
@@ -930,7 +1161,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_stream(Dev D) {
     constexpr int CH = 4;
     int wcnt = 0;                                   // slots used by this warp (uniform)
     for (int s = warp; s < NS; s += SP_WARPS) {
-        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+        const int p0 = sh.sec[s], p1 = sh.sec[s + 1];
         const int start = wcnt;
         int gs = p1;
         float sL = 0.f, slo = 0.f;
@@ -988,193 +1219,265 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_stream(Dev D) {
             sh.ce[s] = warp * SP_CW + wcnt;
         }
     }
-    __syncthreads();
-    // ---- budget multiplier
-    float TL = 0.f;
-    for (int s = 0; s < NS; ++s) TL += fminf(fmaxf(sh.SL[s], sh.blo[s]), sh.bhi[s]);
-    const bool below = !(TL >= 1.f - 1e-6f);           // the root lies below L (or T is not finite)
-    bool redo_all = below;
-    if (below) {
-        // every sector from global memory; the entries written above are redone
-        __syncthreads();
-        for (int s = tid; s < NS; s += blockDim.x) {
-            sh.gs[s] = D.sec_start[s];
-            sh.ce[s] = sh.cb[s];
-            sh.sumlo[s] = 0.f;
-        }
-        __syncthreads();
-    }
-    bool compact = !below;
-    for (int s = 0; s < NS; ++s) compact &= (sh.gs[s] == D.sec_start[s + 1]);
-    if (compact) {
-        // every sector's entries are in shared memory: warp 0 solves the budget and the
-        // edge equations with lane s owning sector s (and s + 32), no block barriers
-        if (warp == 0) lane_solve(D, sh, G, a, L, TL, nu0, rho, irho);
-        __syncthreads();
-    }
-    Root R;
-    root_init(R, nu0, 0.05f * rho + 1e-6f);
-    if (!below) R.a = L;
-    float x_eval = NAN;
-    if (compact) {
-        R.x = sh.nu;
-    } else
-    if (!below && L > -INFINITY && TL <= 1.f + 1e-6f) {
-        R.x = L;                                         // L itself solves the budget equation
-        x_eval = L;
-        for (int s = tid; s < NS; s += blockDim.x) { sh.Sx[s] = sh.SL[s]; sh.Cx[s] = sh.CL[s]; }
-        __syncthreads();
-    } else {
-        for (int it = 0; it < PROX_MAXIT; ++it) {
-            for (int s = warp; s < NS; s += SP_WARPS) {
-                float sum; int cnt;
-                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
-                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
-            }
-            __syncthreads();
-            float T = 0.f;
-            int Cn = 0;
-            for (int s = 0; s < NS; ++s) {
-                const float v = sh.Sx[s];
-                T += fminf(fmaxf(v, sh.blo[s]), sh.bhi[s]);
-                if (v > sh.blo[s] && v < sh.bhi[s]) Cn += sh.Cx[s];
-            }
-            __syncthreads();
-            x_eval = R.x;
-            root_update(R, T - 1.f, Cn, rho, 1e-6f);
-            if (D.stats && tid == 0) atomicAdd(D.stats + 2, 1ull);
-            if (R.done) break;
-        }
-        if (R.x != x_eval) {
-            for (int s = warp; s < NS; s += SP_WARPS) {
-                float sum; int cnt;
-                stream_sector_eval(D, sh, G, s, R.x, irho, sum, cnt);
-                if (lane == 0) { sh.Sx[s] = sum; sh.Cx[s] = cnt; }
-            }
-            __syncthreads();
-        }
-    }
-    const float nu = R.x;
-    // ---- edge roots of the sectors that bind (warp per sector), then the kept and
-    // global-memory entries of the sector
-    int redo_mine = 0;
-    for (int s = warp; s < NS; s += SP_WARPS) {
-        float eh = -FLT_MAX, el = FLT_MAX;
-        const float Sv = compact ? 0.f : sh.Sx[s];
-        const float hi = sh.bhi[s], lo = sh.blo[s];
-        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-        if (compact) {
-            eh = sh.eta_hi[s];
-            el = sh.eta_lo[s];
-            if (sh.gs[s] == p0 && p1 > p0) redo_mine = 1;   // a lower edge below L, redone in global memory
-        } else if (Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
-            Root E;
-            const float w = D.eta_hi[a * NS + s];
-            root_init(E, (w > nu && w < FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
-            E.a = nu;
-            int it = 0;
-            for (; it < PROX_MAXIT && !E.done; ++it) {
-                float sum; int cnt;
-                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
-                root_update(E, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
-            }
-            if (D.stats && lane == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
-            eh = E.x;
-        } else if (Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
-            if (!redo_all && sh.SL[s] < lo) {
-                // this sector's root lies below L: all of it from global memory
-                __syncwarp();
-                if (lane == 0) { sh.gs[s] = p0; sh.ce[s] = sh.cb[s]; sh.sumlo[s] = 0.f; }
-                __syncwarp();
-                redo_mine = 1;
-            }
-            Root E;
-            const float w = D.eta_lo[a * NS + s];
-            root_init(E, (w < nu && w > -FLT_MAX) ? w : nu, 0.05f * rho + 1e-6f);
-            E.b = nu;
-            for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
-                float sum; int cnt;
-                stream_sector_eval(D, sh, G, s, E.x, irho, sum, cnt);
-                root_update(E, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
-            }
-            el = E.x;
-        }
-        if (lane == 0) { sh.eta_hi[s] = eh; sh.eta_lo[s] = el; }
-        if (D.stats && lane == 0 && sh.gs[s] < p1) atomicAdd(D.stats + 3, 1ull);
-        const float arg = fminf(fmaxf(nu, eh), el);
-        for (int q = sh.cb[s] + lane; q < sh.ce[s]; q += 32) {
-            const int p = sh.pos[q];
-            const float z = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], arg, irho).z;
-            res.put(D, base + p, z, sh.v[q], sh.zo[q], sh.yo[q], D.mu32[p], D.d32[p], rho, irho);
-        }
-        for (int p = sh.gs[s] + lane; p < p1; p += 32) {
-            const float z = eval_entry(D, G, p, arg, 0.f, irho).z;
-            const size_t e = base + p;
-            res.put(D, e, z, G.v[p], D.z[e], D.y[e], D.mu32[p], D.d32[p], rho, irho);
-        }
-    }
-    float rp = warp_max(res.rp), rd = warp_max(res.rd), nx = warp_max(res.nx), nz = warp_max(res.nz),
-          ny = warp_max(res.ny);
-    int bad = warp_sum(res.bad) > 0 ? 1 : 0;
-    redo_mine = warp_sum(redo_mine);
-    if (lane == 0) {
-        sh.red5[0][warp] = rp; sh.red5[1][warp] = rd; sh.red5[2][warp] = nx; sh.red5[3][warp] = nz;
-        sh.red5[4][warp] = ny; sh.red_bad[warp] = bad | (redo_mine ? 2 : 0);
-    }
-    __syncthreads();
-    if (tid == 0) {
-        int redo = redo_all ? 1 : 0;
-        bad = bad & 1;
-        redo |= sh.red_bad[0] >> 1;
-        for (int w = 1; w < SP_WARPS; ++w) {
-            rp = fmaxf(rp, sh.red5[0][w]); rd = fmaxf(rd, sh.red5[1][w]); nx = fmaxf(nx, sh.red5[2][w]);
-            nz = fmaxf(nz, sh.red5[3][w]); ny = fmaxf(ny, sh.red5[4][w]);
-            bad |= sh.red_bad[w] & 1;
-            redo |= sh.red_bad[w] >> 1;
-        }
-        if (redo) { rp = INFINITY; rd = INFINITY; }    // entries were rewritten: no residual this call
-        const int it = D.iters[a] + 1;
-        D.iters[a] = it;
-        if (D.stats) atomicAdd(D.stats, 1ull);
-        D.rp[a] = rp;
-        D.rd[a] = rd;
-        D.nu[a] = nu;
-        D.theta[a] = 0.f;
-        // the next call's margin: four times the last move of nu, or more after a miss
-        D.dnu[a] = redo ? fmaxf(fabsf(nu - nu0), margin) : fabsf(nu - nu0);
-        int newj = j;
-        if (bad) {
-            D.status[a] = PRISM_NUMERICAL_FAILURE;
-            D.active[a] = 0;
-        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
-            D.active[a] = 0;
-        } else if (it >= D.max_iter) {
-            D.active[a] = 0;
-            D.status[a] = PRISM_TIMEOUT;
-        } else if (!redo && it % D.adapt_every == 0) {
-            const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
-            const float du = rd / fmaxf(ny, 1e-12f);
-            const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
-            int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
-            dj = max(-4, min(4, dj));
-            newj = max(0, min(NRHO - 1, j + dj));
-        }
-        sh.newj = newj;
-    }
-    __syncthreads();
-    const int newj = sh.newj;
+    stream_tail(D, sh, G, a, j, rho, irho, nu0, L, margin, res, nullptr);
+}
+
+// ---------------------------------------------------------------------------
+// G5/G6 after the fused pass (k_tc_xprox). That kernel evaluated every entry at L inside
+// the x-update's epilogue, wrote v for all entries and z, y, X for the entries pinned at
+// their lower bound, and left per-quarter candidate masks, per-tile residual maxima and (when
+// l differs over the account) per-segment sums of l over the pinned entries. Here, one block
+// per active account: the candidates (mask bits) are gathered into the shared-memory slots of
+// their sectors in position order, the sector sums at L are formed from them in a fixed
+// order, and the rest is the streaming form's tail.
+// ---------------------------------------------------------------------------
+struct RootsShared {
+    StreamShared st;
+    float mu[SP_WARPS * SP_CW], dd[SP_WARPS * SP_CW];   // mu_i, d_i of each slot
+    uint8_t ssec[SP_WARPS * SP_CW];                     // sector of each slot
+    int nslots;
+    unsigned mask[XP_NQMAX];
+    int qoff[XP_NQMAX];                 // candidates before quarter q
+    int rank0[SMAX];                    // candidates before the first position of sector s
+    int wsum[SP_WARPS];
+    int total;
+    int all_fit;                        // every sector's candidates are in slots (slot = rank)
+};
+
+__device__ __forceinline__ int cand_rank(const RootsShared& R, int nq, int p) {
+    const int q = p >> 5;
+    if (q >= nq) return R.total;
+    return R.qoff[q] + __popc(R.mask[q] & ((1u << (p & 31)) - 1u));
+}
+
+__global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
+    const int a = blockIdx.x;
+    if (!D.active[a]) return;
+    extern __shared__ float4 dyn4[];
+    RootsShared& R = *reinterpret_cast<RootsShared*>(dyn4);
+    StreamShared& sh = R.st;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    const int NS = D.S, M = D.M, nq = D.nq;
     for (int s = tid; s < NS; s += blockDim.x) {
-        D.eta_hi[a * NS + s] = sh.eta_hi[s];
-        D.eta_lo[a * NS + s] = sh.eta_lo[s];
+        sh.blo[s] = D.band_lo[a * NS + s];
+        sh.bhi[s] = D.band_hi[a * NS + s];
     }
-    if (newj != j) {
-        if (tid == 0) D.rho_idx[a] = newj;
-        const float rn = rho_val(newj);
-        for (int p = tid; p < D.N; p += blockDim.x) {
-            const size_t e = base + p;
-            store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+    for (int s = tid; s <= NS; s += blockDim.x) sh.sec[s] = D.sec_start[s];
+    for (int s = tid; s < NS; s += blockDim.x) { sh.wh[s] = D.eta_hi[a * NS + s]; sh.wl[s] = D.eta_lo[a * NS + s]; }
+    if (tid == 0) sh.it0 = D.iters[a];
+    const size_t base = (size_t)a * D.Npad;
+    const GlobalSrc G(D, base);
+    const int j = D.rho_idx[a];
+    const float rho = rho_val(j), irho = 1.f / rho;
+    const float nu0 = D.nu[a];
+    const float margin = fmaxf(4.f * D.dnu[a], 2e-3f);
+    const float L = nu0 - margin;
+    // candidate masks and their exclusive prefix counts (four quarters per thread)
+    unsigned w4[4];
+    int c4 = 0;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+        const int q = 4 * tid + u;
+        w4[u] = q < nq ? D.Cm[(size_t)q * M + a] : 0u;
+        c4 += __popc(w4[u]);
+    }
+    int incl = c4;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+    }
+    if (lane == 31) R.wsum[warp] = incl;
+    // residual maxima of the pinned entries, per asset tile
+    StreamRes res;
+    for (int t = tid; t < D.nt; t += blockDim.x) {
+        float r5[5];
+#pragma unroll
+        for (int k = 0; k < 5; ++k) r5[k] = D.Rt[((size_t)k * D.nt + t) * M + a];
+        if (isnan(r5[0])) res.bad = 1;
+        else res.rp = fmaxf(res.rp, r5[0]);
+        res.rd = fmaxf(res.rd, r5[1]); res.nx = fmaxf(res.nx, r5[2]);
+        res.nz = fmaxf(res.nz, r5[3]); res.ny = fmaxf(res.ny, r5[4]);
+    }
+    __syncthreads();
+    // exclusive prefix counts per quarter; each candidate's position goes to the slot of its
+    // rank, which is its final slot whenever every sector fits (the common case)
+    constexpr int CAP = SP_WARPS * SP_CW;
+    {
+        int off = incl - c4;
+        for (int w = 0; w < warp; ++w) off += R.wsum[w];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int q = 4 * tid + u;
+            if (q < nq) { R.mask[q] = w4[u]; R.qoff[q] = off; }
+            unsigned w = w4[u];
+            int r = off;
+            while (w) {
+                const int b = __ffs(w) - 1;
+                w &= w - 1u;
+                if (r < CAP) sh.pos[r] = 32 * q + b;
+                ++r;
+            }
+            off += __popc(w4[u]);
+        }
+        if (tid == blockDim.x - 1) R.total = off;
+    }
+    // the sum of l over each sector's pinned entries when l differs over the account: the
+    // pass's segment sums (fixed order: lane g, then the warp sum)
+    const float lo_u = D.lo_u[a], c_u = D.c_u[a];
+    if (isnan(lo_u)) {
+        for (int s = warp; s < NS; s += SP_WARPS) {
+            float so = 0.f;
+            for (int g = D.sseg[s] + lane; g < D.sseg[s + 1]; g += 32) so += D.SOp[(size_t)g * M + a];
+            so = warp_sum(so);
+            if (lane == 0) sh.sumlo[s] = so;
         }
     }
+    __syncthreads();
+    // gather the candidates' records into the rank slots (all loads issued first), and in the
+    // meantime thread 0 lays out the slot ranges: sectors in order while the slots last; a
+    // sector that does not fit is evaluated from global memory (v is there for every entry)
+    const int nfit = min(R.total, CAP);
+    const float4* recs = reinterpret_cast<const float4*>(D.crec) + 2 * base;
+    auto gather = [&](int slot, int p, int s) {
+        const float4 r0 = recs[2 * (size_t)p], r1 = recs[2 * (size_t)p + 1];
+        sh.v[slot] = r0.x; sh.w0[slot] = r0.y; sh.up[slot] = r0.z; sh.zo[slot] = r0.w; sh.yo[slot] = r1.x;
+        R.mu[slot] = r1.y; R.dd[slot] = r1.z; R.ssec[slot] = (uint8_t)s;
+        sh.lo[slot] = isnan(lo_u) ? G.lo[p] : lo_u;
+        sh.k[slot] = (isnan(c_u) ? G.c[p] : c_u) * irho;
+    };
+    for (int r0 = tid; r0 < nfit; r0 += 4 * blockDim.x) {
+        int pp[4];
+        float4 ra[4], rb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int r = r0 + u * blockDim.x;
+            pp[u] = r < nfit ? sh.pos[r] : -1;
+            if (pp[u] >= 0) { ra[u] = recs[2 * (size_t)pp[u]]; rb[u] = recs[2 * (size_t)pp[u] + 1]; }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            if (pp[u] < 0) continue;
+            const int r = r0 + u * blockDim.x, p = pp[u];
+            // the sector of position p: the last s with sec[s] <= p
+            int lo_s = 0, hi_s = NS - 1;
+            while (lo_s < hi_s) {
+                const int mid = (lo_s + hi_s + 1) >> 1;
+                if (sh.sec[mid] <= p) lo_s = mid; else hi_s = mid - 1;
+            }
+            sh.v[r] = ra[u].x; sh.w0[r] = ra[u].y; sh.up[r] = ra[u].z; sh.zo[r] = ra[u].w; sh.yo[r] = rb[u].x;
+            R.mu[r] = rb[u].y; R.dd[r] = rb[u].z; R.ssec[r] = (uint8_t)lo_s;
+            sh.lo[r] = isnan(lo_u) ? G.lo[p] : lo_u;
+            sh.k[r] = (isnan(c_u) ? G.c[p] : c_u) * irho;
+        }
+    }
+    if (tid == 0) {
+        int used = 0;
+        for (int s = 0; s < NS; ++s) {
+            const int p0 = sh.sec[s], p1 = sh.sec[s + 1];
+            const int r0 = cand_rank(R, nq, p0), n = cand_rank(R, nq, p1) - r0;
+            R.rank0[s] = r0;
+            if (!isnan(lo_u)) sh.sumlo[s] = lo_u * float(p1 - p0 - n);
+            sh.cb[s] = used;
+            if (used + n <= CAP) {
+                sh.ce[s] = used + n;
+                sh.gs[s] = p1;
+                used += n;
+            } else {
+                sh.ce[s] = used;
+                sh.gs[s] = p0;
+                sh.sumlo[s] = 0.f;
+            }
+        }
+        R.all_fit = (used == R.total);
+        R.nslots = used;
+    }
+    __syncthreads();
+    const bool all_fit = R.all_fit;
+    if (!all_fit) {
+        // a sector did not fit: the slots of the later sectors move down (rare)
+        __syncthreads();
+        for (int q = tid; q < nq; q += blockDim.x) {
+            unsigned w = R.mask[q];
+            const int qo = R.qoff[q];
+            while (w) {
+                const int b = __ffs(w) - 1;
+                w &= w - 1u;
+                const int p = 32 * q + b;
+                const int s = D.sector[p];
+                if (s < 0 || sh.gs[s] != sh.sec[s + 1]) continue;
+                const int rank = qo + __popc(R.mask[q] & ((1u << b) - 1u));
+                const int slot = sh.cb[s] + rank - R.rank0[s];
+                if (slot < rank || rank >= CAP) {   // still unwritten or moved: rewrite it here
+                    gather(slot, p, s);
+                    sh.pos[slot] = p;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    if (tid == 0 && !isnan(lo_u) && R.total < D.N) res.nz = fmaxf(res.nz, fabsf(lo_u));   // pinned z = l
+    // S_s(L) and the linear count at L, from the candidates (the pinned entries add sumlo):
+    // a thread per sector over its slots; a sector in global memory by a warp
+    if (tid < NS && sh.gs[tid] == sh.sec[tid + 1]) {
+        float acc = sh.sumlo[tid];
+        int n = 0;
+        for (int q = sh.cb[tid]; q < sh.ce[tid]; ++q) {
+            const EntryEval r = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], L, irho);
+            acc += r.z;
+            n += r.lin;
+        }
+        sh.SL[tid] = acc;
+        sh.CL[tid] = n;
+    }
+    if (!all_fit) {
+        for (int s = warp; s < NS; s += SP_WARPS) {
+            if (sh.gs[s] == sh.sec[s + 1]) continue;
+            float sum;
+            int cnt;
+            stream_sector_eval(D, sh, G, s, L, irho, sum, cnt);
+            if (lane == 0) { sh.SL[s] = sum; sh.CL[s] = cnt; }
+        }
+    }
+    stream_tail(D, sh, G, a, j, rho, irho, nu0, L, margin, res, R.mask, R.mu, R.dd, R.ssec, R.nslots);
+}
+
+size_t prox_roots_smem_bytes() { return sizeof(RootsShared); }
+
+void launch_prox_roots(const Dev& D, cudaStream_t st) {
+    const size_t smem = sizeof(RootsShared);
+    cudaFuncSetAttribute(k_prox_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    k_prox_roots<<<D.M, 32 * SP_WARPS, smem, st>>>(D);
+}
+
+// Per account: l when it is the same at every position (else NaN), and c when it is the
+// same at every position with u > l (else NaN; an entry with u = l is l whatever c is).
+__global__ void k_uniform(Dev D, float* lo_u, float* c_u) {
+    const int a = blockIdx.x;
+    const size_t base = (size_t)a * D.Npad;
+    float lmin = FLT_MAX, lmax = -FLT_MAX, cmin = FLT_MAX, cmax = -FLT_MAX;
+    for (int p = threadIdx.x; p < D.N; p += blockDim.x) {
+        const float l = D.lo[base + p], u = D.up[base + p];
+        lmin = fminf(lmin, l); lmax = fmaxf(lmax, l);
+        if (u > l) { const float c = D.c[base + p]; cmin = fminf(cmin, c); cmax = fmaxf(cmax, c); }
+    }
+    __shared__ float red[4][32];
+    lmin = warp_min(lmin); lmax = warp_max(lmax); cmin = warp_min(cmin); cmax = warp_max(cmax);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (lane == 0) { red[0][warp] = lmin; red[1][warp] = lmax; red[2][warp] = cmin; red[3][warp] = cmax; }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int w = 1; w < (int)(blockDim.x >> 5); ++w) {
+            lmin = fminf(lmin, red[0][w]); lmax = fmaxf(lmax, red[1][w]);
+            cmin = fminf(cmin, red[2][w]); cmax = fmaxf(cmax, red[3][w]);
+        }
+        lo_u[a] = (lmin == lmax) ? lmin : NAN;
+        c_u[a] = (cmin > cmax) ? 0.f : ((cmin == cmax) ? cmin : NAN);
+    }
+}
+
+void launch_uniform(const Dev& D, float* lo_u, float* c_u, cudaStream_t st) {
+    k_uniform<<<D.M, 256, 0, st>>>(D, lo_u, c_u);
 }
 
 size_t prox_stream_smem_bytes(const Dev&) { return sizeof(StreamShared); }

@@ -37,6 +37,11 @@ struct Universe {
     int* d_perm = nullptr;         // N: sorted position -> original asset
     int* d_sec_start = nullptr;    // S+1
     int* d_sector = nullptr;       // Npad: sector of each sorted position (-1 = padding)
+    // segments: the nonempty intersections of the 32-position quarters [32q, 32q + 32) with the
+    // sector ranges, numbered in position order (so each sector's segments are consecutive)
+    int nq = 0, nseg = 0;          // nq = Npad / 32
+    int* d_qseg = nullptr;         // nq + 1: first segment of each quarter
+    int* d_sseg = nullptr;         // S + 1: first segment of each sector
     double* d_B64 = nullptr;       // Npad x K (sorted, zero rows in padding)
     double* d_f64 = nullptr;       // K
     double* d_d64 = nullptr;       // Npad (1 in padding)

@@ -392,6 +392,12 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.nu = A.take<float>(M); D.dnu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
         D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(2);
         D.stats = A.take<unsigned long long>(4);
+        // partials of the fused pass (tensor-core mode)
+        const int nt = cdiv(N, 128);
+        D.SOp = A.take<float>((size_t)U.nseg * M);
+        D.Rt = A.take<float>((size_t)5 * nt * M); D.Cm = A.take<unsigned>((size_t)U.nq * M);
+        D.lo_u = A.take<float>(M); D.c_u = A.take<float>(M);
+        D.crec = A.take<float>(MN * 8);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
@@ -567,6 +573,10 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.pw_idx = pwidx; D.pw_bp = BD.pw_bpf; D.pw_sl = BD.pw_slf; D.pw_nbp = BD.pw_nbp;
     D.band_lo = BD.band_lof; D.band_hi = BD.band_hif; D.tau = BD.tauf;
     D.stream_prox = (pwidx == nullptr && !BD.has_cap) ? 1 : 0;
+    // the streaming pass runs inside the tensor-core x-update when the roots kernel can hold
+    // the account's candidate masks
+    D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && !std::getenv("PRISM_NO_FUSED")) ? 1 : 0;
+    D.nq = U.nq; D.nseg = U.nseg; D.nt = cdiv(N, 128); D.qseg = U.d_qseg; D.sseg = U.d_sseg;
     D.nsplit = nsplit;
     D.pstride = batched_mode_bf16 ? KMAX : K;
     D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
@@ -619,6 +629,17 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
                                       BD.tau, D.status, P.skip, D.active);
         launch_init_state(D, st);
     });
+    if (D.fused) {
+        SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_uniform(D, (float*)D.lo_u, (float*)D.c_u, st); });
+        // the fused kernel's variant: per-account l and c throughout, or per-entry where they differ
+        std::vector<float> lu(M), cu(M);
+        PRISM_CUDA_TRY(cudaMemcpyAsync(lu.data(), D.lo_u, M * 4, cudaMemcpyDeviceToHost, st));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(cu.data(), D.c_u, M * 4, cudaMemcpyDeviceToHost, st));
+        PRISM_CUDA_TRY(cudaStreamSynchronize(st));
+        D.uniform = 1;
+        for (int a = 0; a < M; ++a)
+            if (std::isnan(lu[a]) || std::isnan(cu[a])) D.uniform = 0;
+    }
     cudaEventRecord(SC.ev[1], st);
     // ---- ADMM iterations
     const int check_every = std::max(1, o->check_every);
@@ -626,6 +647,11 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         for (int it = 0; it < n; ++it) {
             SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
             SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
+            if (D.fused) {
+                SC.prof.run(PRISM_K_XPROX, 1, st, [&] { launch_tc_xprox(D, st); });
+                SC.prof.run(PRISM_K_ROOTS, 1, st, [&] { launch_prox_roots(D, st); });
+                continue;
+            }
             SC.prof.run(PRISM_K_GEMM_X, 1, st, [&] { if (D.bf16) launch_tc_gemm_x(D, st); else launch_gemm_x(D, st); });
             SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st); });
         }

@@ -66,6 +66,21 @@ struct Dev {
     bool bf16 = false;                  // X / Q split in BF16 for tensor-core products
     int raw_out = 0;                    // diagnostics: G4 writes B Q itself into v
     int stream_prox = 0;                // prox in the streaming form (no lots, no turnover cap)
+    // the streaming pass fused into the tensor-core x-update (k_tc_xprox), finished per
+    // account by k_prox_roots. Partials are indexed [row][account], rows as follows.
+    int fused = 0;
+    int uniform = 0;                    // every account has uniform l and c (lo_u, c_u not NaN)
+    int nq = 0, nseg = 0, nt = 0;       // quarters (32 positions), segments, asset tiles (128 positions)
+    const int* qseg = nullptr;          // nq + 1: first segment of each quarter
+    const int* sseg = nullptr;          // S + 1: first segment of each sector
+    const float* lo_u = nullptr;        // M: l when equal over the account's positions, else NaN
+    const float* c_u = nullptr;         // M: c when equal over its positions with u > l, else NaN
+    float* SOp = nullptr;               // nseg x M: sum of l_i over the segment's entries pinned at L
+                                        // (written only for accounts whose l differs over positions)
+    float* Rt = nullptr;                // 5 x nt x M: residual maxima (rp, rd, nx, nz, ny) of the pinned
+                                        // entries of each asset tile; rp is NaN when one was not finite
+    unsigned* Cm = nullptr;             // nq x M: bit b of quarter q set = entry 32q + b not pinned at L
+    float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
 };
 
@@ -86,5 +101,9 @@ bool tc_available();                                     // tensor-map encoder r
 int tc_nsplit(int M, int N, int* chunk);                 // partial sets of the tensor-core G2 (its asset chunk)
 void launch_tc_gemm_P(const Dev& D, cudaStream_t st);    // G2 on tcgen05
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
+void launch_tc_xprox(const Dev& D, cudaStream_t st);     // G4 + the streaming pass of G5 (fused)
+void launch_prox_roots(const Dev& D, cudaStream_t st);   // G5/G6 per account after k_tc_xprox
+void launch_uniform(const Dev& D, float* lo_u, float* c_u, cudaStream_t st);   // per-account uniform l, c
+constexpr int XP_NQMAX = 1024;                           // quarters the roots kernel holds (N <= 32768)
 
 }  // namespace prism

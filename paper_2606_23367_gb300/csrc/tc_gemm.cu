@@ -456,6 +456,278 @@ __global__ void __launch_bounds__(G4_THREADS, 3) k_tc_gemm_x(const __grid_consta
 }
 
 // ---------------------------------------------------------------------------
+// G4 fused with the streaming pass of G5 (books with the L1 cost only, no cap).
+// Tiles of 128 assets x 32 accounts (TMEM lane = asset, column = account), so that about six
+// small CTAs share each SM and the loads of many of them are in flight together. For
+// each entry the epilogue forms v, writes it, and evaluates the prox at L = nu_prev - margin:
+//   z_i(L) = clip(soft(v_i - L/rho - w0_i, c_i/rho) + w0_i, l_i, u_i).
+// z_i(eta) is nonincreasing in eta, so an entry with z_i(L) = l_i keeps z = l_i at every
+// eta >= L: its z, y = rho (v - l) and X are final and written here. Per account and
+// 32-position quarter the warp leaves the mask of the other entries (the candidates that
+// k_prox_roots gathers) and the residual maxima of the pinned entries (combined over the
+// tile's quarters); when l differs over the account, also the sum of l over the pinned
+// entries of each sector segment.
+// ---------------------------------------------------------------------------
+constexpr int XP_CC = 4;          // accounts per epilogue chunk
+constexpr int XP_TN = 32;         // accounts per tile (MMA N): small tiles, many CTAs per SM
+constexpr int XP_THREADS = 128;   // warp w reads TMEM lane quarter w (32 assets) for all XP_TN accounts
+constexpr uint32_t XP_Q_BYTES = XP_TN * KP * 2;
+
+struct __align__(1024) XPSmem {
+    __nv_bfloat16 a[TM * KP];
+    __nv_bfloat16 bhi[XP_TN * KP];
+    __nv_bfloat16 blo[XP_TN * KP];
+    uint64_t full;
+    uint64_t done;
+    uint32_t tmem;
+    int fail;
+    float4 pa[XP_TN];                 // per account column: rho, 1/rho, L, c (NaN: c differs over positions)
+    float4 pb[XP_TN];                 // l (NaN: differs), active, adaptation call, unused
+    // per-warp staging: [warp][quantity][account column]
+    float r5[XP_THREADS / 32][5][XP_TN];
+    unsigned cm[XP_THREADS / 32][XP_TN];
+};
+
+__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
+    uint32_t r[4];
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+                 : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
+}
+
+// 1/x to within 1 ulp (the hardware approximation; x > 0 and normal here)
+__device__ __forceinline__ float rcp_approx(float x) {
+    float r;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+    return r;
+}
+
+struct XPIn {
+    float z[XP_CC], y[XP_CC], w0[XP_CC], up[XP_CC];
+};
+
+// z, y, w0, u of one chunk of accounts for this thread's asset (coalesced over the warp);
+// inactive accounts are not read. off0: offset of the chunk's first account at this asset.
+__device__ __forceinline__ void xp_load(const Dev& D, const XPSmem& s, int off0, int c0, XPIn& in) {
+#pragma unroll
+    for (int j = 0; j < XP_CC; ++j) {
+        const bool ok = s.pb[c0 + j].y != 0.f;
+        const int off = off0 + j * D.Npad;
+        in.z[j] = ok ? __ldg(D.z + off) : 0.f;
+        in.y[j] = ok ? __ldg(D.y + off) : 0.f;
+        in.w0[j] = ok ? __ldg(D.w0 + off) : 0.f;
+        in.up[j] = ok ? __ldg(D.up + off) : 0.f;
+    }
+}
+
+__device__ __forceinline__ float warp_sum_f(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// maximum over the warp of nonnegative floats (their bit patterns order as integers; a NaN
+// with the sign bit clear orders above +inf, so it survives)
+__device__ __forceinline__ float warp_max_nn(float v) {
+    return __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(v)));
+}
+
+// UNIFORM: every account has one l over its positions and one c over those with u > l (the
+// values come from shared memory; no per-entry l, c and no segment sums of l)
+template <bool UNIFORM>
+__global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constant__ CUtensorMap mB,
+                                                           const __grid_constant__ CUtensorMap mQhi,
+                                                           const __grid_constant__ CUtensorMap mQlo, Dev D) {
+    extern __shared__ unsigned char raw[];
+    XPSmem& s = *reinterpret_cast<XPSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int at = blockIdx.x, mt = blockIdx.y;
+    constexpr uint32_t IDESC = idesc_bf16(TM, XP_TN);
+    {
+        const int m = mt * XP_TN + tid;
+        const int act = tid < XP_TN && (m < D.M && D.active[m]);
+        if (!__syncthreads_or(act)) return;
+    }
+    if (warp == 0) tmem_alloc(&s.tmem, XP_TN);
+    if (tid == 0) {
+        mbar_init(&s.full, 1);
+        mbar_init(&s.done, 1);
+        s.fail = 0;
+        fence_barrier_init();
+    }
+    if (tid < XP_TN) {
+        const int m = mt * XP_TN + tid;
+        const bool ok = m < D.M;
+        const float r = ok ? rho_of_idx(D.rho_idx[m]) : 1.f;
+        const float L = ok ? D.nu[m] - fmaxf(4.f * D.dnu[m], 2e-3f) : 0.f;
+        s.pa[tid] = make_float4(r, 1.f / r, L, ok ? D.c_u[m] : 0.f);
+        const bool act = ok && D.active[m];
+        const bool adapt = act && ((D.iters[m] + 1) % D.adapt_every == 0);
+        s.pb[tid] = make_float4(ok ? D.lo_u[m] : 0.f, act ? 1.f : 0.f, adapt ? 1.f : 0.f, 0.f);
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s.tmem;
+    if (tid == 0) {
+        mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
+        tma_load_2d(s.a, &mB, &s.full, 0, at * TM);
+        tma_load_2d(s.bhi, &mQhi, &s.full, 0, mt * XP_TN);
+        tma_load_2d(s.blo, &mQlo, &s.full, 0, mt * XP_TN);
+    }
+    const int q = warp;
+    const int i = at * TM + q * 32 + lane;              // asset of this TMEM lane
+    const int ii = i < D.N ? i : 0;
+    const int col0 = 0;
+    const int m_base = mt * XP_TN;
+    const int obase = m_base * D.Npad + ii;             // offset of (first account of the tile, asset)
+    XPIn ba, bb;
+    xp_load(D, s, obase, col0, ba);
+    xp_load(D, s, obase + XP_CC * D.Npad, col0 + XP_CC, bb);
+    const float mu = D.mu32[ii], dd = 2.f * D.d32[ii];
+    // sector segments of this quarter: lanes with equal sectors are consecutive
+    const int sec = i < D.N ? D.sector[i] : -1;
+    const int prev = __shfl_up_sync(0xffffffffu, sec, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, i < D.N && (lane == 0 || prev != sec));
+    const int nsegq = __popc(starts);
+    const int segl = __popc(starts & ((2u << lane) - 1u)) - 1;
+    const int gq = at * 4 + q;
+    const int sbase = (gq < D.nq) ? D.qseg[gq] : 0;
+    if (tid == 0) {
+        if (mbar_wait(&s.full, 0, D.err, 16)) {
+            fence_after_sync();
+            const uint64_t da = sw128_desc(s.a), dh = sw128_desc(s.bhi), dl = sw128_desc(s.blo);
+#pragma unroll
+            for (int kk = 0; kk < KP / 16; ++kk) {
+                umma_bf16(tmem, da + 2 * kk, dh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
+                umma_bf16(tmem, da + 2 * kk, dl + 2 * kk, IDESC, 1u);
+            }
+            umma_commit(&s.done);
+        } else {
+            s.fail = 1;
+        }
+    }
+    __syncthreads();
+    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
+    have = __syncthreads_and(have);
+    fence_after_sync();
+    const bool row_ok = have && i < D.N;
+    const uint32_t lane_addr = tmem + (uint32_t(q * 32) << 16) + col0;
+    const float alpha = D.alpha;
+    float4* crec = reinterpret_cast<float4*>(D.crec);
+    // The XP_CC accounts of a chunk are processed without branches on the entry (an inactive
+    // account's values are zero and nothing of it is stored), so their reductions interleave.
+    auto consume = [&](int c, XPIn& in) {
+        float bq[XP_CC];
+        if (have) tmem_ld4(lane_addr + c * XP_CC, bq);
+        else
+#pragma unroll
+            for (int j = 0; j < XP_CC; ++j) bq[j] = 0.f;
+#pragma unroll
+        for (int j = 0; j < XP_CC; ++j) {
+            const int ch = c * XP_CC + j;               // account column within the tile
+            const int col = col0 + ch;
+            const float4 pa = s.pa[col], pb = s.pb[col];
+            const float rho = pa.x, irho = pa.y, L = pa.z;
+            const bool ok = row_ok && pb.y != 0.f;
+            const int off = obase + ch * D.Npad;
+            float lo = pb.x, cc = pa.w;
+            const bool lou = UNIFORM || !isnan(lo);     // warp-uniform
+            if (!UNIFORM) {
+                if (ok && !lou) lo = D.lo[off];
+                if (ok && isnan(cc)) cc = D.c[off];
+            }
+            const float k = cc * irho;
+            const float z0 = in.z[j], y0 = in.y[j], w0 = in.w0[j], up = in.up[j];
+            const float inv = rcp_approx(dd + rho);
+            const float x = (mu + rho * z0 - y0 - bq[j]) * inv;
+            const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
+            const float t = v - L * irho;
+            float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+            z = fminf(fmaxf(z, lo), up);
+            const bool pin = ok && (z == lo);
+            const bool cand = ok && !pin;
+            const float yn = rho * (v - lo);
+            // a non-finite pinned update makes rp NaN (reported as a numerical failure)
+            const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
+            const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
+            if (ok) D.v[off] = v;
+            if (pin) {
+                D.z[off] = lo;
+                D.y[off] = yn;
+                const float X = (mu + rho * lo - yn) * inv;
+                const __nv_bfloat16 h = __float2bfloat16_rn(X);
+                D.Xhi[off] = h;
+                D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+            }
+            if (cand) {
+                // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
+                // z, y, mu, d (l and c are read per entry there when they differ over the account)
+                crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
+                crec[2 * (size_t)off + 1] = make_float4(y0, mu, 0.5f * dd, 0.f);
+            }
+            const unsigned cm = __ballot_sync(0xffffffffu, cand);
+            const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
+            float nx = 0.f, nz = 0.f, ny = 0.f;
+            if (pb.z != 0.f) {                          // penalty adaptation on this call (uniform)
+                nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
+                ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
+                if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
+            }
+            if (!UNIFORM && !lou) {
+                // l differs over the account: the sums of l over the pinned entries, per segment
+                const int m = m_base + ch;
+                for (int g = 0; g < nsegq; ++g) {
+                    const bool mine = (i < D.N) && segl == g && pin;
+                    const float sg = warp_sum_f(mine ? lo : 0.f);
+                    if (lane == 0 && pb.y != 0.f) D.SOp[(size_t)(sbase + g) * D.M + m] = sg;
+                }
+            }
+            if (lane == 0) {
+                s.r5[warp][0][ch] = rp;
+                s.r5[warp][1][ch] = rd; s.r5[warp][2][ch] = nx; s.r5[warp][3][ch] = nz; s.r5[warp][4][ch] = ny;
+                s.cm[warp][ch] = cm;
+            }
+        }
+        if (c + 2 < XP_TN / XP_CC)
+            xp_load(D, s, obase + (c + 2) * XP_CC * D.Npad, col0 + (c + 2) * XP_CC, in);
+    };
+#pragma unroll 1
+    for (int c = 0; c < XP_TN / XP_CC; c += 2) {
+        consume(c, ba);
+        consume(c + 1, bb);
+    }
+    fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tmem_dealloc(tmem, XP_TN);
+    if (!have) return;
+    // per-tile residual maxima (over the four quarters, NaN kept) and the masks, each row
+    // written coalesced over the tile's accounts
+    for (int it = tid; it < 5 * XP_TN; it += XP_THREADS) {
+        const int kq = it / XP_TN, col = it % XP_TN, m = mt * XP_TN + col;
+        if (m >= D.M || s.pb[col].y == 0.f) continue;
+        float r = 0.f;
+        bool nan_ = false;
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const float x = s.r5[qq][kq][col];
+            nan_ |= isnan(x);
+            r = fmaxf(r, x);
+        }
+        D.Rt[((size_t)kq * D.nt + at) * D.M + m] = nan_ ? NAN : r;
+    }
+    for (int it = tid; it < 4 * XP_TN; it += XP_THREADS) {
+        const int w = it / XP_TN, col = it % XP_TN, m = mt * XP_TN + col;
+        const int g = at * 4 + w;
+        if (m >= D.M || s.pb[col].y == 0.f || g >= D.nq) continue;
+        D.Cm[(size_t)g * D.M + m] = s.cm[w][col];
+    }
+}
+
+// ---------------------------------------------------------------------------
 // host side: tensor maps and launches
 // ---------------------------------------------------------------------------
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -542,6 +814,23 @@ void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
     cudaFuncSetAttribute(tc::k_tc_gemm_x, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::G4_TN));
     tc::k_tc_gemm_x<<<grid, tc::G4_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
+}
+
+void launch_tc_xprox(const Dev& D, cudaStream_t st) {
+    CUtensorMap mB, mQhi, mQlo;
+    bool ok = tc::map2d(&mB, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
+              tc::map2d(&mQhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
+              tc::map2d(&mQlo, D.Qlo, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN);
+    if (!ok) { set_error("tensor map encoding failed (G4 fused)"); return; }
+    const size_t smem = sizeof(tc::XPSmem) + 1024;
+    dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::XP_TN));
+    if (D.uniform) {
+        cudaFuncSetAttribute(tc::k_tc_xprox<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc::k_tc_xprox<true><<<grid, tc::XP_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
+    } else {
+        cudaFuncSetAttribute(tc::k_tc_xprox<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        tc::k_tc_xprox<false><<<grid, tc::XP_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
+    }
 }
 
 }  // namespace prism

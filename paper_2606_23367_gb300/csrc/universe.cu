@@ -152,7 +152,7 @@ static int fetch(const T* src, size_t n, std::vector<T>& dst) {
 }
 
 static void free_universe(Universe& U) {
-    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1, U.d_Bn1f,
+    void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_qseg, U.d_sseg, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1, U.d_Bn1f,
                     U.d_mu64, U.d_B32, U.d_B32p, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
                     U.d_Cinv32, U.d_Cinv16};
     for (void* p : ptrs)
@@ -238,6 +238,17 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         secs[p] = sec[i];
     }
     std::vector<float> f32(f.begin(), f.end()), d32(ds.begin(), ds.end()), mu32(mus.begin(), mus.end());
+    // quarter / sector segments (sorted positions: sector ids are nondecreasing in p)
+    U.nq = Npad / 32;
+    std::vector<int> qseg(U.nq + 1, 0), sseg(S + 1, 0);
+    for (int q = 0; q < U.nq; ++q) {
+        int n = 0;
+        for (int p = 32 * q; p < std::min(32 * q + 32, N); ++p)
+            if (p == 32 * q || secs[p] != secs[p - 1]) { ++n; ++sseg[secs[p] + 1]; }
+        qseg[q + 1] = qseg[q] + n;
+    }
+    for (int s = 0; s < S; ++s) sseg[s + 1] += sseg[s];
+    U.nseg = qseg[U.nq];
     std::vector<double> bn1(Npad, 0.0);
     for (int p = 0; p < N; ++p)
         for (int k = 0; k < K; ++k) bn1[p] += std::fabs(Bs[(size_t)p * K + k]);
@@ -248,6 +259,8 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     TRY(dalloc(U, &U.d_perm, N));
     TRY(dalloc(U, &U.d_sec_start, S + 1));
     TRY(dalloc(U, &U.d_sector, Npad));
+    TRY(dalloc(U, &U.d_qseg, U.nq + 1));
+    TRY(dalloc(U, &U.d_sseg, S + 1));
     TRY(dalloc(U, &U.d_B64, (size_t)Npad * K));
     TRY(dalloc(U, &U.d_f64, K));
     TRY(dalloc(U, &U.d_d64, Npad));
@@ -272,6 +285,8 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         H2D(U.d_perm, U.perm.data(), N * sizeof(int)) ||
         H2D(U.d_sec_start, U.sec_start.data(), (S + 1) * sizeof(int)) ||
         H2D(U.d_sector, secs.data(), Npad * sizeof(int)) ||
+        H2D(U.d_qseg, qseg.data(), (U.nq + 1) * sizeof(int)) ||
+        H2D(U.d_sseg, sseg.data(), (S + 1) * sizeof(int)) ||
         H2D(U.d_B64, Bs.data(), Bs.size() * sizeof(double)) ||
         H2D(U.d_f64, f.data(), K * sizeof(double)) ||
         H2D(U.d_d64, ds.data(), Npad * sizeof(double)) ||

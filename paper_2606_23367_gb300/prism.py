@@ -23,7 +23,7 @@ PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16 = 0, 1, 2
 PRISM_NDIAG = 8
 (PRISM_DIAG_BUDGET, PRISM_DIAG_BOX, PRISM_DIAG_EXPOSURE, PRISM_DIAG_TURNOVER, PRISM_DIAG_STAT, PRISM_DIAG_COMP,
  PRISM_DIAG_OBJ, PRISM_DIAG_ITERS) = range(8)
-KERNEL_CLASSES = ("gemm_P", "solve_K", "gemm_x", "prox", "polish", "pack", "other", "unpack")
+KERNEL_CLASSES = ("gemm_P", "solve_K", "gemm_x", "prox", "polish", "pack", "other", "unpack", "xprox", "roots")
 DIAG_NAMES = ("r_budget", "r_box", "r_exposure", "r_turnover", "r_stat", "r_comp", "obj", "polish_rounds")
 STATUS_NAMES = ("CERTIFIED", "FEASIBLE_NONCERTIFIED", "TIMEOUT", "DEADLINE_EXCEEDED",
                 "NO_FEASIBLE_RETURN", "ALLOCATION_FAILURE", "NUMERICAL_FAILURE")
@@ -65,7 +65,7 @@ class _Result(C.Structure):
                 ("status", C.c_void_p), ("iters", C.c_void_p), ("diag", C.c_void_p),
                 ("t_device_ms", C.c_double), ("t_call_ms", C.c_double), ("t_phase_ms", C.c_double * 4),
                 ("device_bytes", C.c_int64), ("n_launches", C.c_int64),
-                ("kernel_ms", C.c_double * 8), ("kernel_launches", C.c_int64 * 8),
+                ("kernel_ms", C.c_double * len(KERNEL_CLASSES)), ("kernel_launches", C.c_int64 * len(KERNEL_CLASSES)),
                 ("state", C.c_void_p)]
 
 
