@@ -124,6 +124,9 @@ typedef struct {
     int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
                                  prism_solve_batch_backward (batched modes only) */
     int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
+    int32_t fuse_prox;        /* 1: for books with the L1 cost only (no lots, no cap) in BATCHED_BF16,
+                                 the prox's streaming pass runs inside the tensor-core x-update
+                                 (default 1); 0: separate x-update and prox kernels (same method) */
     void*   cuda_stream;      /* cudaStream_t to run on (NULL = the library's own stream) */
 } prism_solve_opts;
 

@@ -575,7 +575,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.stream_prox = (pwidx == nullptr && !BD.has_cap) ? 1 : 0;
     // the streaming pass runs inside the tensor-core x-update when the roots kernel can hold
     // the account's candidate masks
-    D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && !std::getenv("PRISM_NO_FUSED")) ? 1 : 0;
+    D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && o->fuse_prox) ? 1 : 0;
     D.nq = U.nq; D.nseg = U.nseg; D.nt = cdiv(N, 128); D.qseg = U.d_qseg; D.sseg = U.d_sseg;
     D.nsplit = nsplit;
     D.pstride = batched_mode_bf16 ? KMAX : K;
@@ -846,6 +846,7 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     o->polish_rounds = 8;
     o->precision = PRISM_BATCHED_BF16;
     o->use_graph = 1;
+    o->fuse_prox = 1;
     o->keep_for_backward = 0;
     o->cuda_stream = nullptr;
 }

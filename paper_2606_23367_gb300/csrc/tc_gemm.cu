@@ -468,59 +468,32 @@ __global__ void __launch_bounds__(G4_THREADS, 3) k_tc_gemm_x(const __grid_consta
 // tile's quarters); when l differs over the account, also the sum of l over the pinned
 // entries of each sector segment.
 // ---------------------------------------------------------------------------
-constexpr int XP_CC = 4;          // accounts per epilogue chunk
-constexpr int XP_TN = 32;         // accounts per tile (MMA N): small tiles, many CTAs per SM
+constexpr int XP_TN = 16;         // accounts per tile (MMA N): small tiles, about four CTAs per SM
 constexpr int XP_THREADS = 128;   // warp w reads TMEM lane quarter w (32 assets) for all XP_TN accounts
 constexpr uint32_t XP_Q_BYTES = XP_TN * KP * 2;
+constexpr uint32_t XP_IN_BYTES = XP_TN * TM * 4;   // one input array of the tile (FP32)
 
 struct __align__(1024) XPSmem {
-    __nv_bfloat16 a[TM * KP];
-    __nv_bfloat16 bhi[XP_TN * KP];
+    __nv_bfloat16 a[TM * KP];         // B tile (operand A of the MMA)
+    __nv_bfloat16 bhi[XP_TN * KP];    // Q split (operand B)
     __nv_bfloat16 blo[XP_TN * KP];
-    uint64_t full;
-    uint64_t done;
+    float in[4][XP_TN][TM];           // z, y, w0, u of the tile: [array][account][asset]
+    uint64_t full;                    // operands landed
+    uint64_t full_in;                 // inputs landed
+    uint64_t done;                    // MMA complete
     uint32_t tmem;
     int fail;
     float4 pa[XP_TN];                 // per account column: rho, 1/rho, L, c (NaN: c differs over positions)
     float4 pb[XP_TN];                 // l (NaN: differs), active, adaptation call, unused
-    // per-warp staging: [warp][quantity][account column]
-    float r5[XP_THREADS / 32][5][XP_TN];
-    unsigned cm[XP_THREADS / 32][XP_TN];
+    float r5[XP_THREADS / 32][5][XP_TN];   // per-warp residual maxima
+    unsigned cm[XP_THREADS / 32][XP_TN];   // per-warp candidate masks
 };
-
-__device__ __forceinline__ void tmem_ld4(uint32_t taddr, float* v) {
-    uint32_t r[4];
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x4.b32 {%0,%1,%2,%3}, [%4];"
-                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-    for (int j = 0; j < 4; ++j) v[j] = __uint_as_float(r[j]);
-}
 
 // 1/x to within 1 ulp (the hardware approximation; x > 0 and normal here)
 __device__ __forceinline__ float rcp_approx(float x) {
     float r;
     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
     return r;
-}
-
-struct XPIn {
-    float z[XP_CC], y[XP_CC], w0[XP_CC], up[XP_CC];
-};
-
-// z, y, w0, u of one chunk of accounts for this thread's asset (coalesced over the warp);
-// inactive accounts are not read. off0: offset of the chunk's first account at this asset.
-__device__ __forceinline__ void xp_load(const Dev& D, const XPSmem& s, int off0, int c0, XPIn& in) {
-#pragma unroll
-    for (int j = 0; j < XP_CC; ++j) {
-        const bool ok = s.pb[c0 + j].y != 0.f;
-        const int off = off0 + j * D.Npad;
-        in.z[j] = ok ? __ldg(D.z + off) : 0.f;
-        in.y[j] = ok ? __ldg(D.y + off) : 0.f;
-        in.w0[j] = ok ? __ldg(D.w0 + off) : 0.f;
-        in.up[j] = ok ? __ldg(D.up + off) : 0.f;
-    }
 }
 
 __device__ __forceinline__ float warp_sum_f(float v) {
@@ -535,12 +508,14 @@ __device__ __forceinline__ float warp_max_nn(float v) {
     return __int_as_float(__reduce_max_sync(0xffffffffu, __float_as_int(v)));
 }
 
+struct XPMaps {
+    CUtensorMap B, Qhi, Qlo, z, y, w0, up;
+};
+
 // UNIFORM: every account has one l over its positions and one c over those with u > l (the
 // values come from shared memory; no per-entry l, c and no segment sums of l)
 template <bool UNIFORM>
-__global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constant__ CUtensorMap mB,
-                                                           const __grid_constant__ CUtensorMap mQhi,
-                                                           const __grid_constant__ CUtensorMap mQlo, Dev D) {
+__global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constant__ XPMaps mp, Dev D) {
     extern __shared__ unsigned char raw[];
     XPSmem& s = *reinterpret_cast<XPSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -551,9 +526,10 @@ __global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constan
         const int act = tid < XP_TN && (m < D.M && D.active[m]);
         if (!__syncthreads_or(act)) return;
     }
-    if (warp == 0) tmem_alloc(&s.tmem, XP_TN);
+    if (warp == 0) tmem_alloc(&s.tmem, 32);
     if (tid == 0) {
         mbar_init(&s.full, 1);
+        mbar_init(&s.full_in, 1);
         mbar_init(&s.done, 1);
         s.fail = 0;
         fence_barrier_init();
@@ -573,20 +549,24 @@ __global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constan
     fence_after_sync();
     const uint32_t tmem = s.tmem;
     if (tid == 0) {
+        // operands, then the tile's inputs (rows of accounts beyond M and columns beyond Npad
+        // arrive as zeros); the inputs need no MMA and are consumed after it
         mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
-        tma_load_2d(s.a, &mB, &s.full, 0, at * TM);
-        tma_load_2d(s.bhi, &mQhi, &s.full, 0, mt * XP_TN);
-        tma_load_2d(s.blo, &mQlo, &s.full, 0, mt * XP_TN);
+        tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
+        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, mt * XP_TN);
+        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, mt * XP_TN);
+        mbar_expect_tx(&s.full_in, 4 * XP_IN_BYTES);
+        tma_load_2d(s.in[0], &mp.z, &s.full_in, at * TM, mt * XP_TN);
+        tma_load_2d(s.in[1], &mp.y, &s.full_in, at * TM, mt * XP_TN);
+        tma_load_2d(s.in[2], &mp.w0, &s.full_in, at * TM, mt * XP_TN);
+        tma_load_2d(s.in[3], &mp.up, &s.full_in, at * TM, mt * XP_TN);
     }
     const int q = warp;
-    const int i = at * TM + q * 32 + lane;              // asset of this TMEM lane
+    const int ia = q * 32 + lane;                       // asset within the tile (TMEM lane)
+    const int i = at * TM + ia;
     const int ii = i < D.N ? i : 0;
-    const int col0 = 0;
     const int m_base = mt * XP_TN;
     const int obase = m_base * D.Npad + ii;             // offset of (first account of the tile, asset)
-    XPIn ba, bb;
-    xp_load(D, s, obase, col0, ba);
-    xp_load(D, s, obase + XP_CC * D.Npad, col0 + XP_CC, bb);
     const float mu = D.mu32[ii], dd = 2.f * D.d32[ii];
     // sector segments of this quarter: lanes with equal sectors are consecutive
     const int sec = i < D.N ? D.sector[i] : -1;
@@ -611,103 +591,87 @@ __global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constan
         }
     }
     __syncthreads();
-    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
+    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32) && mbar_wait(&s.full_in, 0, D.err, 64);
     have = __syncthreads_and(have);
     fence_after_sync();
     const bool row_ok = have && i < D.N;
-    const uint32_t lane_addr = tmem + (uint32_t(q * 32) << 16) + col0;
+    float bq[XP_TN];
+    if (have) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
     const float alpha = D.alpha;
     float4* crec = reinterpret_cast<float4*>(D.crec);
-    // The XP_CC accounts of a chunk are processed without branches on the entry (an inactive
-    // account's values are zero and nothing of it is stored), so their reductions interleave.
-    auto consume = [&](int c, XPIn& in) {
-        float bq[XP_CC];
-        if (have) tmem_ld4(lane_addr + c * XP_CC, bq);
-        else
+    // The accounts are processed without branches on the entry (an inactive account's values
+    // are zero and nothing of it is stored), so their reductions interleave.
 #pragma unroll
-            for (int j = 0; j < XP_CC; ++j) bq[j] = 0.f;
-#pragma unroll
-        for (int j = 0; j < XP_CC; ++j) {
-            const int ch = c * XP_CC + j;               // account column within the tile
-            const int col = col0 + ch;
-            const float4 pa = s.pa[col], pb = s.pb[col];
-            const float rho = pa.x, irho = pa.y, L = pa.z;
-            const bool ok = row_ok && pb.y != 0.f;
-            const int off = obase + ch * D.Npad;
-            float lo = pb.x, cc = pa.w;
-            const bool lou = UNIFORM || !isnan(lo);     // warp-uniform
-            if (!UNIFORM) {
-                if (ok && !lou) lo = D.lo[off];
-                if (ok && isnan(cc)) cc = D.c[off];
-            }
-            const float k = cc * irho;
-            const float z0 = in.z[j], y0 = in.y[j], w0 = in.w0[j], up = in.up[j];
-            const float inv = rcp_approx(dd + rho);
-            const float x = (mu + rho * z0 - y0 - bq[j]) * inv;
-            const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
-            const float t = v - L * irho;
-            float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
-            z = fminf(fmaxf(z, lo), up);
-            const bool pin = ok && (z == lo);
-            const bool cand = ok && !pin;
-            const float yn = rho * (v - lo);
-            // a non-finite pinned update makes rp NaN (reported as a numerical failure)
-            const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
-            const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
-            if (ok) D.v[off] = v;
-            if (pin) {
-                D.z[off] = lo;
-                D.y[off] = yn;
-                const float X = (mu + rho * lo - yn) * inv;
-                const __nv_bfloat16 h = __float2bfloat16_rn(X);
-                D.Xhi[off] = h;
-                D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
-            }
-            if (cand) {
-                // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
-                // z, y, mu, d (l and c are read per entry there when they differ over the account)
-                crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
-                crec[2 * (size_t)off + 1] = make_float4(y0, mu, 0.5f * dd, 0.f);
-            }
-            const unsigned cm = __ballot_sync(0xffffffffu, cand);
-            const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
-            float nx = 0.f, nz = 0.f, ny = 0.f;
-            if (pb.z != 0.f) {                          // penalty adaptation on this call (uniform)
-                nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
-                ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
-                if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
-            }
-            if (!UNIFORM && !lou) {
-                // l differs over the account: the sums of l over the pinned entries, per segment
-                const int m = m_base + ch;
-                for (int g = 0; g < nsegq; ++g) {
-                    const bool mine = (i < D.N) && segl == g && pin;
-                    const float sg = warp_sum_f(mine ? lo : 0.f);
-                    if (lane == 0 && pb.y != 0.f) D.SOp[(size_t)(sbase + g) * D.M + m] = sg;
-                }
-            }
-            if (lane == 0) {
-                s.r5[warp][0][ch] = rp;
-                s.r5[warp][1][ch] = rd; s.r5[warp][2][ch] = nx; s.r5[warp][3][ch] = nz; s.r5[warp][4][ch] = ny;
-                s.cm[warp][ch] = cm;
+    for (int j = 0; j < XP_TN; ++j) {
+        const float4 pa = s.pa[j], pb = s.pb[j];
+        const float rho = pa.x, irho = pa.y, L = pa.z;
+        const bool ok = row_ok && pb.y != 0.f;
+        const int off = obase + j * D.Npad;
+        float lo = pb.x, cc = pa.w;
+        const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
+        if (!UNIFORM) {
+            if (ok && !lou) lo = D.lo[off];
+            if (ok && isnan(cc)) cc = D.c[off];
+        }
+        const float k = cc * irho;
+        const float z0 = s.in[0][j][ia], y0 = s.in[1][j][ia], w0 = s.in[2][j][ia], up = s.in[3][j][ia];
+        const float inv = rcp_approx(dd + rho);
+        const float x = (mu + rho * z0 - y0 - bq[j]) * inv;
+        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
+        const float t = v - L * irho;
+        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+        z = fminf(fmaxf(z, lo), up);
+        const bool pin = ok && (z == lo);
+        const bool cand = ok && !pin;
+        const float yn = rho * (v - lo);
+        // a non-finite pinned update makes rp NaN (reported as a numerical failure)
+        const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
+        const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
+        if (ok) D.v[off] = v;
+        if (pin) {
+            D.z[off] = lo;
+            D.y[off] = yn;
+            const float X = (mu + rho * lo - yn) * inv;
+            const __nv_bfloat16 h = __float2bfloat16_rn(X);
+            D.Xhi[off] = h;
+            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+        }
+        if (cand) {
+            // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
+            // z, y, mu, d (l and c are read per entry there when they differ over the account)
+            crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
+            crec[2 * (size_t)off + 1] = make_float4(y0, mu, 0.5f * dd, 0.f);
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
+        float nx = 0.f, nz = 0.f, ny = 0.f;
+        if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
+            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
+            ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
+            if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
+        }
+        if (!UNIFORM && !lou) {
+            // l differs over the account: the sums of l over the pinned entries, per segment
+            for (int g = 0; g < nsegq; ++g) {
+                const bool mine = (i < D.N) && segl == g && pin;
+                const float sg = warp_sum_f(mine ? lo : 0.f);
+                if (lane == 0 && pb.y != 0.f) D.SOp[(size_t)(sbase + g) * D.M + m_base + j] = sg;
             }
         }
-        if (c + 2 < XP_TN / XP_CC)
-            xp_load(D, s, obase + (c + 2) * XP_CC * D.Npad, col0 + (c + 2) * XP_CC, in);
-    };
-#pragma unroll 1
-    for (int c = 0; c < XP_TN / XP_CC; c += 2) {
-        consume(c, ba);
-        consume(c + 1, bb);
+        if (lane == 0) {
+            s.r5[warp][0][j] = rp;
+            s.r5[warp][1][j] = rd; s.r5[warp][2][j] = nx; s.r5[warp][3][j] = nz; s.r5[warp][4][j] = ny;
+            s.cm[warp][j] = cm;
+        }
     }
     fence_before_sync();
     __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, XP_TN);
+    if (warp == 0) tmem_dealloc(tmem, 32);
     if (!have) return;
     // per-tile residual maxima (over the four quarters, NaN kept) and the masks, each row
     // written coalesced over the tile's accounts
     for (int it = tid; it < 5 * XP_TN; it += XP_THREADS) {
-        const int kq = it / XP_TN, col = it % XP_TN, m = mt * XP_TN + col;
+        const int kq = it / XP_TN, col = it % XP_TN, m = m_base + col;
         if (m >= D.M || s.pb[col].y == 0.f) continue;
         float r = 0.f;
         bool nan_ = false;
@@ -720,7 +684,7 @@ __global__ void __launch_bounds__(XP_THREADS, 6) k_tc_xprox(const __grid_constan
         D.Rt[((size_t)kq * D.nt + at) * D.M + m] = nan_ ? NAN : r;
     }
     for (int it = tid; it < 4 * XP_TN; it += XP_THREADS) {
-        const int w = it / XP_TN, col = it % XP_TN, m = mt * XP_TN + col;
+        const int w = it / XP_TN, col = it % XP_TN, m = m_base + col;
         const int g = at * 4 + w;
         if (m >= D.M || s.pb[col].y == 0.f || g >= D.nq) continue;
         D.Cm[(size_t)g * D.M + m] = s.cm[w][col];
@@ -762,6 +726,20 @@ static bool map2d(CUtensorMap* m, const void* base, uint64_t dim0, uint64_t dim1
     cuuint32_t es[2] = {1, 1};
     return enc(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, es,
                CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// 2-D FP32 map of an M x Npad account-major array: boxes of box0 positions x box1 accounts,
+// no swizzle (the epilogue reads a row of positions per account), zero fill out of range.
+static bool map2d_f32(CUtensorMap* m, const void* base, uint64_t npad, uint64_t rows, uint32_t box0, uint32_t box1) {
+    EncodeTiled enc = encoder();
+    if (!enc) return false;
+    cuuint64_t dims[2] = {npad, rows};
+    cuuint64_t strides[1] = {npad * 4};
+    cuuint32_t box[2] = {box0, box1};
+    cuuint32_t es[2] = {1, 1};
+    return enc(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, es,
+               CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -817,19 +795,23 @@ void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
 }
 
 void launch_tc_xprox(const Dev& D, cudaStream_t st) {
-    CUtensorMap mB, mQhi, mQlo;
-    bool ok = tc::map2d(&mB, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
-              tc::map2d(&mQhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
-              tc::map2d(&mQlo, D.Qlo, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN);
+    tc::XPMaps mp;
+    bool ok = tc::map2d(&mp.B, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
+              tc::map2d(&mp.Qhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
+              tc::map2d(&mp.Qlo, D.Qlo, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
+              tc::map2d_f32(&mp.z, D.z, D.Npad, D.M, tc::TM, tc::XP_TN) &&
+              tc::map2d_f32(&mp.y, D.y, D.Npad, D.M, tc::TM, tc::XP_TN) &&
+              tc::map2d_f32(&mp.w0, D.w0, D.Npad, D.M, tc::TM, tc::XP_TN) &&
+              tc::map2d_f32(&mp.up, D.up, D.Npad, D.M, tc::TM, tc::XP_TN);
     if (!ok) { set_error("tensor map encoding failed (G4 fused)"); return; }
     const size_t smem = sizeof(tc::XPSmem) + 1024;
     dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::XP_TN));
     if (D.uniform) {
         cudaFuncSetAttribute(tc::k_tc_xprox<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc::k_tc_xprox<true><<<grid, tc::XP_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
+        tc::k_tc_xprox<true><<<grid, tc::XP_THREADS, smem, st>>>(mp, D);
     } else {
         cudaFuncSetAttribute(tc::k_tc_xprox<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc::k_tc_xprox<false><<<grid, tc::XP_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
+        tc::k_tc_xprox<false><<<grid, tc::XP_THREADS, smem, st>>>(mp, D);
     }
 }
 

@@ -4,6 +4,8 @@ Tolerances (written here, from the workload targets): 1e-6 max-abs on weights,
 1e-8 relative objective (guard max(|f*|, 1e-4)), primal and stationarity
 residuals <= 1e-6, all after the FP64 polish.
 """
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -90,3 +92,28 @@ def test_full_size_workloads_sampled_against_the_oracle(workload):
     assert float(diag[:, prism.PRISM_DIAG_TURNOVER].max()) <= 1e-6
     assert float(diag[:, prism.PRISM_DIAG_STAT].max()) <= 1e-6
     assert_parity(uni, batch, res, accounts=FULL_SAMPLES[workload])
+
+
+def _varied_costs_and_floors(batch, seed=7):
+    """The same book with a transition cost drawn per entry and a lower bound of 0.001 on
+    about 5% of the eligible names: l and c then differ over every account's positions."""
+    r = np.random.default_rng(seed)
+    tc = r.uniform(5e-4, 5e-3, size=batch.tc.shape)
+    lower = np.where((batch.upper > 0.002) & (r.random(batch.lower.shape) < 0.05), 0.001, 0.0)
+    return dataclasses.replace(batch, tc=tc, lower=lower)
+
+
+@pytest.mark.parametrize("varied", [False, True])
+def test_fused_prox_matches_separate_kernels(varied):
+    # the prox's streaming pass inside the tensor-core x-update against the separate x-update
+    # and prox kernels: the same method, so after the FP64 polish the same weights; the varied
+    # book takes the fused kernel's per-entry l and c path
+    uni, batch = make_workload(1, N=700, K=32, M=20)
+    if varied:
+        batch = _varied_costs_and_floors(batch)
+    rf = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, fuse_prox=1)
+    ru = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, fuse_prox=0)
+    assert np.all(rf["status"] == prism.PRISM_CERTIFIED), rf["status"]
+    assert np.all(ru["status"] == prism.PRISM_CERTIFIED), ru["status"]
+    assert float(np.max(np.abs(rf["w"] - ru["w"]))) <= 1e-9
+    assert_parity(uni, batch, rf, accounts=[0, 7, 19])
