@@ -36,11 +36,11 @@ M_ACCOUNTS = 500
 #   gemm_P : read X (FP32, or its BF16 hi+lo split: 4 B)
 #   gemm_x : read z, y (8 B), write v (4 B)
 #   prox   : read v, z, y and w0, l, u, c (28 B); write z, y and X (12 B)
-#   xprox  : the x-update fused with the streaming pass of the prox, timed together with the
-#            per-account roots kernel that finishes it: read z, y, w0, u (16 B; l and c are
-#            per-account constants in this book); write v, z, y and X (16 B)
-ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": 32}
-COLD_ITERS = 6      # iterations of a solve that run the staged prox before the streaming form
+#   xprox  : the x-update fused with the streaming pass of the prox: read z, y, w0, u (16 B;
+#            l and c are per-account constants in this book) and write v (4 B) for every
+#            entry, plus the final z, y and X (12 B) of each entry pinned at its lower bound
+#            (the library counts the others, the candidates, in profile mode)
+ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": 20, "xprox_pinned": 12}
 
 
 def shard_first_account(rank: int, per_rank: int = M_ACCOUNTS) -> int:
@@ -380,17 +380,14 @@ def run_gpu(args, dist, rank, world, local_rank):
     names = prism.KERNEL_CLASSES
     it_sum = int(dout["iters"].cpu().numpy().sum())
     N = uni.n_assets
-    ix, ir = names.index("xprox"), names.index("roots")
+    ix = names.index("xprox")
     alg = {"gemm_P": ALG_BYTES["gemm_P"] * M * N, "gemm_x": ALG_BYTES["gemm_x"] * M * N,
            "prox": ALG_BYTES["prox"] * N * it_sum / max(1, kl[names.index("prox")])}
-    step_ms = {n: kms[names.index(n)] for n in ("gemm_P", "gemm_x", "prox")}
-    n_launch = {n: kl[names.index(n)] for n in ("gemm_P", "gemm_x", "prox")}
+    step_ms = {n: kms[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
+    n_launch = {n: kl[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
     if kl[ix] > 0:
-        # account-iterations of the fused launches: every iteration after the staged ones
-        it_fused = int(np.maximum(dout["iters"].cpu().numpy() - COLD_ITERS, 0).sum())
-        alg["xprox"] = ALG_BYTES["xprox"] * N * it_fused / kl[ix]
-        step_ms["xprox"] = kms[ix] + kms[ir]
-        n_launch["xprox"] = kl[ix]
+        ent, cand = prof["stream_entries"], prof["stream_candidates"]
+        alg["xprox"] = (ALG_BYTES["xprox"] * ent + ALG_BYTES["xprox_pinned"] * (ent - cand)) / kl[ix]
     dom = max(step_ms, key=lambda n: step_ms[n])
     avg_ms = step_ms[dom] / max(1, n_launch[dom])
     peaks = {}
@@ -400,7 +397,7 @@ def run_gpu(args, dist, rank, world, local_rank):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
-    roofline = {"kernel": "xprox+roots" if dom == "xprox" else dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+    roofline = {"kernel": dom, "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": profiled_traffic(dom),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,

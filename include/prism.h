@@ -175,6 +175,8 @@ typedef struct {
     int64_t  n_launches;    /* kernels this call launched (graph replays included) */
     double   kernel_ms[PRISM_NKCLASS];        /* profile mode: summed event time per class */
     int64_t  kernel_launches[PRISM_NKCLASS];  /* profile mode: launches per class */
+    int64_t  stream_entries;     /* profile mode: account-entries the fused streaming pass evaluated */
+    int64_t  stream_candidates;  /* profile mode: of those, entries not pinned at their lower bound */
     prism_state** state;    /* receives the state for the backward pass, if requested */
 } prism_result;
 

@@ -157,6 +157,8 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
     const float* C = D.Cinv + (size_t)D.rho_idx[m] * K * K + t;
 #pragma unroll
     for (int j = 0; j < KMAX; ++j) c[j] = (t < K && j < K) ? C[(size_t)j * K] : 0.f;
+    pdl_wait();                            // the partials of the product just before
+    pdl_trigger();
     if (t < K) {
         float acc[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
         const float* pp = D.Ppart + (size_t)m * D.pstride + t;
@@ -190,8 +192,8 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
     }
 }
 
-void launch_small_solve(const Dev& D, cudaStream_t st) {
-    k_small_solve<<<D.M, 64, 0, st>>>(D);
+void launch_small_solve(const Dev& D, cudaStream_t st, bool pdl) {
+    launch_ex(k_small_solve, dim3(D.M), dim3(KMAX), 0, st, pdl, D);
 }
 
 // ---------------------------------------------------------------------------
@@ -1272,6 +1274,8 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
     const float nu0 = D.nu[a];
     const float margin = fmaxf(4.f * D.dnu[a], 2e-3f);
     const float L = nu0 - margin;
+    pdl_wait();                            // the masks, residuals and records of the fused pass
+    pdl_trigger();
     // candidate masks and their exclusive prefix counts (four quarters per thread)
     unsigned w4[4];
     int c4 = 0;
@@ -1338,6 +1342,10 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
     // meantime thread 0 lays out the slot ranges: sectors in order while the slots last; a
     // sector that does not fit is evaluated from global memory (v is there for every entry)
     const int nfit = min(R.total, CAP);
+    if (D.pcount && tid == 0) {
+        atomicAdd(D.pcount, (unsigned long long)R.total);
+        atomicAdd(D.pcount + 1, (unsigned long long)D.N);
+    }
     const float4* recs = reinterpret_cast<const float4*>(D.crec) + 2 * base;
     auto gather = [&](int slot, int p, int s) {
         const float4 r0 = recs[2 * (size_t)p], r1 = recs[2 * (size_t)p + 1];
@@ -1444,10 +1452,10 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
 
 size_t prox_roots_smem_bytes() { return sizeof(RootsShared); }
 
-void launch_prox_roots(const Dev& D, cudaStream_t st) {
+void launch_prox_roots(const Dev& D, cudaStream_t st, bool pdl) {
     const size_t smem = sizeof(RootsShared);
     cudaFuncSetAttribute(k_prox_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    k_prox_roots<<<D.M, 32 * SP_WARPS, smem, st>>>(D);
+    launch_ex(k_prox_roots, dim3(D.M), dim3(32 * SP_WARPS), smem, st, pdl, D);
 }
 
 // Per account: l when it is the same at every position (else NaN), and c when it is the

@@ -20,6 +20,30 @@
 namespace prism {
 
 __host__ __device__ inline int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Programmatic dependent launch. A kernel launched with launch_ex(..., pdl = true) may start
+// while the kernel before it in the stream is still running; pdl_wait() returns once that
+// kernel has completed and its writes are visible (at once without the attribute). Each
+// iteration kernel calls pdl_trigger() only after its own pdl_wait(), so when a kernel starts,
+// every kernel two or more launches back has completed: the code before pdl_wait() may read
+// what those wrote, nothing of the kernel just before.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void pdl_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
+template <typename Kern, typename... Args>
+inline void launch_ex(Kern kernel, dim3 grid, dim3 block, size_t smem, cudaStream_t st, bool pdl, Args... args) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl ? 1 : 0;
+    cudaLaunchKernelEx(&cfg, kernel, args...);
+}
 __host__ __device__ inline int64_t cdiv64(int64_t a, int64_t b) { return (a + b - 1) / b; }
 
 __device__ __forceinline__ float warp_sum(float v) {

@@ -398,6 +398,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.Rt = A.take<float>((size_t)5 * nt * M); D.Cm = A.take<unsigned>((size_t)U.nq * M);
         D.lo_u = A.take<float>(M); D.c_u = A.take<float>(M);
         D.crec = A.take<float>(MN * 8);
+        D.pcount = A.take<unsigned long long>(2);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
@@ -567,6 +568,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.B16 = U.d_B16; D.Bt16 = U.d_Bt16; D.B16p = U.d_B16p; D.Bt16p = U.d_Bt16p;
     D.err = D.n_active + 1;
     if (!std::getenv("PRISM_DEBUG_STATS")) D.stats = nullptr;   // counters only when asked for
+    if (!o->profile) D.pcount = nullptr;
     D.bf16 = batched_mode_bf16;
     D.Cinv = batched_mode_bf16 ? U.d_Cinv16 : U.d_Cinv32;
     D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
@@ -623,6 +625,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.Qlo, 0, (size_t)M * KMAX * 2, st);
         cudaMemsetAsync(D.n_active, 0, 8, st);
         if (D.stats) cudaMemsetAsync(D.stats, 0, 32, st);
+        if (D.pcount) cudaMemsetAsync(D.pcount, 0, 16, st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
         k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
@@ -645,13 +648,18 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     const int check_every = std::max(1, o->check_every);
     auto run_chunk = [&](int n) {
         for (int it = 0; it < n; ++it) {
-            SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
-            SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
             if (D.fused) {
-                SC.prof.run(PRISM_K_XPROX, 1, st, [&] { launch_tc_xprox(D, st); });
-                SC.prof.run(PRISM_K_ROOTS, 1, st, [&] { launch_prox_roots(D, st); });
+                // the four kernels of an iteration overlap their prologues with the kernel
+                // before (programmatic dependent launch; see pdl_wait)
+                const bool pdl = !SC.prof.on;
+                SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { launch_tc_gemm_P(D, st, pdl); });
+                SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st, pdl); });
+                SC.prof.run(PRISM_K_XPROX, 1, st, [&] { launch_tc_xprox(D, st, pdl); });
+                SC.prof.run(PRISM_K_ROOTS, 1, st, [&] { launch_prox_roots(D, st, pdl); });
                 continue;
             }
+            SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
+            SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
             SC.prof.run(PRISM_K_GEMM_X, 1, st, [&] { if (D.bf16) launch_tc_gemm_x(D, st); else launch_gemm_x(D, st); });
             SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st); });
         }
@@ -824,6 +832,13 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         nl += SC.prof.launches[q];
     }
     for (auto& mk : SC.prof.marks) res->kernel_ms[mk.cls] += ms_between(mk.a, mk.b);
+    res->stream_entries = res->stream_candidates = 0;
+    if (D.pcount) {
+        unsigned long long pc[2] = {0, 0};
+        cudaMemcpy(pc, D.pcount, 16, cudaMemcpyDeviceToHost);
+        res->stream_candidates = (int64_t)pc[0];
+        res->stream_entries = (int64_t)pc[1];
+    }
     res->n_launches = nl;
     res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_call0).count();
     (void)plain;
@@ -932,6 +947,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     res->device_bytes = dbytes;
     res->n_launches = nlaunch;
     for (int q = 0; q < PRISM_NKCLASS; ++q) { res->kernel_ms[q] = kms[q]; res->kernel_launches[q] = kl[q]; }
+    res->stream_entries = res->stream_candidates = 0;
     res->t_call_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
     return PRISM_OK;
 }

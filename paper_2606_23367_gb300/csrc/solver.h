@@ -80,6 +80,7 @@ struct Dev {
     float* Rt = nullptr;                // 5 x nt x M: residual maxima (rp, rd, nx, nz, ny) of the pinned
                                         // entries of each asset tile; rp is NaN when one was not finite
     unsigned* Cm = nullptr;             // nq x M: bit b of quarter q set = entry 32q + b not pinned at L
+    unsigned long long* pcount = nullptr;   // profile mode: [0] candidates, [1] entries of the fused pass
     float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
 };
@@ -87,7 +88,7 @@ struct Dev {
 // launchers (admm.cu)
 void launch_init_state(const Dev& D, cudaStream_t st);
 void launch_gemm_P(const Dev& D, cudaStream_t st);       // G2: Ppart = X B (SIMT)
-void launch_small_solve(const Dev& D, cudaStream_t st);  // G3: Q = Cinv * sum(Ppart)
+void launch_small_solve(const Dev& D, cudaStream_t st, bool pdl = false);  // G3: Q = Cinv * sum(Ppart)
 void launch_gemm_x(const Dev& D, cudaStream_t st);       // G4: v from X - Delta^{-1} B Q (SIMT)
 // G5/G6: projection, duals, control. cold: the staged form even for L1-only books (the first
 // calls of a solve, before the multipliers have warm starts for the streaming form's margin)
@@ -99,10 +100,10 @@ int choose_nsplit(int M, int N);
 // tensor-core products (tc_gemm.cu)
 bool tc_available();                                     // tensor-map encoder reachable
 int tc_nsplit(int M, int N, int* chunk);                 // partial sets of the tensor-core G2 (its asset chunk)
-void launch_tc_gemm_P(const Dev& D, cudaStream_t st);    // G2 on tcgen05
+void launch_tc_gemm_P(const Dev& D, cudaStream_t st, bool pdl = false);    // G2 on tcgen05
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
-void launch_tc_xprox(const Dev& D, cudaStream_t st);     // G4 + the streaming pass of G5 (fused)
-void launch_prox_roots(const Dev& D, cudaStream_t st);   // G5/G6 per account after k_tc_xprox
+void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl = false);     // G4 + the streaming pass of G5 (fused)
+void launch_prox_roots(const Dev& D, cudaStream_t st, bool pdl = false);   // G5/G6 per account after k_tc_xprox
 void launch_uniform(const Dev& D, float* lo_u, float* c_u, cudaStream_t st);   // per-account uniform l, c
 constexpr int XP_NQMAX = 1024;                           // quarters the roots kernel holds (N <= 32768)
 

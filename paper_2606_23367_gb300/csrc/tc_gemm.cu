@@ -210,6 +210,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     const int i0 = split * chunk, i1 = min(D.N, i0 + chunk);
     const int nk = (i1 > i0) ? (i1 - i0 + TK - 1) / TK : 0;
     constexpr uint32_t IDESC = idesc_bf16(TM, KP);
+    pdl_wait();                            // X and the activity flags of the iteration before
+    pdl_trigger();
     {
         // a tile whose accounts have all stopped iterating has nothing to compute
         const int m = mt * TM + tid;
@@ -549,17 +551,21 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     fence_after_sync();
     const uint32_t tmem = s.tmem;
     if (tid == 0) {
-        // operands, then the tile's inputs (rows of accounts beyond M and columns beyond Npad
-        // arrive as zeros); the inputs need no MMA and are consumed after it
+        // B and the tile's inputs first (rows of accounts beyond M and columns beyond Npad
+        // arrive as zeros): none of them comes from the small solve just before; Q after it
         mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
         tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
-        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, mt * XP_TN);
-        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, mt * XP_TN);
         mbar_expect_tx(&s.full_in, 4 * XP_IN_BYTES);
         tma_load_2d(s.in[0], &mp.z, &s.full_in, at * TM, mt * XP_TN);
         tma_load_2d(s.in[1], &mp.y, &s.full_in, at * TM, mt * XP_TN);
         tma_load_2d(s.in[2], &mp.w0, &s.full_in, at * TM, mt * XP_TN);
         tma_load_2d(s.in[3], &mp.up, &s.full_in, at * TM, mt * XP_TN);
+    }
+    pdl_wait();
+    pdl_trigger();
+    if (tid == 0) {
+        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, mt * XP_TN);
+        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, mt * XP_TN);
     }
     const int q = warp;
     const int ia = q * 32 + lane;                       // asset within the tile (TMEM lane)
@@ -757,7 +763,7 @@ int tc_nsplit(int M, int N, int* chunk_out) {
     return nsets;
 }
 
-void launch_tc_gemm_P(const Dev& D, cudaStream_t st) {
+void launch_tc_gemm_P(const Dev& D, cudaStream_t st, bool pdl) {
     CUtensorMap mXhi, mXlo, mBt;
     bool ok = tc::map2d(&mXhi, D.Xhi, D.Npad, D.M, (uint64_t)D.Npad * 2, tc::TK, tc::TM) &&
               tc::map2d(&mXlo, D.Xlo, D.Npad, D.M, (uint64_t)D.Npad * 2, tc::TK, tc::TM) &&
@@ -772,13 +778,15 @@ void launch_tc_gemm_P(const Dev& D, cudaStream_t st) {
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
-    cudaLaunchAttribute attr[1];
+    cudaLaunchAttribute attr[2];
     attr[0].id = cudaLaunchAttributeClusterDimension;
     attr[0].val.clusterDim.x = 1;
     attr[0].val.clusterDim.y = tc::G2_CL;
     attr[0].val.clusterDim.z = 1;
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.attrs = attr;
-    cfg.numAttrs = 1;
+    cfg.numAttrs = pdl ? 2 : 1;
     cudaLaunchKernelEx(&cfg, tc::k_tc_gemm_P, mXhi, mXlo, mBt, D, chunk);
 }
 
@@ -794,7 +802,7 @@ void launch_tc_gemm_x(const Dev& D, cudaStream_t st) {
     tc::k_tc_gemm_x<<<grid, tc::G4_THREADS, smem, st>>>(mB, mQhi, mQlo, D);
 }
 
-void launch_tc_xprox(const Dev& D, cudaStream_t st) {
+void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl) {
     tc::XPMaps mp;
     bool ok = tc::map2d(&mp.B, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
               tc::map2d(&mp.Qhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
@@ -808,10 +816,10 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st) {
     dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::XP_TN));
     if (D.uniform) {
         cudaFuncSetAttribute(tc::k_tc_xprox<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc::k_tc_xprox<true><<<grid, tc::XP_THREADS, smem, st>>>(mp, D);
+        launch_ex(tc::k_tc_xprox<true>, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
     } else {
         cudaFuncSetAttribute(tc::k_tc_xprox<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        tc::k_tc_xprox<false><<<grid, tc::XP_THREADS, smem, st>>>(mp, D);
+        launch_ex(tc::k_tc_xprox<false>, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
     }
 }
 

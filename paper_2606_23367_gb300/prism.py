@@ -66,7 +66,7 @@ class _Result(C.Structure):
                 ("t_device_ms", C.c_double), ("t_call_ms", C.c_double), ("t_phase_ms", C.c_double * 4),
                 ("device_bytes", C.c_int64), ("n_launches", C.c_int64),
                 ("kernel_ms", C.c_double * len(KERNEL_CLASSES)), ("kernel_launches", C.c_int64 * len(KERNEL_CLASSES)),
-                ("state", C.c_void_p)]
+                ("stream_entries", C.c_int64), ("stream_candidates", C.c_int64), ("state", C.c_void_p)]
 
 
 _lib = None
@@ -232,7 +232,8 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
     res = dict(out)
     res.update(t_device_ms=r.t_device_ms, t_call_ms=r.t_call_ms, t_phase_ms=list(r.t_phase_ms),
                device_bytes=r.device_bytes, n_launches=r.n_launches,
-               kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches))
+               kernel_ms=list(r.kernel_ms), kernel_launches=list(r.kernel_launches),
+               stream_entries=int(r.stream_entries), stream_candidates=int(r.stream_candidates))
     if o.keep_for_backward:
         res["state"] = BackwardState(holder.value, u, nnz)
     return res
