@@ -296,7 +296,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     if not args.no_autotune:
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
-        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every")}
+        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after")}
         opts.update(tuned)
 
     def step(inp, out, **extra):

@@ -124,6 +124,8 @@ typedef struct {
     int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
                                  prism_solve_batch_backward (batched modes only) */
     int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
+    int32_t stream_after;     /* iterations of the staged prox before the streaming form, which
+                                 needs settled multipliers for its margin (default 6) */
     int32_t fuse_prox;        /* 1: for books with the L1 cost only (no lots, no cap) in BATCHED_BF16,
                                  the prox's streaming pass runs inside the tensor-core x-update
                                  (default 1); 0: separate x-update and prox kernels (same method) */
@@ -255,10 +257,11 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
 /* Autotuner (no counterpart in the paper, which discloses no solver internals, Sec. 3):
  * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
- * (1.4 .. 1.8) and the iterations per captured graph (5, 10, 20), starting from *base (or
- * the defaults when base is NULL); a candidate's score is certified accounts per second of
- * device time, and one that certifies fewer accounts never wins. Writes the chosen options
- * to *tuned (the other fields copied from base). Runs about 20 full solves, each allocated
+ * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20) and the staged prox
+ * iterations before the streaming form (4 .. 10), starting from *base (or the defaults when
+ * base is NULL); a candidate's score is certified accounts per second of device time, and
+ * one that certifies fewer accounts never wins. Writes the chosen options to *tuned (the
+ * other fields copied from base). Runs about 50 full solves, each allocated
  * and timed like a normal call; the book's buffers may be host or device memory and are
  * only read. PLAIN_FP32 is returned unchanged. Returns PRISM_OK or the first failing
  * solve's error code. */

@@ -1,9 +1,11 @@
 // autotune.cu -- prism_autotune: pick the solver schedule (initial penalty, over-relaxation,
-// iterations per captured graph) for a book by timing trial solves of that very book.
+// iterations per captured graph, staged iterations before the streaming prox) for a book by
+// timing trial solves of that very book.
 //
 // The search is coordinate-wise over small grids: first the initial penalty rho0 (the
 // schedule's largest effect: it sets how many iterations the accounts need), then the
-// over-relaxation alpha, then the graph chunk length. A candidate's score is certified
+// over-relaxation alpha, then the graph chunk length, then the number of staged prox
+// iterations (fewer are cheaper, but the streaming form then misses its margin more often). A candidate's score is certified
 // accounts per second of device time; a candidate that certifies fewer accounts than the
 // best so far never wins. Each trial is a full prism_solve_batch with the caller's book, so
 // the result is specific to that book's shape and data (and to this GPU).
@@ -110,6 +112,12 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         if (ce == best.check_every) continue;
         prism_solve_opts c = best;
         c.check_every = ce;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    for (int sa : {4, 6, 8, 10}) {
+        if (sa == best.stream_after) continue;
+        prism_solve_opts c = best;
+        c.stream_after = sa;
         if ((rc = consider(c)) != PRISM_OK) return rc;
     }
     *tuned = best;

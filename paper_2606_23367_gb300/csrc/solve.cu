@@ -718,7 +718,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     };
     // the first iterations run the staged prox: the streaming form needs the budget multiplier
     // to have settled (its moves set the streaming form's margin) to keep its candidate lists short
-    const int cold = D.stream_prox ? std::min(6, o->max_iter) : 0;
+    const int cold = D.stream_prox ? std::min(std::max(0, o->stream_after), o->max_iter) : 0;
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
         SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
@@ -862,6 +862,7 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     o->precision = PRISM_BATCHED_BF16;
     o->use_graph = 1;
     o->fuse_prox = 1;
+    o->stream_after = 6;
     o->keep_for_backward = 0;
     o->cuda_stream = nullptr;
 }

@@ -57,7 +57,8 @@ class _Opts(C.Structure):
                 ("alpha", C.c_double), ("time_budget_s", C.c_double), ("max_iter", C.c_int32),
                 ("check_every", C.c_int32), ("min_iter", C.c_int32), ("polish_rounds", C.c_int32),
                 ("precision", C.c_int32), ("use_graph", C.c_int32), ("keep_for_backward", C.c_int32),
-                ("profile", C.c_int32), ("fuse_prox", C.c_int32), ("cuda_stream", C.c_void_p)]
+                ("profile", C.c_int32), ("stream_after", C.c_int32), ("fuse_prox", C.c_int32),
+                ("cuda_stream", C.c_void_p)]
 
 
 class _Result(C.Structure):
@@ -243,7 +244,7 @@ def prism_autotune(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, ba
                    asset_idx=None, turnover_cap=None, lot_offsets=None, lot_size=None, lot_kappa=None,
                    **base) -> dict:
     """Schedule chosen by the library's autotuner for this book (see prism.h): a dict of
-    solve options (rho0, alpha, check_every and the base options) to pass to a solve."""
+    solve options (rho0, alpha, check_every, stream_after and the base options) to pass to a solve."""
     lib = load_library()
     keep = _Keep()
     M = int(len(offsets) - 1)
