@@ -146,7 +146,7 @@ void launch_gemm_P(const Dev& D, cudaStream_t st) {
 // G3: Q[m] = Cinv[rho_idx[m]] * sum_s Ppart[s][m]; one block of K threads per account
 // ---------------------------------------------------------------------------
 __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
-    const int m = blockIdx.x;
+    const int m = D.m0 + blockIdx.x;
     if (D.active && !D.active[m]) return;
     const int K = D.K;
     __shared__ float sP[KMAX];
@@ -193,7 +193,7 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
 }
 
 void launch_small_solve(const Dev& D, cudaStream_t st, bool pdl) {
-    launch_ex(k_small_solve, dim3(D.M), dim3(KMAX), 0, st, pdl, D);
+    launch_ex(k_small_solve, dim3((D.m1 ? D.m1 : D.M) - D.m0), dim3(KMAX), 0, st, pdl, D);
 }
 
 // ---------------------------------------------------------------------------
@@ -1253,7 +1253,7 @@ __device__ __forceinline__ int cand_rank(const RootsShared& R, int nq, int p) {
 }
 
 __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
-    const int a = blockIdx.x;
+    const int a = D.m0 + blockIdx.x;
     if (!D.active[a]) return;
     extern __shared__ float4 dyn4[];
     RootsShared& R = *reinterpret_cast<RootsShared*>(dyn4);
@@ -1455,7 +1455,7 @@ size_t prox_roots_smem_bytes() { return sizeof(RootsShared); }
 void launch_prox_roots(const Dev& D, cudaStream_t st, bool pdl) {
     const size_t smem = sizeof(RootsShared);
     cudaFuncSetAttribute(k_prox_roots, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    launch_ex(k_prox_roots, dim3(D.M), dim3(32 * SP_WARPS), smem, st, pdl, D);
+    launch_ex(k_prox_roots, dim3((D.m1 ? D.m1 : D.M) - D.m0), dim3(32 * SP_WARPS), smem, st, pdl, D);
 }
 
 // Per account: l when it is the same at every position (else NaN), and c when it is the

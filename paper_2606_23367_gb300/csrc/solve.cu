@@ -87,6 +87,8 @@ struct SolveCache {
     int g_iters = 0;
     int64_t g_launches[PRISM_NKCLASS] = {};
     cudaEvent_t ev[6] = {};
+    cudaStream_t st2 = nullptr;     // the second chain of the fused iterations
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
 };
 
 static SolveCache& cache_of(prism_universe* uh) {
@@ -450,6 +452,12 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         if (!SC.pinned) {
             if (cudaMallocHost(&SC.pinned, 64) != cudaSuccess) { set_error("pinned alloc failed"); return PRISM_ERR_ALLOCATION; }
             for (auto& e : SC.ev) cudaEventCreate(&e);
+            if (cudaStreamCreateWithFlags(&SC.st2, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&SC.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+                cudaEventCreateWithFlags(&SC.ev_join, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                SC.st2 = nullptr;           // one chain only
+            }
         }
         Arena A;
         A.base = SC.arena; A.cap = SC.arena_bytes;
@@ -646,7 +654,31 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     cudaEventRecord(SC.ev[1], st);
     // ---- ADMM iterations
     const int check_every = std::max(1, o->check_every);
+    // Two chains: the accounts [0, split) and [split, M) iterate independently on two streams,
+    // so that one half's latency-bound roots kernel runs beside the other half's streaming
+    // x-update. split is a multiple of 128 (a product tile never straddles the two halves).
+    const int split = ((M / 2 + 64) / 128) * 128;
+    const bool two_chains = D.fused && SC.st2 && split > 0 && split < M;
     auto run_chunk = [&](int n) {
+        if (two_chains && !SC.prof.on) {
+            Dev DA = D, DB = D;
+            DA.m0 = 0; DA.m1 = split;
+            DB.m0 = split; DB.m1 = M;
+            cudaStream_t sb = SC.st2;
+            cudaEventRecord(SC.ev_fork, st);
+            cudaStreamWaitEvent(sb, SC.ev_fork, 0);
+            for (int it = 0; it < n; ++it) {
+                SC.prof.run(PRISM_K_GEMM_P, 2, st, [&] { launch_tc_gemm_P(DA, st, true); launch_tc_gemm_P(DB, sb, true); });
+                SC.prof.run(PRISM_K_SOLVE_K, 2, st, [&] { launch_small_solve(DA, st, true); launch_small_solve(DB, sb, true); });
+                SC.prof.run(PRISM_K_XPROX, 2, st, [&] { launch_tc_xprox(DA, st, true); launch_tc_xprox(DB, sb, true); });
+                SC.prof.run(PRISM_K_ROOTS, 2, st, [&] { launch_prox_roots(DA, st, true); launch_prox_roots(DB, sb, true); });
+            }
+            cudaEventRecord(SC.ev_join, sb);
+            cudaStreamWaitEvent(st, SC.ev_join, 0);
+            SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
+            cudaMemcpyAsync(SC.pinned, D.n_active, 8, cudaMemcpyDeviceToHost, st);
+            return;
+        }
         for (int it = 0; it < n; ++it) {
             if (D.fused) {
                 // the four kernels of an iteration overlap their prologues with the kernel

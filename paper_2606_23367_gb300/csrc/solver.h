@@ -69,7 +69,10 @@ struct Dev {
     // the streaming pass fused into the tensor-core x-update (k_tc_xprox), finished per
     // account by k_prox_roots. Partials are indexed [row][account], rows as follows.
     int fused = 0;
-    int uniform = 0;                    // every account has uniform l and c (lo_u, c_u not NaN)
+    int uniform = 0;
+    // the accounts [m0, m1) this launch works on (m1 = 0: all M); G2, G3 and the fused kernels
+    // take it, so that two halves of a book can iterate as independent chains
+    int m0 = 0, m1 = 0;                    // every account has uniform l and c (lo_u, c_u not NaN)
     int nq = 0, nseg = 0, nt = 0;       // quarters (32 positions), segments, asset tiles (128 positions)
     const int* qseg = nullptr;          // nq + 1: first segment of each quarter
     const int* sseg = nullptr;          // S + 1: first segment of each sector

@@ -207,6 +207,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     G2Smem& s = *reinterpret_cast<G2Smem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int mt = blockIdx.x, split = blockIdx.y;
+    const int m_end = D.m1 ? D.m1 : D.M;
+    const int mrow = D.m0 + mt * TM;                    // first account of this tile
     const int i0 = split * chunk, i1 = min(D.N, i0 + chunk);
     const int nk = (i1 > i0) ? (i1 - i0 + TK - 1) / TK : 0;
     constexpr uint32_t IDESC = idesc_bf16(TM, KP);
@@ -214,8 +216,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     pdl_trigger();
     {
         // a tile whose accounts have all stopped iterating has nothing to compute
-        const int m = mt * TM + tid;
-        const int act = (D.active == nullptr) || (m < D.M && D.active[m]);
+        const int m = mrow + tid;
+        const int act = (D.active == nullptr) || (m < m_end && D.active[m]);
         if (!__syncthreads_or(act)) return;
     }
     if (warp == 0) tmem_alloc(&s.tmem, 64);
@@ -236,8 +238,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
         auto load = [&](int kt) {
             const int q = kt % G2_STAGES;
             mbar_expect_tx(&s.full[q], 2 * G2_A_BYTES + G2_B_BYTES);
-            tma_load_2d(s.ahi[q], &mXhi, &s.full[q], i0 + kt * TK, mt * TM);
-            tma_load_2d(s.alo[q], &mXlo, &s.full[q], i0 + kt * TK, mt * TM);
+            tma_load_2d(s.ahi[q], &mXhi, &s.full[q], i0 + kt * TK, mrow);
+            tma_load_2d(s.alo[q], &mXlo, &s.full[q], i0 + kt * TK, mrow);
             tma_load_2d(s.b[q], &mBt, &s.full[q], i0 + kt * TK, 0);
         };
         int issued = 0;
@@ -309,8 +311,8 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
                 const float4 v = ld_dsmem_f4(off, uint32_t(q));
                 sum.x += v.x; sum.y += v.y; sum.z += v.z; sum.w += v.w;
             }
-            const int m = mt * TM + r;
-            if (m < D.M) *reinterpret_cast<float4*>(D.Ppart + ((size_t)set * D.M + m) * KP + c4 * 4) = sum;
+            const int m = mrow + r;
+            if (m < m_end) *reinterpret_cast<float4*>(D.Ppart + ((size_t)set * D.M + m) * KP + c4 * 4) = sum;
         }
     }
     cluster_sync_all();                          // no CTA leaves while another reads its partial
@@ -473,7 +475,6 @@ __global__ void __launch_bounds__(G4_THREADS, 3) k_tc_gemm_x(const __grid_consta
 constexpr int XP_TN = 16;         // accounts per tile (MMA N): small tiles, about four CTAs per SM
 constexpr int XP_THREADS = 128;   // warp w reads TMEM lane quarter w (32 assets) for all XP_TN accounts
 constexpr uint32_t XP_Q_BYTES = XP_TN * KP * 2;
-constexpr uint32_t XP_IN_BYTES = XP_TN * TM * 4;   // one input array of the tile (FP32)
 
 struct __align__(1024) XPSmem {
     __nv_bfloat16 a[TM * KP];         // B tile (operand A of the MMA)
@@ -511,7 +512,8 @@ __device__ __forceinline__ float warp_max_nn(float v) {
 }
 
 struct XPMaps {
-    CUtensorMap B, Qhi, Qlo, z, y, w0, up;
+    CUtensorMap B, Qhi, Qlo, z, y, w0, up;   // inputs in boxes of XP_TN accounts
+    CUtensorMap zr, yr, w0r, upr;            // the same arrays one account row at a time
 };
 
 // UNIFORM: every account has one l over its positions and one c over those with u > l (the
@@ -521,11 +523,13 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     extern __shared__ unsigned char raw[];
     XPSmem& s = *reinterpret_cast<XPSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-    const int at = blockIdx.x, mt = blockIdx.y;
+    const int at = blockIdx.x;
+    const int m_end = D.m1 ? D.m1 : D.M;
+    const int m_base = D.m0 + blockIdx.y * XP_TN;       // first account of the tile
     constexpr uint32_t IDESC = idesc_bf16(TM, XP_TN);
     {
-        const int m = mt * XP_TN + tid;
-        const int act = tid < XP_TN && (m < D.M && D.active[m]);
+        const int m = m_base + tid;
+        const int act = tid < XP_TN && (m < m_end && D.active[m]);
         if (!__syncthreads_or(act)) return;
     }
     if (warp == 0) tmem_alloc(&s.tmem, 32);
@@ -537,8 +541,8 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
         fence_barrier_init();
     }
     if (tid < XP_TN) {
-        const int m = mt * XP_TN + tid;
-        const bool ok = m < D.M;
+        const int m = m_base + tid;
+        const bool ok = m < m_end;
         const float r = ok ? rho_of_idx(D.rho_idx[m]) : 1.f;
         const float L = ok ? D.nu[m] - fmaxf(4.f * D.dnu[m], 2e-3f) : 0.f;
         s.pa[tid] = make_float4(r, 1.f / r, L, ok ? D.c_u[m] : 0.f);
@@ -551,27 +555,42 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     fence_after_sync();
     const uint32_t tmem = s.tmem;
     if (tid == 0) {
-        // B and the tile's inputs first (rows of accounts beyond M and columns beyond Npad
-        // arrive as zeros): none of them comes from the small solve just before; Q after it
+        // B and the tile's inputs first (columns beyond Npad and rows beyond M arrive as
+        // zeros): none of them comes from the small solve just before; Q after it. A tile whose
+        // accounts all iterate takes one box per array; otherwise one 128-position row per
+        // active account and array, so that the traffic follows the accounts still iterating
+        // (the rows of inactive accounts are left unread: their entries are skipped).
         mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
         tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
-        mbar_expect_tx(&s.full_in, 4 * XP_IN_BYTES);
-        tma_load_2d(s.in[0], &mp.z, &s.full_in, at * TM, mt * XP_TN);
-        tma_load_2d(s.in[1], &mp.y, &s.full_in, at * TM, mt * XP_TN);
-        tma_load_2d(s.in[2], &mp.w0, &s.full_in, at * TM, mt * XP_TN);
-        tma_load_2d(s.in[3], &mp.up, &s.full_in, at * TM, mt * XP_TN);
+        int nact = 0;
+        for (int j = 0; j < XP_TN; ++j) nact += s.pb[j].y != 0.f;
+        mbar_expect_tx(&s.full_in, (uint32_t)nact * 4u * (TM * 4u));
+        if (nact == XP_TN) {
+            tma_load_2d(s.in[0], &mp.z, &s.full_in, at * TM, m_base);
+            tma_load_2d(s.in[1], &mp.y, &s.full_in, at * TM, m_base);
+            tma_load_2d(s.in[2], &mp.w0, &s.full_in, at * TM, m_base);
+            tma_load_2d(s.in[3], &mp.up, &s.full_in, at * TM, m_base);
+        } else {
+            for (int j = 0; j < XP_TN; ++j) {
+                if (s.pb[j].y == 0.f) continue;
+                const int m = m_base + j;
+                tma_load_2d(s.in[0][j], &mp.zr, &s.full_in, at * TM, m);
+                tma_load_2d(s.in[1][j], &mp.yr, &s.full_in, at * TM, m);
+                tma_load_2d(s.in[2][j], &mp.w0r, &s.full_in, at * TM, m);
+                tma_load_2d(s.in[3][j], &mp.upr, &s.full_in, at * TM, m);
+            }
+        }
     }
     pdl_wait();
     pdl_trigger();
     if (tid == 0) {
-        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, mt * XP_TN);
-        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, mt * XP_TN);
+        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, m_base);
+        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, m_base);
     }
     const int q = warp;
     const int ia = q * 32 + lane;                       // asset within the tile (TMEM lane)
     const int i = at * TM + ia;
     const int ii = i < D.N ? i : 0;
-    const int m_base = mt * XP_TN;
     const int obase = m_base * D.Npad + ii;             // offset of (first account of the tile, asset)
     const float mu = D.mu32[ii], dd = 2.f * D.d32[ii];
     // sector segments of this quarter: lanes with equal sectors are consecutive
@@ -678,7 +697,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     // written coalesced over the tile's accounts
     for (int it = tid; it < 5 * XP_TN; it += XP_THREADS) {
         const int kq = it / XP_TN, col = it % XP_TN, m = m_base + col;
-        if (m >= D.M || s.pb[col].y == 0.f) continue;
+        if (m >= m_end || s.pb[col].y == 0.f) continue;
         float r = 0.f;
         bool nan_ = false;
 #pragma unroll
@@ -692,7 +711,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     for (int it = tid; it < 4 * XP_TN; it += XP_THREADS) {
         const int w = it / XP_TN, col = it % XP_TN, m = m_base + col;
         const int g = at * 4 + w;
-        if (m >= D.M || s.pb[col].y == 0.f || g >= D.nq) continue;
+        if (m >= m_end || s.pb[col].y == 0.f || g >= D.nq) continue;
         D.Cm[(size_t)g * D.M + m] = s.cm[w][col];
     }
 }
@@ -774,7 +793,7 @@ void launch_tc_gemm_P(const Dev& D, cudaStream_t st, bool pdl) {
     const size_t smem = sizeof(tc::G2Smem) + 1024;
     cudaFuncSetAttribute(tc::k_tc_gemm_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(cdiv(D.M, tc::TM), nsets * tc::G2_CL);
+    cfg.gridDim = dim3(cdiv((D.m1 ? D.m1 : D.M) - D.m0, tc::TM), nsets * tc::G2_CL);
     cfg.blockDim = dim3(128);
     cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
@@ -810,10 +829,14 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl) {
               tc::map2d_f32(&mp.z, D.z, D.Npad, D.M, tc::TM, tc::XP_TN) &&
               tc::map2d_f32(&mp.y, D.y, D.Npad, D.M, tc::TM, tc::XP_TN) &&
               tc::map2d_f32(&mp.w0, D.w0, D.Npad, D.M, tc::TM, tc::XP_TN) &&
-              tc::map2d_f32(&mp.up, D.up, D.Npad, D.M, tc::TM, tc::XP_TN);
+              tc::map2d_f32(&mp.up, D.up, D.Npad, D.M, tc::TM, tc::XP_TN) &&
+              tc::map2d_f32(&mp.zr, D.z, D.Npad, D.M, tc::TM, 1) &&
+              tc::map2d_f32(&mp.yr, D.y, D.Npad, D.M, tc::TM, 1) &&
+              tc::map2d_f32(&mp.w0r, D.w0, D.Npad, D.M, tc::TM, 1) &&
+              tc::map2d_f32(&mp.upr, D.up, D.Npad, D.M, tc::TM, 1);
     if (!ok) { set_error("tensor map encoding failed (G4 fused)"); return; }
     const size_t smem = sizeof(tc::XPSmem) + 1024;
-    dim3 grid(cdiv(D.N, tc::TM), cdiv(D.M, tc::XP_TN));
+    dim3 grid(cdiv(D.N, tc::TM), cdiv((D.m1 ? D.m1 : D.M) - D.m0, tc::XP_TN));
     if (D.uniform) {
         cudaFuncSetAttribute(tc::k_tc_xprox<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         launch_ex(tc::k_tc_xprox<true>, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
