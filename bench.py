@@ -254,6 +254,43 @@ def adjoint_timing(stream, reps=5):
         h.close()
 
 
+def queue_and_burden(h, uni, batch, opts, micro_batch=100, window_s=1500.0):
+    """The production-queue lane (Sec. 5.1 aggregates, E5 shape) of this book in micro-batches
+    through the full-call API with host buffers, and the constraint-burden curve (Table
+    "burden") on books of 64 accounts x 2,000 assets; both outside the timed region."""
+    import numpy as np
+    from paper_2606_23367_gb300 import prism
+    from paper_2606_23367_gb300.queue import burden_books, library_solver, run_queue
+    solve_opts = {k: v for k, v in opts.items() if k != "cuda_stream"}
+    library_solver(h, **solve_opts)(batch.subset(list(range(micro_batch))), window_s)      # warm
+    q = run_queue(uni, batch, library_solver(h, **solve_opts), window_s=window_s, micro_batch=micro_batch)
+    queue = q.summary()
+    queue.update(lane="queue wall clock: dispatch of the queue to the return of each account's call",
+                 call_ms=[round(x, 3) for x in q.call_ms], device_ms=[round(x, 3) for x in q.device_ms])
+    rows = []
+    for name, family, u2, b2 in burden_books(N=2000, K=32, M=64):
+        if b2 is None:
+            rows.append({"bundle": name, "rule_family": family, "taken": False,
+                         "note": "needs a general exposure matrix (not taken by this library)"})
+            continue
+        h2 = prism.create_universe(u2)
+        try:
+            solve_opts2 = {k: v for k, v in solve_opts.items() if k in ("precision",)}
+            prism.solve(h2, b2, **solve_opts2)
+            calls = []
+            for _ in range(3):
+                r2 = prism.solve(h2, b2, **solve_opts2)
+                calls.append(r2["t_call_ms"])
+            rows.append({"bundle": name, "rule_family": family, "taken": True, "accounts": b2.n_accounts,
+                         "full_call_ms": statistics.median(calls),
+                         "certified": int((r2["status"] == prism.PRISM_CERTIFIED).sum())})
+        finally:
+            h2.close()
+    burden = {"workload": "64 accounts x 2,000 assets, K=32 (seeded synthetic), library default schedule",
+              "lane": "full-call wall clock, host buffers, median of 3 after one warm-up", "rows": rows}
+    return queue, burden
+
+
 def run_gpu(args, dist, rank, world, local_rank):
     import numpy as np
     import torch
@@ -432,6 +469,9 @@ def run_gpu(args, dist, rank, world, local_rank):
     if rank != 0:
         return
     adj = None if args.no_adjoint else adjoint_timing(stream)
+    queue = burden = None
+    if not args.no_queue:
+        queue, burden = queue_and_burden(h, uni, batch, opts)
     line = {
         "metric": METRIC, "value": value, "unit": "accounts/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -453,7 +493,7 @@ def run_gpu(args, dist, rank, world, local_rank):
         "gpu_launches": int(launches), "clocks": clocks,
         "per_call_ms": {"call_median": statistics.median(c for c, _ in dev_calls),
                         "device_median": statistics.median(d for _, d in dev_calls)},
-        "adjoint": adj,
+        "adjoint": adj, "queue": queue, "burden": burden,
     }
     print(json.dumps(line), flush=True)
     h.close()
@@ -473,6 +513,8 @@ def main():
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default schedule")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing of the "
                     "differentiation workload")
+    ap.add_argument("--no-queue", action="store_true", help="skip the production-queue and constraint-burden "
+                    "lines")
     args = ap.parse_args()
     dist, rank, world, local_rank = _dist()
     if args.impl == "reference":
