@@ -257,12 +257,12 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
 /* Autotuner (no counterpart in the paper, which discloses no solver internals, Sec. 3):
  * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
- * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20) and the staged prox
- * iterations before the streaming form (4 .. 10), starting from *base (or the defaults when
- * base is NULL); a candidate's score is certified accounts per second of device time, and
- * one that certifies fewer accounts never wins. Writes the chosen options to *tuned (the
- * other fields copied from base). Runs about 50 full solves, each allocated
- * and timed like a normal call; the book's buffers may be host or device memory and are
+ * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
+ * before the streaming form (4 .. 10) and the ADMM target eps_admm (1e-4 .. 7e-4), starting
+ * from *base (or the defaults when base is NULL); a candidate's score is certified accounts
+ * per second of device time, and one that certifies fewer accounts never wins. Writes the
+ * chosen options to *tuned (the other fields copied from base). Runs about 60 full solves,
+ * each allocated and timed like a normal call; the book's buffers may be host or device memory and are
  * only read. PLAIN_FP32 is returned unchanged. Returns PRISM_OK or the first failing
  * solve's error code. */
 int prism_autotune(prism_universe* u, const prism_batch* batch, const prism_solve_opts* base,

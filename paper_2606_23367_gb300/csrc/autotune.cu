@@ -1,11 +1,13 @@
 // autotune.cu -- prism_autotune: pick the solver schedule (initial penalty, over-relaxation,
-// iterations per captured graph, staged iterations before the streaming prox) for a book by
-// timing trial solves of that very book.
+// iterations per captured graph, staged iterations before the streaming prox, ADMM target)
+// for a book by timing trial solves of that very book.
 //
 // The search is coordinate-wise over small grids: first the initial penalty rho0 (the
 // schedule's largest effect: it sets how many iterations the accounts need), then the
 // over-relaxation alpha, then the graph chunk length, then the number of staged prox
-// iterations (fewer are cheaper, but the streaming form then misses its margin more often). A candidate's score is certified
+// iterations (fewer are cheaper, but the streaming form then misses its margin more often),
+// then the ADMM target before the polish (a looser one saves iterations and costs polish
+// rounds). A candidate's score is certified
 // accounts per second of device time; a candidate that certifies fewer accounts than the
 // best so far never wins. Each trial is a full prism_solve_batch with the caller's book, so
 // the result is specific to that book's shape and data (and to this GPU).
@@ -118,6 +120,12 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         if (sa == best.stream_after) continue;
         prism_solve_opts c = best;
         c.stream_after = sa;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    for (double eps : {1e-4, 2e-4, 3e-4, 5e-4, 7e-4}) {
+        if (eps == best.eps_admm) continue;
+        prism_solve_opts c = best;
+        c.eps_admm = eps;
         if ((rc = consider(c)) != PRISM_OK) return rc;
     }
     *tuned = best;

@@ -29,7 +29,10 @@ namespace tc {
 constexpr int TM = 128;            // MMA M (accounts in G2, assets in G4)
 constexpr int TK = 64;             // BF16 elements per 128-byte swizzled row
 constexpr int KP = 64;             // factors, zero-padded, in the BF16 copies of B and Q
-constexpr int G2_STAGES = 2;
+#ifndef PRISM_G2_STAGES
+#define PRISM_G2_STAGES 2
+#endif
+constexpr int G2_STAGES = PRISM_G2_STAGES;   // TMA stages of G2 (each 40 KB of shared memory)
 constexpr int G2_CL = 8;           // CTAs per cluster along the asset splits (reduced over DSMEM)
 constexpr int G2_PR = KP + 4;      // row stride (floats) of a CTA's partial in shared memory
 constexpr uint32_t G2_A_BYTES = TM * TK * 2;      // 16 KB
@@ -482,7 +485,7 @@ struct __align__(1024) XPSmem {
     __nv_bfloat16 blo[XP_TN * KP];
     float in[4][XP_TN][TM];           // z, y, w0, u of the tile: [array][account][asset]
     uint64_t full;                    // operands landed
-    uint64_t full_in;                 // inputs landed
+    uint64_t full_in[XP_TN / 4];      // inputs of accounts 4g .. 4g + 3 landed
     uint64_t done;                    // MMA complete
     uint32_t tmem;
     int fail;
@@ -512,7 +515,7 @@ __device__ __forceinline__ float warp_max_nn(float v) {
 }
 
 struct XPMaps {
-    CUtensorMap B, Qhi, Qlo, z, y, w0, up;   // inputs in boxes of XP_TN accounts
+    CUtensorMap B, Qhi, Qlo, z, y, w0, up;   // inputs in boxes of 4 accounts
     CUtensorMap zr, yr, w0r, upr;            // the same arrays one account row at a time
 };
 
@@ -535,7 +538,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     if (warp == 0) tmem_alloc(&s.tmem, 32);
     if (tid == 0) {
         mbar_init(&s.full, 1);
-        mbar_init(&s.full_in, 1);
+        for (int g = 0; g < XP_TN / 4; ++g) mbar_init(&s.full_in[g], 1);
         mbar_init(&s.done, 1);
         s.fail = 0;
         fence_barrier_init();
@@ -556,28 +559,32 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     const uint32_t tmem = s.tmem;
     if (tid == 0) {
         // B and the tile's inputs first (columns beyond Npad and rows beyond M arrive as
-        // zeros): none of them comes from the small solve just before; Q after it. A tile whose
-        // accounts all iterate takes one box per array; otherwise one 128-position row per
-        // active account and array, so that the traffic follows the accounts still iterating
-        // (the rows of inactive accounts are left unread: their entries are skipped).
+        // zeros): none of them comes from the small solve just before; Q after it. The inputs
+        // come in four groups of four accounts, each with its own barrier, so that the epilogue
+        // starts on the first group while the others are in flight. A group whose accounts all
+        // iterate takes one box per array; otherwise one 128-position row per active account
+        // and array, so that the traffic follows the accounts still iterating (the rows of
+        // inactive accounts are left unread: their entries are skipped).
         mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
         tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
-        int nact = 0;
-        for (int j = 0; j < XP_TN; ++j) nact += s.pb[j].y != 0.f;
-        mbar_expect_tx(&s.full_in, (uint32_t)nact * 4u * (TM * 4u));
-        if (nact == XP_TN) {
-            tma_load_2d(s.in[0], &mp.z, &s.full_in, at * TM, m_base);
-            tma_load_2d(s.in[1], &mp.y, &s.full_in, at * TM, m_base);
-            tma_load_2d(s.in[2], &mp.w0, &s.full_in, at * TM, m_base);
-            tma_load_2d(s.in[3], &mp.up, &s.full_in, at * TM, m_base);
-        } else {
-            for (int j = 0; j < XP_TN; ++j) {
-                if (s.pb[j].y == 0.f) continue;
-                const int m = m_base + j;
-                tma_load_2d(s.in[0][j], &mp.zr, &s.full_in, at * TM, m);
-                tma_load_2d(s.in[1][j], &mp.yr, &s.full_in, at * TM, m);
-                tma_load_2d(s.in[2][j], &mp.w0r, &s.full_in, at * TM, m);
-                tma_load_2d(s.in[3][j], &mp.upr, &s.full_in, at * TM, m);
+        for (int g = 0; g < XP_TN / 4; ++g) {
+            int nact = 0;
+            for (int j = 4 * g; j < 4 * g + 4; ++j) nact += s.pb[j].y != 0.f;
+            mbar_expect_tx(&s.full_in[g], (uint32_t)nact * 4u * (TM * 4u));
+            if (nact == 4) {
+                tma_load_2d(s.in[0][4 * g], &mp.z, &s.full_in[g], at * TM, m_base + 4 * g);
+                tma_load_2d(s.in[1][4 * g], &mp.y, &s.full_in[g], at * TM, m_base + 4 * g);
+                tma_load_2d(s.in[2][4 * g], &mp.w0, &s.full_in[g], at * TM, m_base + 4 * g);
+                tma_load_2d(s.in[3][4 * g], &mp.up, &s.full_in[g], at * TM, m_base + 4 * g);
+            } else {
+                for (int j = 4 * g; j < 4 * g + 4; ++j) {
+                    if (s.pb[j].y == 0.f) continue;
+                    const int m = m_base + j;
+                    tma_load_2d(s.in[0][j], &mp.zr, &s.full_in[g], at * TM, m);
+                    tma_load_2d(s.in[1][j], &mp.yr, &s.full_in[g], at * TM, m);
+                    tma_load_2d(s.in[2][j], &mp.w0r, &s.full_in[g], at * TM, m);
+                    tma_load_2d(s.in[3][j], &mp.upr, &s.full_in[g], at * TM, m);
+                }
             }
         }
     }
@@ -616,7 +623,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
         }
     }
     __syncthreads();
-    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32) && mbar_wait(&s.full_in, 0, D.err, 64);
+    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
     have = __syncthreads_and(have);
     fence_after_sync();
     const bool row_ok = have && i < D.N;
@@ -628,6 +635,11 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     // are zero and nothing of it is stored), so their reductions interleave.
 #pragma unroll
     for (int j = 0; j < XP_TN; ++j) {
+        if (j % 4 == 0) {
+            // this group's inputs (an expired wait sets the error flag; the values are then
+            // not used: the host fails the call)
+            if (have) mbar_wait(&s.full_in[j / 4], 0, D.err, 64);
+        }
         const float4 pa = s.pa[j], pb = s.pb[j];
         const float rho = pa.x, irho = pa.y, L = pa.z;
         const bool ok = row_ok && pb.y != 0.f;
@@ -826,10 +838,10 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl) {
     bool ok = tc::map2d(&mp.B, D.B16p, tc::KP, D.Npad, tc::KP * 2, tc::KP, tc::TM) &&
               tc::map2d(&mp.Qhi, D.Qhi, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
               tc::map2d(&mp.Qlo, D.Qlo, tc::KP, D.M, tc::KP * 2, tc::KP, tc::XP_TN) &&
-              tc::map2d_f32(&mp.z, D.z, D.Npad, D.M, tc::TM, tc::XP_TN) &&
-              tc::map2d_f32(&mp.y, D.y, D.Npad, D.M, tc::TM, tc::XP_TN) &&
-              tc::map2d_f32(&mp.w0, D.w0, D.Npad, D.M, tc::TM, tc::XP_TN) &&
-              tc::map2d_f32(&mp.up, D.up, D.Npad, D.M, tc::TM, tc::XP_TN) &&
+              tc::map2d_f32(&mp.z, D.z, D.Npad, D.M, tc::TM, 4) &&
+              tc::map2d_f32(&mp.y, D.y, D.Npad, D.M, tc::TM, 4) &&
+              tc::map2d_f32(&mp.w0, D.w0, D.Npad, D.M, tc::TM, 4) &&
+              tc::map2d_f32(&mp.up, D.up, D.Npad, D.M, tc::TM, 4) &&
               tc::map2d_f32(&mp.zr, D.z, D.Npad, D.M, tc::TM, 1) &&
               tc::map2d_f32(&mp.yr, D.y, D.Npad, D.M, tc::TM, 1) &&
               tc::map2d_f32(&mp.w0r, D.w0, D.Npad, D.M, tc::TM, 1) &&
