@@ -338,8 +338,13 @@ def run_gpu(args, dist, rank, world, local_rank):
     if not args.no_autotune:
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
-        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "eps_admm")}
+        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm")}
         opts.update(tuned)
+
+    if args.chains is not None:
+        opts["chains"] = args.chains
+        if tuned is not None:
+            tuned["chains"] = args.chains
 
     def step(inp, out, **extra):
         return prism.prism_solve_batch(h, inp["offsets"], inp["w0"], inp["lower"], inp["upper"], inp["tc"],
@@ -519,6 +524,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prewarm-s", type=float, default=2.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default schedule")
+    ap.add_argument("--chains", type=int, default=None, help="account chains of the fused iterations "
+                    "(overrides the schedule; 1 = one range, as in the profile pass)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing of the "
                     "differentiation workload")
     ap.add_argument("--no-queue", action="store_true", help="skip the production-queue and constraint-burden "

@@ -111,12 +111,12 @@ typedef struct {
 /* ---- options -------------------------------------------------------------- */
 typedef struct {
     double  eps_kkt;          /* certification gate on every residual (default 1e-6) */
-    double  eps_admm;         /* ADMM residual target before the polish (default 3e-4) */
-    double  rho0;             /* initial ADMM penalty (default 2.0) */
-    double  alpha;            /* over-relaxation (default 1.6) */
+    double  eps_admm;         /* ADMM residual target before the polish (default 5e-4) */
+    double  rho0;             /* initial ADMM penalty (default 3.0) */
+    double  alpha;            /* over-relaxation (default 1.5) */
     double  time_budget_s;    /* wall-clock ceiling for the call (<= 0: none) */
     int32_t max_iter;         /* ADMM iteration cap per account (default 4000) */
-    int32_t check_every;      /* iterations per captured graph launch (default 10) */
+    int32_t check_every;      /* iterations per captured graph launch (default 20) */
     int32_t min_iter;         /* iterations before a convergence test may stop an account */
     int32_t polish_rounds;    /* active-set correction rounds per polish (default 8) */
     int32_t precision;        /* PRISM_PLAIN_FP32 | PRISM_BATCHED_FP32 | PRISM_BATCHED_BF16 */
@@ -124,6 +124,9 @@ typedef struct {
     int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
                                  prism_solve_batch_backward (batched modes only) */
     int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
+    int32_t chains;           /* fused iterations: the book is cut into this many account ranges
+                                 (multiples of 128) that iterate independently on their own
+                                 streams; 0 = as many as fit, up to 4 (default 0) */
     int32_t stream_after;     /* iterations of the staged prox before the streaming form, which
                                  needs settled multipliers for its margin (default 6) */
     int32_t fuse_prox;        /* 1: for books with the L1 cost only (no lots, no cap) in BATCHED_BF16,
@@ -258,10 +261,12 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
- * before the streaming form (4 .. 10) and the ADMM target eps_admm (1e-4 .. 7e-4), starting
+ * before the streaming form (4 .. 10), the account chains (1, 2, 4) and the ADMM target
+ * eps_admm (1e-4 .. 7e-4), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts
- * per second of device time, and one that certifies fewer accounts never wins. Writes the
- * chosen options to *tuned (the other fields copied from base). Runs about 60 full solves,
+ * per second of device time; one that certifies fewer accounts never wins, and one that
+ * certifies as many must be faster than the best so far by more than 1%. Writes the
+ * chosen options to *tuned (the other fields copied from base). Runs about 70 full solves,
  * each allocated and timed like a normal call; the book's buffers may be host or device memory and are
  * only read. PLAIN_FP32 is returned unchanged. Returns PRISM_OK or the first failing
  * solve's error code. */

@@ -1,15 +1,17 @@
 // autotune.cu -- prism_autotune: pick the solver schedule (initial penalty, over-relaxation,
-// iterations per captured graph, staged iterations before the streaming prox, ADMM target)
+// iterations per captured graph, staged iterations before the streaming prox, account
+// chains, ADMM target)
 // for a book by timing trial solves of that very book.
 //
 // The search is coordinate-wise over small grids: first the initial penalty rho0 (the
 // schedule's largest effect: it sets how many iterations the accounts need), then the
 // over-relaxation alpha, then the graph chunk length, then the number of staged prox
 // iterations (fewer are cheaper, but the streaming form then misses its margin more often),
-// then the ADMM target before the polish (a looser one saves iterations and costs polish
-// rounds). A candidate's score is certified
+// then the number of independent account chains, then the ADMM target before the polish
+// (a looser one saves iterations and costs polish rounds). A candidate's score is certified
 // accounts per second of device time; a candidate that certifies fewer accounts than the
-// best so far never wins. Each trial is a full prism_solve_batch with the caller's book, so
+// best so far never wins, and one that certifies as many must be faster by more than 1% (the
+// run-to-run spread of a trial). Each trial is a full prism_solve_batch with the caller's book, so
 // the result is specific to that book's shape and data (and to this GPU).
 #include <algorithm>
 #include <cstring>
@@ -48,9 +50,11 @@ Trial run_trial(prism_universe* u, const prism_batch* b, const prism_solve_opts&
     return t;
 }
 
+// a candidate replaces the best schedule only if it certifies more accounts, or as many and
+// is faster by more than the run-to-run spread of a trial's time (1%)
 bool better(const Trial& a, const Trial& b) {
     if (a.certified != b.certified) return a.certified > b.certified;
-    return a.score > b.score;
+    return a.score > b.score * 1.01;
 }
 
 }  // namespace
@@ -120,6 +124,12 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         if (sa == best.stream_after) continue;
         prism_solve_opts c = best;
         c.stream_after = sa;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    for (int ch : {1, 2, 4}) {
+        if (ch == best.chains) continue;
+        prism_solve_opts c = best;
+        c.chains = ch;
         if ((rc = consider(c)) != PRISM_OK) return rc;
     }
     for (double eps : {1e-4, 2e-4, 3e-4, 5e-4, 7e-4}) {

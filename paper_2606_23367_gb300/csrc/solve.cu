@@ -87,8 +87,10 @@ struct SolveCache {
     int g_iters = 0;
     int64_t g_launches[PRISM_NKCLASS] = {};
     cudaEvent_t ev[6] = {};
-    cudaStream_t st2 = nullptr;     // the second chain of the fused iterations
-    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    static constexpr int MAXCH = 4;               // independent chains of the fused iterations
+    cudaStream_t chst[MAXCH - 1] = {};            // streams of chains 1 .. MAXCH-1 (chain 0: the solve stream)
+    cudaEvent_t ev_fork = nullptr, ev_join[MAXCH - 1] = {};
+    bool chains_ok = false;
 };
 
 static SolveCache& cache_of(prism_universe* uh) {
@@ -125,21 +127,31 @@ struct PackArgs {
 __global__ void k_pack(PackArgs A) {
     int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= A.nnz) return;
-    // account of entry e: last a with offsets[a] <= e
-    int lo = 0, hi = A.M;
-    while (hi - lo > 1) {
-        int mid = (lo + hi) >> 1;
-        if (A.offsets[mid] <= e) lo = mid; else hi = mid;
+    // account of entry e: last a with offsets[a] <= e (every account spans the universe
+    // when there is no asset_idx: then a = e / N)
+    int a;
+    if (A.asset_idx) {
+        int lo = 0, hi = A.M;
+        while (hi - lo > 1) {
+            int mid = (lo + hi) >> 1;
+            if (A.offsets[mid] <= e) lo = mid; else hi = mid;
+        }
+        a = lo;
+    } else {
+        a = int(e / A.N);
     }
-    const int a = lo;
-    int i = A.asset_idx ? A.asset_idx[e] : int(e - A.offsets[a]);
+    int i = A.asset_idx ? A.asset_idx[e] : int(e - (int64_t)a * A.N);
     if (i < 0 || i >= A.N) { atomicOr(A.err, ERR_INDEX); return; }
     const double w0 = A.w0[e], l = A.lo[e], u = A.up[e], c = A.tc[e];
     if (!(isfinite(w0) && isfinite(l) && isfinite(u) && isfinite(c))) { atomicOr(A.err, ERR_NONFINITE); return; }
     if (l > u) { atomicOr(A.err, ERR_BOUNDS); return; }
     if (c < 0) { atomicOr(A.err, ERR_COST); return; }
     const size_t d = (size_t)a * A.Npad + A.inv_perm[i];
-    if (atomicExch(&A.member[d], 1) != 0) { atomicOr(A.err, ERR_DUP); return; }
+    if (A.asset_idx) {
+        if (atomicExch(&A.member[d], 1) != 0) { atomicOr(A.err, ERR_DUP); return; }
+    } else {
+        A.member[d] = 1;                   // position i of account a: no duplicate is possible
+    }
     A.W0[d] = w0; A.LO[d] = l; A.UP[d] = u; A.C[d] = c;
     A.W0f[d] = float(w0); A.LOf[d] = float(l); A.UPf[d] = float(u); A.Cf[d] = float(c);
 }
@@ -169,16 +181,84 @@ __global__ void k_unpack(UnpackArgs A) {
 
 // Closed-form feasibility of budget + box + bands (+ the least-turnover test for a
 // cap): sum_s max(lo_s, sum_{i in s} l_i) <= 1 <= sum_s min(hi_s, sum_{i in s} u_i).
-__global__ void k_capacity(int S, int Npad, const int* sec_start, const double* LO, const double* UP,
-                           const double* W0, const double* band_lo, const double* band_hi,
-                           const double* tau, int* status, int* skip, int* active) {
+// Closed-form feasibility of one account (budget, box, bands, and the cap when w0 sums to 1).
+// The per-sector sums are taken first in FP32 from the iteration copies, one contiguous chunk
+// of positions per thread (float4 loads, one pass); relative to their exact values they are
+// off by less than 1e-5. The account is decided there when every comparison clears its
+// threshold by 1e-4 relative; otherwise, and whenever a turnover cap is set, the sums are
+// taken again in FP64 and decided as before.
+__global__ void k_capacity(int S, int N, int Npad, const int* sec_start, const double* LO, const double* UP,
+                           const double* W0, const float* LOf, const float* UPf, const float* W0f,
+                           const double* band_lo, const double* band_hi, const double* tau, int* status, int* skip,
+                           int* active) {
     const int a = blockIdx.x;
     __shared__ double s_up[SMAX], s_lo[SMAX], s_kept[SMAX], s_forced[SMAX], s_w0[SMAX];
+    __shared__ float f_up[SMAX], f_lo[SMAX];
+    __shared__ int sec[SMAX + 1];
+    __shared__ int decided;
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
     const size_t base = (size_t)a * Npad;
+    for (int s = threadIdx.x; s <= S; s += blockDim.x) sec[s] = sec_start[s];
+    for (int s = threadIdx.x; s < S; s += blockDim.x) { f_up[s] = 0.f; f_lo[s] = 0.f; }
+    __syncthreads();
+    if (!isfinite(tau[a])) {
+        // FP32 pass: Npad is a multiple of 64, so chunks of whole float4s cover it
+        const int nq = Npad / 4, per = (nq + blockDim.x - 1) / blockDim.x;
+        const int q0 = threadIdx.x * per, q1 = min(nq, q0 + per);
+        int cs = 0;
+        float su = 0.f, sl = 0.f;
+        auto flush = [&](int s) {
+            if (s < S) { atomicAdd(&f_up[s], su); atomicAdd(&f_lo[s], sl); }
+            su = 0.f; sl = 0.f;
+        };
+        if (q0 < q1) {
+            const int p0 = 4 * q0;
+            while (cs < S && p0 >= sec[cs + 1]) ++cs;
+            for (int q = q0; q < q1; ++q) {
+                const float4 u4 = reinterpret_cast<const float4*>(UPf + base)[q];
+                const float4 l4 = reinterpret_cast<const float4*>(LOf + base)[q];
+                const float uu[4] = {u4.x, u4.y, u4.z, u4.w}, ll[4] = {l4.x, l4.y, l4.z, l4.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int p = 4 * q + k;
+                    if (p >= N) break;
+                    while (cs < S && p >= sec[cs + 1]) { flush(cs); ++cs; }
+                    su += uu[k]; sl += ll[k];
+                }
+            }
+            flush(cs);
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            // each comparison is decided only when it clears its threshold by 1e-4 relative
+            bool ok = true, sure = true;
+            double cap = 0, flo = 0, mag = 0;
+            for (int s = 0; s < S; ++s) {
+                const double hi = band_hi[a * S + s], lo = band_lo[a * S + s];
+                const double u = f_up[s], l = f_lo[s];
+                const double tol_u = 1e-4 * (u + fabs(lo)) + 1e-12, tol_l = 1e-4 * (l + fabs(hi)) + 1e-12;
+                if (fabs(lo - u) <= tol_u && !(lo == 0.0 && u == 0.0)) sure = false;
+                if (fabs(l - hi) <= tol_l && !(l == 0.0 && hi == 0.0)) sure = false;
+                if (lo > u + 1e-12 || l > hi + 1e-12) ok = false;
+                cap += fmin(hi, u);
+                flo += fmax(lo, l);
+                mag += fabs(fmin(hi, u)) + fabs(fmax(lo, l));
+            }
+            if (fabs(cap - 1.0) <= 1e-4 * fmax(mag, 1.0) || fabs(flo - 1.0) <= 1e-4 * fmax(mag, 1.0)) sure = false;
+            if (!(cap >= 1.0 - 1e-12 && flo <= 1.0 + 1e-12)) ok = false;
+            decided = sure;
+            if (sure && !ok) {
+                status[a] = PRISM_NO_FEASIBLE_RETURN;
+                skip[a] = 1;
+                active[a] = 0;
+            }
+        }
+        __syncthreads();
+        if (decided) return;
+    }
     for (int s = warp; s < S; s += nw) {
         double su = 0, sl = 0, sk = 0, sf = 0, sw = 0;
-        for (int p = sec_start[s] + lane; p < sec_start[s + 1]; p += 32) {
+        for (int p = sec[s] + lane; p < sec[s + 1]; p += 32) {
             double u = UP[base + p], l = LO[base + p], w = W0[base + p];
             su += u; sl += l; sk += fmin(w, u); sf += fmax(w - u, 0.0); sw += w;
         }
@@ -452,12 +532,11 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         if (!SC.pinned) {
             if (cudaMallocHost(&SC.pinned, 64) != cudaSuccess) { set_error("pinned alloc failed"); return PRISM_ERR_ALLOCATION; }
             for (auto& e : SC.ev) cudaEventCreate(&e);
-            if (cudaStreamCreateWithFlags(&SC.st2, cudaStreamNonBlocking) != cudaSuccess ||
-                cudaEventCreateWithFlags(&SC.ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-                cudaEventCreateWithFlags(&SC.ev_join, cudaEventDisableTiming) != cudaSuccess) {
-                cudaGetLastError();
-                SC.st2 = nullptr;           // one chain only
-            }
+            SC.chains_ok = cudaEventCreateWithFlags(&SC.ev_fork, cudaEventDisableTiming) == cudaSuccess;
+            for (int c = 0; c + 1 < SolveCache::MAXCH && SC.chains_ok; ++c)
+                SC.chains_ok = cudaStreamCreateWithFlags(&SC.chst[c], cudaStreamNonBlocking) == cudaSuccess &&
+                               cudaEventCreateWithFlags(&SC.ev_join[c], cudaEventDisableTiming) == cudaSuccess;
+            if (!SC.chains_ok) cudaGetLastError();        // one chain only
         }
         Arena A;
         A.base = SC.arena; A.cap = SC.arena_bytes;
@@ -488,11 +567,24 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     PA.W0 = BD.w0; PA.LO = BD.lo; PA.UP = BD.up; PA.C = BD.c;
     PA.W0f = BD.w0f; PA.LOf = BD.lof; PA.UPf = BD.upf; PA.Cf = BD.cf;
     PA.member = member; PA.err = err;
-    cudaMemsetAsync(BD.w0, 0, MN * 8, st); cudaMemsetAsync(BD.lo, 0, MN * 8, st);
-    cudaMemsetAsync(BD.up, 0, MN * 8, st); cudaMemsetAsync(BD.c, 0, MN * 8, st);
-    cudaMemsetAsync(BD.w0f, 0, MN * 4, st); cudaMemsetAsync(BD.lof, 0, MN * 4, st);
-    cudaMemsetAsync(BD.upf, 0, MN * 4, st); cudaMemsetAsync(BD.cf, 0, MN * 4, st);
-    cudaMemsetAsync(member, 0, MN * 4, st);
+    if (b->asset_idx) {
+        // ragged accounts: every position the pack does not write is a non-member (zeros)
+        cudaMemsetAsync(BD.w0, 0, MN * 8, st); cudaMemsetAsync(BD.lo, 0, MN * 8, st);
+        cudaMemsetAsync(BD.up, 0, MN * 8, st); cudaMemsetAsync(BD.c, 0, MN * 8, st);
+        cudaMemsetAsync(BD.w0f, 0, MN * 4, st); cudaMemsetAsync(BD.lof, 0, MN * 4, st);
+        cudaMemsetAsync(BD.upf, 0, MN * 4, st); cudaMemsetAsync(BD.cf, 0, MN * 4, st);
+        cudaMemsetAsync(member, 0, MN * 4, st);
+    } else if (Npad > N) {
+        // every account spans the universe, so the pack writes every position below N: only
+        // the padding columns N .. Npad-1 are cleared
+        auto pad = [&](void* p, size_t es) {
+            cudaMemset2DAsync(static_cast<char*>(p) + (size_t)N * es, (size_t)Npad * es, 0, (size_t)(Npad - N) * es,
+                              (size_t)M, st);
+        };
+        pad(BD.w0, 8); pad(BD.lo, 8); pad(BD.up, 8); pad(BD.c, 8);
+        pad(BD.w0f, 4); pad(BD.lof, 4); pad(BD.upf, 4); pad(BD.cf, 4);
+        pad(member, 4);
+    }
     cudaMemsetAsync(err, 0, 16, st);
     if (nnz > 0) SC.prof.run(PRISM_K_PACK, 1, st, [&] { k_pack<<<(unsigned)cdiv64(nnz, 256), 256, 0, st>>>(PA); });
     // bands and caps
@@ -636,8 +728,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         if (D.pcount) cudaMemsetAsync(D.pcount, 0, 16, st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
-        k_capacity<<<M, 256, 0, st>>>(S, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.band_lo, BD.band_hi,
-                                      BD.tau, D.status, P.skip, D.active);
+        k_capacity<<<M, 256, 0, st>>>(S, N, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.lof, BD.upf, BD.w0f,
+                                      BD.band_lo, BD.band_hi, BD.tau, D.status, P.skip, D.active);
         launch_init_state(D, st);
     });
     if (D.fused) {
@@ -654,27 +746,35 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     cudaEventRecord(SC.ev[1], st);
     // ---- ADMM iterations
     const int check_every = std::max(1, o->check_every);
-    // Two chains: the accounts [0, split) and [split, M) iterate independently on two streams,
-    // so that one half's latency-bound roots kernel runs beside the other half's streaming
-    // x-update. split is a multiple of 128 (a product tile never straddles the two halves).
-    const int split = ((M / 2 + 64) / 128) * 128;
-    const bool two_chains = D.fused && SC.st2 && split > 0 && split < M;
+    // Chains: the accounts are cut into up to MAXCH ranges that iterate independently on their
+    // own streams, so that one range's latency-bound kernels (the roots, the small products)
+    // run beside another range's streaming x-update. Every cut is a multiple of 128 (a product
+    // tile never straddles two ranges); a range holds at least 128 accounts.
+    int nch = 1;
+    if (D.fused && SC.chains_ok) nch = std::min(SolveCache::MAXCH, std::max(1, M / 128));
+    if (o->chains > 0) nch = std::min(nch, o->chains);
     auto run_chunk = [&](int n) {
-        if (two_chains && !SC.prof.on) {
-            Dev DA = D, DB = D;
-            DA.m0 = 0; DA.m1 = split;
-            DB.m0 = split; DB.m1 = M;
-            cudaStream_t sb = SC.st2;
-            cudaEventRecord(SC.ev_fork, st);
-            cudaStreamWaitEvent(sb, SC.ev_fork, 0);
-            for (int it = 0; it < n; ++it) {
-                SC.prof.run(PRISM_K_GEMM_P, 2, st, [&] { launch_tc_gemm_P(DA, st, true); launch_tc_gemm_P(DB, sb, true); });
-                SC.prof.run(PRISM_K_SOLVE_K, 2, st, [&] { launch_small_solve(DA, st, true); launch_small_solve(DB, sb, true); });
-                SC.prof.run(PRISM_K_XPROX, 2, st, [&] { launch_tc_xprox(DA, st, true); launch_tc_xprox(DB, sb, true); });
-                SC.prof.run(PRISM_K_ROOTS, 2, st, [&] { launch_prox_roots(DA, st, true); launch_prox_roots(DB, sb, true); });
+        if (nch > 1 && !SC.prof.on) {
+            Dev DC[SolveCache::MAXCH];
+            cudaStream_t cs[SolveCache::MAXCH];
+            for (int c = 0; c < nch; ++c) {
+                DC[c] = D;
+                DC[c].m0 = ((M * c / nch) + 64) / 128 * 128;
+                DC[c].m1 = (c + 1 == nch) ? M : ((M * (c + 1) / nch) + 64) / 128 * 128;
+                cs[c] = c == 0 ? st : SC.chst[c - 1];
             }
-            cudaEventRecord(SC.ev_join, sb);
-            cudaStreamWaitEvent(st, SC.ev_join, 0);
+            cudaEventRecord(SC.ev_fork, st);
+            for (int c = 1; c < nch; ++c) cudaStreamWaitEvent(cs[c], SC.ev_fork, 0);
+            for (int it = 0; it < n; ++it) {
+                SC.prof.run(PRISM_K_GEMM_P, nch, st, [&] { for (int c = 0; c < nch; ++c) launch_tc_gemm_P(DC[c], cs[c], true); });
+                SC.prof.run(PRISM_K_SOLVE_K, nch, st, [&] { for (int c = 0; c < nch; ++c) launch_small_solve(DC[c], cs[c], true); });
+                SC.prof.run(PRISM_K_XPROX, nch, st, [&] { for (int c = 0; c < nch; ++c) launch_tc_xprox(DC[c], cs[c], true); });
+                SC.prof.run(PRISM_K_ROOTS, nch, st, [&] { for (int c = 0; c < nch; ++c) launch_prox_roots(DC[c], cs[c], true); });
+            }
+            for (int c = 1; c < nch; ++c) {
+                cudaEventRecord(SC.ev_join[c - 1], cs[c]);
+                cudaStreamWaitEvent(st, SC.ev_join[c - 1], 0);
+            }
             SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
             cudaMemcpyAsync(SC.pinned, D.n_active, 8, cudaMemcpyDeviceToHost, st);
             return;
@@ -883,18 +983,19 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     if (!o) return;
     std::memset(o, 0, sizeof(*o));
     o->eps_kkt = 1e-6;
-    o->eps_admm = 3e-4;
-    o->rho0 = 2.0;
-    o->alpha = 1.6;
+    o->eps_admm = 5e-4;
+    o->rho0 = 3.0;
+    o->alpha = 1.5;
     o->time_budget_s = 0.0;
     o->max_iter = 4000;
-    o->check_every = 10;
+    o->check_every = 20;
     o->min_iter = 20;
     o->polish_rounds = 8;
     o->precision = PRISM_BATCHED_BF16;
     o->use_graph = 1;
     o->fuse_prox = 1;
     o->stream_after = 6;
+    o->chains = 0;
     o->keep_for_backward = 0;
     o->cuda_stream = nullptr;
 }

@@ -26,8 +26,10 @@ def test_autotune_schedule_is_valid_and_certifies():
         assert tuned["check_every"] in (5, 10, 20)
         assert tuned["stream_after"] in (4, 6, 8, 10)
         assert tuned["eps_admm"] in (1e-4, 2e-4, 3e-4, 5e-4, 7e-4)
+        assert tuned["chains"] in (0, 1, 2, 4)
         assert tuned["precision"] == prism.PRISM_BATCHED_BF16
-        opts = {k: tuned[k] for k in ("rho0", "alpha", "check_every", "stream_after", "eps_admm", "precision")}
+        opts = {k: tuned[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm",
+                                      "precision")}
         res = prism.solve(h, batch, **opts)
         assert np.all(res["status"] == prism.PRISM_CERTIFIED)
         assert_parity(uni, batch, res, accounts=[0, 7, 15])

@@ -117,3 +117,15 @@ def test_fused_prox_matches_separate_kernels(varied):
     assert np.all(ru["status"] == prism.PRISM_CERTIFIED), ru["status"]
     assert float(np.max(np.abs(rf["w"] - ru["w"]))) <= 1e-9
     assert_parity(uni, batch, rf, accounts=[0, 7, 19])
+
+
+def test_account_chains_do_not_change_results():
+    # the fused iterations cut into 1, 2 or 4 independent account ranges on their own streams:
+    # the same arithmetic for every account, so the same weights bit for bit
+    uni, batch = make_workload(1, N=600, K=16, M=520)
+    res = {ch: gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, chains=ch) for ch in (1, 2, 4)}
+    for ch in (1, 2, 4):
+        assert np.all(res[ch]["status"] == prism.PRISM_CERTIFIED), ch
+    assert np.array_equal(res[1]["w"], res[2]["w"]) and np.array_equal(res[1]["w"], res[4]["w"])
+    assert np.array_equal(res[1]["iters"], res[4]["iters"])
+    assert_parity(uni, batch, res[4], accounts=[0, 200, 519])
