@@ -43,6 +43,16 @@ M_ACCOUNTS = 500
 ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": 20, "xprox_pinned": 12}
 
 
+def iter_histogram(iters, width: int = 10):
+    """Counts of ADMM iterations per account in bins of `width` iterations: {"40-49": n, ...}."""
+    out = {}
+    for lo in range(0, int(max(iters)) + 1 if len(iters) else 0, width):
+        c = int(((iters >= lo) & (iters < lo + width)).sum())
+        if c:
+            out[f"{lo}-{lo + width - 1}"] = c
+    return out
+
+
 def shard_first_account(rank: int, per_rank: int = M_ACCOUNTS) -> int:
     """First account id of a rank's book: ranks solve disjoint blocks of accounts."""
     return rank * per_rank
@@ -94,11 +104,34 @@ def _cores():
         return os.cpu_count() or 1
 
 
-def oracle_rate(pool, n_workers, accounts):
-    """Wall-clock accounts/s of the oracle over a list of account ids."""
+def oracle_rate(pool, n_workers, accounts, per_account=None):
+    """Wall-clock accounts/s of the oracle over a list of account ids. per_account, when a
+    list, receives each account's own solve time (one single-threaded worker per account)."""
     t = time.perf_counter()
-    pool.map(_oracle_worker, [(a, 0) for a in accounts], chunksize=1)
+    times = pool.map(_oracle_worker, [(a, 0) for a in accounts], chunksize=1)
+    if per_account is not None:
+        per_account.extend(times)
     return len(accounts) / (time.perf_counter() - t)
+
+
+def _cpu_model():
+    """The host CPU's name from /proc/cpuinfo ("model name" on x86; implementer and part
+    numbers on Arm), else the machine type."""
+    import platform
+    try:
+        info = open("/proc/cpuinfo").read().splitlines()
+    except OSError:
+        return platform.machine()
+    kv = {}
+    for line in info:
+        if ":" in line:
+            k, v = line.split(":", 1)
+            kv.setdefault(k.strip(), v.strip())
+    if "model name" in kv:
+        return kv["model name"]
+    if "CPU part" in kv:
+        return f"{platform.machine()} implementer {kv.get('CPU implementer', '?')} part {kv['CPU part']}"
+    return platform.machine()
 
 
 def run_reference(args, rank):
@@ -108,10 +141,10 @@ def run_reference(args, rank):
     pool = _oracle_pool(n)
     try:
         pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)       # spawn / import warm-up
-        rates = []
+        rates, per_acc = [], []
         for s in range(args.warmup + args.steps):
             acc = [(s * n + k) % M_ACCOUNTS for k in range(n)]
-            r = oracle_rate(pool, n, acc)
+            r = oracle_rate(pool, n, acc, per_acc if s >= args.warmup else None)
             if s >= args.warmup:
                 rates.append(r)
     finally:
@@ -125,7 +158,8 @@ def run_reference(args, rank):
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": WORKLOAD, "solver": "FP64 primal active-set oracle (CPU)"},
             "cpu_baseline": {"value": value, "unit": "accounts/s", "cores": n, "kind": "oracle",
-                             "sample": sample},
+                             "sample": sample, "cpu_model": _cpu_model(),
+                             "s_per_account_one_core": statistics.median(per_acc) if per_acc else None},
             "e2e": {"value": value, "unit": "accounts/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -451,7 +485,9 @@ def run_gpu(args, dist, rank, world, local_rank):
                 "frac": achieved / peak, "traffic": profiled_traffic(dom, entries_per_launch),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,
-                "kernel_share": {n: kms[i] / max(1e-9, sum(kms)) for i, n in enumerate(names)}}
+                "kernel_share": {n: kms[i] / max(1e-9, sum(kms)) for i, n in enumerate(names)},
+                "kernel_gbs": {n: alg[n] / (step_ms[n] / n_launch[n] / 1000.0) / 1e9
+                               for n in alg if n_launch[n] > 0 and step_ms[n] > 0}}
     # ---- plain FP32 single-account form on a sample (same GPU, one account per call)
     plain = None
     if rank == 0 and args.plain_sample > 0:
@@ -473,12 +509,14 @@ def run_gpu(args, dist, rank, world, local_rank):
         try:
             pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)
             acc = list(range(n, n + args.cpu_accounts))
-            rate = oracle_rate(pool, n, acc)
+            per_acc = []
+            rate = oracle_rate(pool, n, acc, per_acc)
         finally:
             pool.close()
             pool.join()
         cpu = {"value": rate, "unit": "accounts/s", "cores": n, "kind": "oracle",
-               "sample": f"{len(acc)} accounts of the same workload on {n} worker processes (FP64 active-set oracle)"}
+               "sample": f"{len(acc)} accounts of the same workload on {n} worker processes (FP64 active-set oracle)",
+               "cpu_model": _cpu_model(), "s_per_account_one_core": statistics.median(per_acc)}
     if rank != 0:
         return
     adj = None if args.no_adjoint else adjoint_timing(stream)
@@ -497,12 +535,15 @@ def run_gpu(args, dist, rank, world, local_rank):
                    "schedule": tuned if tuned is not None else "library defaults"},
         "certified": int(cert_all), "certified_frac": cert_all / (args.steps * M * world),
         "status_counts": {prism.STATUS_NAMES[s]: int((status == s).sum()) for s in set(status.tolist())},
-        "admm_iters": {"median": float(np.median(iters)), "max": int(iters.max())},
+        "admm_iters": {"median": float(np.median(iters)), "max": int(iters.max()),
+                       "p10": float(np.percentile(iters, 10)), "p90": float(np.percentile(iters, 90)),
+                       "hist": iter_histogram(iters)},
         "max_residual": {"stat": float(diag[:, 4].max()), "budget": float(diag[:, 0].max()),
                          "box": float(diag[:, 1].max())},
         "phase_ms": dict(zip(("setup", "iterate", "polish", "certify"), prof["t_phase_ms"])),
         "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
-        "e2e": {"value": e2e_value, "unit": "accounts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "e2e": {"value": e2e_value, "unit": "accounts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "bytes_per_account": (h2d + d2h) / M, "ms_per_step": ms_e2e / args.steps},
         "gpu_launches": int(launches), "clocks": clocks,
         "per_call_ms": {"call_median": statistics.median(c for c, _ in dev_calls),
                         "device_median": statistics.median(d for _, d in dev_calls)},

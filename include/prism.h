@@ -124,6 +124,9 @@ typedef struct {
     int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
                                  prism_solve_batch_backward (batched modes only) */
     int32_t profile;          /* 1: no graph; CUDA events around every launch, per kernel class */
+    double  polish_overlap;   /* accounts that stop iterating are polished beside the iterations once
+                                 fewer than this fraction of the book still iterates (0 = never:
+                                 the whole book is polished after the iterations; default 0) */
     int32_t chains;           /* fused iterations: the book is cut into this many account ranges
                                  (multiples of 128) that iterate independently on their own
                                  streams; 0 = as many as fit, up to 4 (default 0) */

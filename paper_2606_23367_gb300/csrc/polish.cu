@@ -122,7 +122,7 @@ __device__ __forceinline__ double phi_value(const Pieces& pc, double w) {
 __global__ void __launch_bounds__(PB) k_classify(PolDev P) {
     const int a = blockIdx.x;
     const size_t base = (size_t)a * P.Npad;
-    if ((P.skip && P.skip[a]) || P.done[a] == 1) return;
+    if ((P.skip && P.skip[a]) || P.done[a] == 1 || (P.sel && P.sel[a] != P.gen)) return;
     for (int p = threadIdx.x; p < P.N; p += PB) {
         const size_t e = base + p;
         Pieces pc;
@@ -299,7 +299,7 @@ __device__ void woodbury32(const PolDev& P, PolishShared& sh, const FreeSet& F, 
 
 __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
     const int a = blockIdx.x;
-    if ((P.skip && P.skip[a]) || P.done[a]) return;
+    if ((P.skip && P.skip[a]) || P.done[a] || (P.sel && P.sel[a] != P.gen)) return;
     extern __shared__ unsigned char smem_raw[];
     PolishShared& sh = *reinterpret_cast<PolishShared*>(smem_raw);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;

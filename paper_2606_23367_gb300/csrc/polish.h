@@ -42,6 +42,8 @@ struct PolDev {
     const float* eta_lo_f = nullptr;
     const float* theta_f = nullptr;     // M
     int* skip = nullptr;                // M: 1 = leave this account alone
+    const int* sel = nullptr;           // M: when set, only the accounts with sel[a] == gen
+    int gen = 0;
     // state and scratch
     int8_t* st = nullptr;               // M x Npad entry state
     int* wband = nullptr;               // M x S working bands

@@ -87,6 +87,11 @@ struct SolveCache {
     int g_iters = 0;
     int64_t g_launches[PRISM_NKCLASS] = {};
     cudaEvent_t ev[6] = {};
+    cudaStream_t pst = nullptr;                   // polish of the accounts that stopped iterating
+    cudaEvent_t ev_pol = nullptr;
+    int* hact = nullptr;                          // pinned: activity flags after each chunk (M)
+    int* hsel = nullptr;                          // pinned: polish batch of each account (M)
+    int hcap = 0;
     static constexpr int MAXCH = 4;               // independent chains of the fused iterations
     cudaStream_t chst[MAXCH - 1] = {};            // streams of chains 1 .. MAXCH-1 (chain 0: the solve stream)
     cudaEvent_t ev_fork = nullptr, ev_join[MAXCH - 1] = {};
@@ -455,6 +460,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     int tc_chunk = 0;
     const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk) : choose_nsplit(M, N);
     const int FMAX = std::min(N, 2048);
+    int* dsel = nullptr;               // device copy of SC.hsel (polish batches)
     auto layout = [&](Arena& A, Dev& D, PolDev& P, BatchDev& BD, void** stage, int** member, int** err,
                       int** pwidx_dev, double** ragged_out) {
         BD.w0 = A.take<double>(MN); BD.lo = A.take<double>(MN); BD.up = A.take<double>(MN); BD.c = A.take<double>(MN);
@@ -493,6 +499,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P.theta = A.take<double>(M); P.diag = A.take<double>((size_t)M * PRISM_NDIAG);
         int* skip = A.take<int>(M);
         P.skip = skip;
+        dsel = A.take<int>(M);
         *err = A.take<int>(4);
         // staging for host inputs / outputs (ragged FP64 x 4, offsets, asset_idx, out)
         stage[0] = A.take<double>((size_t)nnz); stage[1] = A.take<double>((size_t)nnz);
@@ -522,6 +529,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         if (SC.arena_bytes < need) {
             if (SC.arena) { cudaFree(SC.arena); SC.arena = nullptr; SC.arena_bytes = 0; }
             if (SC.have_graph) { cudaGraphExecDestroy(SC.gexec); SC.have_graph = false; }
+            if (SC.hact) { cudaFreeHost(SC.hact); cudaFreeHost(SC.hsel); SC.hact = SC.hsel = nullptr; SC.hcap = 0; }
             if (cudaMalloc(&SC.arena, need) != cudaSuccess) {
                 cudaGetLastError();
                 set_error("device workspace allocation failed");
@@ -532,11 +540,27 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         if (!SC.pinned) {
             if (cudaMallocHost(&SC.pinned, 64) != cudaSuccess) { set_error("pinned alloc failed"); return PRISM_ERR_ALLOCATION; }
             for (auto& e : SC.ev) cudaEventCreate(&e);
+            if (cudaStreamCreateWithFlags(&SC.pst, cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&SC.ev_pol, cudaEventDisableTiming) != cudaSuccess) {
+                cudaGetLastError();
+                SC.pst = nullptr;                        // the polish waits for the iterations
+            }
             SC.chains_ok = cudaEventCreateWithFlags(&SC.ev_fork, cudaEventDisableTiming) == cudaSuccess;
             for (int c = 0; c + 1 < SolveCache::MAXCH && SC.chains_ok; ++c)
                 SC.chains_ok = cudaStreamCreateWithFlags(&SC.chst[c], cudaStreamNonBlocking) == cudaSuccess &&
                                cudaEventCreateWithFlags(&SC.ev_join[c], cudaEventDisableTiming) == cudaSuccess;
             if (!SC.chains_ok) cudaGetLastError();        // one chain only
+        }
+        if (SC.hcap < M) {
+            if (SC.have_graph) { cudaGraphExecDestroy(SC.gexec); SC.have_graph = false; }
+            if (SC.hact) { cudaFreeHost(SC.hact); cudaFreeHost(SC.hsel); SC.hact = SC.hsel = nullptr; SC.hcap = 0; }
+            if (cudaMallocHost(&SC.hact, (size_t)M * 4) != cudaSuccess ||
+                cudaMallocHost(&SC.hsel, (size_t)M * 4) != cudaSuccess) {
+                cudaGetLastError();
+                set_error("pinned alloc failed");
+                return PRISM_ERR_ALLOCATION;
+            }
+            SC.hcap = M;
         }
         Arena A;
         A.base = SC.arena; A.cap = SC.arena_bytes;
@@ -777,6 +801,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             }
             SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
             cudaMemcpyAsync(SC.pinned, D.n_active, 8, cudaMemcpyDeviceToHost, st);
+            cudaMemcpyAsync(SC.hact, D.active, (size_t)M * 4, cudaMemcpyDeviceToHost, st);
             return;
         }
         for (int it = 0; it < n; ++it) {
@@ -797,10 +822,26 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         }
         SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_count_active(D, st); });
         cudaMemcpyAsync(SC.pinned, D.n_active, 8, cudaMemcpyDeviceToHost, st);
+        cudaMemcpyAsync(SC.hact, D.active, (size_t)M * 4, cudaMemcpyDeviceToHost, st);
     };
     int64_t chunk_launches[PRISM_NKCLASS] = {};
-    auto admm_loop = [&](int iter_budget) -> int {
+    // Accounts that stop iterating are polished on their own stream while the others iterate:
+    // after each chunk, those that stopped since the last check form a batch (hsel[a] = its
+    // number) and are classified and polished beside the next chunk. Only the accounts' own
+    // rows are touched, which the iterations no longer read or write.
+    const int rounds = std::max(1, o->polish_rounds);
+    int pol_gen = 0;
+    std::vector<char> was_active(M, 1);
+    auto polish_batch = [&](int gen, cudaStream_t s) {
+        PolDev PB2 = P;
+        PB2.sel = dsel;
+        PB2.gen = gen;
+        SC.prof.run(PRISM_K_OTHER, 1, s, [&] { launch_classify(PB2, s); });
+        SC.prof.run(PRISM_K_POLISH, 1, s, [&] { launch_polish(PB2, rounds, s); });
+    };
+    auto admm_loop = [&](int iter_budget, bool overlap) -> int {
         int done_iters = 0;
+        overlap = overlap && SC.pst && !SC.prof.on && o->polish_overlap > 0;
         bool use_graph = o->use_graph != 0 && !SC.prof.on;
         if (use_graph) {
             bool same = SC.have_graph && SC.g_iters == check_every && std::memcmp(&SC.gdev, &D, sizeof(Dev)) == 0;
@@ -840,6 +881,16 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             done_iters += check_every;
             if (cudaStreamSynchronize(st) != cudaSuccess) return -1;
             if (SC.pinned[1] != 0) return -2;      // a bounded tensor-core wait expired
+            if (overlap && SC.pinned[0] < o->polish_overlap * M) {
+                int nnew = 0;
+                for (int a = 0; a < M; ++a)
+                    if (was_active[a] && !SC.hact[a]) { was_active[a] = 0; SC.hsel[a] = pol_gen + 1; ++nnew; }
+                if (nnew) {
+                    ++pol_gen;
+                    cudaMemcpyAsync(dsel, SC.hsel, (size_t)M * 4, cudaMemcpyHostToDevice, SC.pst);
+                    polish_batch(pol_gen, SC.pst);
+                }
+            }
             if (SC.pinned[0] == 0) break;
             if (o->time_budget_s > 0) {
                 double el = std::chrono::duration<double>(std::chrono::steady_clock::now() - t_call0).count();
@@ -857,7 +908,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         SC.prof.run(PRISM_K_GEMM_X, 1, st, [&] { if (D.bf16) launch_tc_gemm_x(D, st); else launch_gemm_x(D, st); });
         SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st, true); });
     }
-    int total_iters = admm_loop(o->max_iter + check_every - cold);
+    std::memset(SC.hsel, 0, (size_t)M * 4);
+    int total_iters = admm_loop(o->max_iter + check_every - cold, true);
     if (total_iters >= 0) total_iters += cold;
     if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
@@ -873,7 +925,6 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
                      h[0] ? double(h[3]) / h[0] : 0.0);
     }
     // ---- polish, with up to two returns to the iterations at a tighter target
-    const int rounds = std::max(1, o->polish_rounds);
     // polish rounds until no account needs another (checked after each round)
     int n_rounds_run = 0, n_retried = 0;
     // all active-set rounds of every account in one launch; each block stops when settled
@@ -882,8 +933,18 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         SC.prof.run(PRISM_K_POLISH, 1, st, [&] { launch_polish(P, rounds, st); });
         return 0;
     };
-    SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });
-    if (polish_rounds() < 0) { set_error("polish failed"); return PRISM_ERR_CUDA; }
+    if (pol_gen > 0) {
+        // the batches polished beside the iterations, then every account not in one of them
+        // (those that stopped in the last chunk, or were still iterating at the cap)
+        cudaEventRecord(SC.ev_pol, SC.pst);
+        cudaStreamWaitEvent(st, SC.ev_pol, 0);
+        cudaMemcpyAsync(dsel, SC.hsel, (size_t)M * 4, cudaMemcpyHostToDevice, st);
+        ++n_rounds_run;
+        polish_batch(0, st);
+    } else {
+        SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_classify(P, st); });
+        if (polish_rounds() < 0) { set_error("polish failed"); return PRISM_ERR_CUDA; }
+    }
     for (int retry = 0; retry < 2; ++retry) {
         std::vector<int> done(M), skip(M), status(M);
         cudaMemcpyAsync(done.data(), P.done, M * 4, cudaMemcpyDeviceToHost, st);
@@ -911,7 +972,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         Dev saved = D;
         D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);
         D.max_iter = saved.max_iter * (retry + 2);
-        int more = admm_loop(D.max_iter);
+        int more = admm_loop(D.max_iter, false);
         D = saved;
         if (more == -2) { set_error("tensor-core pipeline wait timed out"); return PRISM_ERR_CUDA; }
         if (more < 0) { set_error("ADMM retry failed"); return PRISM_ERR_CUDA; }
@@ -996,6 +1057,7 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     o->fuse_prox = 1;
     o->stream_after = 6;
     o->chains = 0;
+    o->polish_overlap = 0.0;
     o->keep_for_backward = 0;
     o->cuda_stream = nullptr;
 }

@@ -1,6 +1,8 @@
 """Failure vocabulary on the GPU without any device fault: bad inputs are rejected on the
 host, infeasible accounts and iteration caps map to the paper's statuses (Table
 "Status vocabulary", Sec. 10.2)."""
+import dataclasses
+
 import numpy as np
 import pytest
 
@@ -56,3 +58,35 @@ def test_iteration_cap_gives_timeout_or_certified():
     res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32, max_iter=2, min_iter=1,
                     check_every=1, polish_rounds=1)
     assert set(res["status"].tolist()) <= {prism.PRISM_TIMEOUT, prism.PRISM_CERTIFIED}
+
+
+@pytest.mark.parametrize("mode", [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16])
+def test_empty_account_gets_no_feasible_return(mode):
+    # a ragged account with no names cannot meet the budget; its neighbours are unaffected
+    uni, batch = make_workload(2, N=300, M=3)
+    keep = np.ones(batch.w0.shape[0], bool)
+    keep[batch.account_slice(1)] = False
+    offsets = batch.offsets.copy()
+    n1 = offsets[2] - offsets[1]
+    offsets[2:] -= n1
+    empty = dataclasses.replace(batch, offsets=offsets, asset_idx=batch.asset_idx[keep], w0=batch.w0[keep],
+                                lower=batch.lower[keep], upper=batch.upper[keep], tc=batch.tc[keep])
+    res = gpu_solve(uni, empty, precision=mode)
+    assert res["status"][1] == prism.PRISM_NO_FEASIBLE_RETURN
+    assert res["status"][0] == prism.PRISM_CERTIFIED and res["status"][2] == prism.PRISM_CERTIFIED
+
+
+@pytest.mark.parametrize("excess", [-1e-7, 1e-7])
+def test_capacity_at_the_threshold_is_decided_exactly(excess):
+    # total capacity 1 -/+ 1e-7 with no binding band: too close for the FP32 sums, so the
+    # closed-form test decides it from FP64 sums (infeasible below 1, attempted above)
+    uni, batch = make_workload(1, N=600, K=16, M=2)
+    sl = batch.account_slice(1)
+    batch.upper[sl] = (1.0 + excess) / 600
+    batch.band_hi[1, :] = np.inf
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, max_iter=60, polish_rounds=2)
+    if excess < 0:
+        assert res["status"][1] == prism.PRISM_NO_FEASIBLE_RETURN
+    else:
+        assert res["status"][1] != prism.PRISM_NO_FEASIBLE_RETURN
+    assert res["status"][0] == prism.PRISM_CERTIFIED
