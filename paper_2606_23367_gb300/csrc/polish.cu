@@ -8,9 +8,10 @@
 //
 //   2 Sigma_FF w_F + E_F' lambda = mu_F - s_F - 2 Sigma_FA w_A,   E_F w_F = e,
 //
-// is solved in FP64 through the Woodbury identity
+// is solved in FP64 through a Cholesky factor of Sigma_FF itself when |F| <= K, else
+// through the Woodbury identity
 //   Sigma_FF^{-1} = D_F^{-1} - D_F^{-1} B_F (F^{-1} + B_F' D_F^{-1} B_F)^{-1} B_F' D_F^{-1}
-// (K x K Cholesky) and a Schur complement over the working rows, so the
+// (K x K Cholesky), and a Schur complement over the working rows, so the
 // budget row holds exactly in FP64. Then every KKT condition (Sec. 4.4) is
 // checked from the recomputed FP64 gradient 2 (B F B' w + D w) - mu: free
 // weights must stay inside their segment, fixed weights must satisfy
@@ -155,14 +156,15 @@ __global__ void __launch_bounds__(PB) k_classify(PolDev P) {
 //
 // Each round (a) compacts the free set, (b) solves the equality-constrained QP on it,
 // (c) checks every KKT condition and switches the violators. The solve factors the
-// Woodbury capacitance and the Schur complement in FP32 and then applies FP64
+// smaller of Sigma_FF (|F| x |F|) and the Woodbury capacitance (K x K), and the Schur
+// complement, in FP32 and then applies FP64
 // iterative refinement to the full reduced KKT system
 //     [2 Sigma_FF  E_F'] [w_F]   [g0]
 //     [E_F         0   ] [lam] = [e ]
 // (FP64 residuals, FP32 corrections), which converges to FP64 accuracy because the
 // system's condition number times the FP32 unit roundoff is far below one. GB300
-// runs FP64 at 1/64 of its FP32 rate, so this keeps the O(|F| K^2 + K^3) work in
-// FP32 and only O(|F| K) per refinement step in FP64.
+// runs FP64 at 1/64 of its FP32 rate, so this keeps the O(min(|F|, K)^2 max(|F|, K))
+// factorisation in FP32 and only O(|F| K) per refinement step in FP64.
 // ---------------------------------------------------------------------------
 constexpr int FS = 64;                    // free entries whose data live in shared memory
 constexpr int COL_W = PMAXROWS - 1;       // column of Y holding w_F (FP64)
@@ -178,9 +180,11 @@ struct PolishShared {
     double Bd[FS][KMAX + 1];              // FP64 rows of B of the first FS free entries
     double Ys[FS][YS];                    // Y rows of the first FS free entries
     double dinv_s[FS], sig_s[FS];
+    double gF[FS];                        // B_p . (f .* h) of the free entries, for their checks
     float dinvf_s[FS];
     int Fl_s[FS];
     float Ldinv[KMAX];                    // reciprocal of the Cholesky diagonal
+    float f32s[KMAX];                     // FP32 factor variances
     float T[KMAX][PMAXROWS + 1];          // FP32 Woodbury workspace
     double Sf[PMAXROWS][PMAXROWS + 1];    // Schur matrix after pivoted elimination
     double hA[KMAX], fhA[KMAX], fh[KMAX], t64[KMAX];
@@ -192,8 +196,9 @@ struct PolishShared {
     int cntF[PB / 32], cntN[PB / 32];
     int qp[PB / 32][64];                  // per-warp queue of entries that need FP64 work
     float qg[PB / 32][64];
-    double sumA[PB / 32], capA[PB / 32];
+    double sumA[PB / 32], capA[PB / 32], turnA[PB / 32], objA[PB / 32];
     double lam_s[SMAX];
+    float lam_s32[SMAX];                  // its FP32 copy (the filter of the checks)
     double red[PB / 32][8];
     double secsum[SMAX];
     double mmin[PB / 32];
@@ -257,9 +262,43 @@ __device__ __forceinline__ double brow64(const PolDev& P, const PolishShared& sh
     return q < FS ? sh.Bd[q][k] : P.B64[(size_t)F.Fl[q] * P.K + k];
 }
 
+// FP64 products with the free rows of B, spread over the whole block (the FP64 pipe
+// runs a warp instruction at the same cost however few of its lanes are active, so the
+// work goes to full warps): fin(q, sum_k B_F[q][k] x[k]) for each free row q, eight lanes per
+// row, and fin(k, sum_q y(q) B_F[q][k]) for each factor k, four lanes per factor. The partial
+// sums are combined in a fixed order. Block-collective (no barrier inside).
+template <class Fin>
+__device__ __forceinline__ void rows_dot64(const PolDev& P, const PolishShared& sh, const FreeSet& F, int nF,
+                                           const double* x, Fin&& fin) {
+    const int tid = threadIdx.x, g = tid >> 3, sub = tid & 7, K = P.K;
+    for (int q0 = 0; q0 < nF; q0 += PB / 8) {
+        const int q = q0 + g;
+        double acc = 0.0;
+        if (q < nF)
+            for (int k = sub; k < K; k += 8) acc += brow64(P, sh, F, q, k) * x[k];
+        acc += __shfl_xor_sync(0xffffffffu, acc, 4);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+        if (sub == 0 && q < nF) fin(q, acc);
+    }
+}
+
+static_assert(PB / 4 >= KMAX, "four lanes per factor");
+template <class Yf, class Fin>
+__device__ __forceinline__ void cols_dot64(const PolDev& P, const PolishShared& sh, const FreeSet& F, int nF,
+                                           Yf&& y, Fin&& fin) {
+    const int tid = threadIdx.x, k = tid >> 2, sub = tid & 3, K = P.K;
+    double acc = 0.0;
+    if (k < K)
+        for (int q = sub; q < nF; q += 4) acc += y(q) * brow64(P, sh, F, q, k);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+    acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+    if (sub == 0 && k < K) fin(k, acc);
+}
+
 // FP32 Woodbury solve of Sigma_FF x = r for the columns c0..c1 of Y (in: D^{-1} r;
 // out: x). Block-collective.
-__device__ void woodbury32(const PolDev& P, PolishShared& sh, const FreeSet& F, int nF, int c0, int c1) {
+__device__ __noinline__ void woodbury32(const PolDev& P, PolishShared& sh, const FreeSet& F, int nF, int c0, int c1) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int K = P.K, nc = c1 - c0;
     for (int e2 = tid; e2 < K * nc; e2 += PB) {
@@ -297,6 +336,92 @@ __device__ void woodbury32(const PolDev& P, PolishShared& sh, const FreeSet& F, 
     __syncthreads();
 }
 
+// FP32 solve of Sigma_FF x = r for the columns c0..c1 of Y (in: D^{-1} r; out: x) with the
+// Cholesky factor of Sigma_FF itself (|F| <= K, free set in shared memory): one warp per
+// column, rows lane and lane + 32 in registers. Block-collective.
+__device__ __noinline__ void direct32(PolishShared& sh, const FreeSet& F, int nF, int c0, int c1) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    for (int c = c0 + warp; c < c1; c += PB / 32) {
+        float v0 = lane < nF ? float(F.Y[(size_t)lane * YS + c] / F.dinv[lane]) : 0.f;
+        float v1 = lane + 32 < nF ? float(F.Y[(size_t)(lane + 32) * YS + c] / F.dinv[lane + 32]) : 0.f;
+        for (int r = 0; r < nF; ++r) {
+            const float x = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) * sh.Ldinv[r];
+            if (lane > r && lane < nF) v0 = fmaf(-sh.C[lane][r], x, v0);
+            if (lane + 32 > r && lane + 32 < nF) v1 = fmaf(-sh.C[lane + 32][r], x, v1);
+            if (lane == (r & 31)) { if (r < 32) v0 = x; else v1 = x; }
+        }
+        for (int r = nF - 1; r >= 0; --r) {
+            const float x = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) * sh.Ldinv[r];
+            if (lane < r) v0 = fmaf(-sh.C[r][lane], x, v0);
+            if (lane + 32 < r) v1 = fmaf(-sh.C[r][lane + 32], x, v1);
+            if (lane == (r & 31)) { if (r < 32) v0 = x; else v1 = x; }
+        }
+        if (lane < nF) F.Y[(size_t)lane * YS + c] = v0;
+        if (lane + 32 < nF) F.Y[(size_t)(lane + 32) * YS + c] = v1;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ void solve32(const PolDev& P, PolishShared& sh, const FreeSet& F, int nF, int c0,
+                                        int c1, bool direct) {
+    if (direct) direct32(sh, F, nF, c0, c1);
+    else woodbury32(P, sh, F, nF, c0, c1);
+}
+
+// (b3) of a polish round: the FP32 matrix to factor (Sigma_FF = B_F F B_F' + D_F when
+// ``direct``, else the Woodbury capacitance C = F^{-1} + B_F' D_F^{-1} B_F) and its Cholesky
+// factor in sh.C (lower triangle, diagonal included) with the reciprocal diagonal in sh.Ldinv.
+// Returns false when a pivot is not positive. Block-collective.
+__device__ __noinline__ bool factor32(const PolDev& P, PolishShared& sh, const FreeSet& F, int nF, bool direct) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int K = P.K, nS = direct ? nF : K;
+    if (direct) {
+        for (int e2 = tid; e2 < nS * nS; e2 += PB) {
+            const int r = e2 / nS, c = e2 % nS;
+            if (c > r) continue;
+            float acc = (r == c) ? float(P.d64[F.Fl[r]]) : 0.f;
+            for (int k = 0; k < K; ++k) acc = fmaf(sh.Bc[r][k] * sh.f32s[k], sh.Bc[c][k], acc);
+            sh.C[r][c] = acc;
+        }
+    } else {
+        for (int e2 = tid; e2 < K * K; e2 += PB) {
+            const int r = e2 / K, c = e2 % K;
+            if (c > r) continue;
+            float acc = (r == c) ? 1.f / sh.f32s[r] : 0.f;
+            const int q1 = min(nF, FS);
+            for (int q = 0; q < q1; ++q) acc = fmaf(sh.Bc[q][r] * sh.dinvf_s[q], sh.Bc[q][c], acc);
+            for (int q = q1; q < nF; ++q)
+                acc = fmaf(brow32(P, sh, F, q, r) * float(F.dinv[q]), brow32(P, sh, F, q, c), acc);
+            sh.C[r][c] = acc;
+        }
+    }
+    __syncthreads();
+    // Cholesky in the L D L' form (column c of the trailing update reads only column c),
+    // then L = L D^{1/2}
+    bool chol_ok = true;
+    for (int c = 0; c < nS; ++c) {
+        const float piv = sh.C[c][c];
+        if (!(piv > 0.f)) { chol_ok = false; break; }          // every thread reads the same pivot
+        const float ip = 1.f / piv;
+        for (int r = c + 1 + warp; r < nS; r += PB / 32) {
+            const float lr = sh.C[r][c] * ip;
+            for (int q = c + 1 + lane; q <= r; q += 32) sh.C[r][q] = fmaf(-lr, sh.C[q][c], sh.C[r][q]);
+        }
+        __syncthreads();
+    }
+    if (chol_ok) {
+        for (int c = tid; c < nS; c += PB) sh.Ldinv[c] = sqrtf(sh.C[c][c]);
+        __syncthreads();
+        for (int e2 = tid; e2 < nS * nS; e2 += PB) {
+            const int r = e2 / nS, c = e2 % nS;
+            if (c < r) sh.C[r][c] /= sh.Ldinv[c];
+        }
+        __syncthreads();
+        for (int c = tid; c < nS; c += PB) { sh.C[c][c] = sh.Ldinv[c]; sh.Ldinv[c] = 1.f / sh.Ldinv[c]; }
+    }
+    return chol_ok;
+}
+
 __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
     const int a = blockIdx.x;
     if ((P.skip && P.skip[a]) || P.done[a] || (P.sel && P.sel[a] != P.gen)) return;
@@ -314,7 +439,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         const int Lw = cdiv(cdiv(N, PB / 32), 32) * 32;
         const int w0r = min(N, warp * Lw), w1r = min(N, w0r + Lw);
         int nf = 0, nn = 0;
-        double sa = 0.0, ca = 0.0;
+        double sa = 0.0, ca = 0.0, ta = 0.0, oa = 0.0;
         WarpQueue wq;
         wq.p = sh.qp[warp];
         wq.g = sh.qg[warp];
@@ -326,10 +451,15 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 ++nf;
                 ca -= seg_sign(pc, code - ST_FREE) * pc.w0;
             } else {
+                // a fixed entry: its weight, and its parts of the budget, turnover and
+                // objective sums of the checks (a fixed weight keeps its value all round)
                 const double wv = pc.bp[code];
                 W[p] = wv;
                 sa += wv;
-                ca += fabs(wv - pc.w0);
+                const double tv = fabs(wv - pc.w0);
+                ca += tv;
+                ta += tv;
+                oa += P.d64[p] * wv * wv - P.mu64[p] * wv + phi_value(pc, wv);
                 nn += (wv != 0.0);
             }
         };
@@ -359,19 +489,24 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         nn = warp_sum(nn);
         sa = warp_sum(sa);
         ca = warp_sum(ca);
-        if (lane == 0) { sh.cntF[warp] = nf; sh.cntN[warp] = nn; sh.sumA[warp] = sa; sh.capA[warp] = ca; }
+        ta = warp_sum(ta);
+        oa = warp_sum(oa);
+        if (lane == 0) {
+            sh.cntF[warp] = nf; sh.cntN[warp] = nn;
+            sh.sumA[warp] = sa; sh.capA[warp] = ca; sh.turnA[warp] = ta; sh.objA[warp] = oa;
+        }
         __syncthreads();
         if (tid == 0) {
             int of = 0, on = 0;
-            double ss = 0.0, cc = 0.0;
+            double ss = 0.0, cc = 0.0, tt = 0.0, oo = 0.0;
             for (int t = 0; t < PB / 32; ++t) {
                 const int f = sh.cntF[t], n = sh.cntN[t];
                 sh.cntF[t] = of; sh.cntN[t] = on;
                 of += f; on += n;
-                ss += sh.sumA[t]; cc += sh.capA[t];
+                ss += sh.sumA[t]; cc += sh.capA[t]; tt += sh.turnA[t]; oo += sh.objA[t];
             }
             sh.nF = of; sh.nNZ = on;
-            sh.sumA[0] = ss; sh.capA[0] = cc;
+            sh.sumA[0] = ss; sh.capA[0] = cc; sh.turnA[0] = tt; sh.objA[0] = oo;
             int r = 0;
             sh.rows[r++] = -1;
             for (int q = 0; q < S; ++q)
@@ -412,16 +547,22 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         }
         __syncthreads();
         const int nF = sh.nF, nNZ = sh.nNZ, m = sh.nrows;
-        const double sumA = sh.sumA[0], capA = sh.capA[0];
+        const double sumA = sh.sumA[0], capA = sh.capA[0], turnA = sh.turnA[0], objA = sh.objA[0];
         // ---- (b1) h_A = B' w_A (FP64) over the nonzero fixed entries
-        for (int k = tid; k < K; k += PB) {
+        {
+            const int k = tid >> 2, sub = tid & 3;
             double acc = 0.0;
-            for (int q = 0; q < nNZ; ++q) {
-                const int p = NZl[q];
-                acc += W[p] * P.B64[(size_t)p * K + k];
+            if (k < K)
+                for (int q = sub; q < nNZ; q += 4) {
+                    const int p = NZl[q];
+                    acc += W[p] * P.B64[(size_t)p * K + k];
+                }
+            acc += __shfl_xor_sync(0xffffffffu, acc, 2);
+            acc += __shfl_xor_sync(0xffffffffu, acc, 1);
+            if (sub == 0 && k < K) {
+                sh.hA[k] = acc;
+                sh.fhA[k] = P.f64[k] * acc;
             }
-            sh.hA[k] = acc;
-            sh.fhA[k] = P.f64[k] * acc;
         }
         __syncthreads();
         // ---- (b2) the free set: shared memory when small; rows of B in FP32 and FP64
@@ -436,6 +577,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             F.dinv = P.Fdinv + (size_t)a * P.FMAX;
             F.sig = P.Fsig + (size_t)a * P.FMAX;
         }
+        for (int k = tid; k < K; k += PB) sh.f32s[k] = float(P.f64[k]);
         for (int e2 = tid; e2 < min(nF, FS) * K; e2 += PB) {
             const int q = e2 / K, k = e2 % K;
             const double b = P.B64[(size_t)Flg[q] * K + k];
@@ -444,61 +586,25 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         }
         __syncthreads();
         // g0 (FP64), 1/d, cap signs
-        for (int q = tid; q < nF; q += PB) {
+        rows_dot64(P, sh, F, nF, sh.fhA, [&](int q, double bf) {
             const int p = F.Fl[q];
             const size_t e = base + p;
             Pieces pc;
             entry_pieces(P, e, pc);
             const int seg = P.st[e] - ST_FREE;
-            double b0 = 0.0, b1 = 0.0;
-            for (int k = 0; k + 1 < K; k += 2) {
-                b0 += brow64(P, sh, F, q, k) * sh.fhA[k];
-                b1 += brow64(P, sh, F, q, k + 1) * sh.fhA[k + 1];
-            }
-            if (K & 1) b0 += brow64(P, sh, F, q, K - 1) * sh.fhA[K - 1];
             double* Yq = F.Y + (size_t)q * YS;
-            Yq[0] = P.mu64[p] - pc.sl[seg] - 2.0 * (b0 + b1);
+            Yq[0] = P.mu64[p] - pc.sl[seg] - 2.0 * bf;
             Yq[COL_W] = 0.0;
             F.dinv[q] = 1.0 / P.d64[p];
             if (q < FS) sh.dinvf_s[q] = float(F.dinv[q]);
             F.sig[q] = seg_sign(pc, seg);
-        }
+        });
         __syncthreads();
-        // ---- (b3) FP32 capacitance C = F^{-1} + B_F' D_F^{-1} B_F and its Cholesky factor
-        for (int e2 = tid; e2 < K * K; e2 += PB) {
-            const int r = e2 / K, c = e2 % K;
-            if (c > r) continue;
-            float acc = (r == c) ? float(1.0 / P.f64[r]) : 0.f;
-            const int q1 = min(nF, FS);
-            for (int q = 0; q < q1; ++q) acc = fmaf(sh.Bc[q][r] * sh.dinvf_s[q], sh.Bc[q][c], acc);
-            for (int q = q1; q < nF; ++q)
-                acc = fmaf(brow32(P, sh, F, q, r) * float(F.dinv[q]), brow32(P, sh, F, q, c), acc);
-            sh.C[r][c] = acc;
-        }
-        __syncthreads();
-        // Cholesky in the L D L' form (column c of the trailing update reads only column c),
-        // then L = L D^{1/2}
-        bool chol_ok = true;
-        for (int c = 0; c < K; ++c) {
-            const float piv = sh.C[c][c];
-            if (!(piv > 0.f)) { chol_ok = false; break; }          // every thread reads the same pivot
-            const float ip = 1.f / piv;
-            for (int r = c + 1 + warp; r < K; r += PB / 32) {
-                const float lr = sh.C[r][c] * ip;
-                for (int q = c + 1 + lane; q <= r; q += 32) sh.C[r][q] = fmaf(-lr, sh.C[q][c], sh.C[r][q]);
-            }
-            __syncthreads();
-        }
-        if (chol_ok) {
-            for (int c = tid; c < K; c += PB) sh.Ldinv[c] = sqrtf(sh.C[c][c]);
-            __syncthreads();
-            for (int e2 = tid; e2 < K * K; e2 += PB) {
-                const int r = e2 / K, c = e2 % K;
-                if (c < r) sh.C[r][c] /= sh.Ldinv[c];
-            }
-            __syncthreads();
-            for (int c = tid; c < K; c += PB) { sh.C[c][c] = sh.Ldinv[c]; sh.Ldinv[c] = 1.f / sh.Ldinv[c]; }
-        }
+        // ---- (b3) the FP32 matrix to factor: Sigma_FF = B_F F B_F' + D_F itself when the free
+        // set is no larger than K (it then lives in shared memory), else the Woodbury
+        // capacitance C = F^{-1} + B_F' D_F^{-1} B_F; then its Cholesky factor
+        const bool direct = nF <= K && nF <= FS;
+        const bool chol_ok = factor32(P, sh, F, nF, direct);
         __syncthreads();
         if (!chol_ok) {
             if (tid == 0) P.done[a] = 2;
@@ -510,7 +616,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             F.Y[(size_t)q * YS + 1 + r] = row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.dinv[q];
         }
         __syncthreads();
-        woodbury32(P, sh, F, nF, 1, 1 + m);
+        solve32(P, sh, F, nF, 1, 1 + m, direct);
         // Schur matrix S = 1/2 E Y_E, and row edges e = edge - fixed part
         for (int e2 = tid; e2 < m * m; e2 += PB) {
             const int r = e2 / m, c = e2 % m;
@@ -574,28 +680,19 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         // ---- (b5) iterative refinement: FP64 residuals, FP32 corrections
         for (int it = 0; it < IR_STEPS; ++it) {
             // t = B_F' w_F (FP64)
-            for (int k = tid; k < K; k += PB) {
-                double acc = 0.0;
-                for (int q = 0; q < nF; ++q) acc += F.Y[(size_t)q * YS + COL_W] * brow64(P, sh, F, q, k);
-                sh.t64[k] = P.f64[k] * acc;
-            }
+            cols_dot64(P, sh, F, nF, [&](int q) { return F.Y[(size_t)q * YS + COL_W]; },
+                       [&](int k, double acc) { sh.t64[k] = P.f64[k] * acc; });
             __syncthreads();
             // r1 = g0 - 2 Sigma_FF w - E' lam ; stored scaled by D^{-1} in COL_R
             double rmax = 0.0;
-            for (int q = tid; q < nF; q += PB) {
+            rows_dot64(P, sh, F, nF, sh.t64, [&](int q, double bt) {
                 const int p = F.Fl[q];
-                double b0 = 0.0, b1 = 0.0;
-                for (int k = 0; k + 1 < K; k += 2) {
-                    b0 += brow64(P, sh, F, q, k) * sh.t64[k];
-                    b1 += brow64(P, sh, F, q, k + 1) * sh.t64[k + 1];
-                }
-                if (K & 1) b0 += brow64(P, sh, F, q, K - 1) * sh.t64[K - 1];
                 double* Yq = F.Y + (size_t)q * YS;
-                double r1 = Yq[0] - 2.0 * ((b0 + b1) + P.d64[p] * Yq[COL_W]);
+                double r1 = Yq[0] - 2.0 * (bt + P.d64[p] * Yq[COL_W]);
                 for (int r = 0; r < m; ++r) r1 -= row_coef(P, sh.rows[r], p, F.sig[q]) * sh.lam[r];
                 rmax = fmax(rmax, fabs(r1));
                 Yq[COL_R] = r1 * F.dinv[q];
-            }
+            });
             // r2 = e - E w
             for (int r = tid; r < m; r += PB) {
                 double acc = 0.0;
@@ -611,7 +708,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             for (int r = 0; r < m; ++r) r2m = fmax(r2m, fabs(sh.rr2[r]));
             if (it > 0 && rm <= 1e-15 && r2m <= 1e-16) break;
             // Yr = Sigma_FF^{-1} r1 (FP32)
-            woodbury32(P, sh, F, nF, COL_R, COL_R + 1);
+            solve32(P, sh, F, nF, COL_R, COL_R + 1, direct);
             // dlam = S^{-1} (1/2 E Yr - r2) with the eliminated S
             for (int r = tid; r < m; r += PB) {
                 double acc = 0.0;
@@ -652,14 +749,13 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         }
         // ---- (b6) the solved point: W_F, h = h_A + B_F' w_F, multipliers
         for (int q = tid; q < nF; q += PB) W[F.Fl[q]] = F.Y[(size_t)q * YS + COL_W];
-        for (int k = tid; k < K; k += PB) {
-            double acc = sh.hA[k];
-            for (int q = 0; q < nF; ++q) acc += F.Y[(size_t)q * YS + COL_W] * brow64(P, sh, F, q, k);
+        cols_dot64(P, sh, F, nF, [&](int q) { return F.Y[(size_t)q * YS + COL_W]; }, [&](int k, double bw) {
+            const double acc = sh.hA[k] + bw;
             const double fhk = P.f64[k] * acc;
             sh.t64[k] = acc;
             sh.fh[k] = fhk;
             sh.fh32[k] = float(fhk);
-        }
+        });
         for (int k = K + tid; k < KMAX; k += PB) sh.fh32[k] = 0.f;
         for (int s2 = tid; s2 < S; s2 += PB) sh.lam_s[s2] = 0.0;
         __syncthreads();
@@ -677,8 +773,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         int nviol = 0;
         double my_margin = INFINITY;
         int my_who = 0;
-        // FP64 checks of one entry (run 32 entries at a time from the warp's queue)
-        auto check_entry = [&](int p, float g32) {
+        // FP64 checks of one entry (run 32 entries at a time from the warp's queue); gx, when
+        // given, is the entry's exact product B_p . fh computed beforehand
+        auto check_entry3 = [&](int p, float g32, const double* gx) {
             const size_t e = base + p;
             const int code = P.st[e];
             const int sec = P.sector[p];
@@ -689,10 +786,14 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             const double wv = rw.W;
             const double dd = rw.d, mu = rw.mu;
             const double lam_s = sh.lam_s[sec];
-            sum_w += wv;
-            turn += fabs(wv - pc.w0);
-            obj_lin += dd * wv * wv - mu * wv + phi_value(pc, wv);
-            r_box = fmax(r_box, fmax(rw.lo - wv, wv - rw.up));
+            if (code >= ST_FREE) {
+                // the fixed entries' parts of these sums come from the compaction; a fixed
+                // weight sits on a breakpoint inside its box
+                sum_w += wv;
+                turn += fabs(wv - pc.w0);
+                obj_lin += dd * wv * wv - mu * wv + phi_value(pc, wv);
+                r_box = fmax(r_box, fmax(rw.lo - wv, wv - rw.up));
+            }
             const double g_a = 2.0 * (double(g32) + dd * wv) - mu;
             const double delta = 1e-5 * (2.0 * rw.bn1 * fhmax + 2.0 * fabs(dd * wv) + fabs(mu) + fabs(nu) + fabs(lam_s));
             auto exact_rr = [&]() {
@@ -708,7 +809,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             };
             if (code >= ST_FREE) {
                 const int seg = code - ST_FREE;
-                const double rr = exact_rr();
+                const double rr = gx ? 2.0 * (*gx + dd * wv) - mu + nu + lam_s : exact_rr();
                 r_stat = fmax(r_stat, fabs(rr + pc.sl[seg] + theta * seg_sign(pc, seg)));
                 if (wv > pc.bp[seg + 1] + tol_p) { ++nviol; P.st[e] = (int8_t)(seg + 1); }
                 else if (wv < pc.bp[seg] - tol_p) { ++nviol; P.st[e] = (int8_t)seg; }
@@ -732,6 +833,13 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 else if (dn > tol_d) { ++nviol; P.st[e] = (int8_t)(ST_FREE + j - 1); }
             }
         };
+        auto check_entry = [&](int p, float g32) { check_entry3(p, g32, nullptr); };
+        // the free entries of a free set in shared memory are checked in a pass of their own,
+        // with their exact products computed here by the whole block
+        const bool free_pass = F.in_smem;
+        if (free_pass) rows_dot64(P, sh, F, nF, sh.fh, [&](int q, double v) { sh.gF[q] = v; });
+        for (int s2 = tid; s2 < S; s2 += PB) sh.lam_s32[s2] = float(sh.lam_s[s2]);
+        __syncthreads();
         float fmargin = INFINITY;
         int fwho = 0;
         // lane (4 r + j) holds columns 16 i + 4 j .. + 3 (i < 4) of fh in FP32
@@ -739,14 +847,26 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
 #pragma unroll
         for (int i = 0; i < 4; ++i) fr[i] = *reinterpret_cast<const float4*>(&sh.fh32[16 * i + 4 * (lane & 3)]);
         const int ntiles = cdiv(N, 32);
-        for (int ti = warp; ti < ntiles; ti += PB / 32) {
-            const int p = ti * 32 + lane;                 // entries of padding (p >= N) are skipped below
+        // the per-entry inputs of a tile; the next tile's are loaded before the current one
+        // is processed, so that their latency overlaps its product and checks
+        struct TileIn { int code, pw, sec; float w0, lo, up, c, mu, bn1; };
+        auto load_tile = [&](int ti, TileIn& t) {
+            const int p = ti * 32 + lane;
             const size_t e = base + p;
-            const int code = P.st[e];
-            const int pwv = P.pw_idx ? P.pw_idx[e] : -1;
-            const int sec = P.sector[p];
-            const float w0v = P.w0f[e], lov = P.lof[e], upv = P.upf[e], cv = P.cf[e];
-            const float muf = P.mu32[p], bn1f = P.Bn1f[p];
+            t.code = P.st[e];
+            t.pw = P.pw_idx ? P.pw_idx[e] : -1;
+            t.sec = P.sector[p];
+            t.w0 = P.w0f[e]; t.lo = P.lof[e]; t.up = P.upf[e]; t.c = P.cf[e];
+            t.mu = P.mu32[p]; t.bn1 = P.Bn1f[p];
+        };
+        TileIn cur{}, nxt{};
+        if (warp < ntiles) load_tile(warp, cur);
+        for (int ti = warp; ti < ntiles; ti += PB / 32) {
+            if (ti + PB / 32 < ntiles) load_tile(ti + PB / 32, nxt);
+            const int p = ti * 32 + lane;                 // entries of padding (p >= N) are skipped below
+            const int code = cur.code, pwv = cur.pw, sec = cur.sec;
+            const float w0v = cur.w0, lov = cur.lo, upv = cur.up, cv = cur.c;
+            const float muf = cur.mu, bn1f = cur.bn1;
             // g32 = B_p . fh for the tile's 32 rows: four rows of 64 floats per group of 8 lanes x 4
             // float4, coalesced over the tile's contiguous 8 KB; lane p ends with its own row
             float g32 = 0.f;
@@ -769,24 +889,32 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 if ((lane >> 3) == grp) g32 = v;
             }
             bool need = p < N;
-            if (need && pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv > 0.f) {
-                const float lam_f = float(sh.lam_s[sec]);
+            if (need && pwv < 0 && code == 0 && lov == 0.f && upv > 0.f) {
+                // fixed at a lower bound of 0: the one condition is on the right slope of the
+                // cost, c + theta when w0 <= 0 and -(c + theta) when w0 > 0 (a name sold out)
+                const float lam_f = sh.lam_s32[sec];
                 const float rr = 2.f * g32 - muf + nu_f + lam_f;
-                const float up = -rr - (cv + theta_f);
-                const float delta = 1e-5f * (2.f * bn1f * fhmax_f + fabsf(muf) + fabsf(nu_f) + fabsf(lam_f)) + 1e-9f;
+                const float right = (w0v > 0.f) ? -(cv + theta_f) : cv + theta_f;
+                const float up = -rr - right;
+                const float delta =
+                    1e-5f * (2.f * bn1f * fhmax_f + fabsf(muf) + fabsf(nu_f) + fabsf(lam_f) + cv + theta_f) + 1e-9f;
                 if (up < -delta) {
                     if (-up < fmargin) { fmargin = -up; fwho = p + 1; }
                     need = false;
                 }
-            } else if (need && pwv < 0 && code == 0 && w0v == 0.f && lov == 0.f && upv == 0.f) {
-                // an excluded name that is not held: its box is the point 0 and w0 = 0, so it adds
-                // nothing to any sum and has no stationarity condition
+            } else if (need && pwv < 0 && code == 0 && lov == 0.f && upv == 0.f) {
+                // an excluded name: its box is the point 0, so it has no stationarity
+                // condition (its turnover and cost are summed in the compaction)
                 need = false;
             }
+            if (free_pass && code >= ST_FREE) need = false;
             wq.push(need, p, g32, lane);
             wq.drain(false, lane, check_entry);
+            cur = nxt;
         }
         wq.drain(true, lane, check_entry);
+        if (free_pass)
+            for (int q = tid; q < nF; q += PB) check_entry3(F.Fl[q], 0.f, &sh.gF[q]);
         if (double(fmargin) < my_margin) { my_margin = double(fmargin); my_who = fwho; }
         r_stat = warp_max(r_stat); r_box = warp_max(r_box);
         obj_lin = warp_sum(obj_lin); sum_w = warp_sum(sum_w); turn = warp_sum(turn);
@@ -801,9 +929,15 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             sh.red[warp][3] = sum_w; sh.red[warp][4] = turn; sh.red[warp][5] = double(nviol);
             sh.mmin[warp] = my_margin; sh.mwho[warp] = my_who;
         }
+        // sector sums over the entries of nonzero weight: the nonzero fixed and the free ones
         for (int s2 = warp; s2 < S; s2 += PB / 32) {
             double acc = 0.0;
-            for (int p = P.sec_start[s2] + lane; p < P.sec_start[s2 + 1]; p += 32) acc += W[p];
+            for (int q = lane; q < nNZ; q += 32) {
+                const int p = NZl[q];
+                if (P.sector[p] == s2) acc += W[p];
+            }
+            for (int q = lane; q < nF; q += 32)
+                if (P.sector[F.Fl[q]] == s2) acc += F.Y[(size_t)q * YS + COL_W];
             acc = warp_sum(acc);
             if (lane == 0) sh.secsum[s2] = acc;
         }
@@ -814,6 +948,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 rs = fmax(rs, sh.red[w][0]); rb = fmax(rb, sh.red[w][1]); ol += sh.red[w][2];
                 sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5];
             }
+            sw += sumA;
+            tu += turnA;
+            ol += objA;
             double r_exp = 0.0, r_comp = 0.0;
             int bviol = 0, dep_in = 0, dep_out = 0;
             // a working row is dependent when the pivoted elimination left it unpivoted

@@ -475,8 +475,17 @@ __global__ void __launch_bounds__(G4_THREADS, 3) k_tc_gemm_x(const __grid_consta
 // tile's quarters); when l differs over the account, also the sum of l over the pinned
 // entries of each sector segment.
 // ---------------------------------------------------------------------------
-constexpr int XP_TN = 16;         // accounts per tile (MMA N): small tiles, about four CTAs per SM
-constexpr int XP_THREADS = 128;   // warp w reads TMEM lane quarter w (32 assets) for all XP_TN accounts
+constexpr int XP_TN = 16;         // accounts per tile (MMA N): small tiles, four CTAs per SM
+#ifndef PRISM_XP_WARPS
+#define PRISM_XP_WARPS 8
+#endif
+// warp w reads TMEM lane quarter w % 4 (32 assets) for the accounts of its half (w / 4) of the
+// tile's columns: with eight warps each entry of a quarter has two warps over its accounts,
+// so that more warps hide the epilogue's latencies
+constexpr int XP_THREADS = 32 * PRISM_XP_WARPS;
+constexpr int XP_SPLIT = XP_THREADS / 128;        // warps per lane quarter
+constexpr int XP_JN = XP_TN / XP_SPLIT;           // accounts per warp
+static_assert(XP_SPLIT == 1 || XP_SPLIT == 2, "four or eight warps");
 constexpr uint32_t XP_Q_BYTES = XP_TN * KP * 2;
 
 struct __align__(1024) XPSmem {
@@ -491,8 +500,8 @@ struct __align__(1024) XPSmem {
     int fail;
     float4 pa[XP_TN];                 // per account column: rho, 1/rho, L, c (NaN: c differs over positions)
     float4 pb[XP_TN];                 // l (NaN: differs), active, adaptation call, unused
-    float r5[XP_THREADS / 32][5][XP_TN];   // per-warp residual maxima
-    unsigned cm[XP_THREADS / 32][XP_TN];   // per-warp candidate masks
+    float r5[4][5][XP_TN];            // per lane quarter and account: residual maxima
+    unsigned cm[4][XP_TN];            // per lane quarter and account: candidate masks
 };
 
 // 1/x to within 1 ulp (the hardware approximation; x > 0 and normal here)
@@ -594,7 +603,8 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
         tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, m_base);
         tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, m_base);
     }
-    const int q = warp;
+    const int q = warp & 3;                             // TMEM lane quarter
+    const int j0 = (warp >> 2) * XP_JN;                 // first account (column) of this warp
     const int ia = q * 32 + lane;                       // asset within the tile (TMEM lane)
     const int i = at * TM + ia;
     const int ii = i < D.N ? i : 0;
@@ -627,15 +637,19 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     have = __syncthreads_and(have);
     fence_after_sync();
     const bool row_ok = have && i < D.N;
-    float bq[XP_TN];
-    if (have) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
+    float bq[XP_JN];
+    if (have) {
+        if constexpr (XP_JN == 16) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
+        else tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(j0), bq);
+    }
     const float alpha = D.alpha;
     float4* crec = reinterpret_cast<float4*>(D.crec);
     // The accounts are processed without branches on the entry (an inactive account's values
     // are zero and nothing of it is stored), so their reductions interleave.
 #pragma unroll
-    for (int j = 0; j < XP_TN; ++j) {
-        if (j % 4 == 0) {
+    for (int jj = 0; jj < XP_JN; ++jj) {
+        const int j = j0 + jj;
+        if (jj % 4 == 0) {
             // this group's inputs (an expired wait sets the error flag; the values are then
             // not used: the host fails the call)
             if (have) mbar_wait(&s.full_in[j / 4], 0, D.err, 64);
@@ -653,7 +667,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
         const float k = cc * irho;
         const float z0 = s.in[0][j][ia], y0 = s.in[1][j][ia], w0 = s.in[2][j][ia], up = s.in[3][j][ia];
         const float inv = rcp_approx(dd + rho);
-        const float x = (mu + rho * z0 - y0 - bq[j]) * inv;
+        const float x = (mu + rho * z0 - y0 - bq[jj]) * inv;
         const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
         const float t = v - L * irho;
         float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
@@ -696,9 +710,9 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
             }
         }
         if (lane == 0) {
-            s.r5[warp][0][j] = rp;
-            s.r5[warp][1][j] = rd; s.r5[warp][2][j] = nx; s.r5[warp][3][j] = nz; s.r5[warp][4][j] = ny;
-            s.cm[warp][j] = cm;
+            s.r5[q][0][j] = rp;
+            s.r5[q][1][j] = rd; s.r5[q][2][j] = nx; s.r5[q][3][j] = nz; s.r5[q][4][j] = ny;
+            s.cm[q][j] = cm;
         }
     }
     fence_before_sync();
