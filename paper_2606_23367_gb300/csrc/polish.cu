@@ -198,7 +198,11 @@ struct PolishShared {
     float qg[PB / 32][64];
     double sumA[PB / 32], capA[PB / 32], turnA[PB / 32], objA[PB / 32];
     double lam_s[SMAX];
-    float lam_s32[SMAX];                  // its FP32 copy (the filter of the checks)
+    float lam_s32[SMAX];
+    double blo_s[SMAX], bhi_s[SMAX];      // the account's band edges
+    int wb_s[SMAX];                       // working bands (mirrors P.wband of the account)
+    double fixS[SMAX];                    // per sector: sum of the fixed weights
+    int secF[FS];                         // sector of each of the first FS free entries                  // its FP32 copy (the filter of the checks)
     double red[PB / 32][8];
     double secsum[SMAX];
     double mmin[PB / 32];
@@ -248,11 +252,11 @@ struct WarpQueue {
     }
 };
 
-// coefficient of free entry p (cap sign sig) in working row ``row``
-__device__ __forceinline__ double row_coef(const PolDev& P, int row, int p, double sig) {
-    if (row < 0) return 1.0;                                  // budget
-    if (row < P.S) return (P.sector[p] == row) ? 1.0 : 0.0;   // band
-    return sig;                                               // cap
+// coefficient of free entry q in working row ``row`` (sector from shared memory when q < FS)
+__device__ __forceinline__ double coef_q(const PolDev& P, const PolishShared& sh, const FreeSet& F, int row, int q) {
+    if (row < 0) return 1.0;
+    if (row < P.S) return ((q < FS ? sh.secF[q] : P.sector[F.Fl[q]]) == row) ? 1.0 : 0.0;
+    return F.sig[q];
 }
 
 __device__ __forceinline__ float brow32(const PolDev& P, const PolishShared& sh, const FreeSet& F, int q, int k) {
@@ -434,6 +438,12 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
     int* NZl = P.NZlist + (size_t)a * P.FMAX;
     double* W = P.W + base;
     const double tol_d = P.tol_dual, tol_p = P.tol_primal;
+    for (int s2 = tid; s2 < S; s2 += PB) {
+        sh.blo_s[s2] = P.band_lo[a * S + s2];
+        sh.bhi_s[s2] = P.band_hi[a * S + s2];
+        sh.wb_s[s2] = P.wband[a * S + s2];
+    }
+    __syncthreads();
     for (int round = 0; round < rounds; ++round) {
         // ---- (a) ordered compaction in coalesced warp tiles; W of the fixed entries
         const int Lw = cdiv(cdiv(N, PB / 32), 32) * 32;
@@ -510,7 +520,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             int r = 0;
             sh.rows[r++] = -1;
             for (int q = 0; q < S; ++q)
-                if (P.wband[a * S + q] != 0) { if (r < PMAXROWS) sh.rows[r] = q; ++r; }
+                if (sh.wb_s[q] != 0) { if (r < PMAXROWS) sh.rows[r] = q; ++r; }
             if (P.wcap[a]) { if (r < PMAXROWS) sh.rows[r] = S; ++r; }
             sh.nrows = r;
             sh.fail = (of > P.FMAX || on > P.FMAX || of == 0 || r > MAXWROWS);
@@ -564,6 +574,18 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 sh.fhA[k] = P.f64[k] * acc;
             }
         }
+        // per sector, the sum of the fixed weights (one warp per sector); the sectors of the
+        // free entries whose data live in shared memory
+        for (int s2 = warp; s2 < S; s2 += PB / 32) {
+            double acc = 0.0;
+            for (int q = lane; q < nNZ; q += 32) {
+                const int p = NZl[q];
+                if (P.sector[p] == s2) acc += W[p];
+            }
+            acc = warp_sum(acc);
+            if (lane == 0) sh.fixS[s2] = acc;
+        }
+        for (int q = tid; q < min(nF, FS); q += PB) sh.secF[q] = P.sector[Flg[q]];
         __syncthreads();
         // ---- (b2) the free set: shared memory when small; rows of B in FP32 and FP64
         FreeSet F;
@@ -613,7 +635,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         // ---- (b4) Y_E = Sigma_FF^{-1} E_F' (FP32, stored in Y columns 1..m)
         for (int e2 = tid; e2 < nF * m; e2 += PB) {
             const int q = e2 / m, r = e2 % m;
-            F.Y[(size_t)q * YS + 1 + r] = row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.dinv[q];
+            F.Y[(size_t)q * YS + 1 + r] = coef_q(P, sh, F, sh.rows[r], q) * F.dinv[q];
         }
         __syncthreads();
         solve32(P, sh, F, nF, 1, 1 + m, direct);
@@ -622,7 +644,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             const int r = e2 / m, c = e2 % m;
             double acc = 0.0;
             for (int q = 0; q < nF; ++q)
-                acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + 1 + c];
+                acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + 1 + c];
             sh.Sf[r][c] = 0.5 * acc;
         }
         for (int r = tid; r < m; r += PB) {
@@ -631,11 +653,8 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             if (row < 0) {
                 e_r = 1.0 - sumA;
             } else if (row < S) {
-                double fixed_s = 0.0;
-                for (int q = 0; q < nNZ; ++q)
-                    if (P.sector[NZl[q]] == row) fixed_s += W[NZl[q]];
-                const double edge = (P.wband[a * S + row] > 0) ? P.band_hi[a * S + row] : P.band_lo[a * S + row];
-                e_r = edge - fixed_s;
+                const double edge = (sh.wb_s[row] > 0) ? sh.bhi_s[row] : sh.blo_s[row];
+                e_r = edge - sh.fixS[row];
             } else {
                 e_r = P.tau[a] - capA;
             }
@@ -689,7 +708,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 const int p = F.Fl[q];
                 double* Yq = F.Y + (size_t)q * YS;
                 double r1 = Yq[0] - 2.0 * (bt + P.d64[p] * Yq[COL_W]);
-                for (int r = 0; r < m; ++r) r1 -= row_coef(P, sh.rows[r], p, F.sig[q]) * sh.lam[r];
+                for (int r = 0; r < m; ++r) r1 -= coef_q(P, sh, F, sh.rows[r], q) * sh.lam[r];
                 rmax = fmax(rmax, fabs(r1));
                 Yq[COL_R] = r1 * F.dinv[q];
             });
@@ -697,7 +716,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             for (int r = tid; r < m; r += PB) {
                 double acc = 0.0;
                 for (int q = 0; q < nF; ++q)
-                    acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + COL_W];
+                    acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + COL_W];
                 sh.rr2[r] = sh.erhs[r] - acc;
             }
             rmax = warp_max(rmax);
@@ -713,7 +732,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             for (int r = tid; r < m; r += PB) {
                 double acc = 0.0;
                 for (int q = 0; q < nF; ++q)
-                    acc += row_coef(P, sh.rows[r], F.Fl[q], F.sig[q]) * F.Y[(size_t)q * YS + COL_R];
+                    acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + COL_R];
                 sh.dlam[r] = 0.5 * acc - sh.rr2[r];
             }
             __syncthreads();
@@ -932,14 +951,10 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         // sector sums over the entries of nonzero weight: the nonzero fixed and the free ones
         for (int s2 = warp; s2 < S; s2 += PB / 32) {
             double acc = 0.0;
-            for (int q = lane; q < nNZ; q += 32) {
-                const int p = NZl[q];
-                if (P.sector[p] == s2) acc += W[p];
-            }
             for (int q = lane; q < nF; q += 32)
-                if (P.sector[F.Fl[q]] == s2) acc += F.Y[(size_t)q * YS + COL_W];
+                if ((q < FS ? sh.secF[q] : P.sector[F.Fl[q]]) == s2) acc += F.Y[(size_t)q * YS + COL_W];
             acc = warp_sum(acc);
-            if (lane == 0) sh.secsum[s2] = acc;
+            if (lane == 0) sh.secsum[s2] = sh.fixS[s2] + acc;
         }
         __syncthreads();
         if (tid == 0) {
@@ -954,6 +969,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             double r_exp = 0.0, r_comp = 0.0;
             int bviol = 0, dep_in = 0, dep_out = 0;
             // a working row is dependent when the pivoted elimination left it unpivoted
+            auto set_wb = [&](int s2, int v) { sh.wb_s[s2] = v; P.wband[a * S + s2] = v; };
             auto row_dependent = [&](int row) {
                 for (int r = 1; r < m; ++r)
                     if (sh.rows[r] == row) return sh.used[r] == 0;
@@ -961,30 +977,30 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             };
             for (int s2 = 0; s2 < S; ++s2) {
                 const double ssum = sh.secsum[s2];
-                const double hi = P.band_hi[a * S + s2], lo = P.band_lo[a * S + s2];
+                const double hi = sh.bhi_s[s2], lo = sh.blo_s[s2];
                 r_exp = fmax(r_exp, fmax(lo - ssum, ssum - hi));
-                const int wb = P.wband[a * S + s2];
+                const int wb = sh.wb_s[s2];
                 const double ls = sh.lam_s[s2];
                 const bool off = wb != 0 && fabs(ssum - (wb > 0 ? hi : lo)) > tol_p;
                 if (off && row_dependent(s2)) {
                     // dropped from the solve: inside the band it is inactive and leaves the
                     // working set; outside, a fixed entry is released
                     ++bviol;
-                    if (wb > 0 ? ssum < hi : ssum > lo) { P.wband[a * S + s2] = 0; ++dep_in; }
+                    if (wb > 0 ? ssum < hi : ssum > lo) { set_wb(s2, 0); ++dep_in; }
                     else ++dep_out;
                 } else if (wb == 0) {
-                    if (ssum > hi + tol_p) { ++bviol; P.wband[a * S + s2] = 1; }
-                    else if (ssum < lo - tol_p) { ++bviol; P.wband[a * S + s2] = -1; }
+                    if (ssum > hi + tol_p) { ++bviol; set_wb(s2, 1); }
+                    else if (ssum < lo - tol_p) { ++bviol; set_wb(s2, -1); }
                 } else {
                     // an independent working row is off its bound only when free weights left
                     // their segments (counted in nviol): the next round solves again
                     if (off) ++bviol;
                     if (wb > 0) {
                         r_comp = fmax(r_comp, fabs(ls) * fabs(hi - ssum));
-                        if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); P.wband[a * S + s2] = 0; }
+                        if (ls < -tol_d) { ++bviol; r_comp = fmax(r_comp, -ls); set_wb(s2, 0); }
                     } else {
                         r_comp = fmax(r_comp, fabs(ls) * fabs(ssum - lo));
-                        if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); P.wband[a * S + s2] = 0; }
+                        if (ls > tol_d) { ++bviol; r_comp = fmax(r_comp, ls); set_wb(s2, 0); }
                     }
                 }
             }

@@ -528,6 +528,149 @@ struct XPMaps {
     CUtensorMap zr, yr, w0r, upr;            // the same arrays one account row at a time
 };
 
+// The shared-memory views of one tile, for the per-tile epilogue of the fused x-update.
+struct XPTileView {
+    const float (*in)[XP_TN][TM];     // [4][XP_TN][TM]: z, y, w0, u
+    const float4* pa;                 // [XP_TN]
+    const float4* pb;                 // [XP_TN]
+    uint64_t* full_in;                // [XP_TN / 4]: inputs of each group of four accounts
+    uint32_t par;                     // parity of the phase of those barriers
+    float (*r5)[5][XP_TN];            // [4][5][XP_TN]
+    unsigned (*cm)[XP_TN];            // [4][XP_TN]
+};
+
+// A thread's asset of a tile: position, output offset, mu and 2 d, and the sector segments of
+// its lane quarter (lanes with equal sectors are consecutive). Warp-collective.
+struct XPAsset {
+    int ia, i, obase, nsegq, segl, sbase;
+    float mu, dd;
+};
+
+__device__ __forceinline__ XPAsset xp_asset(const Dev& D, int at, int q, int lane, int m_base) {
+    XPAsset ax;
+    ax.ia = q * 32 + lane;
+    ax.i = at * TM + ax.ia;
+    const int ii = ax.i < D.N ? ax.i : 0;
+    ax.obase = m_base * D.Npad + ii;
+    ax.mu = D.mu32[ii];
+    ax.dd = 2.f * D.d32[ii];
+    const int sec = ax.i < D.N ? D.sector[ax.i] : -1;
+    const int prev = __shfl_up_sync(0xffffffffu, sec, 1);
+    const unsigned starts = __ballot_sync(0xffffffffu, ax.i < D.N && (lane == 0 || prev != sec));
+    ax.nsegq = __popc(starts);
+    ax.segl = __popc(starts & ((2u << lane) - 1u)) - 1;
+    const int gq = at * 4 + q;
+    ax.sbase = (gq < D.nq) ? D.qseg[gq] : 0;
+    return ax;
+}
+
+// The epilogue of one tile for this warp's XP_JN accounts j0 .. j0 + XP_JN - 1: for each entry
+// v, the prox at L, the final z, y, X of a pinned entry or the record of a candidate; per
+// account and lane quarter the residual maxima and the candidate mask.
+template <bool UNIFORM>
+__device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, const XPAsset& ax, const float* bq,
+                                            int j0, int q, int lane, int m_base, bool have) {
+    const bool row_ok = have && ax.i < D.N;
+    const float alpha = D.alpha;
+    float4* crec = reinterpret_cast<float4*>(D.crec);
+    // The accounts are processed without branches on the entry (an inactive account's values
+    // are zero and nothing of it is stored), so their reductions interleave.
+#pragma unroll
+    for (int jj = 0; jj < XP_JN; ++jj) {
+        const int j = j0 + jj;
+        if (jj % 4 == 0) {
+            // this group's inputs (an expired wait sets the error flag; the values are then
+            // not used: the host fails the call)
+            if (have) mbar_wait(&tv.full_in[j / 4], tv.par, D.err, 64);
+        }
+        const float4 pa = tv.pa[j], pb = tv.pb[j];
+        const float rho = pa.x, irho = pa.y, L = pa.z;
+        const bool ok = row_ok && pb.y != 0.f;
+        const int off = ax.obase + j * D.Npad;
+        float lo = pb.x, cc = pa.w;
+        const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
+        if (!UNIFORM) {
+            if (ok && !lou) lo = D.lo[off];
+            if (ok && isnan(cc)) cc = D.c[off];
+        }
+        const float k = cc * irho;
+        const float z0 = tv.in[0][j][ax.ia], y0 = tv.in[1][j][ax.ia], w0 = tv.in[2][j][ax.ia], up = tv.in[3][j][ax.ia];
+        const float inv = rcp_approx(ax.dd + rho);
+        const float x = (ax.mu + rho * z0 - y0 - bq[jj]) * inv;
+        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
+        const float t = v - L * irho;
+        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+        z = fminf(fmaxf(z, lo), up);
+        const bool pin = ok && (z == lo);
+        const bool cand = ok && !pin;
+        const float yn = rho * (v - lo);
+        // a non-finite pinned update makes rp NaN (reported as a numerical failure)
+        const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
+        const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
+        if (ok) D.v[off] = v;
+        if (pin) {
+            D.z[off] = lo;
+            D.y[off] = yn;
+            const float X = (ax.mu + rho * lo - yn) * inv;
+            const __nv_bfloat16 h = __float2bfloat16_rn(X);
+            D.Xhi[off] = h;
+            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+        }
+        if (cand) {
+            // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
+            // z, y, mu, d (l and c are read per entry there when they differ over the account)
+            crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
+            crec[2 * (size_t)off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
+        float nx = 0.f, nz = 0.f, ny = 0.f;
+        if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
+            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
+            ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
+            if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
+        }
+        if (!UNIFORM && !lou) {
+            // l differs over the account: the sums of l over the pinned entries, per segment
+            for (int g = 0; g < ax.nsegq; ++g) {
+                const bool mine = (ax.i < D.N) && ax.segl == g && pin;
+                const float sg = warp_sum_f(mine ? lo : 0.f);
+                if (lane == 0 && pb.y != 0.f) D.SOp[(size_t)(ax.sbase + g) * D.M + m_base + j] = sg;
+            }
+        }
+        if (lane == 0) {
+            tv.r5[q][0][j] = rp;
+            tv.r5[q][1][j] = rd; tv.r5[q][2][j] = nx; tv.r5[q][3][j] = nz; tv.r5[q][4][j] = ny;
+            tv.cm[q][j] = cm;
+        }
+    }
+}
+
+// Per-tile outputs: the residual maxima over the four quarters (NaN kept) and the masks, each
+// row written coalesced over the tile's accounts. nthr threads, thread index t.
+__device__ __forceinline__ void xp_tile_out(const Dev& D, const float (*r5)[5][XP_TN], const unsigned (*cm)[XP_TN],
+                                            const float4* pb, int m_base, int m_end, int at, int t, int nthr) {
+    for (int it = t; it < 5 * XP_TN; it += nthr) {
+        const int kq = it / XP_TN, col = it % XP_TN, m = m_base + col;
+        if (m >= m_end || pb[col].y == 0.f) continue;
+        float r = 0.f;
+        bool nan_ = false;
+#pragma unroll
+        for (int qq = 0; qq < 4; ++qq) {
+            const float x = r5[qq][kq][col];
+            nan_ |= isnan(x);
+            r = fmaxf(r, x);
+        }
+        D.Rt[((size_t)kq * D.nt + at) * D.M + m] = nan_ ? NAN : r;
+    }
+    for (int it = t; it < 4 * XP_TN; it += nthr) {
+        const int w = it / XP_TN, col = it % XP_TN, m = m_base + col;
+        const int g = at * 4 + w;
+        if (m >= m_end || pb[col].y == 0.f || g >= D.nq) continue;
+        D.Cm[(size_t)g * D.M + m] = cm[w][col];
+    }
+}
+
 // UNIFORM: every account has one l over its positions and one c over those with u > l (the
 // values come from shared memory; no per-entry l, c and no segment sums of l)
 template <bool UNIFORM>
@@ -605,19 +748,7 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     }
     const int q = warp & 3;                             // TMEM lane quarter
     const int j0 = (warp >> 2) * XP_JN;                 // first account (column) of this warp
-    const int ia = q * 32 + lane;                       // asset within the tile (TMEM lane)
-    const int i = at * TM + ia;
-    const int ii = i < D.N ? i : 0;
-    const int obase = m_base * D.Npad + ii;             // offset of (first account of the tile, asset)
-    const float mu = D.mu32[ii], dd = 2.f * D.d32[ii];
-    // sector segments of this quarter: lanes with equal sectors are consecutive
-    const int sec = i < D.N ? D.sector[i] : -1;
-    const int prev = __shfl_up_sync(0xffffffffu, sec, 1);
-    const unsigned starts = __ballot_sync(0xffffffffu, i < D.N && (lane == 0 || prev != sec));
-    const int nsegq = __popc(starts);
-    const int segl = __popc(starts & ((2u << lane) - 1u)) - 1;
-    const int gq = at * 4 + q;
-    const int sbase = (gq < D.nq) ? D.qseg[gq] : 0;
+    const XPAsset ax = xp_asset(D, at, q, lane, m_base);
     if (tid == 0) {
         if (mbar_wait(&s.full, 0, D.err, 16)) {
             fence_after_sync();
@@ -636,110 +767,18 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
     have = __syncthreads_and(have);
     fence_after_sync();
-    const bool row_ok = have && i < D.N;
     float bq[XP_JN];
     if (have) {
         if constexpr (XP_JN == 16) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
         else tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(j0), bq);
     }
-    const float alpha = D.alpha;
-    float4* crec = reinterpret_cast<float4*>(D.crec);
-    // The accounts are processed without branches on the entry (an inactive account's values
-    // are zero and nothing of it is stored), so their reductions interleave.
-#pragma unroll
-    for (int jj = 0; jj < XP_JN; ++jj) {
-        const int j = j0 + jj;
-        if (jj % 4 == 0) {
-            // this group's inputs (an expired wait sets the error flag; the values are then
-            // not used: the host fails the call)
-            if (have) mbar_wait(&s.full_in[j / 4], 0, D.err, 64);
-        }
-        const float4 pa = s.pa[j], pb = s.pb[j];
-        const float rho = pa.x, irho = pa.y, L = pa.z;
-        const bool ok = row_ok && pb.y != 0.f;
-        const int off = obase + j * D.Npad;
-        float lo = pb.x, cc = pa.w;
-        const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
-        if (!UNIFORM) {
-            if (ok && !lou) lo = D.lo[off];
-            if (ok && isnan(cc)) cc = D.c[off];
-        }
-        const float k = cc * irho;
-        const float z0 = s.in[0][j][ia], y0 = s.in[1][j][ia], w0 = s.in[2][j][ia], up = s.in[3][j][ia];
-        const float inv = rcp_approx(dd + rho);
-        const float x = (mu + rho * z0 - y0 - bq[jj]) * inv;
-        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
-        const float t = v - L * irho;
-        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
-        z = fminf(fmaxf(z, lo), up);
-        const bool pin = ok && (z == lo);
-        const bool cand = ok && !pin;
-        const float yn = rho * (v - lo);
-        // a non-finite pinned update makes rp NaN (reported as a numerical failure)
-        const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
-        const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
-        if (ok) D.v[off] = v;
-        if (pin) {
-            D.z[off] = lo;
-            D.y[off] = yn;
-            const float X = (mu + rho * lo - yn) * inv;
-            const __nv_bfloat16 h = __float2bfloat16_rn(X);
-            D.Xhi[off] = h;
-            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
-        }
-        if (cand) {
-            // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
-            // z, y, mu, d (l and c are read per entry there when they differ over the account)
-            crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
-            crec[2 * (size_t)off + 1] = make_float4(y0, mu, 0.5f * dd, 0.f);
-        }
-        const unsigned cm = __ballot_sync(0xffffffffu, cand);
-        const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
-        float nx = 0.f, nz = 0.f, ny = 0.f;
-        if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
-            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
-            ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
-            if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
-        }
-        if (!UNIFORM && !lou) {
-            // l differs over the account: the sums of l over the pinned entries, per segment
-            for (int g = 0; g < nsegq; ++g) {
-                const bool mine = (i < D.N) && segl == g && pin;
-                const float sg = warp_sum_f(mine ? lo : 0.f);
-                if (lane == 0 && pb.y != 0.f) D.SOp[(size_t)(sbase + g) * D.M + m_base + j] = sg;
-            }
-        }
-        if (lane == 0) {
-            s.r5[q][0][j] = rp;
-            s.r5[q][1][j] = rd; s.r5[q][2][j] = nx; s.r5[q][3][j] = nz; s.r5[q][4][j] = ny;
-            s.cm[q][j] = cm;
-        }
-    }
+    const XPTileView tv{s.in, s.pa, s.pb, s.full_in, 0u, s.r5, s.cm};
+    xp_accounts<UNIFORM>(D, tv, ax, bq, j0, q, lane, m_base, have);
     fence_before_sync();
     __syncthreads();
     if (warp == 0) tmem_dealloc(tmem, 32);
     if (!have) return;
-    // per-tile residual maxima (over the four quarters, NaN kept) and the masks, each row
-    // written coalesced over the tile's accounts
-    for (int it = tid; it < 5 * XP_TN; it += XP_THREADS) {
-        const int kq = it / XP_TN, col = it % XP_TN, m = m_base + col;
-        if (m >= m_end || s.pb[col].y == 0.f) continue;
-        float r = 0.f;
-        bool nan_ = false;
-#pragma unroll
-        for (int qq = 0; qq < 4; ++qq) {
-            const float x = s.r5[qq][kq][col];
-            nan_ |= isnan(x);
-            r = fmaxf(r, x);
-        }
-        D.Rt[((size_t)kq * D.nt + at) * D.M + m] = nan_ ? NAN : r;
-    }
-    for (int it = tid; it < 4 * XP_TN; it += XP_THREADS) {
-        const int w = it / XP_TN, col = it % XP_TN, m = m_base + col;
-        const int g = at * 4 + w;
-        if (m >= m_end || s.pb[col].y == 0.f || g >= D.nq) continue;
-        D.Cm[(size_t)g * D.M + m] = s.cm[w][col];
-    }
+    xp_tile_out(D, s.r5, s.cm, s.pb, m_base, m_end, at, tid, XP_THREADS);
 }
 
 // ---------------------------------------------------------------------------
