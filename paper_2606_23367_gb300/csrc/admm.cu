@@ -1282,7 +1282,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
         const int q = 4 * tid + u;
-        w4[u] = q < nq ? D.Cm[(size_t)q * M + a] : 0u;
+        w4[u] = q < nq ? D.Cm[(size_t)a * nq + q] : 0u;
         c4 += __popc(w4[u]);
     }
     int incl = c4;
@@ -1297,7 +1297,7 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
     for (int t = tid; t < D.nt; t += blockDim.x) {
         float r5[5];
 #pragma unroll
-        for (int k = 0; k < 5; ++k) r5[k] = D.Rt[((size_t)k * D.nt + t) * M + a];
+        for (int k = 0; k < 5; ++k) r5[k] = D.Rt[((size_t)a * 5 + k) * D.nt + t];
         if (isnan(r5[0])) res.bad = 1;
         else res.rp = fmaxf(res.rp, r5[0]);
         res.rd = fmaxf(res.rd, r5[1]); res.nx = fmaxf(res.nx, r5[2]);

@@ -259,6 +259,15 @@ __device__ __forceinline__ double coef_q(const PolDev& P, const PolishShared& sh
     return F.sig[q];
 }
 
+// sum over the free set of coef(row, q) * Y[q][col]: one warp, lanes over q, combined in a
+// fixed order (every lane returns the sum)
+__device__ __forceinline__ double erow_dot(const PolDev& P, const PolishShared& sh, const FreeSet& F, int nF, int row,
+                                           int col, int lane) {
+    double acc = 0.0;
+    for (int q = lane; q < nF; q += 32) acc += coef_q(P, sh, F, row, q) * F.Y[(size_t)q * YS + col];
+    return warp_sum(acc);
+}
+
 __device__ __forceinline__ float brow32(const PolDev& P, const PolishShared& sh, const FreeSet& F, int q, int k) {
     return q < FS ? sh.Bc[q][k] : P.B32[(size_t)F.Fl[q] * P.K + k];
 }
@@ -640,12 +649,10 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         __syncthreads();
         solve32(P, sh, F, nF, 1, 1 + m, direct);
         // Schur matrix S = 1/2 E Y_E, and row edges e = edge - fixed part
-        for (int e2 = tid; e2 < m * m; e2 += PB) {
+        for (int e2 = warp; e2 < m * m; e2 += PB / 32) {
             const int r = e2 / m, c = e2 % m;
-            double acc = 0.0;
-            for (int q = 0; q < nF; ++q)
-                acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + 1 + c];
-            sh.Sf[r][c] = 0.5 * acc;
+            const double acc = erow_dot(P, sh, F, nF, sh.rows[r], 1 + c, lane);
+            if (lane == 0) sh.Sf[r][c] = 0.5 * acc;
         }
         for (int r = tid; r < m; r += PB) {
             const int row = sh.rows[r];
@@ -713,11 +720,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 Yq[COL_R] = r1 * F.dinv[q];
             });
             // r2 = e - E w
-            for (int r = tid; r < m; r += PB) {
-                double acc = 0.0;
-                for (int q = 0; q < nF; ++q)
-                    acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + COL_W];
-                sh.rr2[r] = sh.erhs[r] - acc;
+            for (int r = warp; r < m; r += PB / 32) {
+                const double acc = erow_dot(P, sh, F, nF, sh.rows[r], COL_W, lane);
+                if (lane == 0) sh.rr2[r] = sh.erhs[r] - acc;
             }
             rmax = warp_max(rmax);
             if (lane == 0) sh.red[warp][0] = rmax;
@@ -729,11 +734,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             // Yr = Sigma_FF^{-1} r1 (FP32)
             solve32(P, sh, F, nF, COL_R, COL_R + 1, direct);
             // dlam = S^{-1} (1/2 E Yr - r2) with the eliminated S
-            for (int r = tid; r < m; r += PB) {
-                double acc = 0.0;
-                for (int q = 0; q < nF; ++q)
-                    acc += coef_q(P, sh, F, sh.rows[r], q) * F.Y[(size_t)q * YS + COL_R];
-                sh.dlam[r] = 0.5 * acc - sh.rr2[r];
+            for (int r = warp; r < m; r += PB / 32) {
+                const double acc = erow_dot(P, sh, F, nF, sh.rows[r], COL_R, lane);
+                if (lane == 0) sh.dlam[r] = 0.5 * acc - sh.rr2[r];
             }
             __syncthreads();
             if (tid == 0) {

@@ -927,7 +927,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     // ---- polish, with up to two returns to the iterations at a tighter target
     // polish rounds until no account needs another (checked after each round)
     int n_rounds_run = 0, n_retried = 0;
-    // all active-set rounds of every account in one launch; each block stops when settled
+    // all active-set rounds of every account in one launch; each block stops when settled (one
+    // launch per round measured slower: each launch waits for its slowest block)
     auto polish_rounds = [&]() -> int {
         ++n_rounds_run;
         SC.prof.run(PRISM_K_POLISH, 1, st, [&] { launch_polish(P, rounds, st); });

@@ -80,9 +80,9 @@ struct Dev {
     const float* c_u = nullptr;         // M: c when equal over its positions with u > l, else NaN
     float* SOp = nullptr;               // nseg x M: sum of l_i over the segment's entries pinned at L
                                         // (written only for accounts whose l differs over positions)
-    float* Rt = nullptr;                // 5 x nt x M: residual maxima (rp, rd, nx, nz, ny) of the pinned
+    float* Rt = nullptr;                // M x 5 x nt: residual maxima (rp, rd, nx, nz, ny) of the pinned
                                         // entries of each asset tile; rp is NaN when one was not finite
-    unsigned* Cm = nullptr;             // nq x M: bit b of quarter q set = entry 32q + b not pinned at L
+    unsigned* Cm = nullptr;             // M x nq: bit b of quarter q set = entry 32q + b not pinned at L
     unsigned long long* pcount = nullptr;   // profile mode: [0] candidates, [1] entries of the fused pass
     float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations

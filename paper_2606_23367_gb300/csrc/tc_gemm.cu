@@ -661,13 +661,13 @@ __device__ __forceinline__ void xp_tile_out(const Dev& D, const float (*r5)[5][X
             nan_ |= isnan(x);
             r = fmaxf(r, x);
         }
-        D.Rt[((size_t)kq * D.nt + at) * D.M + m] = nan_ ? NAN : r;
+        D.Rt[((size_t)m * 5 + kq) * D.nt + at] = nan_ ? NAN : r;
     }
     for (int it = t; it < 4 * XP_TN; it += nthr) {
         const int w = it / XP_TN, col = it % XP_TN, m = m_base + col;
         const int g = at * 4 + w;
         if (m >= m_end || pb[col].y == 0.f || g >= D.nq) continue;
-        D.Cm[(size_t)g * D.M + m] = cm[w][col];
+        D.Cm[(size_t)m * D.nq + g] = cm[w][col];
     }
 }
 
