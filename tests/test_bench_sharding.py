@@ -51,3 +51,17 @@ def test_two_rank_aggregation():
 def test_single_rank_is_identity():
     assert bench.reduce_over_ranks(None, 3.5, "max", "cpu") == 3.5
     assert bench.shard_first_account(0) == 0
+
+
+def test_iteration_histogram_bins():
+    import numpy as np
+    iters = np.asarray([3, 9, 10, 38, 45, 45, 53])
+    h = bench.iter_histogram(iters)
+    assert h == {"0-9": 2, "10-19": 1, "30-39": 1, "40-49": 2, "50-59": 1}
+    assert sum(h.values()) == iters.size
+    assert bench.iter_histogram(np.asarray([], dtype=int)) == {}
+
+
+def test_cpu_model_is_a_nonempty_string():
+    m = bench._cpu_model()
+    assert isinstance(m, str) and m.strip()
