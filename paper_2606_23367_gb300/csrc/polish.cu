@@ -193,6 +193,7 @@ struct PolishShared {
     int order[PMAXROWS], used[PMAXROWS];
     int rows[PMAXROWS];
     int nrows, nF, nNZ, fail, nc, go;
+    double fhmax_s, quad_s;               // max_k |f_k h_k| and h' F h of the solved point
     int cntF[PB / 32], cntN[PB / 32];
     int qp[PB / 32][64];                  // per-warp queue of entries that need FP64 work
     float qg[PB / 32][64];
@@ -727,10 +728,12 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             rmax = warp_max(rmax);
             if (lane == 0) sh.red[warp][0] = rmax;
             __syncthreads();
-            double rm = 0.0, r2m = 0.0;
-            for (int w = 0; w < PB / 32; ++w) rm = fmax(rm, sh.red[w][0]);
-            for (int r = 0; r < m; ++r) r2m = fmax(r2m, fabs(sh.rr2[r]));
-            if (it > 0 && rm <= 1e-15 && r2m <= 1e-16) break;
+            // converged: every warp's residual maximum and every row residual within its limit,
+            // tested lane-wise in each warp (the same answer in every warp; a NaN never passes)
+            bool conv = lane >= PB / 32 || sh.red[lane][0] <= 1e-15;
+            for (int r = lane; r < m; r += 32) conv = conv && fabs(sh.rr2[r]) <= 1e-16;
+            conv = __all_sync(0xffffffffu, conv);
+            if (it > 0 && conv) break;
             // Yr = Sigma_FF^{-1} r1 (FP32)
             solve32(P, sh, F, nF, COL_R, COL_R + 1, direct);
             // dlam = S^{-1} (1/2 E Yr - r2) with the eliminated S
@@ -784,10 +787,20 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         double theta = 0.0;
         for (int r = 1; r < m; ++r) if (sh.rows[r] == S) theta = sh.lam[r];
         if (tid == 0) for (int r = 1; r < m; ++r) if (sh.rows[r] < S) sh.lam_s[sh.rows[r]] = sh.lam[r];
+        if (warp == 1) {
+            // once per block: lanes over the factors, combined in a fixed order
+            double fm = 0.0, qd = 0.0;
+            for (int k = lane; k < K; k += 32) {
+                fm = fmax(fm, fabs(sh.fh[k]));
+                qd += sh.t64[k] * sh.fh[k];
+            }
+            fm = warp_max(fm);
+            qd = warp_sum(qd);
+            if (lane == 0) { sh.fhmax_s = fm; sh.quad_s = qd; }
+        }
         __syncthreads();
         const double nu = sh.lam[0];
-        double fhmax = 0.0, quad = 0.0;
-        for (int k = 0; k < K; ++k) { fhmax = fmax(fhmax, fabs(sh.fh[k])); quad += sh.t64[k] * sh.fh[k]; }
+        const double fhmax = sh.fhmax_s, quad = sh.quad_s;
         // ---- (c) checks of every entry (Sec. 4.4): FP32 gradient as a filter, FP64 where it
         // cannot decide; violators switch state for the next round
         const float nu_f = float(nu), theta_f = float(theta), fhmax_f = float(fhmax);
