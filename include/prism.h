@@ -222,7 +222,7 @@ int prism_solve_batch_backward(prism_state* state, const double* dL_dw,
 void prism_free_state(prism_state* state);
 
 /* Diagnostic: the two shared-B products of one ADMM x-update, run on the solver's
- * own kernels for the given precision (spec method; the paper discloses no
+ * own kernels for the given precision (this library's method; the paper discloses no
  * solver internals, Sec. 3):
  *   P  = X B   (M x K, FP64 out)   and   BQ = Q B'  (M x N, FP64 out),
  * with X (M x N) and Q (M x K) row-major FP64 in universe asset order, host or

@@ -1,6 +1,6 @@
 // admm.cu -- the batched ADMM iteration (SIMT products, prox/projection, control).
 //
-// Splitting (spec method; the paper discloses none of its own, Sec. 3):
+// Splitting (this library's method; the paper discloses none of its own, Sec. 3):
 // x = z with f(x) = x' Sigma x - mu' x and g(z) = sum_i phi_i(z_i) + indicator of
 // Z = {1'z = 1, l <= z <= u, lo_s <= sum_{i in s} z_i <= hi_s, ||z - w0||_1 <= tau}
 // (Eq. 1 constraints, Sec. 4.2). One iteration, with penalty rho and relaxation alpha:
