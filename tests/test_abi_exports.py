@@ -53,3 +53,25 @@ def test_struct_layouts_match_the_c_compiler(tmp_path):
     want = [ctypes.sizeof(prism._UniverseDesc), ctypes.sizeof(prism._Batch), ctypes.sizeof(prism._Opts),
             ctypes.sizeof(prism._Result), prism._Result.t_device_ms.offset, prism._Opts.cuda_stream.offset]
     assert got == want
+
+
+def test_every_field_offset_matches_the_c_compiler(tmp_path):
+    """Field by field: the ctypes structures of the binding and the C header agree on every
+    member's offset (a reordered or resized member in either fails here)."""
+    structs = [(prism._UniverseDesc, "prism_universe_desc"), (prism._Batch, "prism_batch"),
+               (prism._Opts, "prism_solve_opts"), (prism._Result, "prism_result")]
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "prism.h"', 'int main(void){']
+    want = []
+    for cls, cname in structs:
+        for name, _ in cls._fields_:
+            lines.append(f'printf("%zu\\n", offsetof({cname}, {name}));')
+            want.append((cname, name, getattr(cls, name).offset))
+    lines.append('return 0;}')
+    src = tmp_path / "off.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "off"
+    subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = [int(x) for x in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split()]
+    assert len(got) == len(want)
+    bad = [(c, n, w, g) for (c, n, w), g in zip(want, got) if w != g]
+    assert not bad, bad
