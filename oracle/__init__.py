@@ -23,4 +23,9 @@ D_a = I, A = sector incidence; objective scaling as in the Sec. 9 display):
     subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,
                ||w - w0||_1 <= tau,
     Sigma = B F B' + D.
+
+The active-set oracle also takes, optionally, the further families of Eq. 1: general rows
+a_lo <= A w <= a_hi (factor exposure bounds with A = B', policy halfspaces G w <= h), a
+per-account tilt of mu and a benchmark w_b in the risk term (pinned in
+tests/test_oracle_general_rows.py). The CUDA path does not take them yet.
 """

@@ -5,7 +5,14 @@ workloads instantiate it (objective scaled as in the Sec. 9 display):
 
     minimise   f(w) = w' Sigma w - mu' w + sum_i phi_i(w_i)
     subject to 1'w = 1,  l <= w <= u,  lo_s <= sum_{i in s} w_i <= hi_s,
-               ||w - w0||_1 <= tau,      Sigma = B F B' + D.
+               ||w - w0||_1 <= tau,      Sigma = B F B' + D,
+
+and, optionally, the further constraint families of Eq. 1: general linear rows
+a_lo <= A w <= a_hi (factor exposure bounds B'w in [a, b] are the rows A = B';
+policy halfspaces G w <= h are rows with a_lo = -inf), a per-account tilt t of
+the expected returns (mu -> mu + t) and a benchmark w_b, whose tracking risk
+(w - w_b)' Sigma (w - w_b) replaces w' Sigma w: it differs from it by the
+linear term -2 (Sigma w_b)' w and a constant, so mu -> mu + t + 2 Sigma w_b.
 
 D > 0 makes f strictly convex, so the minimiser is unique, and the strict
 feasibility the generator enforces (Slater, Sec. 4.2) makes the KKT
@@ -58,17 +65,35 @@ class OracleResult:
     pos: np.ndarray = None     # (n,) breakpoint index (fixed) or segment index (free)
     wband: np.ndarray = None   # (S,) +1 band held at hi, -1 at lo, 0 not a working row
     wcap: bool = False         # cap a working row
+    kappa: np.ndarray = None   # (R,) multipliers of the general rows (0 when slack)
+    wgen: np.ndarray = None    # (R,) +1 row held at a_hi, -1 at a_lo, 0 not a working row
 
 
 class AccountProblem:
     """One account's data in its own (local) asset order."""
 
     def __init__(self, B, f, d, mu, sector, n_sectors, w0, lower, upper, tc,
-                 band_lo, band_hi, tau=np.inf, lots=None):
+                 band_lo, band_hi, tau=np.inf, lots=None, rows=None, rows_lo=None, rows_hi=None,
+                 mu_tilt=None, w_bench=None):
         self.B = np.ascontiguousarray(B, np.float64)
         self.f = np.asarray(f, np.float64)
         self.d = np.asarray(d, np.float64)
         self.mu = np.asarray(mu, np.float64)
+        # general rows a_lo <= A w <= a_hi (none by default)
+        n0 = self.d.shape[0]
+        self.A = np.zeros((0, n0)) if rows is None else np.atleast_2d(np.asarray(rows, np.float64))
+        self.R = self.A.shape[0]
+        self.a_lo = np.full(self.R, -np.inf) if rows_lo is None else np.asarray(rows_lo, np.float64)
+        self.a_hi = np.full(self.R, np.inf) if rows_hi is None else np.asarray(rows_hi, np.float64)
+        # tilt and benchmark fold into the linear term (the constant is kept for the objective)
+        self.obj_const = 0.0
+        if mu_tilt is not None:
+            self.mu = self.mu + np.asarray(mu_tilt, np.float64)
+        if w_bench is not None:
+            wb = np.asarray(w_bench, np.float64)
+            sb = self.B @ (self.f * (self.B.T @ wb)) + self.d * wb
+            self.mu = self.mu + 2.0 * sb
+            self.obj_const = float(wb @ sb)
         self.sector = np.asarray(sector, np.int64)
         self.S = int(n_sectors)
         self.w0 = np.asarray(w0, np.float64)
@@ -125,7 +150,10 @@ class AccountProblem:
     # ---- feasible start -----------------------------------------------
     def feasible_start(self):
         """Greedy least-turnover feasible point: clip to the box, trim sectors above
-        their bands, then sell or buy pro rata to room until the budget holds."""
+        their bands, then sell or buy pro rata to room until the budget holds. With
+        general rows, the least-turnover point of a linear program instead."""
+        if self.R:
+            return self._feasible_start_lp()
         w = np.clip(self.w0, self.lower, self.upper)
         S, sec = self.S, self.sector
 
@@ -169,6 +197,40 @@ class AccountProblem:
             raise RuntimeError("greedy start violates the turnover cap (infeasible account?)")
         return w
 
+    def _feasible_start_lp(self):
+        """min sum_i t_i over (w, t) with t_i >= |w_i - w0_i| and every constraint (a
+        library LP solve, HiGHS); the cap is sum_i t_i <= tau."""
+        from scipy.optimize import linprog
+        n, S = self.n, self.S
+        c = np.concatenate([np.zeros(n), np.ones(n)])
+        I = np.eye(n)
+        A_ub = [np.hstack([I, -I]), np.hstack([-I, -I])]
+        b_ub = [self.w0, -self.w0]
+        for s in range(S):
+            m = (self.sector == s).astype(np.float64)
+            if np.isfinite(self.band_hi[s]):
+                A_ub.append(np.concatenate([m, np.zeros(n)])[None, :]); b_ub.append([self.band_hi[s]])
+            if np.isfinite(self.band_lo[s]):
+                A_ub.append(np.concatenate([-m, np.zeros(n)])[None, :]); b_ub.append([-self.band_lo[s]])
+        for r in range(self.R):
+            if np.isfinite(self.a_hi[r]):
+                A_ub.append(np.concatenate([self.A[r], np.zeros(n)])[None, :]); b_ub.append([self.a_hi[r]])
+            if np.isfinite(self.a_lo[r]):
+                A_ub.append(np.concatenate([-self.A[r], np.zeros(n)])[None, :]); b_ub.append([-self.a_lo[r]])
+        if np.isfinite(self.tau):
+            A_ub.append(np.concatenate([np.zeros(n), np.ones(n)])[None, :]); b_ub.append([self.tau])
+        A_eq = np.concatenate([np.ones(n), np.zeros(n)])[None, :]
+        bounds = [(self.lower[i], self.upper[i]) for i in range(n)] + [(0, None)] * n
+        res = linprog(c, A_ub=np.vstack(A_ub), b_ub=np.concatenate(b_ub), A_eq=A_eq, b_eq=[1.0],
+                      bounds=bounds, method="highs")
+        if res.status != 0:
+            raise RuntimeError("no feasible point (infeasible account?)")
+        w = np.clip(res.x[:n], self.lower, self.upper)
+        return w
+
+    def _gen_values(self, w):
+        return self.A @ w if self.R else np.zeros(0)
+
     # ---- the method -----------------------------------------------------
     def _classify(self, w):
         """Segment state of each weight: fixed at breakpoint p, or free in segment p."""
@@ -186,14 +248,18 @@ class AccountProblem:
                 pos[i] = int(np.searchsorted(bp, w[i])) - 1
         return fixed, pos
 
-    def _rows(self, F, wband, wcap, pos):
-        """Working rows restricted to the free set, in order: budget, bands, cap."""
+    def _rows(self, F, wband, wcap, pos, wgen=None):
+        """Working rows restricted to the free set, in order: budget, bands, cap, general rows."""
         rows = [np.ones(F.shape[0])]
         for s in range(self.S):
             if wband[s] != 0:
                 rows.append((self.sector[F] == s).astype(np.float64))
         if wcap:
             rows.append(self.sg[F, pos[F]])
+        if wgen is not None:
+            for r in range(self.R):
+                if wgen[r] != 0:
+                    rows.append(self.A[r, F])
         return np.asarray(rows)
 
     def solve(self, dual_tol=1e-12, max_iter=None, w_start=None):
@@ -202,6 +268,10 @@ class AccountProblem:
         fixed, pos = self._classify(w)
         wband = np.zeros(S, np.int64)      # +1 held at hi, -1 held at lo, 0 not in W
         wcap = False
+        # the same for the general rows: they enter only through the ratio test, which keeps
+        # the working rows independent (a blocking row has a nonzero rate along a step that
+        # the working rows annihilate)
+        wgen = np.zeros(self.R, np.int64)
         if fixed.all():
             # the budget row needs a free weight; free one with room to move
             cand = np.nonzero(self.nbp > 1)[0]
@@ -216,14 +286,14 @@ class AccountProblem:
             h = self.B.T @ w
             gF = 2.0 * (self.B[F] @ (self.f * h) + self.d[F] * w[F]) - self.mu[F]
             q = gF + self.sl[F, pos[F]]
-            E = self._rows(F, wband, wcap, pos)
+            E = self._rows(F, wband, wcap, pos, wgen if self.R else None)
             Y = self.solve_sigma_ff(F, np.column_stack([q, E.T]))
             Yq, YE = Y[:, 0], Y[:, 1:]
             lam_full = np.linalg.solve(E @ YE, -(E @ Yq))
             step = -0.5 * (Yq + YE @ lam_full)
             scale = max(1.0, float(np.max(np.abs(w[np.isfinite(w)]), initial=0.0)))
             if np.max(np.abs(step), initial=0.0) > 1e-14 * scale:
-                wcap = self._take_step(w, F, step, fixed, pos, wband, wcap)
+                wcap = self._take_step(w, F, step, fixed, pos, wband, wcap, wgen)
                 continue
             # zero step: check the multipliers
             nu = lam_full[0]
@@ -234,8 +304,16 @@ class AccountProblem:
                     lam[s] = lam_full[k]
                     k += 1
             theta = lam_full[k] if wcap else 0.0
+            kappa = np.zeros(self.R)
+            k += 1 if wcap else 0
+            for rr in range(self.R):
+                if wgen[rr] != 0:
+                    kappa[rr] = lam_full[k]
+                    k += 1
             g = 2.0 * self.sigma_w(w) - self.mu
             r = g + nu + lam[self.sector]
+            if self.R:
+                r = r + self.A.T @ kappa
             best, what = dual_tol, None
             A = np.nonzero(fixed)[0]
             if A.size:
@@ -259,10 +337,15 @@ class AccountProblem:
                     best, what = v, ("band", s)
             if wcap and -theta > best:
                 best, what = -theta, ("cap", 0)
+            for rr in range(self.R):
+                v = -kappa[rr] if wgen[rr] > 0 else (kappa[rr] if wgen[rr] < 0 else -np.inf)
+                if v > best:
+                    best, what = v, ("gen", rr)
             if what is None:
                 return OracleResult(w=w, nu=float(nu), lam=lam, theta=float(theta),
                                     iters=it, n_free=int(F.shape[0]), fixed=fixed.copy(),
-                                    pos=pos.copy(), wband=wband.copy(), wcap=bool(wcap))
+                                    pos=pos.copy(), wband=wband.copy(), wcap=bool(wcap),
+                                    kappa=kappa, wgen=wgen.copy())
             kind, j = what
             if kind == "up":
                 fixed[j] = False            # pos stays: segment p lies right of breakpoint p
@@ -271,11 +354,13 @@ class AccountProblem:
                 pos[j] -= 1
             elif kind == "band":
                 wband[j] = 0
+            elif kind == "gen":
+                wgen[j] = 0
             else:
                 wcap = False
         raise RuntimeError(f"active-set method did not finish in {max_iter} iterations")
 
-    def _take_step(self, w, F, step, fixed, pos, wband, wcap):
+    def _take_step(self, w, F, step, fixed, pos, wband, wcap, wgen=None):
         """Ratio test: largest alpha <= 1 keeping every free weight in its segment and
         every row outside the working set feasible; the first blocker joins W.
         Returns whether the cap is in the working set afterwards."""
@@ -307,6 +392,20 @@ class AccountProblem:
                 t = max((self.band_lo[s] - sec_w[s]) / sec_d[s], 0.0)
                 if t < alpha:
                     alpha, block = t, ("blo", s)
+        if self.R:
+            gv = self.A @ w
+            gd = self.A[:, F] @ step
+            for r in range(self.R):
+                if wgen[r] != 0:
+                    continue
+                if gd[r] > 0 and np.isfinite(self.a_hi[r]):
+                    t = max((self.a_hi[r] - gv[r]) / gd[r], 0.0)
+                    if t < alpha:
+                        alpha, block = t, ("ghi", r)
+                elif gd[r] < 0 and np.isfinite(self.a_lo[r]):
+                    t = max((self.a_lo[r] - gv[r]) / gd[r], 0.0)
+                    if t < alpha:
+                        alpha, block = t, ("glo", r)
         if np.isfinite(self.tau) and not wcap:
             rate = float(self.sg[F, pos[F]] @ step)
             if rate > 0:
@@ -329,6 +428,10 @@ class AccountProblem:
             wband[j] = 1
         elif kind == "blo":
             wband[j] = -1
+        elif kind == "ghi":
+            wgen[j] = 1
+        elif kind == "glo":
+            wgen[j] = -1
         else:
             wcap = True
         return wcap

@@ -19,7 +19,9 @@ from . import kkt, pwl
 
 
 def solve_brute(B, f, d, mu, sector, n_sectors, w0, lower, upper, tc, band_lo, band_hi,
-                tau=np.inf, lots=None, tol=1e-11):
+                tau=np.inf, lots=None, tol=1e-11, rows=None, rows_lo=None, rows_hi=None):
+    """The minimiser by enumeration; ``rows``: optional general rows rows_lo <= A w <= rows_hi,
+    each slack or held at one of its edges."""
     n = d.shape[0]
     Sigma = B @ np.diag(f) @ B.T + np.diag(d)
     pieces = []
@@ -41,6 +43,11 @@ def solve_brute(B, f, d, mu, sector, n_sectors, w0, lower, upper, tc, band_lo, b
     band_states = [(0,) if not (np.isfinite(band_lo[s]) or np.isfinite(band_hi[s])) else (0, -1, 1)
                    for s in range(n_sectors)]
     cap_states = (0, 1) if np.isfinite(tau) else (0,)
+    Ag = np.zeros((0, n)) if rows is None else np.atleast_2d(np.asarray(rows, np.float64))
+    glo = np.full(Ag.shape[0], -np.inf) if rows_lo is None else np.asarray(rows_lo, np.float64)
+    ghi = np.full(Ag.shape[0], np.inf) if rows_hi is None else np.asarray(rows_hi, np.float64)
+    gen_states = [tuple([0] + ([-1] if np.isfinite(glo[r]) else []) + ([1] if np.isfinite(ghi[r]) else []))
+                  for r in range(Ag.shape[0])]
     best = None
     for assign in itertools.product(*opts):
         F = [i for i in range(n) if assign[i][0] == "free"]
@@ -49,7 +56,7 @@ def solve_brute(B, f, d, mu, sector, n_sectors, w0, lower, upper, tc, band_lo, b
         for i in A:
             wA[i] = assign[i][1]
         for bst in itertools.product(*band_states):
-            for cst in cap_states:
+            for cst, gst in itertools.product(cap_states, itertools.product(*gen_states)):
                 rows, rhs = [], []
                 r = np.zeros(n); r[F] = 1.0
                 rows.append(r); rhs.append(1.0 - wA.sum())
@@ -70,6 +77,12 @@ def solve_brute(B, f, d, mu, sector, n_sectors, w0, lower, upper, tc, band_lo, b
                     for i in A:
                         const += abs(wA[i] - w0[i])
                     rows.append(r); rhs.append(tau - const)
+                for rg in range(Ag.shape[0]):
+                    if gst[rg] == 0:
+                        continue
+                    r = np.zeros(n); r[F] = Ag[rg, F]
+                    edge = ghi[rg] if gst[rg] > 0 else glo[rg]
+                    rows.append(r); rhs.append(edge - float(Ag[rg] @ wA))
                 E = np.asarray(rows)[:, F] if F else np.zeros((len(rows), 0))
                 e = np.asarray(rhs)
                 w = wA.copy()
@@ -90,7 +103,8 @@ def solve_brute(B, f, d, mu, sector, n_sectors, w0, lower, upper, tc, band_lo, b
                     if np.max(np.abs(e)) > tol:
                         continue
                 diag = kkt.diagnostics(B, f, d, mu, sector, n_sectors, w, w0, lower, upper, tc,
-                                       band_lo, band_hi, tau, lots=lots)
+                                       band_lo, band_hi, tau, lots=lots,
+                                       rows=Ag if Ag.shape[0] else None, rows_lo=glo, rows_hi=ghi)
                 if diag["r_primal"] > tol:
                     continue
                 if best is None or diag["obj"] < best[0]:

@@ -22,6 +22,10 @@ with the bound multipliers implicit in the normal cone N. A weight within
     r_comp = max over bands and the cap of |multiplier| * |slack|, plus any
              multiplier of the wrong sign.
 
+General rows a_lo <= A w <= a_hi (Eq. 1's exposure matrix and policy rows), when
+given, enter r_exposure, add A' kappa to the stationarity and their kappa to the
+complementarity check, like the bands.
+
 Objective (Sec. 9 display, Eq. 1 with Q = 2 Sigma): f(w) = w'Sigma w - mu'w + sum_i phi_i(w_i).
 Quality gates (Sec. 5.5): budget <= 1e-4 and bound <= 1e-6 in the paper; the
 workloads here hold every residual to 1e-6.
@@ -79,7 +83,7 @@ def _one_sided_slopes(x, lower, upper, w0, c, sizes, kappas, theta, tol):
 
 def diagnostics(B, f, d, mu, sector, n_sectors, w, w0, lower, upper, tc,
                 band_lo, band_hi, tau, nu=None, lam=None, theta=None, lots=None,
-                kink_tol=KINK_TOL):
+                kink_tol=KINK_TOL, rows=None, rows_lo=None, rows_hi=None, kappa=None):
     """All residuals of Sec. 4.4 plus the objective for one account (FP64 dict)."""
     w = np.asarray(w, np.float64)
     out = {}
@@ -89,6 +93,12 @@ def diagnostics(B, f, d, mu, sector, n_sectors, w, w0, lower, upper, tc,
     sec_sum = np.bincount(sector, weights=w, minlength=n_sectors)
     out["r_exposure"] = float(max(np.max(np.maximum(band_lo - sec_sum, 0.0), initial=0.0),
                                   np.max(np.maximum(sec_sum - band_hi, 0.0), initial=0.0)))
+    if rows is not None:
+        A = np.atleast_2d(np.asarray(rows, np.float64))
+        av = A @ w
+        out["r_exposure"] = float(max(out["r_exposure"],
+                                      np.max(np.maximum(np.asarray(rows_lo) - av, 0.0), initial=0.0),
+                                      np.max(np.maximum(av - np.asarray(rows_hi), 0.0), initial=0.0)))
     turn = float(np.abs(w - w0).sum())
     out["r_turnover"] = max(turn - tau, 0.0) if np.isfinite(tau) else 0.0
     out["r_primal"] = max(out["r_budget"], out["r_box"], out["r_exposure"], out["r_turnover"])
@@ -98,6 +108,8 @@ def diagnostics(B, f, d, mu, sector, n_sectors, w, w0, lower, upper, tc,
     lam = np.zeros(n_sectors) if lam is None else np.asarray(lam, np.float64)
     theta = 0.0 if theta is None else float(theta)
     g = 2.0 * sigma_times(B, f, d, w) - mu + nu + lam[sector]
+    if rows is not None and kappa is not None:
+        g = g + A.T @ np.asarray(kappa, np.float64)
     r_stat = 0.0
     for i in range(w.shape[0]):
         sizes, kappas = (lots[i] if lots is not None else ((), ()))
@@ -117,6 +129,12 @@ def diagnostics(B, f, d, mu, sector, n_sectors, w, w0, lower, upper, tc,
         comp = max(comp, theta * abs(tau - turn) if np.isfinite(tau) else theta)
     elif theta < 0:
         comp = max(comp, -theta)
+    if rows is not None and kappa is not None:
+        for r, kr in enumerate(np.asarray(kappa, np.float64)):
+            if kr > 0:
+                comp = max(comp, kr * abs(rows_hi[r] - av[r]) if np.isfinite(rows_hi[r]) else kr)
+            elif kr < 0:
+                comp = max(comp, -kr * abs(av[r] - rows_lo[r]) if np.isfinite(rows_lo[r]) else -kr)
     out["r_comp"] = float(comp)
     out["r_kkt"] = max(out["r_primal"], out["r_stat"])
     return out
