@@ -32,15 +32,19 @@ METRIC = "accounts/s at KKT res<=1e-6, 500 accts x 10k assets; batched-BF16 vs p
 WORKLOAD = "500 accounts x 10,000 assets, K=64, 20 sector bands, L1 turnover (seeded synthetic)"
 M_ACCOUNTS = 500
 
-# algorithmic bytes per account-entry moved by one launch of each kernel class
-#   gemm_P : read X (FP32, or its BF16 hi+lo split: 4 B)
+# Algorithmic bytes per account-entry and iteration of the method: read z and y, write z and
+# y (16 B, FP32), read the per-entry constants w0 and u (8 B; l and c are per-account constants
+# in this book). Intermediates of this design (v, the split X, the candidate records) are
+# overhead, not method bytes.
+METHOD_BYTES = 24
+# per account-entry moved by one launch of each kernel class, by the same rule
+#   gemm_P : read X (its BF16 hi+lo split: 4 B) -- the operand of the product
 #   gemm_x : read z, y (8 B), write v (4 B)
 #   prox   : read v, z, y and w0, l, u, c (28 B); write z, y and X (12 B)
-#   xprox  : the x-update fused with the streaming pass of the prox: read z, y, w0, u (16 B;
-#            l and c are per-account constants in this book) and write v (4 B) for every
-#            entry, plus the final z, y and X (12 B) of each entry pinned at its lower bound
-#            (the library counts the others, the candidates, in profile mode)
-ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": 20, "xprox_pinned": 12}
+#   xprox  : the x-update fused with the streaming pass of the prox: the method's 24 B (read z,
+#            y, w0, u; write z, y); v (4 B) and the split X (4 B) are reported as overhead
+ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": METHOD_BYTES}
+OVERHEAD_BYTES = {"xprox": 8}
 
 
 def iter_histogram(iters, width: int = 10):
@@ -82,13 +86,15 @@ def _dist():
 # CPU oracle (reference arm and cpu_baseline)
 # ---------------------------------------------------------------------------
 def _oracle_worker(args):
-    first, seed = args
+    first, seed = args[0], args[1]
+    want_w = len(args) > 2 and args[2]
     from oracle.active_set import account_problem
     from paper_2606_23367_gb300.workloads import make_workload
     uni, batch = make_workload(1, seed=seed, first_account=first, M=1)
     t = time.perf_counter()
-    account_problem(uni, batch, 0).solve()
-    return time.perf_counter() - t
+    r = account_problem(uni, batch, 0).solve()
+    dt = time.perf_counter() - t
+    return (dt, r.w) if want_w else dt
 
 
 def _oracle_pool(n):
@@ -104,14 +110,20 @@ def _cores():
         return os.cpu_count() or 1
 
 
-def oracle_rate(pool, n_workers, accounts, per_account=None):
+def oracle_rate(pool, n_workers, accounts, per_account=None, weights=None):
     """Wall-clock accounts/s of the oracle over a list of account ids. per_account, when a
-    list, receives each account's own solve time (one single-threaded worker per account)."""
+    list, receives each account's own solve time (one single-threaded worker per account);
+    weights, when a dict, receives each account's oracle minimiser."""
     t = time.perf_counter()
-    times = pool.map(_oracle_worker, [(a, 0) for a in accounts], chunksize=1)
+    out = pool.map(_oracle_worker, [(a, 0, weights is not None) for a in accounts], chunksize=1)
+    rate = len(accounts) / (time.perf_counter() - t)
+    times = [o[0] for o in out] if weights is not None else out
+    if weights is not None:
+        for a, o in zip(accounts, out):
+            weights[a] = o[1]
     if per_account is not None:
         per_account.extend(times)
-    return len(accounts) / (time.perf_counter() - t)
+    return rate
 
 
 def _cpu_model():
@@ -137,7 +149,7 @@ def _cpu_model():
 def run_reference(args, rank):
     if rank != 0:
         return
-    n = max(1, min(_cores(), 16))
+    n = _cores()
     pool = _oracle_pool(n)
     try:
         pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)       # spawn / import warm-up
@@ -446,6 +458,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     status = dout["status"].numpy().copy()
     iters = dout["iters"].cpu().numpy()
     diag = dout["diag"].cpu().numpy()
+    w_dev = dout["w"].cpu().numpy()
     # ---- end-to-end lane: pinned host inputs and outputs, copies inside the call
     hin, hout = inputs("host"), outputs("host")
     for _ in range(max(1, args.warmup // 2)):
@@ -462,13 +475,17 @@ def run_gpu(args, dist, rank, world, local_rank):
     it_sum = int(dout["iters"].cpu().numpy().sum())
     N = uni.n_assets
     ix = names.index("xprox")
-    alg = {"gemm_P": ALG_BYTES["gemm_P"] * M * N, "gemm_x": ALG_BYTES["gemm_x"] * M * N,
-           "prox": ALG_BYTES["prox"] * N * it_sum / max(1, kl[names.index("prox")])}
     step_ms = {n: kms[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
     n_launch = {n: kl[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
-    if kl[ix] > 0:
-        ent, cand = prof["stream_entries"], prof["stream_candidates"]
-        alg["xprox"] = (ALG_BYTES["xprox"] * ent + ALG_BYTES["xprox_pinned"] * (ent - cand)) / kl[ix]
+    # account-entries per launch of each class: the staged prox of the fused schedule runs only
+    # the first iterations, over every account; without the fused form it runs every iteration
+    # of the accounts still iterating
+    fused = kl[ix] > 0
+    ent = {"gemm_P": M * N, "gemm_x": M * N,
+           "prox": M * N if fused else N * it_sum / max(1, n_launch["prox"])}
+    if fused:
+        ent["xprox"] = prof["stream_entries"] / kl[ix]
+    alg = {n: ALG_BYTES[n] * ent[n] for n in ent}
     dom = max(step_ms, key=lambda n: step_ms[n])
     avg_ms = step_ms[dom] / max(1, n_launch[dom])
     peaks = {}
@@ -478,44 +495,70 @@ def run_gpu(args, dist, rank, world, local_rank):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
-    entries_per_launch = {"xprox": prof["stream_entries"] / max(1, kl[ix])}.get(dom, M * N)
     kernel_of = {"gemm_P": "k_tc_gemm_P", "gemm_x": "k_tc_gemm_x", "prox": "k_prox_stream / k_prox_smem",
                  "xprox": "k_tc_xprox"}
+    # the whole iteration: the method's bytes of every account-iteration of the step over the
+    # step's device time (setup, polish and certification included in the time)
+    iter_bytes = METHOD_BYTES * N * float(iters.sum())
+    iter_gbs = iter_bytes / (ms / args.steps / 1000.0) / 1e9
     roofline = {"kernel": kernel_of.get(dom, dom), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(dom, entries_per_launch),
+                "frac": achieved / peak, "traffic": profiled_traffic(dom, ent[dom]),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
+                "alg_bytes_per_unit": ALG_BYTES[dom], "units_per_launch": ent[dom],
                 "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,
+                "overhead_bytes_per_launch": OVERHEAD_BYTES.get(dom, 0) * ent[dom],
                 "kernel_share": {n: kms[i] / max(1e-9, sum(kms)) for i, n in enumerate(names)},
                 "kernel_gbs": {n: alg[n] / (step_ms[n] / n_launch[n] / 1000.0) / 1e9
-                               for n in alg if n_launch[n] > 0 and step_ms[n] > 0}}
-    # ---- plain FP32 single-account form on a sample (same GPU, one account per call)
+                               for n in alg if n_launch[n] > 0 and step_ms[n] > 0},
+                "whole_iteration": {"alg_bytes_per_step": iter_bytes, "achieved": iter_gbs,
+                                    "frac": iter_gbs / peak,
+                                    "rule": f"{METHOD_BYTES} B per account-entry and ADMM iteration over the "
+                                            "step's device time"}}
+    # ---- plain FP32 single-account form (same GPU, one account per call), in the same lane as
+    # value: device-resident inputs, device time of each call from the library's CUDA events
     plain = None
     if rank == 0 and args.plain_sample > 0:
-        sub = batch.subset(list(range(args.plain_sample)))
-        step_p = lambda: prism.solve(h, sub, precision=prism.PRISM_PLAIN_FP32, cuda_stream=stream.cuda_stream)
-        step_p()
+        np_ = min(args.plain_sample, M)
+        e1 = int(batch.offsets[np_])
+        sub_in = {k: (v[: np_ + 1] if k == "offsets" else v[:e1] if k in ("w0", "lower", "upper", "tc")
+                      else v[:np_]) for k, v in din.items()}
+        sub_out = {k: (v[:e1] if k == "w" else v[:np_]) for k, v in dout.items()}
+        stp = lambda: prism.prism_solve_batch(h, sub_in["offsets"], sub_in["w0"], sub_in["lower"],
+                                              sub_in["upper"], sub_in["tc"], sub_in["band_lo"],
+                                              sub_in["band_hi"], turnover_cap=sub_in["turnover_cap"],
+                                              out=sub_out, precision=prism.PRISM_PLAIN_FP32,
+                                              cuda_stream=stream.cuda_stream)
+        stp()
         torch.cuda.synchronize()
-        t = time.perf_counter()
-        rp = step_p()
-        torch.cuda.synchronize()
-        dt = time.perf_counter() - t
-        plain = {"value": int((rp["status"] == 0).sum()) / dt, "unit": "accounts/s",
-                 "sample": f"{args.plain_sample} accounts, one launch sequence per account, FP32 B, host wall clock"}
-    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only)
+        rp = stp()
+        ncert = int((sub_out["status"].numpy() == 0).sum())
+        plain = {"value": ncert / (rp["t_device_ms"] / 1000.0), "unit": "accounts/s",
+                 "e2e_call": ncert / (rp["t_call_ms"] / 1000.0),
+                 "sample": f"{np_} accounts of the same book, one launch sequence per account, FP32 B; "
+                           "device-resident inputs, device time (CUDA events) as for value"}
+    # ---- CPU baseline: the oracle on a bounded sample (rank 0, N = 1 only), on every host core;
+    # its minimisers also give the measured weight error of the same accounts of this step
     cpu = None
+    w_err = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        n = max(1, min(_cores(), 16))
+        n = _cores()
         pool = _oracle_pool(n)
         try:
             pool.map(_oracle_worker, [(a, 0) for a in range(n)], chunksize=1)
-            acc = list(range(n, n + args.cpu_accounts))
-            per_acc = []
-            rate = oracle_rate(pool, n, acc, per_acc)
+            n_acc = min(M, args.cpu_accounts if args.cpu_accounts > 0 else 8 * n)
+            acc = list(range(n_acc))
+            per_acc, ref_w = [], {}
+            rate = oracle_rate(pool, n, acc, per_acc, ref_w)
         finally:
             pool.close()
             pool.join()
+        errs = [float(np.max(np.abs(w_dev[batch.account_slice(a)] - ref_w[a]))) for a in acc]
+        bnd = diag[acc, prism.PRISM_DIAG_ERR_EST]
+        w_err = {"max_w_err_vs_oracle": max(errs), "accounts": len(acc),
+                 "max_stated_bound": float(bnd.max()), "bound_holds": bool(all(e <= b + 1e-10 for e, b in zip(errs, bnd)))}
         cpu = {"value": rate, "unit": "accounts/s", "cores": n, "kind": "oracle",
-               "sample": f"{len(acc)} accounts of the same workload on {n} worker processes (FP64 active-set oracle)",
+               "sample": f"accounts 0..{len(acc) - 1} of the same workload on {n} worker processes, one "
+                         "single-threaded FP64 active-set solve per account",
                "cpu_model": _cpu_model(), "s_per_account_one_core": statistics.median(per_acc)}
     if rank != 0:
         return
@@ -540,6 +583,10 @@ def run_gpu(args, dist, rank, world, local_rank):
                        "hist": iter_histogram(iters)},
         "max_residual": {"stat": float(diag[:, 4].max()), "budget": float(diag[:, 0].max()),
                          "box": float(diag[:, 1].max())},
+        "error_vs_oracle": w_err,
+        "stated_error_bound": {"max": float(diag[:, prism.PRISM_DIAG_ERR_EST].max()),
+                               "median": float(np.median(diag[:, prism.PRISM_DIAG_ERR_EST])),
+                               "what": "per-account a-posteriori bound on max|w - w*| (result diag column 7)"},
         "phase_ms": dict(zip(("setup", "iterate", "polish", "certify"), prof["t_phase_ms"])),
         "roofline": roofline, "cpu_baseline": cpu, "plain_fp32": plain,
         "e2e": {"value": e2e_value, "unit": "accounts/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
@@ -560,8 +607,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="bf16", choices=["bf16", "fp32"])
-    ap.add_argument("--plain-sample", type=int, default=8)
-    ap.add_argument("--cpu-accounts", type=int, default=16)
+    ap.add_argument("--plain-sample", type=int, default=64)
+    ap.add_argument("--cpu-accounts", type=int, default=0, help="oracle sample (0: 8 per host core)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--prewarm-s", type=float, default=2.0)
     ap.add_argument("--no-autotune", action="store_true", help="use the library's default schedule")

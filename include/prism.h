@@ -151,7 +151,13 @@ void prism_default_opts(prism_solve_opts* o);
 #define PRISM_DIAG_STAT      4  /* subgradient stationarity distance */
 #define PRISM_DIAG_COMP      5  /* complementarity of bands and cap */
 #define PRISM_DIAG_OBJ       6  /* objective w'Sigma w - mu'w + sum phi_i(w_i) */
-#define PRISM_DIAG_ITERS     7  /* polish rounds used (as a double) */
+#define PRISM_DIAG_ERR_EST   7  /* a-posteriori bound on max_i |w_i - w*_i| against the exact
+                                     minimiser w*: (|r|_2 + sqrt(|r|_2^2 + 4 m C)) / (2 m) with r
+                                     the per-entry stationarity residuals, m = 2 min_i d_i the
+                                     strong-convexity modulus of the risk and C the multipliers
+                                     times their constraints' slacks; valid for a point that
+                                     meets the constraints (columns 0-3 give how far the returned
+                                     point misses them); +inf for an uncertified account */
 #define PRISM_NDIAG          8
 
 /* Kernel classes of prism_result.kernel_ms / kernel_launches (profile mode). */
@@ -235,21 +241,21 @@ int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double*
  *
  * The paper has no counterpart to this entry point. It exists for callers that
  * cannot allocate device memory when they need an answer: a process that has
- * reserved the whole GPU for its own memory pool, a latency-bound thread that
- * must not wait on the allocator, or code recording a CUDA graph (where
- * cudaMalloc is not allowed). Given weights w_in (ragged, the prism_batch
+ * reserved the whole GPU for its own memory pool, or a latency-bound thread that
+ * must not wait on the allocator. Given weights w_in (ragged, the prism_batch
  * layout; for example an earlier solve's result or a warm start) it runs the
- * same FP64 active-set polish and Sec. 4.4 certification kernels as
- * prism_solve_batch and fills res (w, status, nu, lambda_band, theta, diag;
- * iters is set to 0; timings other than t_call_ms are 0).
+ * same FP64 active-set polish and certification kernels as prism_solve_batch
+ * and fills res (w, status, nu, lambda_band, theta, diag; iters is set to 0;
+ * timings other than t_call_ms are 0).
  *
  * It calls no cudaMalloc / cudaFree and no allocating library routine: all
- * device scratch comes from one static __device__ array that
- * every GPU loading the library holds until the process exits (about 17 MB). Limits
+ * device scratch comes from one static __device__ array that every GPU loading
+ * the library holds until the process exits (about 17 MB). Limits
  * (PRISM_ERR_ARGUMENT beyond them): n_accounts <= 32, n_accounts x (universe
  * width rounded up to 64) <= 131072, no tax lots (PRISM_ERR_UNSUPPORTED); an
  * account with more than 512 free weights falls back to the given weights
- * (status FEASIBLE_NONCERTIFIED at best).
+ * (status FEASIBLE_NONCERTIFIED at best). Buffers are host memory or memory of
+ * the universe's device (PRISM_ERR_ARGUMENT for another GPU's memory).
  *
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress; make that first call before any stream capture. Every
@@ -259,7 +265,6 @@ int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double*
 int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const double* w_in,
                          const prism_solve_opts* opts, prism_result* res);
 
-/* Message of the last failed call on this thread ("" when none). */
 /* Autotuner (no counterpart in the paper, which discloses no solver internals, Sec. 3):
  * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
@@ -276,6 +281,7 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
 int prism_autotune(prism_universe* u, const prism_batch* batch, const prism_solve_opts* base,
                    prism_solve_opts* tuned);
 
+/* Message of the last failed call on this thread ("" when none). */
 const char* prism_last_error(void);
 
 /* Library version string. */

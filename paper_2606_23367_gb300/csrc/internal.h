@@ -59,6 +59,7 @@ struct Universe {
     __nv_bfloat16* d_Bt16p = nullptr; // 64 x Npad
     float* d_Cinv32 = nullptr;     // NRHO x K x K, capacitance inverses for FP32 B
     float* d_Cinv16 = nullptr;     // NRHO x K x K, for the BF16-rounded B
+    double dmin = 0.0;             // smallest idiosyncratic variance d_i (strong convexity of the risk)
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
 };

@@ -2,9 +2,8 @@
 // weights, with every byte of device scratch taken from a fixed static array.
 //
 // Some callers cannot allocate device memory at the moment they need a result: a
-// process that has reserved all of the GPU's memory up front for its own pool, a
-// host thread that must not block on the allocator inside a latency budget, or a
-// caller that records its work into a CUDA graph, where cudaMalloc is not allowed.
+// process that has reserved all of the GPU's memory up front for its own pool, or a
+// host thread that must not block on the allocator inside a latency budget.
 // For them this entry point runs the same polish / certification kernels as
 // prism_solve_batch on weights they already hold (for example the result of an
 // earlier solve, or a warm start), and takes its scratch from g_noalloc_scratch
@@ -154,11 +153,16 @@ __global__ void k_na_fill(double* p, int n, double v) {
     if (i < n) p[i] = v;
 }
 
-static bool na_is_dev(const void* p) {
-    if (!p) return false;
+// Where a caller pointer lives: 0 host memory (staged through the scratch), 1 memory the
+// kernels on `device` can read in place (that device's memory, or managed memory), -1 device
+// memory of another GPU (rejected: the kernels would read it across devices).
+static int na_where(const void* p, int device) {
+    if (!p) return 0;
     cudaPointerAttributes attr;
-    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) { cudaGetLastError(); return false; }
-    return attr.type == cudaMemoryTypeDevice || attr.type == cudaMemoryTypeManaged;
+    if (cudaPointerGetAttributes(&attr, p) != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (attr.type == cudaMemoryTypeManaged) return 1;
+    if (attr.type == cudaMemoryTypeDevice) return attr.device == device ? 1 : -1;
+    return 0;
 }
 
 // Bump carve over the static array; returns nullptr past the end.
@@ -214,8 +218,17 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     if (opts) o = *opts; else prism_default_opts(&o);
     cudaStream_t st = o.cuda_stream ? (cudaStream_t)o.cuda_stream : U.stream;
     // offsets on the host (fixed-size buffer: no allocation)
+    // every caller pointer is host memory or memory of this universe's device
+    {
+        const void* ptrs[] = {b->offsets, b->asset_idx, b->w0, b->lower, b->upper, b->tc, b->band_lo, b->band_hi,
+                              b->turnover_cap, w_in, res->w, res->status, res->iters, res->nu, res->lambda_band,
+                              res->theta, res->diag};
+        for (const void* q : ptrs)
+            if (na_where(q, U.device) < 0)
+                return na_fail(PRISM_ERR_ARGUMENT, "prism_polish_noalloc: a buffer is on another GPU than the universe");
+    }
     int64_t offs[NA_MAX_ACCOUNTS + 1];
-    if (na_is_dev(b->offsets)) {
+    if (na_where(b->offsets, U.device) > 0) {
         if (cudaMemcpy(offs, b->offsets, (M + 1) * sizeof(int64_t), cudaMemcpyDeviceToHost) != cudaSuccess)
             return na_fail(PRISM_ERR_CUDA, "offsets copy failed");
     } else {
@@ -269,7 +282,7 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     if (cv.overflow) return na_fail(PRISM_ERR_ARGUMENT, "prism_polish_noalloc: request exceeds the static scratch");
     // stage the inputs (host pointers are copied into the scratch, device pointers used in place)
     auto stage = [&](const void* src, void* dst, size_t bytes) -> const void* {
-        if (na_is_dev(src)) return src;
+        if (na_where(src, U.device) > 0) return src;
         cudaMemcpyAsync(dst, src, bytes, cudaMemcpyHostToDevice, st);
         return dst;
     };
@@ -321,13 +334,14 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     P.z = Z; P.nu_f = nu_f; P.eta_hi_f = eta_hi; P.eta_lo_f = eta_lo; P.theta_f = theta_f;
     P.skip = skip; P.st = stt; P.wband = wband; P.wcap = wcap; P.done = done;
     P.Flist = Fl; P.NZlist = NZl; P.Fsig = Fsig; P.Y = Y; P.FMAX = FMAX;
+    P.dmin = U.dmin;
     P.W = W; P.nu = nu; P.lam = lam; P.theta = theta; P.diag = diag; P.status = status;
     launch_classify(P, st);
     const int rounds = std::max(1, o.polish_rounds);
     launch_polish(P, rounds, st);
     launch_fallback(P, st);
     launch_finish_status(P, o.eps_kkt, st);
-    const bool w_dev = na_is_dev(res->w);
+    const bool w_dev = na_where(res->w, U.device) > 0;
     if (nnz > 0)
         k_na_unpack<<<(unsigned)cdiv64(nnz, 256), 256, 0, st>>>(M, Npad, nnz, s_off, A.asset_idx, U.d_inv_perm, W,
                                                                  w_dev ? res->w : s_out);

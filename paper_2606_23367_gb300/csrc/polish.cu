@@ -436,6 +436,45 @@ __device__ __noinline__ bool factor32(const PolDev& P, PolishShared& sh, const F
     return chol_ok;
 }
 
+// A-posteriori bound on ||w - w*||_inf for the polished point w of one account.
+// The risk term makes the objective strongly convex with modulus m = lambda_min(2 Sigma)
+// >= 2 min_i d_i. Let r be the vector of per-entry stationarity residuals (the distances
+// that r_stat takes the maximum of) and L the Lagrangian with the returned multipliers.
+// Multipliers of the wrong sign are replaced by 0 for the argument, which moves every
+// residual by at most their size (|lambda_s| on the entries of sector s, |theta| on all).
+// With the signs right, L <= F on the feasible set, L is m-strongly convex and r is in
+// its subdifferential at w, and F(w) >= F(w*) + m/2 ||w - w*||^2; together
+//   m ||w - w*||^2 <= ||r||_2 ||w - w*|| + C,
+//   C = sum_s |lambda_s| |slack_s| + |theta| |tau - ||w - w0||_1| + |nu| |1'w - 1|,
+// so ||w - w*||_2 <= (||r||_2 + sqrt(||r||_2^2 + 4 m C)) / (2 m). This holds for a point
+// that meets the constraints; the primal residuals reported beside it say by how much
+// the returned point misses them (to FP64 rounding for a certified account).
+__device__ double err_bound(const PolDev& P, const PolishShared& sh, double r2, double sw, double tu, double tau,
+                            double nu, double theta) {
+    const double m = 2.0 * P.dmin;
+    if (!(m > 0.0)) return INFINITY;
+    double wrong = 0.0, C = fabs(nu) * fabs(sw - 1.0);
+    for (int s = 0; s < P.S; ++s) {
+        // lambda_s >= 0 prices the upper edge and lambda_s <= 0 the lower one; a multiplier
+        // on an infinite edge has no such reading and counts as of the wrong sign
+        // Either reading gives a valid bound, so each multiplier takes the one that adds less
+        // (a tiny multiplier of a band held at its other edge is cheaper set to zero).
+        const double ls = sh.lam_s[s], ssum = sh.secsum[s];
+        const double edge = ls > 0.0 ? sh.bhi_s[s] : sh.blo_s[s];
+        if (ls == 0.0) continue;
+        const double as_comp = isfinite(edge) ? fabs(ls) * fabs(edge - ssum) : INFINITY;
+        if (sqrt(as_comp / m) <= sqrt(double(P.N)) * fabs(ls) / m) C += as_comp;
+        else wrong += fabs(ls);
+    }
+    if (theta != 0.0) {
+        const double as_comp = (isfinite(tau) && theta > 0.0) ? theta * fabs(tau - tu) : INFINITY;
+        if (sqrt(as_comp / m) <= sqrt(double(P.N)) * fabs(theta) / m) C += as_comp;
+        else wrong += fabs(theta);
+    }
+    const double re = r2 + sqrt(double(P.N)) * wrong;
+    return (re + sqrt(re * re + 4.0 * m * C)) / (2.0 * m);
+}
+
 __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
     const int a = blockIdx.x;
     if ((P.skip && P.skip[a]) || P.done[a] || (P.sel && P.sel[a] != P.gen)) return;
@@ -805,6 +844,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         // cannot decide; violators switch state for the next round
         const float nu_f = float(nu), theta_f = float(theta), fhmax_f = float(fhmax);
         double r_stat = 0.0, r_box = 0.0, obj_lin = 0.0, sum_w = 0.0, turn = 0.0;
+        double r_sq = 0.0;                 // squared 2-norm of the stationarity residuals
         int nviol = 0;
         double my_margin = INFINITY;
         int my_who = 0;
@@ -845,7 +885,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             if (code >= ST_FREE) {
                 const int seg = code - ST_FREE;
                 const double rr = gx ? 2.0 * (*gx + dd * wv) - mu + nu + lam_s : exact_rr();
-                r_stat = fmax(r_stat, fabs(rr + pc.sl[seg] + theta * seg_sign(pc, seg)));
+                const double res = fabs(rr + pc.sl[seg] + theta * seg_sign(pc, seg));
+                r_stat = fmax(r_stat, res);
+                r_sq += res * res;
                 if (wv > pc.bp[seg + 1] + tol_p) { ++nviol; P.st[e] = (int8_t)(seg + 1); }
                 else if (wv < pc.bp[seg] - tol_p) { ++nviol; P.st[e] = (int8_t)seg; }
             } else {
@@ -859,7 +901,9 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                     up = -rr - right;
                     dn = left + rr;
                 }
-                r_stat = fmax(r_stat, fmax(fmax(up, dn), 0.0));
+                const double res = fmax(fmax(up, dn), 0.0);
+                r_stat = fmax(r_stat, res);
+                r_sq += res * res;
                 if (pc.nb > 1) {
                     if (isfinite(right) && -up < my_margin) { my_margin = -up; my_who = p + 1; }
                     if (isfinite(left) && -dn < my_margin) { my_margin = -dn; my_who = -(p + 1); }
@@ -951,7 +995,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         if (free_pass)
             for (int q = tid; q < nF; q += PB) check_entry3(F.Fl[q], 0.f, &sh.gF[q]);
         if (double(fmargin) < my_margin) { my_margin = double(fmargin); my_who = fwho; }
-        r_stat = warp_max(r_stat); r_box = warp_max(r_box);
+        r_stat = warp_max(r_stat); r_box = warp_max(r_box); r_sq = warp_sum(r_sq);
         obj_lin = warp_sum(obj_lin); sum_w = warp_sum(sum_w); turn = warp_sum(turn);
         nviol = warp_sum(nviol);
         for (int o = 16; o > 0; o >>= 1) {
@@ -962,6 +1006,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         if (lane == 0) {
             sh.red[warp][0] = r_stat; sh.red[warp][1] = r_box; sh.red[warp][2] = obj_lin;
             sh.red[warp][3] = sum_w; sh.red[warp][4] = turn; sh.red[warp][5] = double(nviol);
+            sh.red[warp][6] = r_sq;
             sh.mmin[warp] = my_margin; sh.mwho[warp] = my_who;
         }
         // sector sums over the entries of nonzero weight: the nonzero fixed and the free ones
@@ -974,10 +1019,10 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         }
         __syncthreads();
         if (tid == 0) {
-            double rs = 0, rb = 0, ol = 0, sw = 0, tu = 0, nv = 0;
+            double rs = 0, rb = 0, ol = 0, sw = 0, tu = 0, nv = 0, rq = 0;
             for (int w = 0; w < PB / 32; ++w) {
                 rs = fmax(rs, sh.red[w][0]); rb = fmax(rb, sh.red[w][1]); ol += sh.red[w][2];
-                sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5];
+                sw += sh.red[w][3]; tu += sh.red[w][4]; nv += sh.red[w][5]; rq += sh.red[w][6];
             }
             sw += sumA;
             tu += turnA;
@@ -1063,7 +1108,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             dg[PRISM_DIAG_STAT] = rs;
             dg[PRISM_DIAG_COMP] = r_comp;
             dg[PRISM_DIAG_OBJ] = quad + ol;
-            dg[PRISM_DIAG_ITERS] = dg[PRISM_DIAG_ITERS] + 1.0;
+            dg[PRISM_DIAG_ERR_EST] = err_bound(P, sh, sqrt(rq), sw, tu, tau, nu, theta);
             P.nu[a] = nu;
             P.theta[a] = theta;
             for (int s2 = 0; s2 < S; ++s2) P.lam[a * S + s2] = sh.lam_s[s2];
@@ -1131,6 +1176,7 @@ __global__ void __launch_bounds__(PB) k_diag_only(PolDev P) {
         dg[PRISM_DIAG_STAT] = INFINITY;
         dg[PRISM_DIAG_COMP] = INFINITY;
         dg[PRISM_DIAG_OBJ] = quad + s2;
+        dg[PRISM_DIAG_ERR_EST] = INFINITY;
     }
 }
 

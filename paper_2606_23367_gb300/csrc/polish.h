@@ -68,6 +68,7 @@ struct PolDev {
     double* theta = nullptr;            // M
     double* diag = nullptr;             // M x PRISM_NDIAG
     int* status = nullptr;              // M
+    double dmin = 0.0;                  // smallest d_i of the universe: 2 Sigma >= 2 dmin I
     double tol_dual = 1e-11;
     double tol_primal = 1e-12;
 };

@@ -692,6 +692,12 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.B16 = U.d_B16; D.Bt16 = U.d_Bt16; D.B16p = U.d_B16p; D.Bt16p = U.d_Bt16p;
     D.err = D.n_active + 1;
     if (!std::getenv("PRISM_DEBUG_STATS")) D.stats = nullptr;   // counters only when asked for
+    if (const char* sw = std::getenv("PRISM_TEST_STALLED_WAIT_NS")) {
+        // failure-path test: a bounded tensor-core wait on a barrier nothing completes (at most
+        // 0.1 s, so that the test ends quickly and a stray setting cannot stall a real run long)
+        const long long ns = std::atoll(sw);
+        D.stall_ns = (unsigned long long)std::max(0LL, std::min(ns, 100000000LL));
+    }
     if (!o->profile) D.pcount = nullptr;
     D.bf16 = batched_mode_bf16;
     D.Cinv = batched_mode_bf16 ? U.d_Cinv16 : U.d_Cinv32;
@@ -718,6 +724,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     P.FMAX = FMAX;
     P.status = D.status;
     P.tol_dual = 1e-11; P.tol_primal = 1e-12;
+    P.dmin = U.dmin;
     // ---- control init
     {
         int j0 = (int)std::lround(RHO_PER_DECADE * std::log10(std::max(o->rho0, 1e-12) / RHO_MIN));

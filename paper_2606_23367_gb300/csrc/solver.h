@@ -86,6 +86,10 @@ struct Dev {
     unsigned long long* pcount = nullptr;   // profile mode: [0] candidates, [1] entries of the fused pass
     float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
+    // failure-path test only (environment PRISM_TEST_STALLED_WAIT_NS): the tensor-core G2 issues
+    // no loads and its first bounded wait, on a barrier nothing completes, runs out after this
+    // many ns; 0 in every normal call
+    unsigned long long stall_ns = 0;
 };
 
 // launchers (admm.cu)

@@ -80,12 +80,13 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
     return ok != 0;
 }
 
-// Wait for the phase of parity `parity` to complete, for at most WAIT_LIMIT_NS.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code) {
+// Wait for the phase of parity `parity` to complete, for at most `limit` ns (WAIT_LIMIT_NS).
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, int* err, int code,
+                                          uint64_t limit = WAIT_LIMIT_NS) {
     if (mbar_try_wait(bar, parity)) return true;
     const uint64_t t0 = gtimer();
     while (!mbar_try_wait(bar, parity)) {
-        if (gtimer() - t0 > WAIT_LIMIT_NS) {
+        if (gtimer() - t0 > limit) {
             atomicOr(err, code);
             return false;
         }
@@ -246,13 +247,16 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
             tma_load_2d(s.b[q], &mBt, &s.full[q], i0 + kt * TK, 0);
         };
         int issued = 0;
-        for (; issued < G2_STAGES && issued < nk; ++issued) load(issued);
+        // D.stall_ns (set only by the failure-path test): no load is issued, so the first wait
+        // is on a barrier that nothing completes and runs out after stall_ns
+        if (!D.stall_ns)
+            for (; issued < G2_STAGES && issued < nk; ++issued) load(issued);
         bool ok = true;
         int consumed = 0;
         for (int kt = 0; kt < nk && ok; ++kt) {
             const int q = kt % G2_STAGES;
             const uint32_t par = (kt / G2_STAGES) & 1;
-            if (!mbar_wait(&s.full[q], par, D.err, 1)) { ok = false; break; }
+            if (!mbar_wait(&s.full[q], par, D.err, 1, D.stall_ns ? D.stall_ns : WAIT_LIMIT_NS)) { ok = false; break; }
             consumed = kt + 1;
             fence_after_sync();
             const uint64_t dhi = sw128_desc(s.ahi[q]), dlo = sw128_desc(s.alo[q]), db = sw128_desc(s.b[q]);

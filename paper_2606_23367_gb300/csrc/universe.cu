@@ -217,6 +217,7 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     }
     U.device = desc->device;
     U.N = N; U.K = K; U.S = S;
+    U.dmin = *std::min_element(d.begin(), d.end());
     U.Npad = (N + 63) / 64 * 64;
     const int Npad = U.Npad;
     // stable sort of assets by sector

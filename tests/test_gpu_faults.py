@@ -90,3 +90,47 @@ def test_capacity_at_the_threshold_is_decided_exactly(excess):
     else:
         assert res["status"][1] != prism.PRISM_NO_FEASIBLE_RETURN
     assert res["status"][0] == prism.PRISM_CERTIFIED
+
+
+def test_time_budget_gives_timeout():
+    # a wall-clock budget that runs out during the first graph chunk: the call returns at the
+    # chunk's end, the accounts still iterating get TIMEOUT (unless the one polish round already
+    # certifies them), and no account ran past that chunk
+    uni, batch = make_workload(1, N=600, K=16, M=6)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, time_budget_s=1e-9, check_every=1,
+                    stream_after=1, polish_rounds=1)
+    st = res["status"]
+    assert set(st.tolist()) <= {prism.PRISM_TIMEOUT, prism.PRISM_CERTIFIED}, st
+    assert (st == prism.PRISM_TIMEOUT).any(), st
+    assert int(res["iters"].max()) <= 2
+
+
+@pytest.mark.parametrize("mode", [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16])
+def test_fp32_overflow_gives_numerical_failure(mode):
+    # mu_7 = 1e39 is finite in FP64 (accepted at the boundary) but overflows the FP32 iterates:
+    # every account meets Inf/NaN in its iterations and returns NUMERICAL_FAILURE, the call
+    # itself succeeds, and the context stays usable for the next solve
+    uni, batch = make_workload(1, N=600, K=16, M=3)
+    mu = uni.mu.copy()
+    mu[7] = 1e39
+    bad = dataclasses.replace(uni, mu=mu)
+    res = gpu_solve(bad, batch, precision=mode, max_iter=200)
+    assert np.all(res["status"] == prism.PRISM_NUMERICAL_FAILURE), res["status"]
+    ok = gpu_solve(uni, batch, precision=mode)
+    assert np.all(ok["status"] == prism.PRISM_CERTIFIED), ok["status"]
+
+
+def test_bounded_tensor_core_wait_runs_out_and_reports(monkeypatch):
+    # the library's failure-path hook makes the tensor-core G2 wait on a barrier that nothing
+    # completes (no load is issued, so nothing is in flight); the wait gives up after 1 ms, the
+    # kernel sets its error flag and returns, and the call reports PRISM_ERR_CUDA; the next call,
+    # without the hook, solves normally on the same context
+    uni, batch = make_workload(1, N=600, K=16, M=3)
+    monkeypatch.setenv("PRISM_TEST_STALLED_WAIT_NS", "1000000")
+    with pytest.raises(prism.PrismError) as ei:
+        gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
+    assert ei.value.code == prism.PRISM_ERR_CUDA
+    assert "timed out" in str(ei.value)
+    monkeypatch.delenv("PRISM_TEST_STALLED_WAIT_NS")
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
+    assert np.all(res["status"] == prism.PRISM_CERTIFIED), res["status"]

@@ -11,7 +11,8 @@ import pytest
 
 from paper_2606_23367_gb300 import build, prism
 from paper_2606_23367_gb300.workloads import make_workload
-from tests.parity_util import assert_parity, gpu_solve
+from tests.oracle_pool import compare_all
+from tests.parity_util import assert_parity, check_account, gpu_solve
 
 pytestmark = pytest.mark.gpu
 
@@ -74,24 +75,29 @@ def test_batch_order_does_not_change_results():
         assert np.max(np.abs(w1 - w2)) <= 1e-12
 
 
-FULL_SAMPLES = {1: [0, 250, 499], 2: [0, 128, 255], 3: [0, 100, 199], 4: [0, 64, 127]}
+FULL_WORKLOADS = (1, 2, 3, 4)
 
 
-@pytest.mark.parametrize("workload", sorted(FULL_SAMPLES))
-def test_full_size_workloads_sampled_against_the_oracle(workload):
+@pytest.mark.parametrize("workload", FULL_WORKLOADS)
+def test_full_size_workloads_every_account_against_the_oracle(workload):
     # each workload at its full size, in the launch configuration the benchmark times (batched
-    # BF16, default schedule); the oracle checks three accounts one by one, and the library's own
-    # FP64 certification must hold for every account
+    # BF16, default schedule); the FP64 oracle solves every account in a host process pool and
+    # each is held to the parity bar: weights, objective, the oracle checker's residuals of the
+    # library's weights and multipliers, and the library's stated error bound
     uni, batch = make_workload(workload)
     res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
-    assert np.all(res["status"] == prism.PRISM_CERTIFIED), np.bincount(res["status"])
-    diag = res["diag"]
-    assert float(diag[:, prism.PRISM_DIAG_BUDGET].max()) <= 1e-6
-    assert float(diag[:, prism.PRISM_DIAG_BOX].max()) <= 1e-6
-    assert float(diag[:, prism.PRISM_DIAG_EXPOSURE].max()) <= 1e-6
-    assert float(diag[:, prism.PRISM_DIAG_TURNOVER].max()) <= 1e-6
-    assert float(diag[:, prism.PRISM_DIAG_STAT].max()) <= 1e-6
-    assert_parity(uni, batch, res, accounts=FULL_SAMPLES[workload])
+    st = res["status"]
+    for s in (prism.PRISM_DIAG_BUDGET, prism.PRISM_DIAG_BOX, prism.PRISM_DIAG_EXPOSURE,
+              prism.PRISM_DIAG_TURNOVER, prism.PRISM_DIAG_STAT):
+        assert float(res["diag"][:, s].max()) <= 1e-6, s
+    rows = compare_all(workload, res)
+    assert len(rows) == batch.n_accounts
+    for e in rows:
+        e["status"] = int(st[e["account"]])
+        check_account(e, e["account"])
+    worst = max(e["w_err"] for e in rows)
+    print(f"workload {workload}: {len(rows)} accounts, max |w - w*| {worst:.2e}, "
+          f"max stated bound {max(e['bound'] for e in rows):.2e}")
 
 
 def _varied_costs_and_floors(batch, seed=7):
