@@ -60,6 +60,10 @@ extern "C" {
 #define PRISM_BATCHED_FP32  1  /* all accounts batched, FP32 B, SIMT products */
 #define PRISM_BATCHED_BF16  2  /* all accounts batched, tcgen05 BF16 products (split hi+lo
                                   operands), FP32 accumulate */
+#define PRISM_PLAIN_FP64    3  /* one account per launch sequence, FP64 iterations: all of an
+                                  account's ADMM iterations in one FP64 launch (capacitance
+                                  formed and factored in FP64 per penalty); the time budget is
+                                  checked between accounts */
 
 /* ---- universe ----------------------------------------------------------- */
 /* Universe-level data shared by every account (Eq. 1 risk model, Sec. 4.2
@@ -119,7 +123,7 @@ typedef struct {
     int32_t check_every;      /* iterations per captured graph launch (default 20) */
     int32_t min_iter;         /* iterations before a convergence test may stop an account */
     int32_t polish_rounds;    /* active-set correction rounds per polish (default 8) */
-    int32_t precision;        /* PRISM_PLAIN_FP32 | PRISM_BATCHED_FP32 | PRISM_BATCHED_BF16 */
+    int32_t precision;        /* PRISM_PLAIN_FP32 | PRISM_BATCHED_FP32 | PRISM_BATCHED_BF16 | PRISM_PLAIN_FP64 */
     int32_t use_graph;        /* capture the iteration loop in a CUDA graph (default 1) */
     int32_t keep_for_backward;/* 1: *res->state receives the polished active set for
                                  prism_solve_batch_backward (batched modes only) */

@@ -21,6 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
+#include "plain64.h"
 #include "polish.h"
 #include "solver.h"
 
@@ -393,7 +394,7 @@ static double ms_between(cudaEvent_t a, cudaEvent_t b) {
 // one batched solve (all accounts share the launch sequence)
 // ---------------------------------------------------------------------------
 static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solve_opts* o,
-                      prism_result* res, bool batched_mode_bf16, bool plain) {
+                      prism_result* res, bool batched_mode_bf16, bool plain, bool fp64 = false) {
     Universe& U = uh->u;
     SolveCache& SC = cache_of(uh);
     const auto t_call0 = std::chrono::steady_clock::now();
@@ -461,6 +462,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk) : choose_nsplit(M, N);
     const int FMAX = std::min(N, 2048);
     int* dsel = nullptr;               // device copy of SC.hsel (polish batches)
+    P64Args P64;                       // PLAIN_FP64: the FP64 iteration kernel's arguments
     auto layout = [&](Arena& A, Dev& D, PolDev& P, BatchDev& BD, void** stage, int** member, int** err,
                       int** pwidx_dev, double** ragged_out) {
         BD.w0 = A.take<double>(MN); BD.lo = A.take<double>(MN); BD.up = A.take<double>(MN); BD.c = A.take<double>(MN);
@@ -513,6 +515,10 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         BD.pw_slf = A.take<float>((size_t)std::max(n_pw, 1) * (MAXBP - 1));
         BD.pw_nbp = A.take<int>((size_t)std::max(n_pw, 1));
         stage[6] = A.take<double>((size_t)std::max(n_pw, 1));   // phi_lo
+        // FP64 iteration state of PLAIN_FP64 (z, y, X/v per entry; penalty and cap multiplier)
+        const size_t n64 = fp64 ? MN : 0;
+        P64.z = A.take<double>(n64); P64.y = A.take<double>(n64); P64.X = A.take<double>(n64);
+        P64.rho_state = A.take<double>(fp64 ? M : 0); P64.theta_state = A.take<double>(fp64 ? M : 0);
     };
     Dev D;
     std::memset((void*)&D, 0, sizeof(Dev));   // padding bytes take part in the graph-reuse test
@@ -565,7 +571,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         Arena A;
         A.base = SC.arena; A.cap = SC.arena_bytes;
         std::memset((void*)&D, 0, sizeof(Dev));
-        P = PolDev(); BD = BatchDev();
+        P = PolDev(); BD = BatchDev(); P64 = P64Args();
         layout(A, D, P, BD, stage, &member, &err, &pwidx, &ragged_out);
         if (A.alloc_fail) { set_error("workspace layout overflow"); return PRISM_ERR_ALLOCATION; }
     }
@@ -725,6 +731,18 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     P.status = D.status;
     P.tol_dual = 1e-11; P.tol_primal = 1e-12;
     P.dmin = U.dmin;
+    if (fp64) {
+        P64.M = M; P64.N = N; P64.Npad = Npad; P64.K = K; P64.S = S;
+        P64.B = U.d_B64; P64.f = U.d_f64; P64.d = U.d_d64; P64.mu = U.d_mu64;
+        P64.sec_start = U.d_sec_start; P64.sector = U.d_sector;
+        P64.w0 = BD.w0; P64.lo = BD.lo; P64.up = BD.up; P64.c = BD.c;
+        P64.pw_idx = pwidx; P64.pw_bp = BD.pw_bp; P64.pw_sl = BD.pw_sl; P64.pw_nbp = BD.pw_nbp;
+        P64.band_lo = BD.band_lo; P64.band_hi = BD.band_hi; P64.tau = BD.tau; P64.skip = P.skip;
+        P64.zf = D.z; P64.nu_f = D.nu; P64.eta_hi_f = D.eta_hi; P64.eta_lo_f = D.eta_lo; P64.theta_f = D.theta;
+        P64.iters = D.iters; P64.active = D.active; P64.status = D.status;
+        P64.alpha = o->alpha; P64.eps = o->eps_admm; P64.rho0 = o->rho0;
+        P64.max_iter = o->max_iter; P64.min_iter = o->min_iter; P64.adapt_every = 25;
+    }
     // ---- control init
     {
         int j0 = (int)std::lround(RHO_PER_DECADE * std::log10(std::max(o->rho0, 1e-12) / RHO_MIN));
@@ -908,7 +926,12 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     };
     // the first iterations run the staged prox: the streaming form needs the budget multiplier
     // to have settled (its moves set the streaming form's margin) to keep its candidate lists short
-    const int cold = D.stream_prox ? std::min(std::max(0, o->stream_after), o->max_iter) : 0;
+    const int cold = (D.stream_prox && !fp64) ? std::min(std::max(0, o->stream_after), o->max_iter) : 0;
+    if (fp64) {
+        // PLAIN_FP64: every iteration of the account in one FP64 launch (plain64.cu)
+        P64.resume = 0;
+        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_admm64(P64, st); });
+    }
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
         SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
@@ -916,7 +939,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st, true); });
     }
     std::memset(SC.hsel, 0, (size_t)M * 4);
-    int total_iters = admm_loop(o->max_iter + check_every - cold, true);
+    int total_iters = fp64 ? 0 : admm_loop(o->max_iter + check_every - cold, true);
     if (total_iters >= 0) total_iters += cold;
     if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
@@ -977,11 +1000,21 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         PRISM_CUDA_TRY(cudaMemcpyAsync(D.status, status.data(), M * 4, cudaMemcpyHostToDevice, st));
         PRISM_CUDA_TRY(cudaMemcpyAsync(P.done, done.data(), M * 4, cudaMemcpyHostToDevice, st));
         PRISM_CUDA_TRY(cudaStreamSynchronize(st));
-        Dev saved = D;
-        D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);
-        D.max_iter = saved.max_iter * (retry + 2);
-        int more = admm_loop(D.max_iter, false);
-        D = saved;
+        int more = 0;
+        if (fp64) {
+            // continue the FP64 iterations of the accounts sent back, to a tighter target
+            P64Args R = P64;
+            R.resume = 1;
+            R.eps = P64.eps * (retry == 0 ? 0.1 : 0.01);
+            R.max_iter = P64.max_iter * (retry + 2);
+            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_admm64(R, st); });
+        } else {
+            Dev saved = D;
+            D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);
+            D.max_iter = saved.max_iter * (retry + 2);
+            more = admm_loop(D.max_iter, false);
+            D = saved;
+        }
         if (more == -2) { set_error("tensor-core pipeline wait timed out"); return PRISM_ERR_CUDA; }
         if (more < 0) { set_error("ADMM retry failed"); return PRISM_ERR_CUDA; }
         total_iters += more;
@@ -1089,7 +1122,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         return PRISM_ERR_ARGUMENT;
     }
     if (o.keep_for_backward && !res->state) { set_error("keep_for_backward needs res->state"); return PRISM_ERR_ARGUMENT; }
-    if (o.keep_for_backward && o.precision == PRISM_PLAIN_FP32) {
+    if (o.keep_for_backward && (o.precision == PRISM_PLAIN_FP32 || o.precision == PRISM_PLAIN_FP64)) {
         set_error("keep_for_backward is available in the batched modes");
         return PRISM_ERR_UNSUPPORTED;
     }
@@ -1103,8 +1136,12 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         }
         return solve_core(uh, b, &o, res, true, false);
     }
-    if (o.precision != PRISM_PLAIN_FP32) { set_error("unknown precision mode"); return PRISM_ERR_ARGUMENT; }
-    // PLAIN_FP32: one account per launch sequence (the single-account form)
+    if (o.precision != PRISM_PLAIN_FP32 && o.precision != PRISM_PLAIN_FP64) {
+        set_error("unknown precision mode");
+        return PRISM_ERR_ARGUMENT;
+    }
+    const bool fp64 = o.precision == PRISM_PLAIN_FP64;
+    // PLAIN_FP32 / PLAIN_FP64: one account per launch sequence (the single-account form)
     std::vector<int64_t> offs;
     if (int rc = to_host(b->offsets, (size_t)b->n_accounts + 1, offs)) return rc;
     const int S = uh->u.S;
@@ -1138,7 +1175,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         r1.lambda_band = res->lambda_band ? res->lambda_band + (size_t)a * S : nullptr;
         r1.theta = res->theta ? res->theta + a : nullptr;
         r1.diag = res->diag ? res->diag + (size_t)a * PRISM_NDIAG : nullptr;
-        int rc = solve_core(uh, &sb, &o, &r1, false, true);
+        int rc = solve_core(uh, &sb, &o, &r1, false, true, fp64);
         if (rc != PRISM_OK) return rc;
         tdev += r1.t_device_ms;
         for (int q = 0; q < 4; ++q) tph[q] += r1.t_phase_ms[q];

@@ -19,7 +19,7 @@ PRISM_OK = 0
 PRISM_ERR_ARGUMENT, PRISM_ERR_CUDA, PRISM_ERR_ALLOCATION, PRISM_ERR_UNSUPPORTED = -1, -2, -3, -4
 PRISM_CERTIFIED, PRISM_FEASIBLE_NONCERTIFIED, PRISM_TIMEOUT, PRISM_DEADLINE_EXCEEDED = 0, 1, 2, 3
 PRISM_NO_FEASIBLE_RETURN, PRISM_ALLOCATION_FAILURE, PRISM_NUMERICAL_FAILURE = 4, 5, 6
-PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16 = 0, 1, 2
+PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16, PRISM_PLAIN_FP64 = 0, 1, 2, 3
 PRISM_NDIAG = 8
 (PRISM_DIAG_BUDGET, PRISM_DIAG_BOX, PRISM_DIAG_EXPOSURE, PRISM_DIAG_TURNOVER, PRISM_DIAG_STAT, PRISM_DIAG_COMP,
  PRISM_DIAG_OBJ, PRISM_DIAG_ERR_EST) = range(8)

@@ -23,7 +23,7 @@ def _lib():
     prism.load_library()
 
 
-MODES = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16, prism.PRISM_PLAIN_FP32]
+MODES = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16, prism.PRISM_PLAIN_FP32, prism.PRISM_PLAIN_FP64]
 BATCHED = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16]
 
 
@@ -31,6 +31,15 @@ BATCHED = [prism.PRISM_BATCHED_FP32, prism.PRISM_BATCHED_BF16]
 def test_single_account_n100(mode):
     uni, batch = make_workload(0)
     res = gpu_solve(uni, batch, precision=mode)
+    assert_parity(uni, batch, res)
+
+
+@pytest.mark.parametrize("workload,kw", [(1, dict(N=700, K=32, M=2)), (2, dict(N=900, M=3)),
+                                         (3, dict(N=400, K=12, M=2))])
+def test_plain_fp64_small_books(workload, kw):
+    # the FP64 iterations on a shared-universe book, ragged accounts, and tax lots with a cap
+    uni, batch = make_workload(workload, **kw)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_PLAIN_FP64)
     assert_parity(uni, batch, res)
 
 
