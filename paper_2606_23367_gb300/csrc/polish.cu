@@ -1192,7 +1192,8 @@ __global__ void k_finish_status(PolDev P, double eps) {
     const int prior = P.status[a];
     bool finite = true;
     for (int q = 0; q < PRISM_NDIAG; ++q)
-        if (q != PRISM_DIAG_STAT && q != PRISM_DIAG_COMP && !isfinite(dg[q])) finite = false;
+        if (q != PRISM_DIAG_STAT && q != PRISM_DIAG_COMP && q != PRISM_DIAG_ERR_EST && !isfinite(dg[q]))
+            finite = false;
     int st;
     if (prior == PRISM_NUMERICAL_FAILURE || !finite) st = PRISM_NUMERICAL_FAILURE;
     else if (P.done[a] == 1 && prim <= eps && kkt) st = PRISM_CERTIFIED;

@@ -51,11 +51,12 @@ def test_noalloc_matches_solve_batch_twice(workload, kw):
 
 
 def _perturbed_start(batch, w, seed):
-    """w moved off the optimum: every weight strictly inside its box gets a relative change of
-    up to 1e-3, the result clipped to the box. Sector sums, the budget and the turnover move,
-    so bands and a cap held at an edge may no longer be recognised from the start point."""
+    """w moved off the optimum: every weight strictly inside a linear piece of its cost (not on
+    a bound, not at its current holding) gets a relative change of up to 1e-3, the result
+    clipped to the box. Sector sums, the budget and the turnover move, so bands and a cap held
+    at an edge are no longer recognised from the start point and the polish has to find them."""
     r = np.random.default_rng(seed)
-    inside = (w > batch.lower + 1e-12) & (w < batch.upper - 1e-12)
+    inside = (w > batch.lower + 1e-12) & (w < batch.upper - 1e-12) & (np.abs(w - batch.w0) > 1e-12)
     w2 = w * (1.0 + 1e-3 * r.uniform(-1.0, 1.0, size=w.shape) * inside)
     return np.clip(w2, batch.lower, batch.upper)
 
@@ -86,7 +87,7 @@ def test_noalloc_from_a_perturbed_start_against_the_oracle(workload, kw, on_devi
                                       asset_idx=dev(batch.asset_idx))
             w_in = dev(w_in)
         for _ in range(2):
-            got = _noalloc(h, src, w_in)
+            got = _noalloc(h, src, w_in, polish_rounds=16)
             got = {k: (v.cpu().numpy() if hasattr(v, "cpu") else v) for k, v in got.items()}
             for a in range(batch.n_accounts):
                 check_account(compare_account(uni, batch, got, a), a)
