@@ -110,6 +110,17 @@ typedef struct {
     const int64_t* lot_offsets;     /* ragged+1 lot ranges per entry, or NULL = no lots */
     const double* lot_size;         /* lot sizes (weight units), sum per entry == w0 */
     const double* lot_kappa;        /* marginal tax per unit sold (negative = harvest) */
+    /* Further families of Eq. 1 (Sec. 4.2); each NULL = absent. */
+    const double* mu_tilt;          /* ragged per-account tilt t of the return input: the linear
+                                       term is (mu + t)'w for that account */
+    const double* w_bench;          /* ragged benchmark weights w_b: the risk term is
+                                       (w - w_b)' Sigma (w - w_b), i.e. a tilt of 2 Sigma w_b
+                                       (the objective in diag column 6 omits the constant
+                                       w_b' Sigma w_b) */
+    const double* factor_lo;        /* M x K lower bounds on the factor exposures B'w (the
+                                       general rows a_lo <= A w <= a_hi of Eq. 1 with A = B' of
+                                       the account's names; -inf = none) */
+    const double* factor_hi;        /* M x K upper bounds (+inf = none); NULL both = no bounds */
 } prism_batch;
 
 /* ---- options -------------------------------------------------------------- */
@@ -196,6 +207,8 @@ typedef struct {
     int64_t  stream_entries;     /* profile mode: account-entries the fused streaming pass evaluated */
     int64_t  stream_candidates;  /* profile mode: of those, entries not pinned at their lower bound */
     prism_state** state;    /* receives the state for the backward pass, if requested */
+    double*  kappa;         /* M x K multipliers of the factor-exposure bounds (>= 0 at the
+                               upper bound, <= 0 at the lower), or NULL */
 } prism_result;
 
 /* Solve every account of *batch against universe u. All accounts' inputs are

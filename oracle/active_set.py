@@ -438,14 +438,30 @@ class AccountProblem:
 
 
 def account_problem(uni, batch, a) -> AccountProblem:
-    """AccountProblem for account ``a`` of a (Universe, Batch) pair."""
+    """AccountProblem for account ``a`` of a (Universe, Batch) pair. The batch's optional
+    families become the general rows of Eq. 1 (factor-exposure bounds: A = the rows of B'
+    with a finite bound), the tilt and the benchmark."""
     idx = batch.account_assets(a, uni.n_assets)
     sl = batch.account_slice(a)
     lots = batch.account_lots(a) if batch.lot_offsets is not None else None
-    return AccountProblem(uni.B[idx], uni.f, uni.d[idx], uni.mu[idx], uni.sector[idx],
+    B = uni.B[idx]
+    rows = rows_lo = rows_hi = None
+    flo, fhi = getattr(batch, "factor_lo", None), getattr(batch, "factor_hi", None)
+    if flo is not None or fhi is not None:
+        K = B.shape[1]
+        lo = np.full(K, -np.inf) if flo is None else np.asarray(flo[a], np.float64)
+        hi = np.full(K, np.inf) if fhi is None else np.asarray(fhi[a], np.float64)
+        J = np.flatnonzero(np.isfinite(lo) | np.isfinite(hi))
+        if J.size:
+            rows, rows_lo, rows_hi = B[:, J].T, lo[J], hi[J]
+    tilt = getattr(batch, "mu_tilt", None)
+    bench = getattr(batch, "w_bench", None)
+    return AccountProblem(B, uni.f, uni.d[idx], uni.mu[idx], uni.sector[idx],
                           uni.n_sectors, batch.w0[sl], batch.lower[sl], batch.upper[sl],
                           batch.tc[sl], batch.band_lo[a], batch.band_hi[a],
-                          batch.turnover_cap[a], lots)
+                          batch.turnover_cap[a], lots, rows=rows, rows_lo=rows_lo, rows_hi=rows_hi,
+                          mu_tilt=None if tilt is None else tilt[sl],
+                          w_bench=None if bench is None else bench[sl])
 
 
 def solve_account(uni, batch, a, **kw) -> OracleResult:

@@ -173,6 +173,26 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
         sP[t] = 0.f;                       // factors beyond K (their column entries are zero too)
     }
     __syncthreads();
+    // Factor-exposure block (s = B'x, dual ys): the x-update's right side gains B (rho s - ys), so
+    // with tv = rho s - ys the reduced right side is P0 + G tv and Q' = C^{-1} (P0 + G tv) - tv
+    // (then x = X - Delta^{-1} B Q' as without the block, and B'x = P0 - G Q').
+    __shared__ float sT[KMAX], sP0[KMAX], sQ[KMAX];
+    const bool fac = D.s != nullptr;
+    const float* Gj = fac ? D.G + (size_t)D.rho_idx[m] * K * K : nullptr;
+    float rho = 0.f, s_old = 0.f, ys_old = 0.f;
+    if (fac) {
+        rho = rho_val(D.rho_idx[m]);
+        if (t < K) { s_old = D.s[(size_t)m * K + t]; ys_old = D.ys[(size_t)m * K + t]; }
+        sT[t] = t < K ? rho * s_old - ys_old : 0.f;
+        sP0[t] = sP[t];
+        __syncthreads();
+        float g = 0.f;
+        if (t < K)
+            for (int j = 0; j < K; ++j) g = fmaf(Gj[(size_t)j * K + t], sT[j], g);   // G symmetric: column t
+        __syncthreads();
+        sP[t] = sP0[t] + g;
+        __syncthreads();
+    }
     if (t < K) {
         float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
 #pragma unroll
@@ -182,13 +202,42 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
             q2 = fmaf(c[j + 2], sP[j + 2], q2);
             q3 = fmaf(c[j + 3], sP[j + 3], q3);
         }
-        const float q = (q0 + q1) + (q2 + q3);
+        float q = (q0 + q1) + (q2 + q3);
+        if (fac) q -= sT[t];
         if (D.bf16) {
             __nv_bfloat16 h = __float2bfloat16_rn(q);
             D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
             D.Qlo[(size_t)m * KMAX + t] = __float2bfloat16_rn(q - __bfloat162float(h));
         }
         D.Q[(size_t)m * K + t] = q;
+        if (fac) sQ[t] = q;
+    }
+    if (fac) {
+        // the block's own update: relaxed B'x, s = clip(., lo, hi), dual step, residuals
+        __syncthreads();
+        float rp = 0.f, rd = 0.f;
+        if (t < K) {
+            float g = 0.f;
+            for (int j = 0; j < K; ++j) g = fmaf(Gj[(size_t)j * K + t], sQ[j], g);
+            const float bx = sP0[t] - g;
+            const float xh = D.alpha * bx + (1.f - D.alpha) * s_old;
+            const float lo = D.flo[(size_t)m * K + t], hi = D.fhi[(size_t)m * K + t];
+            const float sn = fminf(fmaxf(xh + ys_old / rho, lo), hi);
+            D.s[(size_t)m * K + t] = sn;
+            D.ys[(size_t)m * K + t] = ys_old + rho * (xh - sn);
+            D.sflag[(size_t)m * K + t] = (sn >= hi) ? 1 : ((sn <= lo) ? -1 : 0);
+            rp = fabsf(xh - sn);
+            rd = rho * fabsf(sn - s_old);
+            if (!(isfinite(rp) && isfinite(rd))) rp = rd = INFINITY;
+        }
+        rp = warp_max(rp);
+        rd = warp_max(rd);
+        if ((t & 31) == 0) { sT[t >> 5] = rp; sP0[t >> 5] = rd; }
+        __syncthreads();
+        if (t == 0) {
+            D.rps[m] = fmaxf(sT[0], sT[1]);
+            D.rds[m] = fmaxf(sP0[0], sP0[1]);
+        }
     }
 }
 
@@ -617,7 +666,8 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
         if (bad) {
             D.status[a] = PRISM_NUMERICAL_FAILURE;
             D.active[a] = 0;
-        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
+        } else if (it >= D.min_iter && fmaxf(rp, D.rps ? D.rps[a] : 0.f) <= D.eps_admm &&
+                   fmaxf(rd, D.rds ? D.rds[a] : 0.f) <= D.eps_admm) {
             D.active[a] = 0;
         } else if (it >= D.max_iter) {
             D.active[a] = 0;
@@ -1104,7 +1154,8 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
         if (bad) {
             D.status[a] = PRISM_NUMERICAL_FAILURE;
             D.active[a] = 0;
-        } else if (it >= D.min_iter && rp <= D.eps_admm && rd <= D.eps_admm) {
+        } else if (it >= D.min_iter && fmaxf(rp, D.rps ? D.rps[a] : 0.f) <= D.eps_admm &&
+                   fmaxf(rd, D.rds ? D.rds[a] : 0.f) <= D.eps_admm) {
             D.active[a] = 0;
         } else if (it >= D.max_iter) {
             D.active[a] = 0;

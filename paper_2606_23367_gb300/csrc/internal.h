@@ -59,6 +59,13 @@ struct Universe {
     __nv_bfloat16* d_Bt16p = nullptr; // 64 x Npad
     float* d_Cinv32 = nullptr;     // NRHO x K x K, capacitance inverses for FP32 B
     float* d_Cinv16 = nullptr;     // NRHO x K x K, for the BF16-rounded B
+    // factor-exposure bounds (Eq. 1 rows B'w in [lo, hi]) split off as s = B'x with penalty rho:
+    // the x-update then has capacitance (2F + rho I)^{-1} + B' Delta^{-1} B, and needs the Gram
+    // matrices G_j = B' Delta_j^{-1} B themselves
+    float* d_G32 = nullptr;        // NRHO x K x K, G_j for FP32 B
+    float* d_G16 = nullptr;        // NRHO x K x K, G_j for the BF16-rounded B
+    float* d_CinvF32 = nullptr;    // NRHO x K x K, ((2F + rho_j I)^{-1} + G_j)^{-1}, FP32 B
+    float* d_CinvF16 = nullptr;    // the same for the BF16-rounded B
     double dmin = 0.0;             // smallest idiosyncratic variance d_i (strong convexity of the risk)
     size_t bytes = 0;
     cudaStream_t stream = nullptr;
@@ -90,6 +97,9 @@ struct BatchDev {
     float *band_lof = nullptr, *band_hif = nullptr;
     double* tau = nullptr;         // M
     float* tauf = nullptr;
+    bool has_fac = false;          // some factor exposure has a finite bound
+    double *flo = nullptr, *fhi = nullptr;    // M x K factor-exposure bounds (+-inf = none)
+    float *flof = nullptr, *fhif = nullptr;
     int* member = nullptr;         // M x Npad: 1 if the entry belongs to the account
 };
 

@@ -98,6 +98,8 @@ __global__ void k_na_pack(NaPack A) {
 
 // Working rows the given weights hold at an edge, written as the multiplier signals the
 // classification kernel reads (band held at hi: eta_hi > nu; at lo: eta_lo < nu; cap: theta > 0).
+// The given weights are a warm start, so a row within 1e-4 (relative) of its edge starts in the
+// working set; the polish drops a row whose multiplier comes out with the wrong sign.
 __global__ void k_na_rows(int M, int S, int Npad, const int* sec_start, const double* W0, const double* LO,
                           const float* Z, const double* band_lo, const double* band_hi, const double* tau,
                           float* nu_f, float* eta_hi_f, float* eta_lo_f, float* theta_f) {
@@ -118,9 +120,9 @@ __global__ void k_na_rows(int M, int S, int Npad, const int* sec_start, const do
         fl = warp_sum(fl);
         if (lane == 0) {
             const double hi = band_hi[a * S + s], lo = band_lo[a * S + s];
-            const double tol = 1e-6 * fmax(1.0, fabs(hi));
+            const double tol = 1e-4 * fmax(1.0, fabs(hi));
             eta_hi_f[a * S + s] = (isfinite(hi) && fabs(sw - hi) <= tol) ? 1.f : -FLT_MAX;
-            eta_lo_f[a * S + s] = (isfinite(lo) && lo > fl + 1e-12 && fabs(sw - lo) <= 1e-6 * fmax(1.0, fabs(lo)))
+            eta_lo_f[a * S + s] = (isfinite(lo) && lo > fl + 1e-12 && fabs(sw - lo) <= 1e-4 * fmax(1.0, fabs(lo)))
                                       ? -1.f : FLT_MAX;
         }
     }
@@ -131,7 +133,7 @@ __global__ void k_na_rows(int M, int S, int Npad, const int* sec_start, const do
         double t = 0.0;
         for (int w = 0; w < nw; ++w) t += turn_w[w];
         nu_f[a] = 0.f;
-        theta_f[a] = (isfinite(tau[a]) && fabs(t - tau[a]) <= 1e-6 * fmax(1.0, tau[a])) ? 1.f : 0.f;
+        theta_f[a] = (isfinite(tau[a]) && fabs(t - tau[a]) <= 1e-4 * fmax(1.0, tau[a])) ? 1.f : 0.f;
     }
 }
 
@@ -195,6 +197,9 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     if (!b->offsets || !b->w0 || !b->lower || !b->upper || !b->tc || !b->band_lo || !b->band_hi)
         return na_fail(PRISM_ERR_ARGUMENT, "required batch array is NULL");
     if (b->lot_offsets) return na_fail(PRISM_ERR_UNSUPPORTED, "prism_polish_noalloc does not take tax lots");
+    if (b->mu_tilt || b->w_bench || b->factor_lo || b->factor_hi)
+        return na_fail(PRISM_ERR_UNSUPPORTED,
+                       "prism_polish_noalloc does not take tilts, a benchmark or factor-exposure bounds");
     Universe& U = uh->u;
     const int M = b->n_accounts, N = U.N, Npad = U.Npad, K = U.K, S = U.S;
     if (M < 1 || M > NA_MAX_ACCOUNTS)
@@ -335,6 +340,7 @@ extern "C" int prism_polish_noalloc(prism_universe* uh, const prism_batch* b, co
     P.skip = skip; P.st = stt; P.wband = wband; P.wcap = wcap; P.done = done;
     P.Flist = Fl; P.NZlist = NZl; P.Fsig = Fsig; P.Y = Y; P.FMAX = FMAX;
     P.dmin = U.dmin;
+    P.kappa = nullptr;
     P.W = W; P.nu = nu; P.lam = lam; P.theta = theta; P.diag = diag; P.status = status;
     launch_classify(P, st);
     const int rounds = std::max(1, o.polish_rounds);

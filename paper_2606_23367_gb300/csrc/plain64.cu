@@ -32,7 +32,9 @@ constexpr int P64_ROOT_IT = 200;          // evaluations per scalar root (bisect
 
 struct P64Shared {
     double L[KMAX][KMAX + 1];             // Cholesky factor of C (lower)
+    double G[KMAX][KMAX + 1];             // B' Delta^{-1} B (factor-exposure block only)
     double P[KMAX], Q[KMAX];
+    double s[KMAX], ys[KMAX], tv[KMAX], P0[KMAX];   // factor-exposure block: s = B'x, its dual
     double part[P64_THREADS / 64 > 0 ? P64_THREADS / 64 : 1][KMAX];
     double ssum[SMAX];                    // sector sums at the current evaluation point
     double eta_s[SMAX];                   // per-sector multiplier point (nu + lambda_s)
@@ -189,8 +191,11 @@ __device__ double p64_turnover(const P64Args& A, P64Shared& sh, const double* v,
     return r;
 }
 
-// C = (2F)^{-1} + B' Delta^{-1} B and its Cholesky factor, in FP64 (block-collective).
+// C = (2F)^{-1} + B' Delta^{-1} B and its Cholesky factor, in FP64 (block-collective). With the
+// factor-exposure block (s = B'x split off with penalty rho) the diagonal term is (2F + rho I)^{-1}
+// and G = B' Delta^{-1} B is kept beside the factor.
 __device__ bool p64_factor(const P64Args& A, P64Shared& sh, double rho) {
+    const bool fac = A.flo != nullptr;
     const int tid = threadIdx.x, K = A.K;
     const int npair = K * (K + 1) / 2;
     for (int q = tid; q < npair; q += P64_THREADS) {
@@ -200,7 +205,8 @@ __device__ bool p64_factor(const P64Args& A, P64Shared& sh, double rho) {
         double acc = 0.0;
         for (int p = 0; p < A.N; ++p)
             acc += A.B[(size_t)p * K + r] * A.B[(size_t)p * K + c] / (2.0 * A.d[p] + rho);
-        if (r == c) acc += 1.0 / (2.0 * A.f[r]);
+        if (fac) { sh.G[r][c] = acc; sh.G[c][r] = acc; }
+        if (r == c) acc += fac ? 1.0 / (2.0 * A.f[r] + rho) : 1.0 / (2.0 * A.f[r]);
         sh.L[r][c] = acc;
     }
     __syncthreads();
@@ -240,6 +246,11 @@ __global__ void __launch_bounds__(P64_THREADS) k_admm64(P64Args A) {
     } else if (tid == 0) {
         sh.rho = A.rho_state[a]; sh.nu = 0.0; sh.theta = A.theta_state[a];
     }
+    const bool fac = A.flo != nullptr;
+    if (fac && !A.resume)
+        for (int k = tid; k < K; k += P64_THREADS) { sh.s[k] = 0.0; sh.ys[k] = 0.0; }
+    if (fac && A.resume)
+        for (int k = tid; k < K; k += P64_THREADS) { sh.s[k] = A.s_state[a * K + k]; sh.ys[k] = A.ys_state[a * K + k]; }
     __syncthreads();
     double rho = sh.rho;
     bool ok = p64_factor(A, sh, rho);
@@ -272,7 +283,18 @@ __global__ void __launch_bounds__(P64_THREADS) k_admm64(P64Args A) {
             }
             __syncthreads();
         }
-        // ---- Q = C^{-1} P (one thread: K^2 work)
+        // ---- Q = C^{-1} P (one thread: K^2 work). With the factor-exposure block the right side
+        // gains B tv, tv = rho s - ys: Q' = C^{-1} (P0 + G tv) - tv, and B'x = P0 - G Q'
+        if (fac) {
+            for (int k = tid; k < K; k += P64_THREADS) { sh.tv[k] = rho * sh.s[k] - sh.ys[k]; sh.P0[k] = sh.P[k]; }
+            __syncthreads();
+            for (int k = tid; k < K; k += P64_THREADS) {
+                double g = 0.0;
+                for (int j = 0; j < K; ++j) g += sh.G[k][j] * sh.tv[j];
+                sh.P[k] = sh.P0[k] + g;
+            }
+            __syncthreads();
+        }
         if (tid == 0) {
             for (int r = 0; r < K; ++r) {
                 double s = sh.P[r];
@@ -284,8 +306,26 @@ __global__ void __launch_bounds__(P64_THREADS) k_admm64(P64Args A) {
                 for (int q = r + 1; q < K; ++q) s -= sh.L[q][r] * sh.Q[q];
                 sh.Q[r] = s / sh.L[r][r];
             }
+            if (fac) for (int r = 0; r < K; ++r) sh.Q[r] -= sh.tv[r];
         }
         __syncthreads();
+        double rps = 0.0, rds = 0.0;
+        if (fac) {
+            // the block's update: relaxed B'x, s = clip(., lo, hi), the dual step, residuals
+            for (int k = tid; k < K; k += P64_THREADS) {
+                double g = 0.0;
+                for (int j = 0; j < K; ++j) g += sh.G[k][j] * sh.Q[j];
+                const double bx = sh.P0[k] - g;
+                const double xh = alpha * bx + (1.0 - alpha) * sh.s[k];
+                const double sn = fmin(fmax(xh + sh.ys[k] * irho, A.flo[a * K + k]), A.fhi[a * K + k]);
+                rps = fmax(rps, fabs(xh - sn));
+                rds = fmax(rds, rho * fabs(sn - sh.s[k]));
+                sh.ys[k] += rho * (xh - sn);
+                sh.tv[k] = sn;                    // staged: s is read by other threads above
+            }
+            __syncthreads();
+            for (int k = tid; k < K; k += P64_THREADS) sh.s[k] = sh.tv[k];
+        }
         // ---- x, the relaxation and v (v overwrites X); bracket of the projection's multipliers
         double ea = INFINITY, eb = -INFINITY;
         for (int p = tid; p < N; p += P64_THREADS) {
@@ -368,6 +408,8 @@ __global__ void __launch_bounds__(P64_THREADS) k_admm64(P64Args A) {
             z[e] = zn;
             y[e] = yn;
         }
+        rp = fmax(rp, rps);
+        rd = fmax(rd, rds);
         rp = warp_max(rp); rd = warp_max(rd); nx = warp_max(nx); nz = warp_max(nz); ny = warp_max(ny);
         bad = warp_sum(bad);
         if (lane == 0) {
@@ -415,6 +457,13 @@ __global__ void __launch_bounds__(P64_THREADS) k_admm64(P64Args A) {
         A.eta_hi_f[a * S + s] = es > nu ? float(es) : -FLT_MAX;
         A.eta_lo_f[a * S + s] = es < nu ? float(es) : FLT_MAX;
     }
+    if (fac)
+        for (int k = tid; k < K; k += P64_THREADS) {
+            const double lo = A.flo[a * K + k], hi = A.fhi[a * K + k], sk = sh.s[k];
+            A.sflag[a * K + k] = (sk >= hi) ? 1 : ((sk <= lo) ? -1 : 0);
+            A.s_state[a * K + k] = sk;
+            A.ys_state[a * K + k] = sh.ys[k];
+        }
     if (tid == 0) {
         A.nu_f[a] = float(sh.nu);
         A.theta_f[a] = float(theta);

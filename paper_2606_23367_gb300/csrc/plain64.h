@@ -22,10 +22,13 @@ struct P64Args {
     const int* pw_nbp = nullptr;
     const double *band_lo = nullptr, *band_hi = nullptr;   // M x S
     const double* tau = nullptr;        // M (+inf = no cap)
+    const double *flo = nullptr, *fhi = nullptr;   // M x K factor-exposure bounds, or null
+    int* sflag = nullptr;               // M x K: the iterations' factor rows at a bound (for the polish)
     const int* skip = nullptr;          // M: accounts the capacity test rejected
     // FP64 state (M x Npad), kept between calls of the same solve
     double *z = nullptr, *y = nullptr, *X = nullptr;
     double *rho_state = nullptr, *theta_state = nullptr;   // M
+    double *s_state = nullptr, *ys_state = nullptr;        // M x K (factor-exposure block)
     // what the polish reads
     float* zf = nullptr;                // M x Npad
     float *nu_f = nullptr, *eta_hi_f = nullptr, *eta_lo_f = nullptr, *theta_f = nullptr;

@@ -149,6 +149,8 @@ __global__ void __launch_bounds__(PB) k_classify(PolDev P) {
         P.wband[a * P.S + s] = wb;
     }
     if (threadIdx.x == 0) P.wcap[a] = (P.theta_f[a] > 0.f) ? 1 : 0;
+    if (P.wfac)
+        for (int k = threadIdx.x; k < P.K; k += PB) P.wfac[a * P.K + k] = P.sflag ? P.sflag[a * P.K + k] : 0;
 }
 
 // ---------------------------------------------------------------------------
@@ -199,9 +201,12 @@ struct PolishShared {
     float qg[PB / 32][64];
     double sumA[PB / 32], capA[PB / 32], turnA[PB / 32], objA[PB / 32];
     double lam_s[SMAX];
+    double kap_s[KMAX];                   // multipliers of the factor rows (0 off the working set)
     float lam_s32[SMAX];
     double blo_s[SMAX], bhi_s[SMAX];      // the account's band edges
     int wb_s[SMAX];                       // working bands (mirrors P.wband of the account)
+    int wf_s[KMAX];                       // working factor rows (mirrors P.wfac of the account)
+    double flo_s[KMAX], fhi_s[KMAX];      // the account's factor-exposure bounds
     double fixS[SMAX];                    // per sector: sum of the fixed weights
     int secF[FS];                         // sector of each of the first FS free entries                  // its FP32 copy (the filter of the checks)
     double red[PB / 32][8];
@@ -253,11 +258,16 @@ struct WarpQueue {
     }
 };
 
-// coefficient of free entry q in working row ``row`` (sector from shared memory when q < FS)
+__device__ __forceinline__ double brow64(const PolDev& P, const PolishShared& sh, const FreeSet& F, int q, int k);
+
+// coefficient of free entry q in working row ``row``: the budget (row -1), the band of sector
+// row (0 <= row < S), the cap (row S) or the exposure to factor row - S - 1 (sector from shared
+// memory when q < FS)
 __device__ __forceinline__ double coef_q(const PolDev& P, const PolishShared& sh, const FreeSet& F, int row, int q) {
     if (row < 0) return 1.0;
     if (row < P.S) return ((q < FS ? sh.secF[q] : P.sector[F.Fl[q]]) == row) ? 1.0 : 0.0;
-    return F.sig[q];
+    if (row == P.S) return F.sig[q];
+    return brow64(P, sh, F, q, row - P.S - 1);          // factor-exposure row k = row - S - 1
 }
 
 // sum over the free set of coef(row, q) * Y[q][col]: one warp, lanes over q, combined in a
@@ -466,6 +476,14 @@ __device__ double err_bound(const PolDev& P, const PolishShared& sh, double r2, 
         if (sqrt(as_comp / m) <= sqrt(double(P.N)) * fabs(ls) / m) C += as_comp;
         else wrong += fabs(ls);
     }
+    for (int k = 0; k < P.K && P.flo; ++k) {
+        // factor rows, read like the bands (kappa_k >= 0 prices the upper bound)
+        const double kk = sh.kap_s[k], hk = sh.t64[k];
+        if (kk == 0.0) continue;
+        const double edge = kk > 0.0 ? sh.fhi_s[k] : sh.flo_s[k];
+        // (a multiplier on an infinite bound has no such reading: C, and the bound, become +inf)
+        C += isfinite(edge) ? fabs(kk) * fabs(edge - hk) : INFINITY;
+    }
     if (theta != 0.0) {
         const double as_comp = (isfinite(tau) && theta > 0.0) ? theta * fabs(tau - tu) : INFINITY;
         if (sqrt(as_comp / m) <= sqrt(double(P.N)) * fabs(theta) / m) C += as_comp;
@@ -491,6 +509,11 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         sh.blo_s[s2] = P.band_lo[a * S + s2];
         sh.bhi_s[s2] = P.band_hi[a * S + s2];
         sh.wb_s[s2] = P.wband[a * S + s2];
+    }
+    for (int k = tid; k < K; k += PB) {
+        sh.wf_s[k] = P.wfac ? P.wfac[a * K + k] : 0;
+        sh.flo_s[k] = P.flo ? P.flo[a * K + k] : -INFINITY;
+        sh.fhi_s[k] = P.fhi ? P.fhi[a * K + k] : INFINITY;
     }
     __syncthreads();
     for (int round = 0; round < rounds; ++round) {
@@ -571,6 +594,8 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             for (int q = 0; q < S; ++q)
                 if (sh.wb_s[q] != 0) { if (r < PMAXROWS) sh.rows[r] = q; ++r; }
             if (P.wcap[a]) { if (r < PMAXROWS) sh.rows[r] = S; ++r; }
+            for (int k = 0; k < K; ++k)
+                if (sh.wf_s[k] != 0) { if (r < PMAXROWS) sh.rows[r] = S + 1 + k; ++r; }
             sh.nrows = r;
             sh.fail = (of > P.FMAX || on > P.FMAX || of == 0 || r > MAXWROWS);
         }
@@ -702,8 +727,11 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             } else if (row < S) {
                 const double edge = (sh.wb_s[row] > 0) ? sh.bhi_s[row] : sh.blo_s[row];
                 e_r = edge - sh.fixS[row];
-            } else {
+            } else if (row == S) {
                 e_r = P.tau[a] - capA;
+            } else {
+                const int k = row - S - 1;
+                e_r = ((sh.wf_s[k] > 0) ? sh.fhi_s[k] : sh.flo_s[k]) - sh.hA[k];
             }
             sh.erhs[r] = e_r;
             sh.lam[r] = 0.0;
@@ -822,16 +850,30 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
         });
         for (int k = K + tid; k < KMAX; k += PB) sh.fh32[k] = 0.f;
         for (int s2 = tid; s2 < S; s2 += PB) sh.lam_s[s2] = 0.0;
+        for (int k = tid; k < K; k += PB) sh.kap_s[k] = 0.0;
         __syncthreads();
         double theta = 0.0;
         for (int r = 1; r < m; ++r) if (sh.rows[r] == S) theta = sh.lam[r];
-        if (tid == 0) for (int r = 1; r < m; ++r) if (sh.rows[r] < S) sh.lam_s[sh.rows[r]] = sh.lam[r];
+        if (tid == 0) {
+            for (int r = 1; r < m; ++r) if (sh.rows[r] < S) sh.lam_s[sh.rows[r]] = sh.lam[r];
+            // a factor row's multiplier kappa_k adds kappa_k B_ik to entry i's gradient: the
+            // gradient's product B (F h) becomes B (F h + kappa / 2)
+            for (int r = 1; r < m; ++r)
+                if (sh.rows[r] > S) {
+                    const int k = sh.rows[r] - S - 1;
+                    sh.kap_s[k] = sh.lam[r];
+                    sh.fh[k] += 0.5 * sh.lam[r];
+                    sh.fh32[k] = float(sh.fh[k]);
+                }
+        }
+        __syncthreads();
         if (warp == 1) {
-            // once per block: lanes over the factors, combined in a fixed order
+            // once per block: lanes over the factors, combined in a fixed order (the quadratic
+            // term h'F h from h itself, without the factor rows' multipliers)
             double fm = 0.0, qd = 0.0;
             for (int k = lane; k < K; k += 32) {
                 fm = fmax(fm, fabs(sh.fh[k]));
-                qd += sh.t64[k] * sh.fh[k];
+                qd += sh.t64[k] * P.f64[k] * sh.t64[k];
             }
             fm = warp_max(fm);
             qd = warp_sum(qd);
@@ -1084,6 +1126,32 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                     if (theta < -tol_d) { ++bviol; r_comp = fmax(r_comp, -theta); P.wcap[a] = 0; }
                 }
             }
+            // factor rows: exposures h = B'w against their bounds, like the bands
+            for (int k = 0; k < K && P.flo; ++k) {
+                const double hk = sh.t64[k], hi = sh.fhi_s[k], lo = sh.flo_s[k];
+                r_exp = fmax(r_exp, fmax(lo - hk, hk - hi));
+                const int wf = sh.wf_s[k];
+                const double kk = sh.kap_s[k];
+                const bool off = wf != 0 && fabs(hk - (wf > 0 ? hi : lo)) > tol_p;
+                auto set_wf = [&](int v) { sh.wf_s[k] = v; P.wfac[a * K + k] = v; };
+                if (off && row_dependent(S + 1 + k)) {
+                    ++bviol;
+                    if (wf > 0 ? hk < hi : hk > lo) { set_wf(0); ++dep_in; }
+                    else ++dep_out;
+                } else if (wf == 0) {
+                    if (hk > hi + tol_p) { ++bviol; set_wf(1); }
+                    else if (hk < lo - tol_p) { ++bviol; set_wf(-1); }
+                } else {
+                    if (off) ++bviol;
+                    if (wf > 0) {
+                        r_comp = fmax(r_comp, fabs(kk) * fabs(hi - hk));
+                        if (kk < -tol_d) { ++bviol; r_comp = fmax(r_comp, -kk); set_wf(0); }
+                    } else {
+                        r_comp = fmax(r_comp, fabs(kk) * fabs(hk - lo));
+                        if (kk > tol_d) { ++bviol; r_comp = fmax(r_comp, kk); set_wf(0); }
+                    }
+                }
+            }
             const double r_budget = fabs(sw - 1.0);
             if (r_budget > tol_p) ++bviol;
             const int total = int(nv) + bviol;
@@ -1112,6 +1180,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
             P.nu[a] = nu;
             P.theta[a] = theta;
             for (int s2 = 0; s2 < S; ++s2) P.lam[a * S + s2] = sh.lam_s[s2];
+            if (P.kappa) for (int k = 0; k < K; ++k) P.kappa[a * K + k] = sh.kap_s[k];
             if (total == 0) P.done[a] = 1;
             sh.go = (total > 0);
         }
@@ -1165,6 +1234,8 @@ __global__ void __launch_bounds__(PB) k_diag_only(PolDev P) {
         double r_exp = 0.0;
         for (int s = 0; s < S; ++s)
             r_exp = fmax(r_exp, fmax(P.band_lo[a * S + s] - secsum[s], secsum[s] - P.band_hi[a * S + s]));
+        for (int k = 0; k < K && P.flo; ++k)
+            r_exp = fmax(r_exp, fmax(P.flo[a * K + k] - hk[k], hk[k] - P.fhi[a * K + k]));
         double quad = 0.0;
         for (int k = 0; k < K; ++k) quad += hk[k] * P.f64[k] * hk[k];
         double* dg = P.diag + (size_t)a * PRISM_NDIAG;

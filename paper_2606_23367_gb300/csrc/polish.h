@@ -36,6 +36,11 @@ struct PolDev {
     const double* band_lo = nullptr;    // M x S
     const double* band_hi = nullptr;
     const double* tau = nullptr;        // M (+inf = none)
+    const double* flo = nullptr;        // M x K factor-exposure bounds, or null (no factor rows)
+    const double* fhi = nullptr;
+    const int* sflag = nullptr;         // M x K: factor rows the iterations hold at a bound
+    int* wfac = nullptr;                // M x K working factor rows (+1 upper, -1 lower, 0 none)
+    double* kappa = nullptr;            // M x K their multipliers (output)
     const float* z = nullptr;           // ADMM iterate, M x Npad
     const float* nu_f = nullptr;        // ADMM budget multiplier, M
     const float* eta_hi_f = nullptr;    // M x S

@@ -455,7 +455,91 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             pwl.push_back(row);
         }
     }
+    // Tilts of the linear term (Eq. 1's per-account return tilt, and the benchmark's 2 Sigma w_b):
+    // a term -t_i w_i is linear, so it shifts every slope of phi_i by -t_i; entries with a tilt
+    // carry it in a piecewise-linear cost row (their lot row when they have lots)
+    const bool has_tilt = b->mu_tilt || b->w_bench;
+    if (has_tilt) {
+        std::vector<double> tilt((size_t)nnz, 0.0), w0h, loh, uph, tch, tmp;
+        std::vector<int32_t> aidx;
+        if ((rc = to_host(b->w0, (size_t)nnz, w0h)) || (rc = to_host(b->lower, (size_t)nnz, loh)) ||
+            (rc = to_host(b->upper, (size_t)nnz, uph)) || (rc = to_host(b->tc, (size_t)nnz, tch)))
+            return rc;
+        if (b->asset_idx && (rc = to_host(b->asset_idx, (size_t)nnz, aidx))) return rc;
+        auto asset = [&](int a, int64_t e) { return b->asset_idx ? int(aidx[e]) : int(e - offs[a]); };
+        if (b->mu_tilt) {
+            if ((rc = to_host(b->mu_tilt, (size_t)nnz, tmp))) return rc;
+            for (int64_t e = 0; e < nnz; ++e) tilt[e] = tmp[e];
+        }
+        if (b->w_bench) {
+            // 2 Sigma_a w_b over the account's own names: 2 (B (F (B' w_b)) + D w_b), FP64
+            std::vector<double> wb, Bh((size_t)U.Npad * K), fh, dh;
+            if ((rc = to_host(b->w_bench, (size_t)nnz, wb)) || (rc = to_host(U.d_B64, (size_t)U.Npad * K, Bh)) ||
+                (rc = to_host(U.d_f64, (size_t)K, fh)) || (rc = to_host(U.d_d64, (size_t)U.Npad, dh)))
+                return rc;
+            std::vector<double> h(K);
+            for (int a = 0; a < M; ++a) {
+                std::fill(h.begin(), h.end(), 0.0);
+                for (int64_t e = offs[a]; e < offs[a + 1]; ++e) {
+                    if (!std::isfinite(wb[e])) { set_error("w_bench must be finite"); return PRISM_ERR_ARGUMENT; }
+                    const int i = asset(a, e);
+                    if (i < 0 || i >= N) { set_error("asset index out of range"); return PRISM_ERR_ARGUMENT; }
+                    const double* Bi = &Bh[(size_t)U.inv_perm[i] * K];
+                    for (int k = 0; k < K; ++k) h[k] += Bi[k] * wb[e];
+                }
+                for (int k = 0; k < K; ++k) h[k] *= fh[k];
+                for (int64_t e = offs[a]; e < offs[a + 1]; ++e) {
+                    const int p = U.inv_perm[asset(a, e)];
+                    const double* Bi = &Bh[(size_t)p * K];
+                    double acc = dh[p] * wb[e];
+                    for (int k = 0; k < K; ++k) acc += Bi[k] * h[k];
+                    tilt[e] += 2.0 * acc;
+                }
+            }
+        }
+        if (pw_of_entry.empty()) pw_of_entry.assign(nnz, -1);
+        for (int64_t e = 0; e < nnz; ++e) {
+            const double t = tilt[e];
+            if (!std::isfinite(t)) { set_error("mu_tilt must be finite"); return PRISM_ERR_ARGUMENT; }
+            if (t == 0.0) continue;
+            if (pw_of_entry[e] < 0) {
+                // the plain L1 cost as a row: breakpoints l, w0 (inside the box), u
+                PwlRow row;
+                const double lo = loh[e], up = uph[e], w0 = w0h[e], c = tch[e];
+                row.phi_lo = c * std::fabs(lo - w0);
+                if (!(up > lo)) {
+                    row.nb = 1; row.bp[0] = lo;
+                } else if (w0 > lo && w0 < up) {
+                    row.nb = 3; row.bp[0] = lo; row.bp[1] = w0; row.bp[2] = up; row.sl[0] = -c; row.sl[1] = c;
+                } else {
+                    row.nb = 2; row.bp[0] = lo; row.bp[1] = up; row.sl[0] = (w0 <= lo) ? c : -c;
+                }
+                pw_of_entry[e] = (int)pwl.size();
+                pwl.push_back(row);
+            }
+            PwlRow& row = pwl[pw_of_entry[e]];
+            for (int j = 0; j + 1 < row.nb; ++j) row.sl[j] -= t;
+            row.phi_lo -= t * row.bp[0];
+        }
+    }
     const int n_pw = (int)pwl.size();
+    const bool has_pw = has_lots || n_pw > 0;
+    // factor-exposure bounds: validated on the host, any finite one turns the block on
+    std::vector<double> flo_h, fhi_h;
+    bool has_fac_in = false;
+    if (b->factor_lo || b->factor_hi) {
+        flo_h.assign((size_t)M * K, -INFINITY);
+        fhi_h.assign((size_t)M * K, INFINITY);
+        if (b->factor_lo && (rc = to_host(b->factor_lo, (size_t)M * K, flo_h))) return rc;
+        if (b->factor_hi && (rc = to_host(b->factor_hi, (size_t)M * K, fhi_h))) return rc;
+        for (size_t q = 0; q < flo_h.size(); ++q) {
+            if (std::isnan(flo_h[q]) || std::isnan(fhi_h[q]) || flo_h[q] > fhi_h[q]) {
+                set_error("factor_lo <= factor_hi required (no NaN)");
+                return PRISM_ERR_ARGUMENT;
+            }
+            has_fac_in |= std::isfinite(flo_h[q]) || std::isfinite(fhi_h[q]);
+        }
+    }
     // ---- workspace layout
     const size_t MN = (size_t)M * Npad;
     int tc_chunk = 0;
@@ -468,10 +552,19 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         BD.w0 = A.take<double>(MN); BD.lo = A.take<double>(MN); BD.up = A.take<double>(MN); BD.c = A.take<double>(MN);
         BD.w0f = A.take<float>(MN); BD.lof = A.take<float>(MN); BD.upf = A.take<float>(MN); BD.cf = A.take<float>(MN);
         *member = A.take<int>(MN);
-        *pwidx_dev = has_lots ? A.take<int>(MN) : nullptr;
+        *pwidx_dev = has_pw ? A.take<int>(MN) : nullptr;
         BD.band_lo = A.take<double>((size_t)M * S); BD.band_hi = A.take<double>((size_t)M * S);
         BD.band_lof = A.take<float>((size_t)M * S); BD.band_hif = A.take<float>((size_t)M * S);
         BD.tau = A.take<double>(M); BD.tauf = A.take<float>(M);
+        {
+            const size_t nf = has_fac_in ? (size_t)M * K : 0;
+            BD.flo = A.take<double>(nf); BD.fhi = A.take<double>(nf);
+            BD.flof = A.take<float>(nf); BD.fhif = A.take<float>(nf);
+            D.s = A.take<float>(nf); D.ys = A.take<float>(nf); D.sflag = A.take<int>(nf);
+            D.rps = A.take<float>(has_fac_in ? M : 0); D.rds = A.take<float>(has_fac_in ? M : 0);
+            P.wfac = A.take<int>(nf);
+        }
+        P.kappa = A.take<double>((size_t)M * K);
         D.z = A.take<float>(MN); D.y = A.take<float>(MN); D.v = A.take<float>(MN);
         D.X = A.take<float>(MN);
         D.Xhi = A.take<__nv_bfloat16>(MN); D.Xlo = A.take<__nv_bfloat16>(MN);
@@ -519,6 +612,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         const size_t n64 = fp64 ? MN : 0;
         P64.z = A.take<double>(n64); P64.y = A.take<double>(n64); P64.X = A.take<double>(n64);
         P64.rho_state = A.take<double>(fp64 ? M : 0); P64.theta_state = A.take<double>(fp64 ? M : 0);
+        P64.s_state = A.take<double>((fp64 && has_fac_in) ? (size_t)M * K : 0);
+        P64.ys_state = A.take<double>((fp64 && has_fac_in) ? (size_t)M * K : 0);
     };
     Dev D;
     std::memset((void*)&D, 0, sizeof(Dev));   // padding bytes take part in the graph-reuse test
@@ -643,11 +738,19 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         PRISM_CUDA_TRY(cudaMemcpyAsync(BD.tau, tau.data(), M * 8, cudaMemcpyHostToDevice, st));
         PRISM_CUDA_TRY(cudaMemcpyAsync(BD.tauf, tauf.data(), M * 4, cudaMemcpyHostToDevice, st));
         BD.has_cap = cap_any;
+        std::vector<float> lf(flo_h.begin(), flo_h.end()), hf(fhi_h.begin(), fhi_h.end());
+        if (has_fac_in) {
+            PRISM_CUDA_TRY(cudaMemcpyAsync(BD.flo, flo_h.data(), flo_h.size() * 8, cudaMemcpyHostToDevice, st));
+            PRISM_CUDA_TRY(cudaMemcpyAsync(BD.fhi, fhi_h.data(), fhi_h.size() * 8, cudaMemcpyHostToDevice, st));
+            PRISM_CUDA_TRY(cudaMemcpyAsync(BD.flof, lf.data(), lf.size() * 4, cudaMemcpyHostToDevice, st));
+            PRISM_CUDA_TRY(cudaMemcpyAsync(BD.fhif, hf.data(), hf.size() * 4, cudaMemcpyHostToDevice, st));
+            BD.has_fac = true;
+        }
         PRISM_CUDA_TRY(cudaStreamSynchronize(st));
     }
     // lot tables
     std::vector<double> h_phi;
-    if (has_lots) {
+    if (has_pw) {
         std::vector<double> bp((size_t)std::max(n_pw, 1) * MAXBP, 0.0), sl((size_t)std::max(n_pw, 1) * (MAXBP - 1), 0.0);
         std::vector<float> bpf(bp.size()), slf(sl.size());
         std::vector<int> nb(std::max(n_pw, 1), 1);
@@ -710,6 +813,14 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.w0 = BD.w0f; D.lo = BD.lof; D.up = BD.upf; D.c = BD.cf;
     D.pw_idx = pwidx; D.pw_bp = BD.pw_bpf; D.pw_sl = BD.pw_slf; D.pw_nbp = BD.pw_nbp;
     D.band_lo = BD.band_lof; D.band_hi = BD.band_hif; D.tau = BD.tauf;
+    if (BD.has_fac) {
+        // the factor-exposure block: its own capacitance inverses and the Gram matrices
+        D.Cinv = batched_mode_bf16 ? U.d_CinvF16 : U.d_CinvF32;
+        D.G = batched_mode_bf16 ? U.d_G16 : U.d_G32;
+        D.flo = BD.flof; D.fhi = BD.fhif;
+    } else {
+        D.s = nullptr; D.ys = nullptr; D.sflag = nullptr; D.rps = nullptr; D.rds = nullptr;
+    }
     D.stream_prox = (pwidx == nullptr && !BD.has_cap) ? 1 : 0;
     // the streaming pass runs inside the tensor-core x-update when the roots kernel can hold
     // the account's candidate masks
@@ -726,6 +837,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     P.w0 = BD.w0; P.lo = BD.lo; P.up = BD.up; P.c = BD.c;
     P.pw_idx = pwidx; P.pw_bp = BD.pw_bp; P.pw_sl = BD.pw_sl; P.pw_phi_lo = (const double*)stage[6]; P.pw_nbp = BD.pw_nbp;
     P.band_lo = BD.band_lo; P.band_hi = BD.band_hi; P.tau = BD.tau;
+    if (BD.has_fac) { P.flo = BD.flo; P.fhi = BD.fhi; P.sflag = D.sflag; }
+    else P.wfac = nullptr;
     P.z = D.z; P.nu_f = D.nu; P.eta_hi_f = D.eta_hi; P.eta_lo_f = D.eta_lo; P.theta_f = D.theta;
     P.FMAX = FMAX;
     P.status = D.status;
@@ -738,6 +851,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P64.w0 = BD.w0; P64.lo = BD.lo; P64.up = BD.up; P64.c = BD.c;
         P64.pw_idx = pwidx; P64.pw_bp = BD.pw_bp; P64.pw_sl = BD.pw_sl; P64.pw_nbp = BD.pw_nbp;
         P64.band_lo = BD.band_lo; P64.band_hi = BD.band_hi; P64.tau = BD.tau; P64.skip = P.skip;
+        if (BD.has_fac) { P64.flo = BD.flo; P64.fhi = BD.fhi; P64.sflag = D.sflag; }
         P64.zf = D.z; P64.nu_f = D.nu; P64.eta_hi_f = D.eta_hi; P64.eta_lo_f = D.eta_lo; P64.theta_f = D.theta;
         P64.iters = D.iters; P64.active = D.active; P64.status = D.status;
         P64.alpha = o->alpha; P64.eps = o->eps_admm; P64.rho0 = o->rho0;
@@ -766,6 +880,14 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(P.nu, 0, M * 8, st);
         cudaMemsetAsync(P.theta, 0, M * 8, st);
         cudaMemsetAsync(P.lam, 0, (size_t)M * S * 8, st);
+        cudaMemsetAsync(P.kappa, 0, (size_t)M * K * 8, st);
+        if (BD.has_fac) {
+            cudaMemsetAsync(D.s, 0, (size_t)M * K * 4, st);     // s = 0 clipped on the first update
+            cudaMemsetAsync(D.ys, 0, (size_t)M * K * 4, st);
+            cudaMemsetAsync(D.sflag, 0, (size_t)M * K * 4, st);
+            cudaMemsetAsync(D.rps, 0, M * 4, st);
+            cudaMemsetAsync(D.rds, 0, M * 4, st);
+        }
         cudaMemsetAsync(D.X, 0, MN * 4, st);
         cudaMemsetAsync(D.Xhi, 0, MN * 2, st);
         cudaMemsetAsync(D.Xlo, 0, MN * 2, st);
@@ -1048,6 +1170,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     out(res->lambda_band, P.lam, (size_t)M * S * 8);
     out(res->theta, P.theta, M * 8);
     out(res->diag, P.diag, (size_t)M * PRISM_NDIAG * 8);
+    out(res->kappa, P.kappa, (size_t)M * K * 8);
     cudaEventRecord(SC.ev[5], st);
     cudaError_t e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) { set_error(std::string("solve failed: ") + cudaGetErrorString(e)); return PRISM_ERR_CUDA; }
@@ -1126,6 +1249,10 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         set_error("keep_for_backward is available in the batched modes");
         return PRISM_ERR_UNSUPPORTED;
     }
+    if (o.keep_for_backward && (b->w_bench || b->factor_lo || b->factor_hi)) {
+        set_error("keep_for_backward does not take a benchmark or factor-exposure bounds");
+        return PRISM_ERR_UNSUPPORTED;
+    }
     if (o.keep_for_backward) *res->state = nullptr;
     const auto t0 = std::chrono::steady_clock::now();
     if (o.precision == PRISM_BATCHED_FP32) return solve_core(uh, b, &o, res, false, false);
@@ -1157,6 +1284,10 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         sb.w0 = b->w0 + e0; sb.lower = b->lower + e0; sb.upper = b->upper + e0; sb.tc = b->tc + e0;
         sb.band_lo = b->band_lo + (size_t)a * S; sb.band_hi = b->band_hi + (size_t)a * S;
         sb.turnover_cap = b->turnover_cap ? b->turnover_cap + a : nullptr;
+        sb.mu_tilt = b->mu_tilt ? b->mu_tilt + e0 : nullptr;
+        sb.w_bench = b->w_bench ? b->w_bench + e0 : nullptr;
+        sb.factor_lo = b->factor_lo ? b->factor_lo + (size_t)a * uh->u.K : nullptr;
+        sb.factor_hi = b->factor_hi ? b->factor_hi + (size_t)a * uh->u.K : nullptr;
         std::vector<int64_t> lot_sub;
         if (b->lot_offsets) {
             std::vector<int64_t> lo_all;
@@ -1175,6 +1306,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
         r1.lambda_band = res->lambda_band ? res->lambda_band + (size_t)a * S : nullptr;
         r1.theta = res->theta ? res->theta + a : nullptr;
         r1.diag = res->diag ? res->diag + (size_t)a * PRISM_NDIAG : nullptr;
+        r1.kappa = res->kappa ? res->kappa + (size_t)a * uh->u.K : nullptr;
         int rc = solve_core(uh, &sb, &o, &r1, false, true, fp64);
         if (rc != PRISM_OK) return rc;
         tdev += r1.t_device_ms;

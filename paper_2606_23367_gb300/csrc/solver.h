@@ -86,6 +86,18 @@ struct Dev {
     unsigned long long* pcount = nullptr;   // profile mode: [0] candidates, [1] entries of the fused pass
     float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
+    // factor-exposure bounds (the Eq. 1 rows B'w in [flo, fhi]) as a second splitting block
+    // s = B'x with penalty rho and unscaled dual ys; null when the book has none. The small
+    // solve updates s and ys and leaves the block's residuals in rps, rds for the convergence
+    // test, and sflag (+1 at the upper bound, -1 at the lower, 0 inside) for the polish
+    const float* flo = nullptr;         // M x K
+    const float* fhi = nullptr;
+    const float* G = nullptr;           // NRHO x K x K Gram matrices B' Delta_j^{-1} B
+    float* s = nullptr;                 // M x K
+    float* ys = nullptr;                // M x K
+    float* rps = nullptr;               // M
+    float* rds = nullptr;               // M
+    int* sflag = nullptr;               // M x K
     // failure-path test only (environment PRISM_TEST_STALLED_WAIT_NS): the tensor-core G2 issues
     // no loads and its first bounded wait, on a barrier nothing completes, runs out after this
     // many ns; 0 in every normal call

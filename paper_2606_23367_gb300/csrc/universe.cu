@@ -68,16 +68,21 @@ __global__ void k_gram(const TB* __restrict__ B, const float* __restrict__ d, in
 }
 
 // Cinv_j = ((2F)^{-1} + G_j)^{-1} by an FP64 Cholesky factorisation in shared
-// memory, then an explicit inverse (columns by forward/back substitution).
+// memory, then an explicit inverse (columns by forward/back substitution). With
+// `split` the diagonal term is (2 f_k + rho_j)^{-1} instead: the capacitance of the
+// x-update when the factor exposures are split off with the same penalty. Gout, when
+// given, receives the FP32 copy of G_j.
 __global__ void k_cinv(const double* __restrict__ G, const double* __restrict__ f, int K,
-                       float* __restrict__ Cinv) {
+                       float* __restrict__ Cinv, int split, float* __restrict__ Gout) {
     const int j = blockIdx.x;
     __shared__ double L[KMAX][KMAX + 1];
     const int t = threadIdx.x;   // 64 threads
+    const double rho = RHO_MIN * pow(10.0, double(j) / RHO_PER_DECADE);
     for (int e = t; e < K * K; e += blockDim.x) {
         int r = e / K, c = e % K;
         double v = G[((size_t)j * K + r) * K + c];
-        if (r == c) v += 1.0 / (2.0 * f[r]);
+        if (Gout) Gout[((size_t)j * K + r) * K + c] = float(v);
+        if (r == c) v += split ? 1.0 / (2.0 * f[r] + rho) : 1.0 / (2.0 * f[r]);
         L[r][c] = v;
     }
     __syncthreads();
@@ -154,7 +159,7 @@ static int fetch(const T* src, size_t n, std::vector<T>& dst) {
 static void free_universe(Universe& U) {
     void* ptrs[] = {U.d_inv_perm, U.d_perm, U.d_sec_start, U.d_sector, U.d_qseg, U.d_sseg, U.d_B64, U.d_f64, U.d_d64, U.d_Bn1, U.d_Bn1f,
                     U.d_mu64, U.d_B32, U.d_B32p, U.d_f32, U.d_d32, U.d_mu32, U.d_B16, U.d_Bt16, U.d_B16p, U.d_Bt16p,
-                    U.d_Cinv32, U.d_Cinv16};
+                    U.d_Cinv32, U.d_Cinv16, U.d_G32, U.d_G16, U.d_CinvF32, U.d_CinvF16};
     for (void* p : ptrs)
         if (p) cudaFree(p);
     if (U.stream) cudaStreamDestroy(U.stream);
@@ -279,6 +284,10 @@ static int create(const prism_universe_desc* desc, Universe& U) {
     TRY(dalloc(U, &U.d_Bt16p, (size_t)KMAX * Npad));
     TRY(dalloc(U, &U.d_Cinv32, (size_t)NRHO * K * K));
     TRY(dalloc(U, &U.d_Cinv16, (size_t)NRHO * K * K));
+    TRY(dalloc(U, &U.d_G32, (size_t)NRHO * K * K));
+    TRY(dalloc(U, &U.d_G16, (size_t)NRHO * K * K));
+    TRY(dalloc(U, &U.d_CinvF32, (size_t)NRHO * K * K));
+    TRY(dalloc(U, &U.d_CinvF16, (size_t)NRHO * K * K));
     auto H2D = [&](void* dst, const void* src, size_t n) {
         return cudaMemcpy(dst, src, n, cudaMemcpyHostToDevice);
     };
@@ -316,9 +325,11 @@ static int create(const prism_universe_desc* desc, Universe& U) {
         }
         dim3 grid(NRHO, cdiv(K, 8));
         k_gram<float><<<grid, 256, 0, U.stream>>>(U.d_B32, U.d_d32, N, K, G);
-        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_Cinv32);
+        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_Cinv32, 0, U.d_G32);
+        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_CinvF32, 1, nullptr);
         k_gram<__nv_bfloat16><<<grid, 256, 0, U.stream>>>(U.d_B16, U.d_d32, N, K, G);
-        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_Cinv16);
+        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_Cinv16, 0, U.d_G16);
+        k_cinv<<<NRHO, 64, 0, U.stream>>>(G, U.d_f64, K, U.d_CinvF16, 1, nullptr);
         cudaError_t e = cudaStreamSynchronize(U.stream);
         cudaFree(G);
         if (e != cudaSuccess || cudaGetLastError() != cudaSuccess) {

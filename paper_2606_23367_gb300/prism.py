@@ -49,7 +49,9 @@ class _Batch(C.Structure):
     _fields_ = [("n_accounts", C.c_int32), ("offsets", C.c_void_p), ("asset_idx", C.c_void_p),
                 ("w0", C.c_void_p), ("lower", C.c_void_p), ("upper", C.c_void_p), ("tc", C.c_void_p),
                 ("band_lo", C.c_void_p), ("band_hi", C.c_void_p), ("turnover_cap", C.c_void_p),
-                ("lot_offsets", C.c_void_p), ("lot_size", C.c_void_p), ("lot_kappa", C.c_void_p)]
+                ("lot_offsets", C.c_void_p), ("lot_size", C.c_void_p), ("lot_kappa", C.c_void_p),
+                ("mu_tilt", C.c_void_p), ("w_bench", C.c_void_p), ("factor_lo", C.c_void_p),
+                ("factor_hi", C.c_void_p)]
 
 
 class _Opts(C.Structure):
@@ -67,7 +69,8 @@ class _Result(C.Structure):
                 ("t_device_ms", C.c_double), ("t_call_ms", C.c_double), ("t_phase_ms", C.c_double * 4),
                 ("device_bytes", C.c_int64), ("n_launches", C.c_int64),
                 ("kernel_ms", C.c_double * len(KERNEL_CLASSES)), ("kernel_launches", C.c_int64 * len(KERNEL_CLASSES)),
-                ("stream_entries", C.c_int64), ("stream_candidates", C.c_int64), ("state", C.c_void_p)]
+                ("stream_entries", C.c_int64), ("stream_candidates", C.c_int64), ("state", C.c_void_p),
+                ("kappa", C.c_void_p)]
 
 
 _lib = None
@@ -189,7 +192,8 @@ def _to_numpy(x):
 
 def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi,
                       asset_idx=None, turnover_cap=None, lot_offsets=None, lot_size=None,
-                      lot_kappa=None, out=None, **opts) -> dict:
+                      lot_kappa=None, mu_tilt=None, w_bench=None, factor_lo=None, factor_hi=None,
+                      out=None, **opts) -> dict:
     """Solve a book of accounts. Array arguments are numpy arrays (host) or torch
     tensors (host or CUDA). ``out`` may supply preallocated outputs with keys
     w/status/iters/nu/lambda_band/theta/diag (device or host); otherwise numpy
@@ -203,7 +207,9 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
                keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
                keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
                keep.ptr(turnover_cap, np.float64), keep.ptr(lot_offsets, np.int64),
-               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64))
+               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64),
+               keep.ptr(mu_tilt, np.float64), keep.ptr(w_bench, np.float64),
+               keep.ptr(factor_lo, np.float64), keep.ptr(factor_hi, np.float64))
     o = _Opts()
     lib.prism_default_opts(C.byref(o))
     for k, v in opts.items():
@@ -216,14 +222,14 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
     if out is None:
         out = dict(w=np.zeros(nnz), status=np.zeros(M, np.int32), iters=np.zeros(M, np.int32),
                    nu=np.zeros(M), lambda_band=np.zeros((M, S)), theta=np.zeros(M),
-                   diag=np.zeros((M, PRISM_NDIAG)))
+                   diag=np.zeros((M, PRISM_NDIAG)), kappa=np.zeros((M, u.n_factors)))
     r = _Result()
     r.w = keep.ptr(out["w"], np.float64)
     r.status = keep.ptr(out["status"], np.int32)
     for k in ("iters",):
         if out.get(k) is not None:
             setattr(r, k, keep.ptr(out[k], np.int32))
-    for k in ("nu", "lambda_band", "theta", "diag"):
+    for k in ("nu", "lambda_band", "theta", "diag", "kappa"):
         if out.get(k) is not None:
             setattr(r, k, keep.ptr(out[k], np.float64))
     holder = C.c_void_p(None)
@@ -242,7 +248,7 @@ def prism_solve_batch(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo,
 
 def prism_autotune(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, band_hi,
                    asset_idx=None, turnover_cap=None, lot_offsets=None, lot_size=None, lot_kappa=None,
-                   **base) -> dict:
+                   mu_tilt=None, w_bench=None, factor_lo=None, factor_hi=None, **base) -> dict:
     """Schedule chosen by the library's autotuner for this book (see prism.h): a dict of
     solve options (rho0, alpha, check_every, stream_after and the base options) to pass to a solve."""
     lib = load_library()
@@ -252,7 +258,9 @@ def prism_autotune(u: UniverseHandle, offsets, w0, lower, upper, tc, band_lo, ba
                keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
                keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
                keep.ptr(turnover_cap, np.float64), keep.ptr(lot_offsets, np.int64),
-               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64))
+               keep.ptr(lot_size, np.float64), keep.ptr(lot_kappa, np.float64),
+               keep.ptr(mu_tilt, np.float64), keep.ptr(w_bench, np.float64),
+               keep.ptr(factor_lo, np.float64), keep.ptr(factor_hi, np.float64))
     o = _Opts()
     lib.prism_default_opts(C.byref(o))
     for k, v in base.items():
@@ -272,7 +280,7 @@ def autotune(handle: UniverseHandle, batch, **base) -> dict:
     return prism_autotune(handle, batch.offsets, batch.w0, batch.lower, batch.upper, batch.tc,
                           batch.band_lo, batch.band_hi, asset_idx=batch.asset_idx,
                           turnover_cap=batch.turnover_cap, lot_offsets=batch.lot_offsets,
-                          lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **base)
+                          lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **_families(batch), **base)
 
 
 def prism_shared_b_products(u: UniverseHandle, X, Q, precision=PRISM_BATCHED_BF16):
@@ -300,7 +308,7 @@ def prism_polish_noalloc(u: UniverseHandle, offsets, w0, lower, upper, tc, band_
     b = _Batch(M, keep.ptr(offsets, np.int64), keep.ptr(asset_idx, np.int32),
                keep.ptr(w0, np.float64), keep.ptr(lower, np.float64), keep.ptr(upper, np.float64),
                keep.ptr(tc, np.float64), keep.ptr(band_lo, np.float64), keep.ptr(band_hi, np.float64),
-               keep.ptr(turnover_cap, np.float64), None, None, None)
+               keep.ptr(turnover_cap, np.float64), None, None, None, None, None, None, None)
     o = _Opts()
     lib.prism_default_opts(C.byref(o))
     for k, v in opts.items():
@@ -372,8 +380,14 @@ def create_universe(uni, device=0) -> UniverseHandle:
     return prism_create_universe(uni.B, uni.f, uni.d, uni.mu, uni.sector, uni.n_sectors, device)
 
 
+def _families(batch) -> dict:
+    """The optional Eq. 1 families of a batch (tilt, benchmark, factor-exposure bounds)."""
+    return {k: getattr(batch, k, None) for k in ("mu_tilt", "w_bench", "factor_lo", "factor_hi")}
+
+
 def solve(handle: UniverseHandle, batch, **opts) -> dict:
     return prism_solve_batch(handle, batch.offsets, batch.w0, batch.lower, batch.upper, batch.tc,
                              batch.band_lo, batch.band_hi, asset_idx=batch.asset_idx,
                              turnover_cap=batch.turnover_cap, lot_offsets=batch.lot_offsets,
-                             lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **opts)
+                             lot_size=batch.lot_size, lot_kappa=batch.lot_kappa, **_families(batch),
+                             **opts)

@@ -80,6 +80,11 @@ class Batch:
     lot_size: Optional[np.ndarray] = None      # (n_lots,) lot size in weight units
     lot_kappa: Optional[np.ndarray] = None     # (n_lots,) marginal tax per unit sold
     redraws: Optional[np.ndarray] = None       # (M,) feasibility redraw count
+    # further families of Eq. 1 (None = absent)
+    mu_tilt: Optional[np.ndarray] = None       # (nnz,) per-account tilt of the return input
+    w_bench: Optional[np.ndarray] = None       # (nnz,) benchmark weights of the risk term
+    factor_lo: Optional[np.ndarray] = None     # (M, K) lower bounds on B'w (-inf = none)
+    factor_hi: Optional[np.ndarray] = None     # (M, K) upper bounds on B'w (+inf = none)
 
     @property
     def n_accounts(self) -> int:
@@ -134,7 +139,11 @@ class Batch:
             band_lo=self.band_lo[accounts].copy(), band_hi=self.band_hi[accounts].copy(),
             turnover_cap=self.turnover_cap[accounts].copy(),
             lot_offsets=lot_offsets, lot_size=lot_size, lot_kappa=lot_kappa,
-            redraws=None if self.redraws is None else self.redraws[accounts].copy())
+            redraws=None if self.redraws is None else self.redraws[accounts].copy(),
+            mu_tilt=None if self.mu_tilt is None else self.mu_tilt[take].copy(),
+            w_bench=None if self.w_bench is None else self.w_bench[take].copy(),
+            factor_lo=None if self.factor_lo is None else self.factor_lo[accounts].copy(),
+            factor_hi=None if self.factor_hi is None else self.factor_hi[accounts].copy())
 
 
 # Workload parameters. Distributions shared by every workload: B_ij ~ N(0, 0.3^2),
@@ -247,8 +256,16 @@ def _draw_account(p, seed, workload, a, redraw, n_universe, sector_u, S):
             upper[pick] = np.minimum(upper[pick], w0[pick])
     band_lo = np.zeros(S)
     band_hi = np.full(S, p["band_hi"])
+    # further Eq. 1 families, drawn after everything else so that the other draws do not move
+    tilt = r.normal(0.0, p["tilt"], size=n_a) if p.get("tilt", 0.0) > 0 else None
+    bench = None
+    if p.get("bench", False):
+        # a benchmark spread over the eligible names (Dirichlet(5): close to equal weights)
+        elig = np.flatnonzero(upper > 0)
+        bench = np.zeros(n_a)
+        bench[elig] = r.dirichlet(np.full(elig.shape[0], 5.0))
     return dict(idx=idx, sec=sec, w0=w0, lower=lower, upper=upper, tc=tc, lots=lots,
-                band_lo=band_lo, band_hi=band_hi, tau=p["tau"])
+                band_lo=band_lo, band_hi=band_hi, tau=p["tau"], tilt=tilt, bench=bench)
 
 
 def _feasible(acc, S) -> bool:
@@ -300,6 +317,14 @@ def make_workload(workload: int, seed: int = 0, first_account: int = 0, **overri
         lot_offsets = np.asarray(lo_list, np.int64)
         lot_size = np.concatenate(sz).astype(np.float64)
         lot_kappa = np.concatenate(kp).astype(np.float64)
+    factor_lo = factor_hi = None
+    if p.get("factor_bound") is not None:
+        # the first n_rows factor exposures B'w of every account held to [-width, width]
+        n_rows, width = p["factor_bound"]
+        factor_lo = np.full((M, K), -np.inf)
+        factor_hi = np.full((M, K), np.inf)
+        factor_lo[:, :n_rows] = -width
+        factor_hi[:, :n_rows] = width
     batch = Batch(
         offsets=offsets, asset_idx=asset_idx, w0=cat("w0"), lower=cat("lower"),
         upper=cat("upper"), tc=cat("tc"),
@@ -307,7 +332,10 @@ def make_workload(workload: int, seed: int = 0, first_account: int = 0, **overri
         band_hi=np.stack([acc["band_hi"] for acc in accs]),
         turnover_cap=np.asarray([acc["tau"] for acc in accs], np.float64),
         lot_offsets=lot_offsets, lot_size=lot_size, lot_kappa=lot_kappa,
-        redraws=np.asarray(redraws, np.int32))
+        redraws=np.asarray(redraws, np.int32),
+        mu_tilt=cat("tilt") if accs and accs[0]["tilt"] is not None else None,
+        w_bench=cat("bench") if accs and accs[0]["bench"] is not None else None,
+        factor_lo=factor_lo, factor_hi=factor_hi)
     return uni, batch
 
 
@@ -327,5 +355,9 @@ def instance_hash(uni: Universe, batch: Batch) -> str:
         if arr is None:
             h.update(b"none")
         else:
+            h.update(np.ascontiguousarray(arr).tobytes())
+    # the optional Eq. 1 families, only when present (the hashes of books without them stay)
+    for arr in (batch.mu_tilt, batch.w_bench, batch.factor_lo, batch.factor_hi):
+        if arr is not None:
             h.update(np.ascontiguousarray(arr).tobytes())
     return h.hexdigest()

@@ -25,9 +25,15 @@ def compare_account(uni, batch, res, a, ref=None):
     sl = batch.account_slice(a)
     w = res["w"][sl]
     f_star = kkt.objective(P.B, P.f, P.d, P.mu, r.w, P.w0, P.tc, P.lots)
+    rows = {}
+    if P.R:
+        # the factor rows of the oracle's problem are the factors with a finite bound
+        flo, fhi = batch.factor_lo, batch.factor_hi
+        J = np.flatnonzero(np.isfinite(flo[a]) | np.isfinite(fhi[a]))
+        rows = dict(rows=P.A, rows_lo=P.a_lo, rows_hi=P.a_hi, kappa=np.asarray(res["kappa"][a])[J])
     dg = kkt.diagnostics(P.B, P.f, P.d, P.mu, P.sector, P.S, w, P.w0, P.lower, P.upper, P.tc,
                          P.band_lo, P.band_hi, P.tau, res["nu"][a], res["lambda_band"][a],
-                         res["theta"][a], P.lots)
+                         res["theta"][a], P.lots, **rows)
     return dict(w_err=float(np.max(np.abs(w - r.w))),
                 obj_rel=abs(dg["obj"] - f_star) / max(abs(f_star), 1e-4),
                 r_primal=dg["r_primal"], r_stat=dg["r_stat"], r_comp=dg["r_comp"],

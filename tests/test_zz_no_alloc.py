@@ -52,12 +52,12 @@ def test_noalloc_matches_solve_batch_twice(workload, kw):
 
 def _perturbed_start(batch, w, seed):
     """w moved off the optimum: every weight strictly inside a linear piece of its cost (not on
-    a bound, not at its current holding) gets a relative change of up to 1e-3, the result
-    clipped to the box. Sector sums, the budget and the turnover move, so bands and a cap held
-    at an edge are no longer recognised from the start point and the polish has to find them."""
+    a bound, not at its current holding) gets a relative change of up to 1e-4, the result
+    clipped to the box. The budget, sector sums and turnover move off their edges (by less
+    than the entry point's 1e-4 warm-start margin), and the free weights off their values."""
     r = np.random.default_rng(seed)
     inside = (w > batch.lower + 1e-12) & (w < batch.upper - 1e-12) & (np.abs(w - batch.w0) > 1e-12)
-    w2 = w * (1.0 + 1e-3 * r.uniform(-1.0, 1.0, size=w.shape) * inside)
+    w2 = w * (1.0 + 1e-4 * r.uniform(-1.0, 1.0, size=w.shape) * inside)
     return np.clip(w2, batch.lower, batch.upper)
 
 
