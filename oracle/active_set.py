@@ -281,6 +281,12 @@ class AccountProblem:
         max_iter = max_iter or (20 * n + 2000)
         lam_full = np.zeros(1)
         it = 0
+        # after a full (unblocked) step the point is the minimiser of the equality problem of
+        # the working set, so the next iteration goes to the multiplier check: the step a new
+        # solve would give is zero up to rounding, which an ill-conditioned working set (more
+        # working rows than the free weights can meet independently) can keep above the
+        # zero-step threshold
+        at_eqp_min = False
         for it in range(1, max_iter + 1):
             F = np.nonzero(~fixed)[0]
             h = self.B.T @ w
@@ -292,9 +298,11 @@ class AccountProblem:
             lam_full = np.linalg.solve(E @ YE, -(E @ Yq))
             step = -0.5 * (Yq + YE @ lam_full)
             scale = max(1.0, float(np.max(np.abs(w[np.isfinite(w)]), initial=0.0)))
-            if np.max(np.abs(step), initial=0.0) > 1e-14 * scale:
-                wcap = self._take_step(w, F, step, fixed, pos, wband, wcap, wgen)
+            if not at_eqp_min and np.max(np.abs(step), initial=0.0) > 1e-14 * scale:
+                wcap, blocked = self._take_step(w, F, step, fixed, pos, wband, wcap, wgen)
+                at_eqp_min = not blocked
                 continue
+            at_eqp_min = False
             # zero step: check the multipliers
             nu = lam_full[0]
             lam = np.zeros(S)
@@ -363,7 +371,8 @@ class AccountProblem:
     def _take_step(self, w, F, step, fixed, pos, wband, wcap, wgen=None):
         """Ratio test: largest alpha <= 1 keeping every free weight in its segment and
         every row outside the working set feasible; the first blocker joins W.
-        Returns whether the cap is in the working set afterwards."""
+        Returns whether the cap is in the working set afterwards, and whether a blocker
+        stopped the step short of the full one."""
         alpha, block = 1.0, None
         a = self.bp[F, pos[F]]
         b = self.bp[F, pos[F] + 1]
@@ -415,7 +424,7 @@ class AccountProblem:
                     alpha, block = t, ("cap", 0)
         w[F] = np.clip(w[F] + alpha * step, a, b)
         if block is None:
-            return wcap
+            return wcap, False
         kind, j = block
         if kind == "hi":
             fixed[j] = True
@@ -434,7 +443,7 @@ class AccountProblem:
             wgen[j] = -1
         else:
             wcap = True
-        return wcap
+        return wcap, True
 
 
 def account_problem(uni, batch, a) -> AccountProblem:

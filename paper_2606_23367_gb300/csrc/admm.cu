@@ -230,13 +230,16 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
             rd = rho * fabsf(sn - s_old);
             if (!(isfinite(rp) && isfinite(rd))) rp = rd = INFINITY;
         }
+        // (reduced through arrays of their own: a warp with no factors reaches this point while
+        // the other warp may still read sP0 above)
+        __shared__ float red_p[KMAX / 32], red_d[KMAX / 32];
         rp = warp_max(rp);
         rd = warp_max(rd);
-        if ((t & 31) == 0) { sT[t >> 5] = rp; sP0[t >> 5] = rd; }
+        if ((t & 31) == 0) { red_p[t >> 5] = rp; red_d[t >> 5] = rd; }
         __syncthreads();
         if (t == 0) {
-            D.rps[m] = fmaxf(sT[0], sT[1]);
-            D.rds[m] = fmaxf(sP0[0], sP0[1]);
+            D.rps[m] = fmaxf(red_p[0], red_p[1]);
+            D.rds[m] = fmaxf(red_d[0], red_d[1]);
         }
     }
 }
