@@ -320,10 +320,6 @@ def queue_and_burden(h, uni, batch, opts, micro_batch=100, window_s=1500.0):
                  call_ms=[round(x, 3) for x in q.call_ms], device_ms=[round(x, 3) for x in q.device_ms])
     rows = []
     for name, family, u2, b2 in burden_books(N=2000, K=32, M=64):
-        if b2 is None:
-            rows.append({"bundle": name, "rule_family": family, "taken": False,
-                         "note": "needs a general exposure matrix (not taken by this library)"})
-            continue
         h2 = prism.create_universe(u2)
         try:
             solve_opts2 = {k: v for k, v in solve_opts.items() if k in ("precision",)}

@@ -69,9 +69,15 @@ def account_identity(universe_id: str, batch, a: int) -> str:
         lo = batch.lot_offsets[sl.start:sl.stop + 1]
         lots = (lo - lo[0], batch.lot_size[lo[0]:lo[-1]], batch.lot_kappa[lo[0]:lo[-1]])
     aidx = None if batch.asset_idx is None else batch.asset_idx[sl]
+    # the further Eq. 1 families, when the book has them (absent ones leave the identity as it was)
+    fam = []
+    for name, per_entry in (("mu_tilt", True), ("w_bench", True), ("factor_lo", False), ("factor_hi", False)):
+        arr = getattr(batch, name, None)
+        if arr is not None:
+            fam.append(arr[sl] if per_entry else arr[a])
     return _h(np.frombuffer(universe_id.encode(), np.uint8), aidx, batch.w0[sl], batch.lower[sl],
               batch.upper[sl], batch.tc[sl], batch.band_lo[a], batch.band_hi[a],
-              np.asarray([batch.turnover_cap[a]]), *lots)
+              np.asarray([batch.turnover_cap[a]]), *lots, *fam)
 
 
 def output_identity(w: np.ndarray, status: int, diag: np.ndarray) -> str:
@@ -205,13 +211,17 @@ def library_solver(handle, **opts) -> Callable:
 # Constraint-burden bundles (Table "burden", E5): rule families added one at a time. B3
 # (factor exposure bounds) needs a general exposure matrix, which this library does not
 # take; it is listed and skipped.
+# factor exposure bounds of the bundles from B3 on: the first four factor exposures B'w of
+# every account held to [-0.03, 0.03]
+FACTOR_BOUND = (4, 0.03)
+
 BURDEN_BUNDLES = [
     ("B0", "budget, long-only, box", dict(tc=(0.0, 0.0), band_hi=np.inf, excl=(0.0, 0.0), lots=False)),
     ("B1", "+ turnover penalty", dict(band_hi=np.inf, excl=(0.0, 0.0), lots=False)),
     ("B2", "+ sector bands", dict(excl=(0.0, 0.0), lots=False)),
-    ("B3", "+ factor exposure bounds", None),
-    ("B4", "+ account exclusions", dict(lots=False)),
-    ("B5", "+ tax-lot proxy", dict(lots=True)),
+    ("B3", "+ factor exposure bounds", dict(excl=(0.0, 0.0), lots=False, factor_bound=FACTOR_BOUND)),
+    ("B4", "+ account exclusions", dict(lots=False, factor_bound=FACTOR_BOUND)),
+    ("B5", "+ tax-lot proxy", dict(lots=True, factor_bound=FACTOR_BOUND)),
 ]
 
 

@@ -93,10 +93,15 @@ def test_audit_identities_bind_inputs_and_outputs():
 
 def test_burden_bundles_add_one_rule_family_each():
     books = {name: (uni, b) for name, _, uni, b in burden_books(N=400, K=8, M=6)}
-    assert books["B3"] == (None, None)              # factor exposure bounds: not taken
     def per_account(b, f):
         return [f(b, a) for a in range(b.n_accounts)]
-    b0, b1, b2, b4, b5 = (books[k][1] for k in ("B0", "B1", "B2", "B4", "B5"))
+    b0, b1, b2, b3, b4, b5 = (books[k][1] for k in ("B0", "B1", "B2", "B3", "B4", "B5"))
+    # factor exposure bounds from B3 on, on the first factors only
+    for b in (b0, b1, b2):
+        assert b.factor_lo is None and b.factor_hi is None
+    for b in (b3, b4, b5):
+        assert np.all(np.isfinite(b.factor_hi[:, :4])) and np.all(np.isinf(b.factor_hi[:, 4:]))
+    assert all(per_account(b3, lambda b, a: np.ptp(b.upper[b.account_slice(a)]) == 0))   # no exclusions yet
     assert np.all(b0.tc == 0) and np.all(np.isinf(b0.band_hi))
     assert all(per_account(b0, lambda b, a: np.ptp(b.upper[b.account_slice(a)]) == 0))   # no exclusions
     assert np.all(b1.tc > 0) and np.all(np.isinf(b1.band_hi))
