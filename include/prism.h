@@ -151,6 +151,12 @@ typedef struct {
                                  the prox's streaming pass runs inside the tensor-core x-update
                                  (default 1); 0: separate x-update and prox kernels (same method) */
     void*   cuda_stream;      /* cudaStream_t to run on (NULL = the library's own stream) */
+    int32_t ragged_layout;    /* books with asset_idx in the batched modes: 1 = dense-masked over the
+                                 universe (every product over all N positions, non-members pinned
+                                 at 0); 2 = packed (each account's own names only, one persistent
+                                 launch of per-account blocks with the account's own capacitance);
+                                 0 = packed when the accounts hold under half of the universe on
+                                 average (default 0) */
 } prism_solve_opts;
 
 /* Fill *o with the defaults documented above. */

@@ -21,7 +21,7 @@
 #include <vector>
 
 #include "common.cuh"
-#include "plain64.h"
+#include "block_admm.h"
 #include "polish.h"
 #include "solver.h"
 
@@ -540,13 +540,20 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             has_fac_in |= std::isfinite(flo_h[q]) || std::isfinite(fhi_h[q]);
         }
     }
+    // ---- ragged books in the batched modes: dense-masked, or packed (each account's own names)
+    bool packed = false;
+    if (b->asset_idx && !plain) {
+        if (o->ragged_layout == 2) packed = true;
+        else if (o->ragged_layout == 0) packed = (double)nnz < 0.5 * (double)M * (double)N;
+    }
     // ---- workspace layout
     const size_t MN = (size_t)M * Npad;
     int tc_chunk = 0;
     const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk) : choose_nsplit(M, N);
     const int FMAX = std::min(N, 2048);
     int* dsel = nullptr;               // device copy of SC.hsel (polish batches)
-    P64Args P64;                       // PLAIN_FP64: the FP64 iteration kernel's arguments
+    BlkArgs<double> P64;               // PLAIN_FP64: the FP64 per-account kernel's arguments
+    BlkArgs<float> PK;                 // ragged books, packed layout: the FP32 per-account kernel's
     auto layout = [&](Arena& A, Dev& D, PolDev& P, BatchDev& BD, void** stage, int** member, int** err,
                       int** pwidx_dev, double** ragged_out) {
         BD.w0 = A.take<double>(MN); BD.lo = A.take<double>(MN); BD.up = A.take<double>(MN); BD.c = A.take<double>(MN);
@@ -614,6 +621,18 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P64.rho_state = A.take<double>(fp64 ? M : 0); P64.theta_state = A.take<double>(fp64 ? M : 0);
         P64.s_state = A.take<double>((fp64 && has_fac_in) ? (size_t)M * K : 0);
         P64.ys_state = A.take<double>((fp64 && has_fac_in) ? (size_t)M * K : 0);
+        P64.queue = A.take<int>(4);
+        // packed layout of a ragged book: position lists, sector ranges, processing order, FP32
+        // state and input copies for accounts too large for shared memory
+        const size_t np = packed ? (size_t)nnz : 0;
+        PK.plist = A.take<int>(np); PK.psec = A.take<int>(packed ? (size_t)M * (S + 1) : 0);
+        PK.order = A.take<int>(packed ? M : 0); PK.queue = A.take<int>(4);
+        PK.z = A.take<float>(np); PK.y = A.take<float>(np); PK.X = A.take<float>(np);
+        PK.w0p = A.take<float>(np); PK.lop = A.take<float>(np); PK.upp = A.take<float>(np); PK.cp = A.take<float>(np);
+        PK.pwp = A.take<int>(np);
+        PK.rho_state = A.take<float>(packed ? M : 0); PK.theta_state = A.take<float>(packed ? M : 0);
+        PK.s_state = A.take<float>((packed && has_fac_in) ? (size_t)M * K : 0);
+        PK.ys_state = A.take<float>((packed && has_fac_in) ? (size_t)M * K : 0);
     };
     Dev D;
     std::memset((void*)&D, 0, sizeof(Dev));   // padding bytes take part in the graph-reuse test
@@ -666,7 +685,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         Arena A;
         A.base = SC.arena; A.cap = SC.arena_bytes;
         std::memset((void*)&D, 0, sizeof(Dev));
-        P = PolDev(); BD = BatchDev(); P64 = P64Args();
+        P = PolDev(); BD = BatchDev(); P64 = BlkArgs<double>(); PK = BlkArgs<float>();
         layout(A, D, P, BD, stage, &member, &err, &pwidx, &ragged_out);
         if (A.alloc_fail) { set_error("workspace layout overflow"); return PRISM_ERR_ALLOCATION; }
     }
@@ -856,6 +875,34 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P64.iters = D.iters; P64.active = D.active; P64.status = D.status;
         P64.alpha = o->alpha; P64.eps = o->eps_admm; P64.rho0 = o->rho0;
         P64.max_iter = o->max_iter; P64.min_iter = o->min_iter; P64.adapt_every = 25;
+    }
+    std::vector<int> order_h;
+    if (packed) {
+        PK.M = M; PK.N = N; PK.Npad = Npad; PK.K = K; PK.S = S;
+        PK.B = U.d_B32; PK.f = U.d_f32; PK.d = U.d_d32; PK.mu = U.d_mu32;
+        PK.sec_start = U.d_sec_start; PK.sector = U.d_sector;
+        PK.w0 = BD.w0f; PK.lo = BD.lof; PK.up = BD.upf; PK.c = BD.cf;
+        PK.pw_idx = pwidx; PK.pw_bp = BD.pw_bpf; PK.pw_sl = BD.pw_slf; PK.pw_nbp = BD.pw_nbp;
+        PK.band_lo = BD.band_lof; PK.band_hi = BD.band_hif; PK.tau = BD.tauf; PK.skip = P.skip;
+        if (BD.has_fac) { PK.flo = BD.flof; PK.fhi = BD.fhif; PK.sflag = D.sflag; }
+        PK.poff = PA.offsets;
+        PK.zf = D.z; PK.nu_f = D.nu; PK.eta_hi_f = D.eta_hi; PK.eta_lo_f = D.eta_lo; PK.theta_f = D.theta;
+        PK.iters = D.iters; PK.active = D.active; PK.status = D.status;
+        PK.alpha = o->alpha; PK.eps = o->eps_admm; PK.rho0 = o->rho0;
+        PK.max_iter = o->max_iter; PK.min_iter = o->min_iter; PK.adapt_every = 25;
+        // accounts largest first (the persistent blocks take them in this order); accounts of at
+        // most stage_cap names keep their entries in shared memory
+        int64_t nmax = 0;
+        order_h.resize(M);
+        for (int a = 0; a < M; ++a) { order_h[a] = a; nmax = std::max(nmax, offs[a + 1] - offs[a]); }
+        std::stable_sort(order_h.begin(), order_h.end(),
+                         [&](int x, int y) { return offs[x + 1] - offs[x] > offs[y + 1] - offs[y]; });
+        BlkArgs<float> probe = PK;
+        probe.stage_cap = 0;
+        const size_t fixed = blk_smem_bytes(probe), per = 7 * sizeof(float) + 2 * sizeof(int);
+        const size_t room = 227 * 1024 - 1024 > fixed ? 227 * 1024 - 1024 - fixed : 0;
+        PK.stage_cap = (int)std::min<int64_t>(nmax, (int64_t)(room / per));
+        PRISM_CUDA_TRY(cudaMemcpyAsync(PK.order, order_h.data(), (size_t)M * 4, cudaMemcpyHostToDevice, st));
     }
     // ---- control init
     {
@@ -1048,11 +1095,20 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     };
     // the first iterations run the staged prox: the streaming form needs the budget multiplier
     // to have settled (its moves set the streaming form's margin) to keep its candidate lists short
-    const int cold = (D.stream_prox && !fp64) ? std::min(std::max(0, o->stream_after), o->max_iter) : 0;
+    const bool blockwise = fp64 || packed;         // every iteration inside the per-account kernel
+    const int cold = (D.stream_prox && !blockwise) ? std::min(std::max(0, o->stream_after), o->max_iter) : 0;
     if (fp64) {
-        // PLAIN_FP64: every iteration of the account in one FP64 launch (plain64.cu)
+        // PLAIN_FP64: every iteration of the account in one FP64 launch (block_admm.cu)
         P64.resume = 0;
-        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_admm64(P64, st); });
+        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(P64, blk_grid(P64), st); });
+    }
+    if (packed) {
+        // ragged book, packed layout: the position lists, then one persistent FP32 launch
+        SC.prof.run(PRISM_K_OTHER, 1, st, [&] {
+            launch_member_lists(M, Npad, S, member, U.d_sec_start, PA.offsets, PK.plist, PK.psec, st);
+        });
+        PK.resume = 0;
+        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(PK, blk_grid(PK), st); });
     }
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
@@ -1061,7 +1117,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st, true); });
     }
     std::memset(SC.hsel, 0, (size_t)M * 4);
-    int total_iters = fp64 ? 0 : admm_loop(o->max_iter + check_every - cold, true);
+    int total_iters = blockwise ? 0 : admm_loop(o->max_iter + check_every - cold, true);
     if (total_iters >= 0) total_iters += cold;
     if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
     if (total_iters < 0) { set_error(std::string("ADMM loop failed: ") + cudaGetErrorString(cudaGetLastError())); return PRISM_ERR_CUDA; }
@@ -1125,11 +1181,17 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         int more = 0;
         if (fp64) {
             // continue the FP64 iterations of the accounts sent back, to a tighter target
-            P64Args R = P64;
+            BlkArgs<double> R = P64;
             R.resume = 1;
             R.eps = P64.eps * (retry == 0 ? 0.1 : 0.01);
             R.max_iter = P64.max_iter * (retry + 2);
-            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_admm64(R, st); });
+            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
+        } else if (packed) {
+            BlkArgs<float> R = PK;
+            R.resume = 1;
+            R.eps = PK.eps * (retry == 0 ? 0.1 : 0.01);
+            R.max_iter = PK.max_iter * (retry + 2);
+            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
         } else {
             Dev saved = D;
             D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);

@@ -51,10 +51,34 @@ def test_batch_shared_universe_small(mode):
     assert_parity(uni, batch, res)
 
 
+@pytest.mark.parametrize("layout", [1, 2])
 @pytest.mark.parametrize("mode", BATCHED)
-def test_ragged_accounts_small(mode):
+def test_ragged_accounts_small(mode, layout):
+    # ragged accounts dense-masked over the universe (1) and packed, one persistent launch of
+    # per-account blocks over each account's own names (2)
     uni, batch = make_workload(2, N=900, M=6)
-    res = gpu_solve(uni, batch, precision=mode)
+    res = gpu_solve(uni, batch, precision=mode, ragged_layout=layout)
+    assert_parity(uni, batch, res)
+
+
+@pytest.mark.parametrize("kw", [dict(N=900, M=40), dict(N=10000, K=16, M=16, ragged=(100, 10000))])
+def test_packed_and_dense_masked_ragged_layouts_agree(kw):
+    # the two layouts run different iterations (the packed one with each account's own
+    # capacitance) to the same minimiser: after the FP64 polish the weights agree; the second
+    # book has two accounts (7,378 and 9,286 names) too large for shared memory, whose packed
+    # state stays in global memory, next to accounts of 123 .. 3,888 names
+    uni, batch = make_workload(2, **kw)
+    rd = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32, ragged_layout=1)
+    rp = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32, ragged_layout=2)
+    assert np.all(rd["status"] == prism.PRISM_CERTIFIED) and np.all(rp["status"] == prism.PRISM_CERTIFIED)
+    assert float(np.max(np.abs(rd["w"] - rp["w"]))) <= 1e-9
+    assert_parity(uni, batch, rp, accounts=[0, batch.n_accounts - 1])
+
+
+def test_packed_ragged_layout_with_lots_cap_and_factor_bounds():
+    # the packed layout with tax lots, a turnover cap and factor-exposure bounds together
+    uni, batch = make_workload(3, N=600, K=12, M=4, ragged=(100, 600), factor_bound=(2, 0.03))
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_FP32, ragged_layout=2)
     assert_parity(uni, batch, res)
 
 
