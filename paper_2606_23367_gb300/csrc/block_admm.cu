@@ -49,7 +49,7 @@ struct BlkShared {
     T ssum[SMAX];                         // sector sums at the current evaluation point
     T eta_s[SMAX];                        // per-sector multiplier point (nu + lambda_s)
     T red[BlkCfg<T>::THREADS / 32][6];
-    T nu, theta, rho, Tv, U;
+    T nu, dnu, theta, rho, Tv, U;         // dnu: the last change of nu (first step of its search)
     int sec[SMAX + 1];                    // the account's sector ranges (entry indices)
     int go, acct;
 };
@@ -147,8 +147,35 @@ __device__ T root(T a, T ga, T b, T gb, Eval&& eval) {
     return (ga < -gb) ? a : b;
 }
 
+// The same root, searched from a warm start x0 in [lo, hi]: steps outward from x0 (growing four
+// times per step) until the sign changes, then root() on that bracket. The function at lo and
+// hi is evaluated only if the search reaches them.
+template <typename T, class Eval>
+__device__ T root_warm(T lo, T hi, T x0, T step, Eval&& eval) {
+    x0 = fmin(fmax(x0, lo), hi);
+    const T g0 = eval(x0);
+    if (g0 == T(0)) return x0;
+    T a = x0, ga = g0;
+    for (int k = 0; k < 80; ++k, step *= T(4)) {
+        if (g0 > T(0)) {
+            const T b = fmin(a + step, hi);
+            const T gb = eval(b);
+            if (gb <= T(0) || !(b < hi)) return root(a, ga, b, gb, eval);
+            a = b; ga = gb;
+        } else {
+            const T b = fmax(a - step, lo);
+            const T gb = eval(b);
+            if (gb >= T(0) || !(b > lo)) return root(b, gb, a, ga, eval);
+            a = b; ga = gb;
+        }
+    }
+    return a;
+}
+
 // The projection of v (in V.X) onto Z for a given theta: the budget multiplier (sh.nu) and
-// each sector's point eta_s (sh.eta_s). Block-collective.
+// each sector's point eta_s (sh.eta_s). The budget's root is searched from the last call's nu,
+// each sector's from its last point (warm starts: they move little between iterations), with a
+// first step of four times the last move of nu. Block-collective.
 template <typename T>
 __device__ void inner(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, int a, T theta, T eta_a, T eta_b,
                       T irho) {
@@ -171,24 +198,28 @@ __device__ void inner(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, i
         __syncthreads();
         return r;
     };
-    const T ga = Tf(eta_a), gb = Tf(eta_b);
-    const T nu = root(eta_a, ga, eta_b, gb, Tf);
+    const T nu_prev = sh.nu;
+    const T step = fmax(T(4) * sh.dnu, BlkCfg<T>::EPS * T(1e3) * fmax(T(1), fabs(nu_prev)));
+    const T nu = root_warm(eta_a, eta_b, nu_prev, step, Tf);
     // each sector held at an edge gets its own point (warp-local roots, no block barriers)
     for (int s = warp; s < S; s += NW) {
         const T lo = A.band_lo[a * S + s], hi = A.band_hi[a * S + s];
         const int q0 = sh.sec[s], q1 = sh.sec[s + 1];
         const T s0 = range_sum(A, V, q0, q1, nu, irho, theta, lane);
+        const T prev = sh.eta_s[s];
         T es = nu;
         if (s0 > hi) {
             auto g = [&](T eta) { return range_sum(A, V, q0, q1, eta, irho, theta, lane) - hi; };
-            es = root(nu, s0 - hi, eta_b, g(eta_b), g);
+            es = root_warm(nu, eta_b, prev > nu ? prev : nu, step, g);
         } else if (s0 < lo) {
             auto g = [&](T eta) { return range_sum(A, V, q0, q1, eta, irho, theta, lane) - lo; };
-            es = root(eta_a, g(eta_a), nu, s0 - lo, g);
+            es = root_warm(eta_a, nu, prev < nu ? prev : nu, step, g);
         }
+        __syncwarp();
         if (lane == 0) sh.eta_s[s] = es;
     }
-    if (tid == 0) sh.nu = nu;
+    __syncthreads();
+    if (tid == 0) { sh.dnu = fabs(nu - nu_prev); sh.nu = nu; }
     __syncthreads();
 }
 
@@ -267,10 +298,10 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             V.z[q] = fmin(fmax(V.w0[q], V.lo[q]), V.up[q]);
             V.y[q] = T(0);
         }
-        if (tid == 0) { sh.rho = T(A.rho0); sh.nu = T(0); sh.theta = T(0); }
+        if (tid == 0) { sh.rho = T(A.rho0); sh.nu = T(0); sh.dnu = T(1); sh.theta = T(0); }
         if (fac) for (int k = tid; k < K; k += NT) { sh.s[k] = T(0); sh.ys[k] = T(0); }
     } else {
-        if (tid == 0) { sh.rho = A.rho_state[a]; sh.nu = T(0); sh.theta = A.theta_state[a]; }
+        if (tid == 0) { sh.rho = A.rho_state[a]; sh.nu = T(0); sh.dnu = T(1); sh.theta = A.theta_state[a]; }
         if (fac)
             for (int k = tid; k < K; k += NT) { sh.s[k] = A.s_state[a * K + k]; sh.ys[k] = A.ys_state[a * K + k]; }
     }
