@@ -192,7 +192,8 @@ void prism_default_opts(prism_solve_opts* o);
 #define PRISM_K_UNPACK   7  /* output unpacking */
 #define PRISM_K_XPROX    8  /* x-update B Q fused with the streaming pass of the prox (L1-only books) */
 #define PRISM_K_ROOTS    9  /* per-account multipliers, candidates and control after PRISM_K_XPROX */
-#define PRISM_NKCLASS   10
+#define PRISM_K_BLOCK   10  /* every iteration of an account in one block (PLAIN_FP64; packed ragged books) */
+#define PRISM_NKCLASS   11
 
 typedef struct {
     double*  w;             /* ragged weights, same layout as prism_batch (required) */

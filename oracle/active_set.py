@@ -199,29 +199,36 @@ class AccountProblem:
 
     def _feasible_start_lp(self):
         """min sum_i t_i over (w, t) with t_i >= |w_i - w0_i| and every constraint (a
-        library LP solve, HiGHS); the cap is sum_i t_i <= tau."""
+        library LP solve, HiGHS); the cap is sum_i t_i <= tau. The constraint matrix is
+        stored sparse (its identity blocks would take gigabytes dense at n = 10,000)."""
+        import scipy.sparse as sp
         from scipy.optimize import linprog
         n, S = self.n, self.S
         c = np.concatenate([np.zeros(n), np.ones(n)])
-        I = np.eye(n)
-        A_ub = [np.hstack([I, -I]), np.hstack([-I, -I])]
+        I = sp.identity(n, format="csr")
+        A_ub = [sp.hstack([I, -I]), sp.hstack([-I, -I])]
         b_ub = [self.w0, -self.w0]
+        zn = sp.csr_matrix((1, n))
+
+        def row(vec_w):
+            return sp.hstack([sp.csr_matrix(vec_w[None, :]), zn])
+
         for s in range(S):
             m = (self.sector == s).astype(np.float64)
             if np.isfinite(self.band_hi[s]):
-                A_ub.append(np.concatenate([m, np.zeros(n)])[None, :]); b_ub.append([self.band_hi[s]])
+                A_ub.append(row(m)); b_ub.append([self.band_hi[s]])
             if np.isfinite(self.band_lo[s]):
-                A_ub.append(np.concatenate([-m, np.zeros(n)])[None, :]); b_ub.append([-self.band_lo[s]])
+                A_ub.append(row(-m)); b_ub.append([-self.band_lo[s]])
         for r in range(self.R):
             if np.isfinite(self.a_hi[r]):
-                A_ub.append(np.concatenate([self.A[r], np.zeros(n)])[None, :]); b_ub.append([self.a_hi[r]])
+                A_ub.append(row(self.A[r])); b_ub.append([self.a_hi[r]])
             if np.isfinite(self.a_lo[r]):
-                A_ub.append(np.concatenate([-self.A[r], np.zeros(n)])[None, :]); b_ub.append([-self.a_lo[r]])
+                A_ub.append(row(-self.A[r])); b_ub.append([-self.a_lo[r]])
         if np.isfinite(self.tau):
-            A_ub.append(np.concatenate([np.zeros(n), np.ones(n)])[None, :]); b_ub.append([self.tau])
-        A_eq = np.concatenate([np.ones(n), np.zeros(n)])[None, :]
+            A_ub.append(sp.hstack([zn, sp.csr_matrix(np.ones((1, n)))])); b_ub.append([self.tau])
+        A_eq = sp.hstack([sp.csr_matrix(np.ones((1, n))), zn])
         bounds = [(self.lower[i], self.upper[i]) for i in range(n)] + [(0, None)] * n
-        res = linprog(c, A_ub=np.vstack(A_ub), b_ub=np.concatenate(b_ub), A_eq=A_eq, b_eq=[1.0],
+        res = linprog(c, A_ub=sp.vstack(A_ub, format="csr"), b_ub=np.concatenate(b_ub), A_eq=A_eq, b_eq=[1.0],
                       bounds=bounds, method="highs")
         if res.status != 0:
             raise RuntimeError("no feasible point (infeasible account?)")

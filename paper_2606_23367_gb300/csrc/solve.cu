@@ -1100,7 +1100,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     if (fp64) {
         // PLAIN_FP64: every iteration of the account in one FP64 launch (block_admm.cu)
         P64.resume = 0;
-        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(P64, blk_grid(P64), st); });
+        SC.prof.run(PRISM_K_BLOCK, 1, st, [&] { launch_block_admm(P64, blk_grid(P64), st); });
     }
     if (packed) {
         // ragged book, packed layout: the position lists, then one persistent FP32 launch
@@ -1108,7 +1108,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             launch_member_lists(M, Npad, S, member, U.d_sec_start, PA.offsets, PK.plist, PK.psec, st);
         });
         PK.resume = 0;
-        SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(PK, blk_grid(PK), st); });
+        SC.prof.run(PRISM_K_BLOCK, 1, st, [&] { launch_block_admm(PK, blk_grid(PK), st); });
     }
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
@@ -1185,13 +1185,13 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
             R.resume = 1;
             R.eps = P64.eps * (retry == 0 ? 0.1 : 0.01);
             R.max_iter = P64.max_iter * (retry + 2);
-            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
+            SC.prof.run(PRISM_K_BLOCK, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
         } else if (packed) {
             BlkArgs<float> R = PK;
             R.resume = 1;
             R.eps = PK.eps * (retry == 0 ? 0.1 : 0.01);
             R.max_iter = PK.max_iter * (retry + 2);
-            SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
+            SC.prof.run(PRISM_K_BLOCK, 1, st, [&] { launch_block_admm(R, blk_grid(R), st); });
         } else {
             Dev saved = D;
             D.eps_admm = saved.eps_admm * (retry == 0 ? 0.1f : 0.01f);

@@ -23,7 +23,8 @@ PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16, PRISM_PLAIN_FP64 = 0, 
 PRISM_NDIAG = 8
 (PRISM_DIAG_BUDGET, PRISM_DIAG_BOX, PRISM_DIAG_EXPOSURE, PRISM_DIAG_TURNOVER, PRISM_DIAG_STAT, PRISM_DIAG_COMP,
  PRISM_DIAG_OBJ, PRISM_DIAG_ERR_EST) = range(8)
-KERNEL_CLASSES = ("gemm_P", "solve_K", "gemm_x", "prox", "polish", "pack", "other", "unpack", "xprox", "roots")
+KERNEL_CLASSES = ("gemm_P", "solve_K", "gemm_x", "prox", "polish", "pack", "other", "unpack", "xprox", "roots",
+                  "block")
 DIAG_NAMES = ("r_budget", "r_box", "r_exposure", "r_turnover", "r_stat", "r_comp", "obj", "w_err_bound")
 STATUS_NAMES = ("CERTIFIED", "FEASIBLE_NONCERTIFIED", "TIMEOUT", "DEADLINE_EXCEEDED",
                 "NO_FEASIBLE_RETURN", "ALLOCATION_FAILURE", "NUMERICAL_FAILURE")

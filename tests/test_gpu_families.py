@@ -65,13 +65,13 @@ def test_benchmark_in_the_risk_term(mode):
 
 
 def test_factor_bounds_at_the_headline_width():
-    # 16 accounts x 10,000 assets, K = 64 (the headline universe), four factor exposures bounded,
+    # 32 accounts x 10,000 assets, K = 64 (the headline universe), four factor exposures bounded,
     # in the launch configuration of the benchmark (batched BF16)
-    uni, batch = make_workload(1, M=16, factor_bound=(4, 0.02))
+    uni, batch = make_workload(1, M=32, factor_bound=(4, 0.02))
     res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
     from tests.oracle_pool import compare_all
     from tests.parity_util import check_account
-    rows = compare_all(1, res, M=16, factor_bound=(4, 0.02))
+    rows = compare_all(1, res, M=32, factor_bound=(4, 0.02))
     for e in rows:
         e["status"] = int(res["status"][e["account"]])
         check_account(e, e["account"])
