@@ -305,6 +305,125 @@ def adjoint_timing(stream, reps=5):
         h.close()
 
 
+# the other workloads, each measured on its own (outside the headline's timed region):
+# (id, description, solve options, oracle sample size)
+OTHER_WORKLOADS = [
+    (0, "1 account x 100 assets, K=10, 10 sector bands (PLAIN_FP64)", dict(precision=3), 1),
+    (0, "1 account x 100 assets, K=10, 10 sector bands (PLAIN_FP32)", dict(precision=0), 1),
+    (2, "256 ragged accounts from 5,000 assets (100-5,000 names), K=32, packed layout",
+     dict(precision=2), 64),
+    (3, "200 accounts x 1,924 assets, K=48, tax lots, turnover cap 0.2", dict(precision=2), 32),
+]
+
+
+def _oracle_sample_worker(args):
+    workload, a = args
+    from oracle.active_set import account_problem
+    from paper_2606_23367_gb300.workloads import make_workload
+    uni, batch = make_workload(workload, first_account=a, M=1)
+    t = time.perf_counter()
+    r = account_problem(uni, batch, 0).solve()
+    return time.perf_counter() - t, r.w
+
+
+def other_workloads(stream, steps=5, with_cpu=True):
+    """Certified accounts/s of each other workload: device lane (inputs resident, CUDA events on
+    the solve stream) and e2e lane (pinned host buffers), the dominant kernel class's share and
+    method-byte rate, the measured weight error against the oracle on a sample of accounts, and
+    the oracle's own rate on that sample (all host cores)."""
+    import numpy as np
+    import torch
+    from paper_2606_23367_gb300 import prism
+    from paper_2606_23367_gb300.workloads import instance_hash, make_workload
+    out = []
+    pool = _oracle_pool(_cores()) if with_cpu else None
+    try:
+        for wid, desc, opts, n_cpu in OTHER_WORKLOADS:
+            uni, batch = make_workload(wid)
+            M, S, nnz = batch.n_accounts, uni.n_sectors, int(batch.offsets[-1])
+            h = prism.create_universe(uni)
+            try:
+                def arrs(where):
+                    def t(x, dt):
+                        if x is None:
+                            return None
+                        tt = torch.from_numpy(np.ascontiguousarray(x)).to(dt)
+                        return tt.cuda() if where == "dev" else tt.pin_memory()
+                    f64, i32, i64 = torch.float64, torch.int32, torch.int64
+                    inp = dict(offsets=t(batch.offsets, i64), asset_idx=t(batch.asset_idx, i32), w0=t(batch.w0, f64),
+                               lower=t(batch.lower, f64), upper=t(batch.upper, f64), tc=t(batch.tc, f64),
+                               band_lo=t(batch.band_lo, f64), band_hi=t(batch.band_hi, f64),
+                               turnover_cap=t(batch.turnover_cap, f64), lot_offsets=t(batch.lot_offsets, i64),
+                               lot_size=t(batch.lot_size, f64), lot_kappa=t(batch.lot_kappa, f64))
+                    z = (lambda *sh, dt=torch.float64: torch.zeros(*sh, dtype=dt, device="cuda")) if where == "dev" \
+                        else (lambda *sh, dt=torch.float64: torch.zeros(*sh, dtype=dt).pin_memory())
+                    res = dict(w=z(nnz), status=torch.zeros(M, dtype=torch.int32).pin_memory(),
+                               iters=z(M, dt=torch.int32), nu=z(M), lambda_band=z(M, S), theta=z(M),
+                               diag=z(M, prism.PRISM_NDIAG), kappa=z(M, uni.n_factors))
+                    return inp, res
+
+                def step(inp, res, **extra):
+                    return prism.prism_solve_batch(h, **inp, out=res, cuda_stream=stream.cuda_stream, **opts, **extra)
+
+                def lane(where):
+                    inp, res = arrs(where)
+                    step(inp, res)
+                    torch.cuda.synchronize()
+                    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                    e0.record(stream)
+                    cert = 0
+                    for _ in range(steps):
+                        step(inp, res)
+                        cert += int((res["status"].numpy() == 0).sum())
+                    e1.record(stream)
+                    torch.cuda.synchronize()
+                    return cert / (e0.elapsed_time(e1) / 1e3), e0.elapsed_time(e1) / steps, inp, res
+
+                value, ms, din, dres = lane("dev")
+                w_dev = dres["w"].cpu().numpy()
+                bound = dres["diag"].cpu().numpy()[:, prism.PRISM_DIAG_ERR_EST]
+                iters = dres["iters"].cpu().numpy()
+                e2e, ms_e2e, hin, hres = lane("host")
+                h2d = sum(t.numel() * t.element_size() for t in hin.values() if t is not None)
+                d2h = sum(t.numel() * t.element_size() for t in hres.values() if t is not None)
+                prof = step(din, dres, profile=1)
+                names = prism.KERNEL_CLASSES
+                kms, kl = prof["kernel_ms"], prof["kernel_launches"]
+                dom = max(range(len(names)), key=lambda i: kms[i])
+                # method bytes of the iterations: 24 B per account-entry and iteration
+                entries = float(sum((batch.offsets[a + 1] - batch.offsets[a]) * iters[a] for a in range(M)))
+                it_ms = sum(kms[names.index(n)] for n in ("gemm_P", "solve_K", "gemm_x", "prox", "xprox", "roots",
+                                                         "block"))
+                line = {"workload": desc, "config_id": wid, "instance_sha256": instance_hash(uni, batch),
+                        "metric": "certified accounts/s", "value": value, "ms_per_step": ms, "steps": steps,
+                        "certified": int((dres["status"].numpy() == 0).sum()), "accounts": M,
+                        "e2e": {"value": e2e, "ms_per_step": ms_e2e, "h2d_bytes_per_step": h2d,
+                                "d2h_bytes_per_step": d2h},
+                        "admm_iters": {"median": float(np.median(iters)), "max": int(iters.max())},
+                        "dominant_kernel_class": names[dom], "kernel_share": {n: kms[i] / max(1e-9, sum(kms))
+                                                                              for i, n in enumerate(names) if kms[i] > 0},
+                        "iterations_method_gbs": 24.0 * entries / max(1e-9, it_ms / 1e3) / 1e9,
+                        "stated_error_bound_max": float(bound.max())}
+                if pool is not None:
+                    acc = list(range(min(M, n_cpu)))
+                    t0 = time.perf_counter()
+                    outs = pool.map(_oracle_sample_worker, [(wid, a) for a in acc], chunksize=1)
+                    rate = len(acc) / (time.perf_counter() - t0)
+                    errs = [float(np.max(np.abs(w_dev[batch.account_slice(a)] - o[1]))) for a, o in zip(acc, outs)]
+                    line["error_vs_oracle"] = {"max_w_err": max(errs), "accounts": len(acc)}
+                    line["cpu_baseline"] = {"value": rate, "unit": "accounts/s", "cores": _cores(), "kind": "oracle",
+                                            "sample": f"accounts 0..{len(acc) - 1}, one single-threaded FP64 "
+                                                      "active-set solve per worker process"}
+                out.append(line)
+            finally:
+                h.close()
+    finally:
+        if pool is not None:
+            pool.close()
+            pool.join()
+    return out
+
+
 def queue_and_burden(h, uni, batch, opts, micro_batch=100, window_s=1500.0):
     """The production-queue lane (Sec. 5.1 aggregates, E5 shape) of this book in micro-batches
     through the full-call API with host buffers, and the constraint-burden curve (Table
@@ -559,6 +678,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     if rank != 0:
         return
     adj = None if args.no_adjoint else adjoint_timing(stream)
+    others = None if args.no_others else other_workloads(stream, with_cpu=not args.no_cpu_baseline)
     queue = burden = None
     if not args.no_queue:
         queue, burden = queue_and_burden(h, uni, batch, opts)
@@ -590,7 +710,7 @@ def run_gpu(args, dist, rank, world, local_rank):
         "gpu_launches": int(launches), "clocks": clocks,
         "per_call_ms": {"call_median": statistics.median(c for c, _ in dev_calls),
                         "device_median": statistics.median(d for _, d in dev_calls)},
-        "adjoint": adj, "queue": queue, "burden": burden,
+        "adjoint": adj, "queue": queue, "burden": burden, "other_workloads": others,
     }
     print(json.dumps(line), flush=True)
     h.close()
@@ -612,6 +732,8 @@ def main():
                     "(overrides the schedule; 1 = one range, as in the profile pass)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing of the "
                     "differentiation workload")
+    ap.add_argument("--no-others", action="store_true", help="skip the lines of the other workloads "
+                    "(single account, ragged, tax-aware)")
     ap.add_argument("--no-queue", action="store_true", help="skip the production-queue and constraint-burden "
                     "lines")
     args = ap.parse_args()

@@ -44,7 +44,9 @@ struct BlkShared {
     T L[KMAX][KMAX + 1];                  // Cholesky factor of C (lower)
     T G[KMAX][KMAX + 1];                  // B' Delta^{-1} B (factor-exposure block only)
     T P[KMAX], Q[KMAX];
-    T part[BlkCfg<T>::THREADS / 64][KMAX];
+    T part[BlkCfg<T>::THREADS / 32][KMAX];  // per-warp partial sums of B'X
+    T Bc[32][KMAX + 1];                   // a chunk of the account's rows of B (capacitance build)
+    T wdi[32];                            // their 1 / (2 d + rho)
     T s[KMAX], ys[KMAX], tv[KMAX], P0[KMAX];   // factor-exposure block: s = B'x and its dual
     T ssum[SMAX];                         // sector sums at the current evaluation point
     T eta_s[SMAX];                        // per-sector multiplier point (nu + lambda_s)
@@ -65,6 +67,45 @@ struct View {
     T *z, *y, *X;
     __device__ int p(int q) const { return pos ? pos[q] : q; }
 };
+
+// B_p . Q for one row: the padded FP32 copy in 16-byte loads, all issued together (they are
+// independent: the latency of the rows, which come from L2, overlaps), else element by element.
+template <typename T>
+__device__ __forceinline__ T brow_dot(const BlkArgs<T>& A, int p, const T* Q) {
+    T acc = 0;
+#pragma unroll 8
+    for (int k = 0; k < A.K; ++k) acc += A.B[(size_t)p * A.K + k] * Q[k];
+    return acc;
+}
+template <>
+__device__ __forceinline__ float brow_dot<float>(const BlkArgs<float>& A, int p, const float* Q) {
+    if (!A.Bp) {
+        float acc = 0.f;
+#pragma unroll 8
+        for (int k = 0; k < A.K; ++k) acc += A.B[(size_t)p * A.K + k] * Q[k];
+        return acc;
+    }
+    const float4* r = reinterpret_cast<const float4*>(A.Bp + (size_t)p * KMAX);
+    float a0 = 0.f, a1 = 0.f;
+#pragma unroll
+    for (int h = 0; h < KMAX / 32; ++h) {        // two halves of 32 factors: 8 loads in flight each
+        if (32 * h >= A.K) break;
+        float4 b[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (32 * h + 4 * c < A.K) b[c] = __ldg(r + 8 * h + c);
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+            if (32 * h + 4 * c < A.K) {          // padding factors are zero in the copy and in Q
+                const float* q = Q + 32 * h + 4 * c;
+                a0 = fmaf(b[c].x, q[0], a0);
+                a1 = fmaf(b[c].y, q[1], a1);
+                a0 = fmaf(b[c].z, q[2], a0);
+                a1 = fmaf(b[c].w, q[3], a1);
+            }
+    }
+    return a0 + a1;
+}
 
 // Breakpoints and slopes of phi_i restricted to [l_i, u_i].
 template <typename T>
@@ -255,21 +296,43 @@ __device__ T turnover(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, T
 template <typename T>
 __device__ bool factor(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, T rho) {
     constexpr int NT = BlkCfg<T>::THREADS;
+    constexpr int PPT = (KMAX * (KMAX + 1) / 2 + NT - 1) / NT;   // pairs per thread at most
     const bool fac = A.flo != nullptr;
     const int tid = threadIdx.x, K = A.K;
     const int npair = K * (K + 1) / 2;
-    for (int q = tid; q < npair; q += NT) {
-        int r = 0, rem = q;
+    // this thread's pairs (r, c), c <= r, and their sums over the account's rows, which are staged
+    // in shared memory 32 at a time
+    int pr[PPT], pc[PPT];
+    T acc[PPT];
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        const int q = tid + j * NT;
+        int r = 0, rem = q < npair ? q : 0;
         while (rem > r) { rem -= r + 1; ++r; }
-        const int c = rem;                                 // pair (r, c), c <= r
-        T acc = 0;
-        for (int e = 0; e < V.n; ++e) {
-            const int p = V.p(e);
-            acc += A.B[(size_t)p * K + r] * A.B[(size_t)p * K + c] / (T(2) * A.d[p] + rho);
+        pr[j] = r; pc[j] = rem; acc[j] = 0;
+    }
+    for (int e0 = 0; e0 < V.n; e0 += 32) {
+        const int ne = min(32, V.n - e0);
+        for (int t = tid; t < ne * K; t += NT) {
+            const int e = t / K, k = t % K, p = V.p(e0 + e);
+            sh.Bc[e][k] = A.B[(size_t)p * K + k];
         }
-        if (fac) { sh.G[r][c] = acc; sh.G[c][r] = acc; }
-        if (r == c) acc += fac ? T(1) / (T(2) * A.f[r] + rho) : T(1) / (T(2) * A.f[r]);
-        sh.L[r][c] = acc;
+        for (int e = tid; e < ne; e += NT) sh.wdi[e] = T(1) / (T(2) * A.d[V.p(e0 + e)] + rho);
+        __syncthreads();
+#pragma unroll
+        for (int j = 0; j < PPT; ++j)
+            if (tid + j * NT < npair)
+                for (int e = 0; e < ne; ++e) acc[j] += sh.Bc[e][pr[j]] * sh.Bc[e][pc[j]] * sh.wdi[e];
+        __syncthreads();
+    }
+#pragma unroll
+    for (int j = 0; j < PPT; ++j) {
+        if (tid + j * NT >= npair) continue;
+        const int r = pr[j], c = pc[j];
+        T v = acc[j];
+        if (fac) { sh.G[r][c] = v; sh.G[c][r] = v; }
+        if (r == c) v += fac ? T(1) / (T(2) * A.f[r] + rho) : T(1) / (T(2) * A.f[r]);
+        sh.L[r][c] = v;
     }
     __syncthreads();
     for (int c = 0; c < K; ++c) {
@@ -306,6 +369,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             for (int k = tid; k < K; k += NT) { sh.s[k] = A.s_state[a * K + k]; sh.ys[k] = A.ys_state[a * K + k]; }
     }
     for (int s = tid; s < S; s += NT) sh.eta_s[s] = T(0);
+    for (int k = tid; k < KMAX; k += NT) sh.Q[k] = T(0);   // factors beyond K stay zero (row dot products)
     __syncthreads();
     T rho = sh.rho;
     bool ok = factor(A, sh, V, rho);
@@ -323,17 +387,31 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
         }
         __syncthreads();
         {
-            constexpr int G = NT / 64;
-            const int g = tid / 64, k = tid % 64;
-            if (k < K) {
-                T acc = 0;
-                for (int q = g; q < n; q += G) acc += A.B[(size_t)V.p(q) * K + k] * V.X[q];
-                sh.part[g][k] = acc;
+            // warp w takes entries w, w + NW, ...; lane l factors l and l + 32 of each row (the
+            // row's loads coalesced), four rows in flight per step
+            const T* Bb = A.Bp ? A.Bp : A.B;
+            const int ld = A.Bp ? KMAX : K;
+            T a0 = 0, a1 = 0;
+            for (int q0 = warp; q0 < n; q0 += 4 * NW) {
+                T b0[4], b1[4], xv[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    const int q = q0 + u * NW;
+                    const bool in = q < n;
+                    const size_t row = in ? (size_t)V.p(q) * ld : 0;
+                    b0[u] = (in && lane < K) ? Bb[row + lane] : T(0);
+                    b1[u] = (in && lane + 32 < K) ? Bb[row + lane + 32] : T(0);
+                    xv[u] = in ? V.X[q] : T(0);
+                }
+#pragma unroll
+                for (int u = 0; u < 4; ++u) { a0 += b0[u] * xv[u]; a1 += b1[u] * xv[u]; }
             }
+            sh.part[warp][lane] = a0;
+            sh.part[warp][lane + 32] = a1;
             __syncthreads();
             if (tid < K) {
                 T s = 0;
-                for (int q = 0; q < G; ++q) s += sh.part[q][tid];
+                for (int w = 0; w < NW; ++w) s += sh.part[w][tid];
                 sh.P[tid] = s;
             }
             __syncthreads();
@@ -384,8 +462,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
         T ea = T(INFINITY), eb = T(-INFINITY);
         for (int q = tid; q < n; q += NT) {
             const int p = V.p(q);
-            T bq = 0;
-            for (int k = 0; k < K; ++k) bq += A.B[(size_t)p * K + k] * sh.Q[k];
+            const T bq = brow_dot(A, p, sh.Q);
             const T x = V.X[q] - bq / (T(2) * A.d[p] + rho);
             const T v = alpha * x + (T(1) - alpha) * V.z[q] + V.y[q] * irho;
             V.X[q] = v;
@@ -533,7 +610,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
 
 // Persistent blocks: each takes the next account from the work counter (in A.order when given).
 template <typename T>
-__global__ void __launch_bounds__(BlkCfg<T>::THREADS) k_block_admm(BlkArgs<T> A) {
+__global__ void __launch_bounds__(BlkCfg<T>::THREADS, 1) k_block_admm(BlkArgs<T> A) {
     constexpr int NT = BlkCfg<T>::THREADS;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     BlkShared<T>& sh = *reinterpret_cast<BlkShared<T>*>(smem_raw);

@@ -12,6 +12,7 @@ struct BlkArgs {
     int M = 0, N = 0, Npad = 0, K = 0, S = 0;
     // universe, sorted positions
     const T* B = nullptr;               // Npad x K
+    const T* Bp = nullptr;              // Npad x 64 (factors zero-padded, 16-byte aligned rows), or null
     const T* f = nullptr;               // K
     const T* d = nullptr;               // Npad
     const T* mu = nullptr;              // Npad

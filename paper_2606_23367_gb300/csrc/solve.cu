@@ -879,7 +879,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     std::vector<int> order_h;
     if (packed) {
         PK.M = M; PK.N = N; PK.Npad = Npad; PK.K = K; PK.S = S;
-        PK.B = U.d_B32; PK.f = U.d_f32; PK.d = U.d_d32; PK.mu = U.d_mu32;
+        PK.B = U.d_B32; PK.Bp = U.d_B32p; PK.f = U.d_f32; PK.d = U.d_d32; PK.mu = U.d_mu32;
         PK.sec_start = U.d_sec_start; PK.sector = U.d_sector;
         PK.w0 = BD.w0f; PK.lo = BD.lof; PK.up = BD.upf; PK.c = BD.cf;
         PK.pw_idx = pwidx; PK.pw_bp = BD.pw_bpf; PK.pw_sl = BD.pw_slf; PK.pw_nbp = BD.pw_nbp;

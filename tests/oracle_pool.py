@@ -36,7 +36,7 @@ def _workload(key):
 
 
 def _compare(job):
-    key, a, w, nu, lam, theta, lib_obj, bound = job
+    key, a, w, nu, lam, theta, lib_obj, bound, kappa = job
     import numpy as np
     from oracle import kkt
     from oracle.active_set import account_problem
@@ -44,8 +44,13 @@ def _compare(job):
     P = account_problem(uni, batch, a)
     r = P.solve()
     f_star = kkt.objective(P.B, P.f, P.d, P.mu, r.w, P.w0, P.tc, P.lots)
+    rows = {}
+    if P.R:
+        # the factor rows of the oracle's problem are the factors with a finite bound
+        J = np.flatnonzero(np.isfinite(batch.factor_lo[a]) | np.isfinite(batch.factor_hi[a]))
+        rows = dict(rows=P.A, rows_lo=P.a_lo, rows_hi=P.a_hi, kappa=np.asarray(kappa)[J])
     dg = kkt.diagnostics(P.B, P.f, P.d, P.mu, P.sector, P.S, w, P.w0, P.lower, P.upper, P.tc,
-                         P.band_lo, P.band_hi, P.tau, nu, lam, theta, P.lots)
+                         P.band_lo, P.band_hi, P.tau, nu, lam, theta, P.lots, **rows)
     return dict(account=a, w_err=float(np.max(np.abs(w - r.w))) if len(w) else 0.0,
                 obj_rel=abs(dg["obj"] - f_star) / max(abs(f_star), 1e-4),
                 r_primal=float(dg["r_primal"]), r_stat=float(dg["r_stat"]), r_comp=float(dg["r_comp"]),
@@ -62,8 +67,9 @@ def compare_all(workload, res, accounts=None, processes=None, **overrides):
     jobs = []
     for a in accounts:
         sl = batch.account_slice(a)
+        kap = res["kappa"][a].copy() if res.get("kappa") is not None else None
         jobs.append((key, a, res["w"][sl].copy(), float(res["nu"][a]), res["lambda_band"][a].copy(),
-                     float(res["theta"][a]), float(res["diag"][a][6]), float(res["diag"][a][7])))
+                     float(res["theta"][a]), float(res["diag"][a][6]), float(res["diag"][a][7]), kap))
     n = max(1, min(processes or _cores(), len(jobs)))
     ctx = mp.get_context("spawn")
     with ctx.Pool(n, initializer=_init) as pool:
