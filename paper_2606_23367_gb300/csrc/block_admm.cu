@@ -380,7 +380,8 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
     const bool has_cap = isfinite(A.tau[a]);
     while (ok) {
         const T irho = T(1) / rho;
-        // ---- X and P = B' X (factor-group layout: thread (g, k) sums over entries q = g mod G)
+        // ---- X and P = B' X
+#pragma unroll 4
         for (int q = tid; q < n; q += NT) {
             const int p = V.p(q);
             V.X[q] = (A.mu[p] + rho * V.z[q] - V.y[q]) / (T(2) * A.d[p] + rho);
@@ -388,14 +389,15 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
         __syncthreads();
         {
             // warp w takes entries w, w + NW, ...; lane l factors l and l + 32 of each row (the
-            // row's loads coalesced), four rows in flight per step
+            // row's loads coalesced), eight rows in flight per step
+            constexpr int RU = 8;
             const T* Bb = A.Bp ? A.Bp : A.B;
             const int ld = A.Bp ? KMAX : K;
             T a0 = 0, a1 = 0;
-            for (int q0 = warp; q0 < n; q0 += 4 * NW) {
-                T b0[4], b1[4], xv[4];
+            for (int q0 = warp; q0 < n; q0 += RU * NW) {
+                T b0[RU], b1[RU], xv[RU];
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
+                for (int u = 0; u < RU; ++u) {
                     const int q = q0 + u * NW;
                     const bool in = q < n;
                     const size_t row = in ? (size_t)V.p(q) * ld : 0;
@@ -404,7 +406,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
                     xv[u] = in ? V.X[q] : T(0);
                 }
 #pragma unroll
-                for (int u = 0; u < 4; ++u) { a0 += b0[u] * xv[u]; a1 += b1[u] * xv[u]; }
+                for (int u = 0; u < RU; ++u) { a0 += b0[u] * xv[u]; a1 += b1[u] * xv[u]; }
             }
             sh.part[warp][lane] = a0;
             sh.part[warp][lane + 32] = a1;
@@ -427,18 +429,24 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             }
             __syncthreads();
         }
-        if (tid == 0) {
+        if (warp == 0) {
+            // L L' Q = P by one warp, lane r holding rows r and r + 32: column-oriented
+            // substitutions (each solved value broadcast, the rows below updated in parallel)
+            T v0 = lane < K ? sh.P[lane] : T(0), v1 = lane + 32 < K ? sh.P[lane + 32] : T(0);
             for (int r = 0; r < K; ++r) {
-                T s = sh.P[r];
-                for (int q = 0; q < r; ++q) s -= sh.L[r][q] * sh.Q[q];
-                sh.Q[r] = s / sh.L[r][r];
+                const T xr = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) / sh.L[r][r];
+                if (lane == (r & 31)) { if (r < 32) v0 = xr; else v1 = xr; }
+                if (lane > r && lane < K) v0 -= sh.L[lane][r] * xr;
+                if (lane + 32 > r && lane + 32 < K) v1 -= sh.L[lane + 32][r] * xr;
             }
             for (int r = K - 1; r >= 0; --r) {
-                T s = sh.Q[r];
-                for (int q = r + 1; q < K; ++q) s -= sh.L[q][r] * sh.Q[q];
-                sh.Q[r] = s / sh.L[r][r];
+                const T xr = __shfl_sync(0xffffffffu, r < 32 ? v0 : v1, r & 31) / sh.L[r][r];
+                if (lane == (r & 31)) { if (r < 32) v0 = xr; else v1 = xr; }
+                if (lane < r) v0 -= sh.L[r][lane] * xr;
+                if (lane + 32 < r) v1 -= sh.L[r][lane + 32] * xr;
             }
-            if (fac) for (int r = 0; r < K; ++r) sh.Q[r] -= sh.tv[r];
+            if (lane < K) sh.Q[lane] = fac ? v0 - sh.tv[lane] : v0;
+            if (lane + 32 < K) sh.Q[lane + 32] = fac ? v1 - sh.tv[lane + 32] : v1;
         }
         __syncthreads();
         T rps = 0, rds = 0;
@@ -460,6 +468,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
         }
         // ---- x, the relaxation and v (v overwrites X); bracket of the projection's multipliers
         T ea = T(INFINITY), eb = T(-INFINITY);
+#pragma unroll 2
         for (int q = tid; q < n; q += NT) {
             const int p = V.p(q);
             const T bq = brow_dot(A, p, sh.Q);
