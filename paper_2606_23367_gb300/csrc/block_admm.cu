@@ -36,8 +36,17 @@ namespace prism {
 constexpr int BLK_ROOT_IT = 200;          // evaluations per scalar root (bisection alone needs ~110)
 
 template <typename T> struct BlkCfg;
-template <> struct BlkCfg<double> { static constexpr int THREADS = 256; static constexpr double EPS = 1e-15; };
-template <> struct BlkCfg<float> { static constexpr int THREADS = 512; static constexpr float EPS = 4e-7f; };
+// EPS: relative width at which a root's bracket is closed; FTOL: a function value (a budget,
+// band or turnover residual, all of order one) accepted as zero: the roots are solved to about the
+// rounding of the sums themselves (the polish settles the final point in FP64)
+template <> struct BlkCfg<double> {
+    static constexpr int THREADS = 256;
+    static constexpr double EPS = 1e-15, FTOL = 1e-13;
+};
+template <> struct BlkCfg<float> {
+    static constexpr int THREADS = 512;
+    static constexpr float EPS = 4e-7f, FTOL = 4e-6f;
+};
 
 template <typename T>
 struct BlkShared {
@@ -174,16 +183,16 @@ __device__ __forceinline__ T range_sum(const BlkArgs<T>& A, const View<T>& V, in
 template <typename T, class Eval>
 __device__ T root(T a, T ga, T b, T gb, Eval&& eval) {
     for (int it = 0; it < BLK_ROOT_IT; ++it) {
-        if (ga == T(0)) return a;
-        if (gb == T(0)) return b;
+        if (fabs(ga) <= BlkCfg<T>::FTOL) return a;
+        if (fabs(gb) <= BlkCfg<T>::FTOL) return b;
         const T w = b - a;
         if (!(w > BlkCfg<T>::EPS * fmax(T(1), fmax(fabs(a), fabs(b))))) break;
         T m = (it & 1) ? T(0.5) * (a + b) : a + w * ga / (ga - gb);
         if (!(m > a && m < b)) m = T(0.5) * (a + b);
         const T gm = eval(m);
+        if (fabs(gm) <= BlkCfg<T>::FTOL) return m;
         if (gm > T(0)) { a = m; ga = gm; }
-        else if (gm < T(0)) { b = m; gb = gm; }
-        else return m;
+        else { b = m; gb = gm; }
     }
     return (ga < -gb) ? a : b;
 }
@@ -195,7 +204,7 @@ template <typename T, class Eval>
 __device__ T root_warm(T lo, T hi, T x0, T step, Eval&& eval) {
     x0 = fmin(fmax(x0, lo), hi);
     const T g0 = eval(x0);
-    if (g0 == T(0)) return x0;
+    if (fabs(g0) <= BlkCfg<T>::FTOL) return x0;
     T a = x0, ga = g0;
     for (int k = 0; k < 80; ++k, step *= T(4)) {
         if (g0 > T(0)) {
