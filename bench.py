@@ -310,8 +310,10 @@ def adjoint_timing(stream, reps=5):
 OTHER_WORKLOADS = [
     (0, "1 account x 100 assets, K=10, 10 sector bands (PLAIN_FP64)", dict(precision=3), 1),
     (0, "1 account x 100 assets, K=10, 10 sector bands (PLAIN_FP32)", dict(precision=0), 1),
+    (2, "256 ragged accounts from 5,000 assets (100-5,000 names), K=32, dense-masked layout",
+     dict(precision=2, ragged_layout=1), 64),
     (2, "256 ragged accounts from 5,000 assets (100-5,000 names), K=32, packed layout",
-     dict(precision=2), 64),
+     dict(precision=2, ragged_layout=2), 64),
     (3, "200 accounts x 1,924 assets, K=48, tax lots, turnover cap 0.2", dict(precision=2), 32),
 ]
 
@@ -499,7 +501,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     if not args.no_autotune:
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
-        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm")}
+        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm", "g2_sets")}
         opts.update(tuned)
 
     if args.chains is not None:

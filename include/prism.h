@@ -155,8 +155,12 @@ typedef struct {
                                  universe (every product over all N positions, non-members pinned
                                  at 0); 2 = packed (each account's own names only, one persistent
                                  launch of per-account blocks with the account's own capacitance);
-                                 0 = packed when the accounts hold under half of the universe on
-                                 average (default 0) */
+                                 0 = dense-masked (the faster of the two on the workloads measured;
+                                 prism_autotune times both for a book) (default 0) */
+    int32_t g2_sets;          /* tile shape of the tensor-core product B'X: clusters of 8 CTAs per
+                                 128-account tile along the assets, each CTA summing an asset chunk
+                                 of N / (8 g2_sets) (rounded up to 64); 0 = about one CTA per SM
+                                 (default 0; searched by prism_autotune) */
 } prism_solve_opts;
 
 /* Fill *o with the defaults documented above. */
@@ -294,7 +298,8 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
  * before the streaming form (4 .. 10), the account chains (1, 2, 4) and the ADMM target
- * eps_admm (1e-4 .. 7e-4), starting
+ * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16)
+ * and, for books of ragged accounts, the layout (dense-masked or packed), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts
  * per second of device time; one that certifies fewer accounts never wins, and one that
  * certifies as many must be faster than the best so far by more than 1%. Writes the

@@ -8,7 +8,8 @@
 // over-relaxation alpha, then the graph chunk length, then the number of staged prox
 // iterations (fewer are cheaper, but the streaming form then misses its margin more often),
 // then the number of independent account chains, then the ADMM target before the polish
-// (a looser one saves iterations and costs polish rounds). A candidate's score is certified
+// (a looser one saves iterations and costs polish rounds), then the tile shape of the
+// tensor-core product B'X (its asset chunk per CTA) and, for ragged books, the layout. A candidate's score is certified
 // accounts per second of device time; a candidate that certifies fewer accounts than the
 // best so far never wins, and one that certifies as many must be faster by more than 1% (the
 // run-to-run spread of a trial). Each trial is a full prism_solve_batch with the caller's book, so
@@ -137,6 +138,24 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         prism_solve_opts c = best;
         c.eps_admm = eps;
         if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
+    if (o.precision == PRISM_BATCHED_BF16) {
+        // the tile shape of the tensor-core B'X: clusters of 8 CTAs per account tile (asset chunk)
+        for (int gs : {1, 2, 3, 4}) {
+            if (gs == best.g2_sets) continue;
+            prism_solve_opts c = best;
+            c.g2_sets = gs;
+            if ((rc = consider(c)) != PRISM_OK) return rc;
+        }
+    }
+    if (b->asset_idx) {
+        // ragged accounts: dense-masked over the universe against packed per-account blocks
+        for (int lay : {1, 2}) {
+            if (lay == best.ragged_layout || (lay == 1 && best.ragged_layout == 0)) continue;
+            prism_solve_opts c = best;
+            c.ragged_layout = lay;
+            if ((rc = consider(c)) != PRISM_OK) return rc;
+        }
     }
     *tuned = best;
     tuned->keep_for_backward = base ? base->keep_for_backward : 0;

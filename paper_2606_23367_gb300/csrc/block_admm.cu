@@ -65,6 +65,12 @@ struct BlkShared {
     int go, acct;
 };
 
+__device__ __forceinline__ unsigned long long blk_clock() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
 // One account's entries: index q = 0 .. n-1 in increasing position order; pos[q] its position
 // (null: q is the position), the per-entry arrays indexed by q.
 template <typename T>
@@ -233,6 +239,7 @@ __device__ void inner(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, i
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int S = A.S;
     auto Tf = [&](T eta) -> T {
+        if (A.dbg && tid == 0) atomicAdd(A.dbg + 7, 1ull);
         for (int s = warp; s < S; s += NW) {
             const T sm = range_sum(A, V, sh.sec[s], sh.sec[s + 1], eta, irho, theta, lane);
             if (lane == 0) sh.ssum[s] = fmin(fmax(sm, A.band_lo[a * S + s]), A.band_hi[a * S + s]);
@@ -249,7 +256,9 @@ __device__ void inner(const BlkArgs<T>& A, BlkShared<T>& sh, const View<T>& V, i
         return r;
     };
     const T nu_prev = sh.nu;
-    const T step = fmax(T(4) * sh.dnu, BlkCfg<T>::EPS * T(1e3) * fmax(T(1), fabs(nu_prev)));
+    // (at least 1e-4 of the multiplier's scale: a step at the rounding level would take many
+    // growth steps to reach a move of ordinary size)
+    const T step = fmax(T(4) * sh.dnu, T(1e-4) * fmax(T(1), fabs(nu_prev)));
     const T nu = root_warm(eta_a, eta_b, nu_prev, step, Tf);
     // each sector held at an edge gets its own point (warp-local roots, no block barriers)
     for (int s = warp; s < S; s += NW) {
@@ -387,6 +396,15 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
     int status = 0;
     T theta = sh.theta;
     const bool has_cap = isfinite(A.tau[a]);
+    unsigned long long tmark = 0;
+    auto mark = [&](int slot) {
+        if (A.dbg && tid == 0) {
+            const unsigned long long t = blk_clock();
+            if (slot >= 0) atomicAdd(A.dbg + slot, t - tmark);
+            tmark = t;
+        }
+    };
+    mark(-1);
     while (ok) {
         const T irho = T(1) / rho;
         // ---- X and P = B' X
@@ -427,6 +445,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             }
             __syncthreads();
         }
+        mark(0);                                     // X and B'X
         // ---- Q = C^{-1} P (one thread: K^2 work); with the factor block Q' = C^{-1}(P0 + G tv) - tv
         if (fac) {
             for (int k = tid; k < K; k += NT) { sh.tv[k] = rho * sh.s[k] - sh.ys[k]; sh.P0[k] = sh.P[k]; }
@@ -475,6 +494,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             __syncthreads();
             for (int k = tid; k < K; k += NT) sh.s[k] = sh.tv[k];
         }
+        mark(1);                                     // the small solve
         // ---- x, the relaxation and v (v overwrites X); bracket of the projection's multipliers
         T ea = T(INFINITY), eb = T(-INFINITY);
 #pragma unroll 2
@@ -510,6 +530,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
         const T pad = has_cap ? T(1) : T(0);
         const T eta_a = sh.red[0][2] - T(1), eta_b = sh.red[0][3] + T(1);
         __syncthreads();
+        mark(2);                                     // x-update and bracket
         // ---- projection: the cap multiplier theta by an outer root when the cap binds
         T th = 0;
         if (has_cap) {
@@ -536,6 +557,7 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             theta = th;
         }
         inner(A, sh, V, a, th, eta_a - th - pad, eta_b + th + pad, irho);
+        mark(3);                                     // the projection's roots
         // ---- z+, y+ and the residuals
         T rp = 0, rd = 0, nx = 0, nz = 0, ny = 0;
         int bad = 0;
@@ -590,11 +612,14 @@ __device__ void solve_account(const BlkArgs<T>& A, BlkShared<T>& sh, const View<
             sh.rho = newrho;
         }
         __syncthreads();
+        mark(4);                                     // z, y, residuals and control
+        if (A.dbg && tid == 0) atomicAdd(A.dbg + 6, 1ull);
         if (!sh.go) break;
         if (sh.rho != rho) {
             rho = sh.rho;
             ok = factor(A, sh, V, rho);
             if (!ok && tid == 0) status = PRISM_NUMERICAL_FAILURE;
+            mark(5);                                 // capacitance at a new penalty
         }
     }
     if (!ok) status = PRISM_NUMERICAL_FAILURE;

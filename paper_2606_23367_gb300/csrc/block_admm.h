@@ -48,6 +48,7 @@ struct BlkArgs {
     int max_iter = 4000, min_iter = 20, adapt_every = 25;
     int resume = 0;                     // 1: continue from the state (a tighter second pass)
     int stage_cap = 0;                  // packed accounts of at most this many names live in shared memory
+    unsigned long long* dbg = nullptr;  // diagnostics (PRISM_DEBUG_STATS): ns per phase, evaluations
 };
 
 template <typename T>

@@ -543,13 +543,12 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     // ---- ragged books in the batched modes: dense-masked, or packed (each account's own names)
     bool packed = false;
     if (b->asset_idx && !plain) {
-        if (o->ragged_layout == 2) packed = true;
-        else if (o->ragged_layout == 0) packed = (double)nnz < 0.5 * (double)M * (double)N;
+        packed = o->ragged_layout == 2;
     }
     // ---- workspace layout
     const size_t MN = (size_t)M * Npad;
     int tc_chunk = 0;
-    const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk) : choose_nsplit(M, N);
+    const int nsplit = batched_mode_bf16 ? tc_nsplit(M, N, &tc_chunk, o->g2_sets) : choose_nsplit(M, N);
     const int FMAX = std::min(N, 2048);
     int* dsel = nullptr;               // device copy of SC.hsel (polish batches)
     BlkArgs<double> P64;               // PLAIN_FP64: the FP64 per-account kernel's arguments
@@ -581,7 +580,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.rho_idx = A.take<int>(M); D.iters = A.take<int>(M); D.active = A.take<int>(M); D.status = A.take<int>(M);
         D.nu = A.take<float>(M); D.dnu = A.take<float>(M); D.eta_hi = A.take<float>((size_t)M * S); D.eta_lo = A.take<float>((size_t)M * S);
         D.theta = A.take<float>(M); D.rp = A.take<float>(M); D.rd = A.take<float>(M); D.n_active = A.take<int>(2);
-        D.stats = A.take<unsigned long long>(4);
+        D.stats = A.take<unsigned long long>(8);
         // partials of the fused pass (tensor-core mode)
         const int nt = cdiv(N, 128);
         D.SOp = A.take<float>((size_t)U.nseg * M);
@@ -846,6 +845,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && o->fuse_prox) ? 1 : 0;
     D.nq = U.nq; D.nseg = U.nseg; D.nt = cdiv(N, 128); D.qseg = U.d_qseg; D.sseg = U.d_sseg;
     D.nsplit = nsplit;
+    D.g2_sets = batched_mode_bf16 ? o->g2_sets : 0;
     D.pstride = batched_mode_bf16 ? KMAX : K;
     D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
     D.adapt_every = 25;
@@ -1110,6 +1110,20 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         PK.resume = 0;
         SC.prof.run(PRISM_K_BLOCK, 1, st, [&] { launch_block_admm(PK, blk_grid(PK), st); });
     }
+    if ((fp64 || packed) && D.stats) {
+        // diagnostics: ns per phase summed over accounts, iterations, projection evaluations
+        unsigned long long h[8] = {};
+        BlkArgs<float> DP = PK;
+        BlkArgs<double> D64 = P64;
+        cudaMemsetAsync(D.stats, 0, 64, st);
+        if (packed) { DP.dbg = D.stats; launch_block_admm(DP, blk_grid(DP), st); }
+        else { D64.dbg = D.stats; launch_block_admm(D64, blk_grid(D64), st); }
+        cudaMemcpyAsync(h, D.stats, 64, cudaMemcpyDeviceToHost, st);
+        cudaStreamSynchronize(st);
+        std::fprintf(stderr, "prism block stats: iterations %llu, ns: X+B'X %llu, solve %llu, x-update %llu, roots %llu, "
+                     "z/y %llu, factor %llu; evaluations per iteration %.1f\n", h[6], h[0], h[1], h[2], h[3], h[4], h[5],
+                     h[6] ? double(h[7]) / h[6] : 0.0);
+    }
     for (int it = 0; it < cold; ++it) {
         SC.prof.run(PRISM_K_GEMM_P, 1, st, [&] { if (D.bf16) launch_tc_gemm_P(D, st); else launch_gemm_P(D, st); });
         SC.prof.run(PRISM_K_SOLVE_K, 1, st, [&] { launch_small_solve(D, st); });
@@ -1302,7 +1316,8 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     if (!res->w || !res->status) { set_error("result w and status are required"); return PRISM_ERR_ARGUMENT; }
     if (b->lot_offsets && (!b->lot_size || !b->lot_kappa)) { set_error("lot arrays incomplete"); return PRISM_ERR_ARGUMENT; }
     if (!(o.eps_kkt > 0) || !(o.eps_admm > 0) || !(o.rho0 > 0) || !(o.alpha > 0 && o.alpha < 2) ||
-        o.max_iter < 1 || o.check_every < 1) {
+        o.max_iter < 1 || o.check_every < 1 || o.g2_sets < 0 || o.g2_sets > 64 || o.ragged_layout < 0 ||
+        o.ragged_layout > 2) {
         set_error("invalid options");
         return PRISM_ERR_ARGUMENT;
     }

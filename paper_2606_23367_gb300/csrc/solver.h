@@ -44,6 +44,7 @@ struct Dev {
     __nv_bfloat16* Qhi = nullptr;       // M x 64 split of Q (factors zero-padded)
     __nv_bfloat16* Qlo = nullptr;
     int nsplit = 1;
+    int g2_sets = 0;                    // tile shape of the tensor-core G2 (0 = automatic)
     // per-account control
     int* rho_idx = nullptr;
     int* iters = nullptr;
@@ -118,7 +119,7 @@ int choose_nsplit(int M, int N);
 
 // tensor-core products (tc_gemm.cu)
 bool tc_available();                                     // tensor-map encoder reachable
-int tc_nsplit(int M, int N, int* chunk);                 // partial sets of the tensor-core G2 (its asset chunk)
+int tc_nsplit(int M, int N, int* chunk, int sets = 0);   // partial sets of the tensor-core G2 (its asset chunk)
 void launch_tc_gemm_P(const Dev& D, cudaStream_t st, bool pdl = false);    // G2 on tcgen05
 void launch_tc_gemm_x(const Dev& D, cudaStream_t st);    // G4 on tcgen05 with fused epilogue
 void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl = false);     // G4 + the streaming pass of G5 (fused)

@@ -841,10 +841,11 @@ static bool map2d_f32(CUtensorMap* m, const void* base, uint64_t npad, uint64_t 
 
 bool tc_available() { return tc::encoder() != nullptr; }
 
-int tc_nsplit(int M, int N, int* chunk_out) {
-    // about one CTA per SM: G2_CL splits per cluster, nsets clusters per account tile
+int tc_nsplit(int M, int N, int* chunk_out, int sets) {
+    // about one CTA per SM: G2_CL splits per cluster, nsets clusters per account tile (or the
+    // caller's tile shape)
     const int mtiles = cdiv(M, tc::TM);
-    int nsets = std::max(1, int(std::lround(152.0 / double(mtiles * tc::G2_CL))));
+    int nsets = sets > 0 ? sets : std::max(1, int(std::lround(152.0 / double(mtiles * tc::G2_CL))));
     nsets = std::min(nsets, std::max(1, cdiv(cdiv(N, tc::TK), tc::G2_CL)));
     const int ns = nsets * tc::G2_CL;
     *chunk_out = std::max(tc::TK, cdiv(cdiv(N, ns), tc::TK) * tc::TK);
@@ -858,7 +859,7 @@ void launch_tc_gemm_P(const Dev& D, cudaStream_t st, bool pdl) {
               tc::map2d(&mBt, D.Bt16p, D.Npad, tc::KP, (uint64_t)D.Npad * 2, tc::TK, tc::KP);
     if (!ok) { set_error("tensor map encoding failed (G2)"); return; }
     int chunk = 0;
-    const int nsets = tc_nsplit(D.M, D.N, &chunk);
+    const int nsets = tc_nsplit(D.M, D.N, &chunk, D.g2_sets);
     const size_t smem = sizeof(tc::G2Smem) + 1024;
     cudaFuncSetAttribute(tc::k_tc_gemm_P, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};

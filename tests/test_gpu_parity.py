@@ -168,3 +168,15 @@ def test_account_chains_do_not_change_results():
     assert np.array_equal(res[1]["w"], res[2]["w"]) and np.array_equal(res[1]["w"], res[4]["w"])
     assert np.array_equal(res[1]["iters"], res[4]["iters"])
     assert_parity(uni, batch, res[4], accounts=[0, 200, 519])
+
+
+@pytest.mark.parametrize("sets", [1, 2, 4])
+def test_g2_tile_shapes_keep_parity(sets):
+    # the tile shape the autotuner searches (asset chunk per CTA of the tensor-core B'X): every
+    # shape is the same product summed in another order, so the polished weights agree
+    uni, batch = make_workload(1, N=1200, K=64, M=130)
+    ref = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, g2_sets=sets)
+    assert np.all(res["status"] == prism.PRISM_CERTIFIED)
+    assert float(np.max(np.abs(res["w"] - ref["w"]))) <= 1e-9
+    assert_parity(uni, batch, res, accounts=[0, 129])
