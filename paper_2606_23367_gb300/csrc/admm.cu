@@ -346,13 +346,22 @@ struct EntryEval {
     int lin;   // 1 when dz/deta = -1/rho (z strictly inside a linear piece)
 };
 
-// per-entry data of one account, from global memory
+// per-entry data of one account, from global memory. After the fused streaming pass, which
+// writes v only for its candidates, cm holds the account's candidate masks: an entry pinned at
+// its lower bound has y = rho (v - l) just written, so v = l + y / rho.
 struct GlobalSrc {
     const float *v, *w0, *lo, *up, *c;
     const int* pw;
+    const unsigned* cm = nullptr;
+    const float* yv = nullptr;
+    float irho = 0.f;
     __device__ __forceinline__ GlobalSrc(const Dev& D, size_t base)
         : v(D.v + base), w0(D.w0 + base), lo(D.lo + base), up(D.up + base), c(D.c + base),
           pw(D.pw_idx ? D.pw_idx + base : nullptr) {}
+    __device__ __forceinline__ float val(int p) const {
+        if (cm && !((cm[p >> 5] >> (p & 31)) & 1u)) return lo[p] + yv[p] * irho;
+        return v[p];
+    }
 };
 
 // z_i(eta) for one entry: prox of (phi_i + theta|.-w0|)/rho on [l, u] at t = v - eta/rho.
@@ -360,7 +369,7 @@ template <class Src>
 __device__ __forceinline__ EntryEval eval_entry(const Dev& D, const Src& S, int p, float eta, float theta,
                                                 float irho) {
     EntryEval r;
-    const float t = S.v[p] - eta * irho;
+    const float t = S.val(p) - eta * irho;
     const float w0 = S.w0[p], lo = S.lo[p], up = S.up[p];
     const int pw = S.pw ? S.pw[p] : -1;
     if (pw < 0) {
@@ -630,7 +639,7 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
                 const int p = pb + 32 * c;
                 if (p >= p1) break;
                 const size_t e = base + p;
-                const float vv = S.v[p];
+                const float vv = S.val(p);
                 const EntryEval r = eval_entry(D, S, p, arg, theta, irho);
                 const float yn = rho * (vv - r.z);
                 rp = fmaxf(rp, fabsf(yn - yo[c]) * irho);
@@ -715,6 +724,7 @@ __global__ void __launch_bounds__(640, 1) k_prox(Dev D) {
 struct SmemSrc {
     const float *v, *w0, *lo, *up, *c;
     const int* pw;
+    __device__ __forceinline__ float val(int p) const { return v[p]; }
 };
 
 __global__ void __launch_bounds__(640, 1) k_prox_smem(Dev D) {
@@ -1109,7 +1119,7 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
             if (mask && !sec_redo && !((mask[p >> 5] >> (p & 31)) & 1u)) continue;   // written by the pass
             const float z = eval_entry(D, G, p, arg, 0.f, irho).z;
             const size_t e = base + p;
-            res.put(D, e, z, G.v[p], D.z[e], D.y[e], D.mu32[p], D.d32[p], rho, irho);
+            res.put(D, e, z, G.val(p), D.z[e], D.y[e], D.mu32[p], D.d32[p], rho, irho);
         }
     }
     if (mask) {
@@ -1322,12 +1332,16 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
     for (int s = tid; s < NS; s += blockDim.x) { sh.wh[s] = D.eta_hi[a * NS + s]; sh.wl[s] = D.eta_lo[a * NS + s]; }
     if (tid == 0) sh.it0 = D.iters[a];
     const size_t base = (size_t)a * D.Npad;
-    const GlobalSrc G(D, base);
+    GlobalSrc G(D, base);
     const int j = D.rho_idx[a];
     const float rho = rho_val(j), irho = 1.f / rho;
     const float nu0 = D.nu[a];
     const float margin = fmaxf(4.f * D.dnu[a], 2e-3f);
     const float L = nu0 - margin;
+    // the fused pass wrote v only for its candidates: a pinned entry's v comes from its new y
+    G.cm = R.mask;
+    G.yv = D.y + base;
+    G.irho = irho;
     pdl_wait();                            // the masks, residuals and records of the fused pass
     pdl_trigger();
     // candidate masks and their exclusive prefix counts (four quarters per thread)

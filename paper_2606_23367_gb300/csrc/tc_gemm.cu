@@ -611,9 +611,11 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
         // a non-finite pinned update makes rp NaN (reported as a numerical failure)
         const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
         const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
-        if (ok) D.v[off] = v;
+        // v of a pinned entry is not stored: it is l + y / rho from the y written below, which is
+        // all a later recomputation of its sector needs; z is stored only when it changes
+        if (cand) D.v[off] = v;
         if (pin) {
-            D.z[off] = lo;
+            if (z0 != lo) D.z[off] = lo;
             D.y[off] = yn;
             const float X = (ax.mu + rho * lo - yn) * inv;
             const __nv_bfloat16 h = __float2bfloat16_rn(X);
