@@ -31,6 +31,12 @@ sys.path.insert(0, ROOT)
 METRIC = "accounts/s at KKT res<=1e-6, 500 accts x 10k assets; batched-BF16 vs plain FP32"
 WORKLOAD = "500 accounts x 10,000 assets, K=64, 20 sector bands, L1 turnover (seeded synthetic)"
 M_ACCOUNTS = 500
+WORKLOADS_DESC = {
+    0: "1 account x 100 assets, K=10, 10 sector bands (seeded synthetic)",
+    2: "256 ragged accounts from 5,000 assets (100-5,000 names), K=32 (seeded synthetic)",
+    3: "200 accounts x 1,924 assets, K=48, tax lots, turnover cap 0.2 (seeded synthetic)",
+    4: "128 accounts x 2,000 assets, K=32 (seeded synthetic)",
+}
 
 # Algorithmic bytes per account-entry and iteration of the method: read z and y, write z and
 # y (16 B, FP32), read the per-entry constants w0 and u (8 B; l and c are per-account constants
@@ -469,7 +475,13 @@ def run_gpu(args, dist, rank, world, local_rank):
     build.build()
     prism.load_library()
     precision = {"bf16": prism.PRISM_BATCHED_BF16, "fp32": prism.PRISM_BATCHED_FP32}[args.precision]
-    uni, batch = make_workload(1, first_account=shard_first_account(rank), M=M_ACCOUNTS)
+    if args.workload == 1:
+        uni, batch = make_workload(1, first_account=shard_first_account(rank), M=M_ACCOUNTS)
+    else:
+        # another workload at its own size (profiling and comparisons; the headline is workload 1)
+        from paper_2606_23367_gb300.workloads import WORKLOADS
+        m_w = WORKLOADS[args.workload]["M"]
+        uni, batch = make_workload(args.workload, first_account=rank * m_w)
     M, S = batch.n_accounts, uni.n_sectors
     nnz = int(batch.offsets[-1])
     dev = torch.device("cuda", local_rank)
@@ -497,6 +509,8 @@ def run_gpu(args, dist, rank, world, local_rank):
                     diag=mk(M, prism.PRISM_NDIAG))
 
     opts = dict(precision=precision, cuda_stream=stream.cuda_stream)
+    if args.ragged_layout is not None:
+        opts["ragged_layout"] = args.ragged_layout
     tuned = None
     if not args.no_autotune:
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
@@ -689,7 +703,8 @@ def run_gpu(args, dist, rank, world, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "bf16-products/f32-iterations/f64-polish" if args.precision == "bf16"
         else "f32-iterations/f64-polish", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "accounts_per_gpu": M, "assets": N, "factors": uni.n_factors,
+        "config": {"workload": WORKLOAD if args.workload == 1 else WORKLOADS_DESC[args.workload],
+                   "accounts_per_gpu": M, "assets": N, "factors": uni.n_factors,
                    "precision": "BATCHED_BF16" if args.precision == "bf16" else "BATCHED_FP32",
                    "l2": "inputs larger than L2 (160 MB of FP64 account data per step)",
                    "parallelism": f"accounts sharded over {world} GPU(s), no collective",
@@ -734,6 +749,10 @@ def main():
                     "(overrides the schedule; 1 = one range, as in the profile pass)")
     ap.add_argument("--no-adjoint", action="store_true", help="skip the forward/backward timing of the "
                     "differentiation workload")
+    ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4],
+                    help="the book the GPU arm times (default 1, the headline; the others for profiling)")
+    ap.add_argument("--ragged-layout", type=int, default=None, choices=[1, 2],
+                    help="ragged books: 1 dense-masked, 2 packed per-account blocks")
     ap.add_argument("--no-others", action="store_true", help="skip the lines of the other workloads "
                     "(single account, ragged, tax-aware)")
     ap.add_argument("--no-queue", action="store_true", help="skip the production-queue and constraint-burden "
