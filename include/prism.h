@@ -297,7 +297,7 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * picks the iteration schedule for a book by timing trial solves of that book on this GPU.
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
- * before the streaming form (4 .. 10), the account chains (1, 2, 4) and the ADMM target
+ * before the streaming form (2 .. 10), the account chains (1, 2, 4) and the ADMM target
  * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16)
  * and, for books of ragged accounts, the layout (dense-masked or packed), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts

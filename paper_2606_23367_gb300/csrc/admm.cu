@@ -583,7 +583,7 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
     const float tau = D.tau ? D.tau[a] : INFINITY;
     if (tau < INFINITY) {
         const float U = turnover_at(D, S, nu, 0.f, irho, sh);
-        if (U > tau * (1.f + 1e-6f)) {
+        if (U > tau * (1.f + 1e-5f)) {
             // bracketed secant (Illinois) on U(theta) - tau, U nonincreasing in theta
             float t_lo = 0.f, u_lo = U - tau;
             float t_hi = fmaxf(D.theta[a], 1e-4f), u_hi = 0.f;
@@ -602,7 +602,9 @@ __device__ void prox_account(const Dev& D, const Src& S, int a, ProxShared& sh) 
                 nu = project_inner(D, S, a, tn, rho, irho, nu, sh);
                 const float un = turnover_at(D, S, nu, tn, irho, sh) - tau;
                 theta = tn;
-                if (fabsf(un) <= 2e-7f * tau || (t_hi - t_lo) <= 1e-7f * t_hi) break;
+                // (the turnover is an FP32 sum of up to N terms: 1e-5 of tau is about its rounding,
+                // and the polish settles the final point in FP64)
+                if (fabsf(un) <= 1e-5f * tau || (t_hi - t_lo) <= 1e-7f * t_hi) break;
                 if (un > 0.f) {
                     t_lo = tn; u_lo = un;
                     if (side == -1) u_hi *= 0.5f;

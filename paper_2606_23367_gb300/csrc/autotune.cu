@@ -121,7 +121,7 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         c.check_every = ce;
         if ((rc = consider(c)) != PRISM_OK) return rc;
     }
-    for (int sa : {4, 6, 8, 10}) {
+    for (int sa : {2, 4, 6, 8, 10}) {
         if (sa == best.stream_after) continue;
         prism_solve_opts c = best;
         c.stream_after = sa;

@@ -459,8 +459,8 @@ __device__ __noinline__ bool factor32(const PolDev& P, PolishShared& sh, const F
 // so ||w - w*||_2 <= (||r||_2 + sqrt(||r||_2^2 + 4 m C)) / (2 m). This holds for a point
 // that meets the constraints; the primal residuals reported beside it say by how much
 // the returned point misses them (to FP64 rounding for a certified account).
-__device__ double err_bound(const PolDev& P, const PolishShared& sh, double r2, double sw, double tu, double tau,
-                            double nu, double theta) {
+__device__ __noinline__ double err_bound(const PolDev& P, const PolishShared& sh, double r2, double sw, double tu,
+                                         double tau, double nu, double theta) {
     const double m = 2.0 * P.dmin;
     if (!(m > 0.0)) return INFINITY;
     double wrong = 0.0, C = fabs(nu) * fabs(sw - 1.0);
@@ -493,7 +493,46 @@ __device__ double err_bound(const PolDev& P, const PolishShared& sh, double r2, 
     return (re + sqrt(re * re + 4.0 * m * C)) / (2.0 * m);
 }
 
-__global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
+// The factor-exposure rows' checks of one account (thread 0), like the bands': a row outside the
+// working set joins it when violated; a working row leaves it when its multiplier has the wrong
+// sign, or, found dependent on the free set, when it holds strictly inside its bounds.
+__device__ __noinline__ void factor_row_checks(const PolDev& P, PolishShared& sh, int a, int m, double tol_p,
+                                               double tol_d, double& r_exp, double& r_comp, int& bviol, int& dep_in,
+                                               int& dep_out) {
+    const int K = P.K, S = P.S;
+    auto row_dependent = [&](int row) {
+        for (int r = 1; r < m; ++r)
+            if (sh.rows[r] == row) return sh.used[r] == 0;
+        return false;
+    };
+    for (int k = 0; k < K; ++k) {
+        const double hk = sh.t64[k], hi = sh.fhi_s[k], lo = sh.flo_s[k];
+        r_exp = fmax(r_exp, fmax(lo - hk, hk - hi));
+        const int wf = sh.wf_s[k];
+        const double kk = sh.kap_s[k];
+        const bool off = wf != 0 && fabs(hk - (wf > 0 ? hi : lo)) > tol_p;
+        auto set_wf = [&](int v) { sh.wf_s[k] = v; P.wfac[a * K + k] = v; };
+        if (off && row_dependent(S + 1 + k)) {
+            ++bviol;
+            if (wf > 0 ? hk < hi : hk > lo) { set_wf(0); ++dep_in; }
+            else ++dep_out;
+        } else if (wf == 0) {
+            if (hk > hi + tol_p) { ++bviol; set_wf(1); }
+            else if (hk < lo - tol_p) { ++bviol; set_wf(-1); }
+        } else {
+            if (off) ++bviol;
+            if (wf > 0) {
+                r_comp = fmax(r_comp, fabs(kk) * fabs(hi - hk));
+                if (kk < -tol_d) { ++bviol; r_comp = fmax(r_comp, -kk); set_wf(0); }
+            } else {
+                r_comp = fmax(r_comp, fabs(kk) * fabs(hk - lo));
+                if (kk > tol_d) { ++bviol; r_comp = fmax(r_comp, kk); set_wf(0); }
+            }
+        }
+    }
+}
+
+__global__ void __launch_bounds__(PB, 2) k_polish(PolDev P, int rounds) {   // two blocks per SM
     const int a = blockIdx.x;
     if ((P.skip && P.skip[a]) || P.done[a] || (P.sel && P.sel[a] != P.gen)) return;
     extern __shared__ unsigned char smem_raw[];
@@ -1127,31 +1166,7 @@ __global__ void __launch_bounds__(PB) k_polish(PolDev P, int rounds) {
                 }
             }
             // factor rows: exposures h = B'w against their bounds, like the bands
-            for (int k = 0; k < K && P.flo; ++k) {
-                const double hk = sh.t64[k], hi = sh.fhi_s[k], lo = sh.flo_s[k];
-                r_exp = fmax(r_exp, fmax(lo - hk, hk - hi));
-                const int wf = sh.wf_s[k];
-                const double kk = sh.kap_s[k];
-                const bool off = wf != 0 && fabs(hk - (wf > 0 ? hi : lo)) > tol_p;
-                auto set_wf = [&](int v) { sh.wf_s[k] = v; P.wfac[a * K + k] = v; };
-                if (off && row_dependent(S + 1 + k)) {
-                    ++bviol;
-                    if (wf > 0 ? hk < hi : hk > lo) { set_wf(0); ++dep_in; }
-                    else ++dep_out;
-                } else if (wf == 0) {
-                    if (hk > hi + tol_p) { ++bviol; set_wf(1); }
-                    else if (hk < lo - tol_p) { ++bviol; set_wf(-1); }
-                } else {
-                    if (off) ++bviol;
-                    if (wf > 0) {
-                        r_comp = fmax(r_comp, fabs(kk) * fabs(hi - hk));
-                        if (kk < -tol_d) { ++bviol; r_comp = fmax(r_comp, -kk); set_wf(0); }
-                    } else {
-                        r_comp = fmax(r_comp, fabs(kk) * fabs(hk - lo));
-                        if (kk > tol_d) { ++bviol; r_comp = fmax(r_comp, kk); set_wf(0); }
-                    }
-                }
-            }
+            if (P.flo) factor_row_checks(P, sh, a, m, tol_p, tol_d, r_exp, r_comp, bviol, dep_in, dep_out);
             const double r_budget = fabs(sw - 1.0);
             if (r_budget > tol_p) ++bviol;
             const int total = int(nv) + bviol;
