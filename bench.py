@@ -493,11 +493,14 @@ def run_gpu(args, dist, rank, world, local_rank):
         return t.to(dev) if where == "dev" else t.pin_memory()
 
     def inputs(where):
+        opt = lambda x, dt: None if x is None else tens(x, dt, where)
         return dict(offsets=tens(batch.offsets, torch.int64, where), w0=tens(batch.w0, torch.float64, where),
                     lower=tens(batch.lower, torch.float64, where), upper=tens(batch.upper, torch.float64, where),
                     tc=tens(batch.tc, torch.float64, where), band_lo=tens(batch.band_lo, torch.float64, where),
                     band_hi=tens(batch.band_hi, torch.float64, where),
-                    turnover_cap=tens(batch.turnover_cap, torch.float64, where))
+                    turnover_cap=tens(batch.turnover_cap, torch.float64, where),
+                    asset_idx=opt(batch.asset_idx, torch.int32), lot_offsets=opt(batch.lot_offsets, torch.int64),
+                    lot_size=opt(batch.lot_size, torch.float64), lot_kappa=opt(batch.lot_kappa, torch.float64))
 
     def outputs(where):
         mk = (lambda *s, dt=torch.float64: torch.zeros(*s, dtype=dt, device=dev)) if where == "dev" else \
@@ -524,9 +527,7 @@ def run_gpu(args, dist, rank, world, local_rank):
             tuned["chains"] = args.chains
 
     def step(inp, out, **extra):
-        return prism.prism_solve_batch(h, inp["offsets"], inp["w0"], inp["lower"], inp["upper"], inp["tc"],
-                                       inp["band_lo"], inp["band_hi"], turnover_cap=inp["turnover_cap"],
-                                       out=out, **opts, **extra)
+        return prism.prism_solve_batch(h, **inp, out=out, **opts, **extra)
 
     def barrier():
         if dist is not None:
@@ -597,7 +598,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     ms_e2e, cert_e2e, _ = timed(hin, hout, args.steps)
     ms_e2e = max_over_ranks(ms_e2e)
     e2e_value = sum_over_ranks(cert_e2e) / (ms_e2e / 1000.0)
-    h2d = sum(t.numel() * t.element_size() for t in hin.values())
+    h2d = sum(t.numel() * t.element_size() for t in hin.values() if t is not None)
     d2h = sum(t.numel() * t.element_size() for t in hout.values())
     # ---- per-kernel profile pass (CUDA events around every launch on the solve stream)
     prof = step(din, dout, profile=1)
@@ -648,15 +649,17 @@ def run_gpu(args, dist, rank, world, local_rank):
     # ---- plain FP32 single-account form (same GPU, one account per call), in the same lane as
     # value: device-resident inputs, device time of each call from the library's CUDA events
     plain = None
-    if rank == 0 and args.plain_sample > 0:
+    if rank == 0 and args.plain_sample > 0 and batch.lot_offsets is None:
         np_ = min(args.plain_sample, M)
         e1 = int(batch.offsets[np_])
-        sub_in = {k: (v[: np_ + 1] if k == "offsets" else v[:e1] if k in ("w0", "lower", "upper", "tc")
-                      else v[:np_]) for k, v in din.items()}
+        sub_in = {k: (None if v is None else v[: np_ + 1] if k == "offsets"
+                      else v[:e1] if k in ("w0", "lower", "upper", "tc", "asset_idx") else v[:np_])
+                  for k, v in din.items() if not k.startswith("lot_")}
         sub_out = {k: (v[:e1] if k == "w" else v[:np_]) for k, v in dout.items()}
         stp = lambda: prism.prism_solve_batch(h, sub_in["offsets"], sub_in["w0"], sub_in["lower"],
                                               sub_in["upper"], sub_in["tc"], sub_in["band_lo"],
                                               sub_in["band_hi"], turnover_cap=sub_in["turnover_cap"],
+                                              asset_idx=sub_in["asset_idx"],
                                               out=sub_out, precision=prism.PRISM_PLAIN_FP32,
                                               cuda_stream=stream.cuda_stream)
         stp()
