@@ -49,7 +49,8 @@ METHOD_BYTES = 24
 #   prox   : read v, z, y and w0, l, u, c (28 B); write z, y and X (12 B)
 #   xprox  : the x-update fused with the streaming pass of the prox: the method's 24 B (read z,
 #            y, w0, u; write z, y); v (4 B) and the split X (4 B) are reported as overhead
-ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": METHOD_BYTES}
+#   block  : the per-account kernel (every iteration of an account in one block): the method's 24 B
+ALG_BYTES = {"gemm_P": 4, "gemm_x": 12, "prox": 40, "xprox": METHOD_BYTES, "block": METHOD_BYTES}
 OVERHEAD_BYTES = {"xprox": 8}
 
 
@@ -607,8 +608,9 @@ def run_gpu(args, dist, rank, world, local_rank):
     it_sum = int(dout["iters"].cpu().numpy().sum())
     N = uni.n_assets
     ix = names.index("xprox")
-    step_ms = {n: kms[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
-    n_launch = {n: kl[names.index(n)] for n in ("gemm_P", "gemm_x", "prox", "xprox")}
+    classes = ("gemm_P", "gemm_x", "prox", "xprox", "block")
+    step_ms = {n: kms[names.index(n)] for n in classes}
+    n_launch = {n: kl[names.index(n)] for n in classes}
     # account-entries per launch of each class: the staged prox of the fused schedule runs only
     # the first iterations, over every account; without the fused form it runs every iteration
     # of the accounts still iterating
@@ -617,6 +619,11 @@ def run_gpu(args, dist, rank, world, local_rank):
            "prox": M * N if fused else N * it_sum / max(1, n_launch["prox"])}
     if fused:
         ent["xprox"] = prof["stream_entries"] / kl[ix]
+    if n_launch["block"] > 0:
+        # the per-account kernel runs every iteration of its accounts in one launch: the
+        # account's own names times its iterations
+        own = np.diff(batch.offsets).astype(np.float64)
+        ent["block"] = float((own * iters).sum()) / n_launch["block"]
     alg = {n: ALG_BYTES[n] * ent[n] for n in ent}
     dom = max(step_ms, key=lambda n: step_ms[n])
     avg_ms = step_ms[dom] / max(1, n_launch[dom])
@@ -628,7 +635,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
     kernel_of = {"gemm_P": "k_tc_gemm_P", "gemm_x": "k_tc_gemm_x", "prox": "k_prox_stream / k_prox_smem",
-                 "xprox": "k_tc_xprox"}
+                 "xprox": "k_tc_xprox", "block": "k_block_admm"}
     # the whole iteration: the method's bytes of every account-iteration of the step over the
     # step's device time (setup, polish and certification included in the time)
     iter_bytes = METHOD_BYTES * N * float(iters.sum())

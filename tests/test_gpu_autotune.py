@@ -24,9 +24,11 @@ def test_autotune_schedule_is_valid_and_certifies():
         assert tuned["rho0"] in (0.5, 1.0, 2.0, 3.0, 5.0, 8.0)
         assert tuned["alpha"] in (1.4, 1.5, 1.6, 1.7, 1.8)
         assert tuned["check_every"] in (5, 10, 20)
-        assert tuned["stream_after"] in (4, 6, 8, 10)
+        assert tuned["stream_after"] in (2, 4, 6, 8, 10)
         assert tuned["eps_admm"] in (1e-4, 2e-4, 3e-4, 5e-4, 7e-4)
         assert tuned["chains"] in (0, 1, 2, 4)
+        assert tuned["g2_sets"] in (0, 1, 2, 3, 4)
+        assert tuned["ragged_layout"] in (0, 1, 2)
         assert tuned["precision"] == prism.PRISM_BATCHED_BF16
         opts = {k: tuned[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm",
                                       "precision")}
