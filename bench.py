@@ -519,13 +519,18 @@ def run_gpu(args, dist, rank, world, local_rank):
     if not args.no_autotune:
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
-        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm", "g2_sets")}
+        tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm", "g2_sets",
+                                   "fold_products")}
         opts.update(tuned)
 
     if args.chains is not None:
         opts["chains"] = args.chains
         if tuned is not None:
             tuned["chains"] = args.chains
+    if args.fold_products is not None:
+        opts["fold_products"] = args.fold_products
+        if tuned is not None:
+            tuned["fold_products"] = args.fold_products
 
     def step(inp, out, **extra):
         return prism.prism_solve_batch(h, **inp, out=out, **opts, **extra)
@@ -761,6 +766,9 @@ def main():
                     "differentiation workload")
     ap.add_argument("--workload", type=int, default=1, choices=[0, 1, 2, 3, 4],
                     help="the book the GPU arm times (default 1, the headline; the others for profiling)")
+    ap.add_argument("--fold-products", type=int, default=None, choices=[0, 1],
+                    help="fused iterations: B'X of the pinned entries inside the x-update (1) or the separate "
+                         "product kernels every iteration (0); default: the library's, or the autotuner's choice")
     ap.add_argument("--ragged-layout", type=int, default=None, choices=[1, 2],
                     help="ragged books: 1 dense-masked, 2 packed per-account blocks")
     ap.add_argument("--no-others", action="store_true", help="skip the lines of the other workloads "

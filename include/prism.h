@@ -161,6 +161,13 @@ typedef struct {
                                  128-account tile along the assets, each CTA summing an asset chunk
                                  of N / (8 g2_sets) (rounded up to 64); 0 = about one CTA per SM
                                  (default 0; searched by prism_autotune) */
+    int32_t fold_products;    /* fused iterations (fuse_prox): 1 = the product B'X of the entries the
+                                 fused x-update pins is formed inside that kernel (a second tensor-core
+                                 product over its tile) and the roots kernel adds the other entries and
+                                 solves for the next Q, so that the separate product and small-solve
+                                 kernels work only for accounts whose penalty changed or whose pinned
+                                 entries were rewritten; 0 = those kernels every iteration (default 0:
+                                 faster on the workloads measured; searched by prism_autotune) */
 } prism_solve_opts;
 
 /* Fill *o with the defaults documented above. */
@@ -261,7 +268,11 @@ void prism_free_state(prism_state* state);
  *   P  = X B   (M x K, FP64 out)   and   BQ = Q B'  (M x N, FP64 out),
  * with X (M x N) and Q (M x K) row-major FP64 in universe asset order, host or
  * device. In BATCHED_BF16 mode B is used rounded to BF16 and X, Q are split into
- * two BF16 terms each, exactly as in the solve. Allocates its own temporaries. */
+ * two BF16 terms each, exactly as in the solve. PRISM_BATCHED_BF16 | PRISM_PRODUCTS_FUSED
+ * takes P from the fused x-update kernel's own product (the one it forms over the entries
+ * it pins during a solve; here over every entry of X) instead of the separate G2 kernel.
+ * Allocates its own temporaries. */
+#define PRISM_PRODUCTS_FUSED 0x100
 int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double* X, const double* Q,
                             int32_t precision, double* P, double* BQ);
 
@@ -298,8 +309,9 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
  * before the streaming form (2 .. 10), the account chains (1, 2, 4) and the ADMM target
- * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16)
- * and, for books of ragged accounts, the layout (dense-masked or packed), starting
+ * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16),
+ * the folded products (fold_products 0, 1; BATCHED_BF16) and, for books of ragged accounts,
+ * the layout (dense-masked or packed), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts
  * per second of device time; one that certifies fewer accounts never wins, and one that
  * certifies as many must be faster than the best so far by more than 1%. Writes the

@@ -143,13 +143,138 @@ void launch_gemm_P(const Dev& D, cudaStream_t st) {
 }
 
 // ---------------------------------------------------------------------------
-// G3: Q[m] = Cinv[rho_idx[m]] * sum_s Ppart[s][m]; one block of K threads per account
+// G3: Q[m] = Cinv[rho_idx[m]] * P[m]. solve_K is the per-account solve on a P in shared memory;
+// k_small_solve runs it after G2 (P = sum_s Ppart[s][m]), k_prox_roots at the end of the fused
+// iteration (P = the fused pass's partial sets plus its own candidates' share).
 // ---------------------------------------------------------------------------
+struct SolveScratch {
+    float sT[KMAX], sP0[KMAX], sQ[KMAX];
+    float red_p[KMAX / 32], red_d[KMAX / 32];
+    float red[4][KMAX];                   // row-group partials of a block matrix-vector product
+};
+
+// y_t = sum_j A[j][t] x_j for t < K (A symmetric K x K, row-major: column t is contiguous over
+// t) by GROUPS groups of KMAX threads, group g over rows g KMAX / GROUPS onwards, combined in
+// shared memory in group order. Block-collective; the value is meaningful in threads t < K.
+template <int GROUPS>
+__device__ __forceinline__ float sym_matvec(const float* A, int K, const float* x, SolveScratch& w) {
+    const int t = threadIdx.x, c = t % KMAX, g = t / KMAX;
+    constexpr int RPG = KMAX / GROUPS;
+    float a0 = 0.f, a1 = 0.f, a2 = 0.f, a3 = 0.f;
+    if (g < GROUPS && c < K) {
+#pragma unroll
+        for (int r = 0; r < RPG; r += 4) {
+            const int j = g * RPG + r;
+            if (j < K) a0 = fmaf(A[(size_t)j * K + c], x[j], a0);
+            if (j + 1 < K) a1 = fmaf(A[(size_t)(j + 1) * K + c], x[j + 1], a1);
+            if (j + 2 < K) a2 = fmaf(A[(size_t)(j + 2) * K + c], x[j + 2], a2);
+            if (j + 3 < K) a3 = fmaf(A[(size_t)(j + 3) * K + c], x[j + 3], a3);
+        }
+    }
+    const float part = (a0 + a1) + (a2 + a3);
+    if (GROUPS == 1) return part;
+    __syncthreads();
+    if (g < GROUPS) w.red[g][c] = part;
+    __syncthreads();
+    float y = 0.f;
+    if (t < KMAX)
+#pragma unroll
+        for (int h = 0; h < GROUPS; ++h) y += w.red[h][t];
+    return y;
+}
+
+// Q = C^{-1} P for account m, P in shared memory (KMAX entries, zero past K), and the update of
+// the factor-exposure block when the book has one. Block-collective: every thread of the block
+// calls it; the block has at least GROUPS x KMAX threads, the products run over GROUPS row
+// groups, and threads t < K write. cpre: column t of C^{-1} already in registers (GROUPS = 1),
+// or null to read it here.
+template <int GROUPS>
+__device__ __forceinline__ void solve_K(const Dev& D, int m, float* sP, SolveScratch& w, const float* cpre) {
+    const int K = D.K, t = threadIdx.x;
+    const int jr = D.rho_idx[m];
+    const float* C = D.Cinv + (size_t)jr * K * K;
+    // Factor-exposure block (s = B'x, dual ys): the x-update's right side gains B (rho s - ys), so
+    // with tv = rho s - ys the reduced right side is P0 + G tv and Q' = C^{-1} (P0 + G tv) - tv
+    // (then x = X - Delta^{-1} B Q' as without the block, and B'x = P0 - G Q').
+    const bool fac = D.s != nullptr;
+    const float* Gj = fac ? D.G + (size_t)jr * K * K : nullptr;
+    float rho = 0.f, s_old = 0.f, ys_old = 0.f;
+    if (fac) {
+        rho = rho_val(jr);
+        if (t < K) { s_old = D.s[(size_t)m * K + t]; ys_old = D.ys[(size_t)m * K + t]; }
+        if (t < KMAX) {
+            w.sT[t] = t < K ? rho * s_old - ys_old : 0.f;
+            w.sP0[t] = sP[t];
+        }
+        __syncthreads();
+        const float g = sym_matvec<GROUPS>(Gj, K, w.sT, w);
+        __syncthreads();
+        if (t < KMAX) sP[t] = w.sP0[t] + g;
+        __syncthreads();
+    }
+    float q = 0.f;
+    if (cpre) {
+        if (t < K) {
+            float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
+#pragma unroll
+            for (int j = 0; j < KMAX; j += 4) {
+                q0 = fmaf(cpre[j], sP[j], q0);
+                q1 = fmaf(cpre[j + 1], sP[j + 1], q1);
+                q2 = fmaf(cpre[j + 2], sP[j + 2], q2);
+                q3 = fmaf(cpre[j + 3], sP[j + 3], q3);
+            }
+            q = (q0 + q1) + (q2 + q3);
+        }
+    } else {
+        q = sym_matvec<GROUPS>(C, K, sP, w);
+    }
+    if (t < K) {
+        if (fac) q -= w.sT[t];
+        if (D.bf16) {
+            __nv_bfloat16 h = __float2bfloat16_rn(q);
+            D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
+            D.Qlo[(size_t)m * KMAX + t] = __float2bfloat16_rn(q - __bfloat162float(h));
+        }
+        D.Q[(size_t)m * K + t] = q;
+        if (fac) w.sQ[t] = q;
+    }
+    if (fac) {
+        // the block's own update: relaxed B'x, s = clip(., lo, hi), dual step, residuals
+        __syncthreads();
+        const float g = sym_matvec<GROUPS>(Gj, K, w.sQ, w);
+        float rp = 0.f, rd = 0.f;
+        if (t < K) {
+            const float bx = w.sP0[t] - g;
+            const float xh = D.alpha * bx + (1.f - D.alpha) * s_old;
+            const float lo = D.flo[(size_t)m * K + t], hi = D.fhi[(size_t)m * K + t];
+            const float sn = fminf(fmaxf(xh + ys_old / rho, lo), hi);
+            D.s[(size_t)m * K + t] = sn;
+            D.ys[(size_t)m * K + t] = ys_old + rho * (xh - sn);
+            D.sflag[(size_t)m * K + t] = (sn >= hi) ? 1 : ((sn <= lo) ? -1 : 0);
+            rp = fabsf(xh - sn);
+            rd = rho * fabsf(sn - s_old);
+            if (!(isfinite(rp) && isfinite(rd))) rp = rd = INFINITY;
+        }
+        // (reduced through arrays of their own: a warp with no factors reaches this point while
+        // another may still read sP0 above)
+        rp = warp_max(rp);
+        rd = warp_max(rd);
+        if ((t & 31) == 0 && t < KMAX) { w.red_p[t >> 5] = rp; w.red_d[t >> 5] = rd; }
+        __syncthreads();
+        if (t == 0) {
+            D.rps[m] = fmaxf(w.red_p[0], w.red_p[1]);
+            D.rds[m] = fmaxf(w.red_d[0], w.red_d[1]);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
     const int m = D.m0 + blockIdx.x;
     if (D.active && !D.active[m]) return;
+    if (D.needP && !D.needP[m]) return;    // its P and Q came from the fused iteration
     const int K = D.K;
     __shared__ float sP[KMAX];
+    __shared__ SolveScratch w;
     const int t = threadIdx.x;
     // C^{-1} is symmetric: thread t reads column t (the block's loads are contiguous). The whole
     // column is loaded into registers first, so that it is in flight with the partial sums.
@@ -173,75 +298,7 @@ __global__ void __launch_bounds__(KMAX) k_small_solve(Dev D) {
         sP[t] = 0.f;                       // factors beyond K (their column entries are zero too)
     }
     __syncthreads();
-    // Factor-exposure block (s = B'x, dual ys): the x-update's right side gains B (rho s - ys), so
-    // with tv = rho s - ys the reduced right side is P0 + G tv and Q' = C^{-1} (P0 + G tv) - tv
-    // (then x = X - Delta^{-1} B Q' as without the block, and B'x = P0 - G Q').
-    __shared__ float sT[KMAX], sP0[KMAX], sQ[KMAX];
-    const bool fac = D.s != nullptr;
-    const float* Gj = fac ? D.G + (size_t)D.rho_idx[m] * K * K : nullptr;
-    float rho = 0.f, s_old = 0.f, ys_old = 0.f;
-    if (fac) {
-        rho = rho_val(D.rho_idx[m]);
-        if (t < K) { s_old = D.s[(size_t)m * K + t]; ys_old = D.ys[(size_t)m * K + t]; }
-        sT[t] = t < K ? rho * s_old - ys_old : 0.f;
-        sP0[t] = sP[t];
-        __syncthreads();
-        float g = 0.f;
-        if (t < K)
-            for (int j = 0; j < K; ++j) g = fmaf(Gj[(size_t)j * K + t], sT[j], g);   // G symmetric: column t
-        __syncthreads();
-        sP[t] = sP0[t] + g;
-        __syncthreads();
-    }
-    if (t < K) {
-        float q0 = 0.f, q1 = 0.f, q2 = 0.f, q3 = 0.f;
-#pragma unroll
-        for (int j = 0; j < KMAX; j += 4) {
-            q0 = fmaf(c[j], sP[j], q0);
-            q1 = fmaf(c[j + 1], sP[j + 1], q1);
-            q2 = fmaf(c[j + 2], sP[j + 2], q2);
-            q3 = fmaf(c[j + 3], sP[j + 3], q3);
-        }
-        float q = (q0 + q1) + (q2 + q3);
-        if (fac) q -= sT[t];
-        if (D.bf16) {
-            __nv_bfloat16 h = __float2bfloat16_rn(q);
-            D.Qhi[(size_t)m * KMAX + t] = h;     // row stride 64: the tensor-core operand layout
-            D.Qlo[(size_t)m * KMAX + t] = __float2bfloat16_rn(q - __bfloat162float(h));
-        }
-        D.Q[(size_t)m * K + t] = q;
-        if (fac) sQ[t] = q;
-    }
-    if (fac) {
-        // the block's own update: relaxed B'x, s = clip(., lo, hi), dual step, residuals
-        __syncthreads();
-        float rp = 0.f, rd = 0.f;
-        if (t < K) {
-            float g = 0.f;
-            for (int j = 0; j < K; ++j) g = fmaf(Gj[(size_t)j * K + t], sQ[j], g);
-            const float bx = sP0[t] - g;
-            const float xh = D.alpha * bx + (1.f - D.alpha) * s_old;
-            const float lo = D.flo[(size_t)m * K + t], hi = D.fhi[(size_t)m * K + t];
-            const float sn = fminf(fmaxf(xh + ys_old / rho, lo), hi);
-            D.s[(size_t)m * K + t] = sn;
-            D.ys[(size_t)m * K + t] = ys_old + rho * (xh - sn);
-            D.sflag[(size_t)m * K + t] = (sn >= hi) ? 1 : ((sn <= lo) ? -1 : 0);
-            rp = fabsf(xh - sn);
-            rd = rho * fabsf(sn - s_old);
-            if (!(isfinite(rp) && isfinite(rd))) rp = rd = INFINITY;
-        }
-        // (reduced through arrays of their own: a warp with no factors reaches this point while
-        // the other warp may still read sP0 above)
-        __shared__ float red_p[KMAX / 32], red_d[KMAX / 32];
-        rp = warp_max(rp);
-        rd = warp_max(rd);
-        if ((t & 31) == 0) { red_p[t >> 5] = rp; red_d[t >> 5] = rd; }
-        __syncthreads();
-        if (t == 0) {
-            D.rps[m] = fmaxf(red_p[0], red_p[1]);
-            D.rds[m] = fmaxf(red_d[0], red_d[1]);
-        }
-    }
+    solve_K<1>(D, m, sP, w, c);
 }
 
 void launch_small_solve(const Dev& D, cudaStream_t st, bool pdl) {
@@ -814,6 +871,8 @@ struct StreamShared {
     float red5[5][SP_WARPS];
     int red_bad[SP_WARPS];
     int newj;
+    int redo;                           // entries written before the tail were rewritten
+    int cont;                           // the account iterates on
     float nu;
     // kept entries
     float v[SP_WARPS * SP_CW], w0[SP_WARPS * SP_CW], lo[SP_WARPS * SP_CW], up[SP_WARPS * SP_CW];
@@ -857,8 +916,9 @@ __device__ __forceinline__ void stream_sector_eval(const Dev& D, const StreamSha
 struct StreamRes {
     float rp = 0.f, rd = 0.f, nx = 0.f, nz = 0.f, ny = 0.f;
     int bad = 0;
-    __device__ __forceinline__ void put(const Dev& D, size_t e, float z, float v, float zo, float yo, float mu,
-                                        float dd, float rho, float irho) {
+    // writes z and y = rho (v - z); returns X = Delta^{-1} (mu + rho z - y)
+    __device__ __forceinline__ float put_zy(const Dev& D, size_t e, float z, float v, float zo, float yo, float mu,
+                                            float dd, float rho, float irho) {
         const float yn = rho * (v - z);
         rp = fmaxf(rp, fabsf(yn - yo) * irho);
         rd = fmaxf(rd, rho * fabsf(z - zo));
@@ -868,7 +928,11 @@ struct StreamRes {
         bad |= !(isfinite(z) && isfinite(yn));
         D.z[e] = z;
         D.y[e] = yn;
-        store_X(D, e, (mu + rho * z - yn) / (2.f * dd + rho));
+        return (mu + rho * z - yn) / (2.f * dd + rho);
+    }
+    __device__ __forceinline__ void put(const Dev& D, size_t e, float z, float v, float zo, float yo, float mu,
+                                        float dd, float rho, float irho) {
+        store_X(D, e, put_zy(D, e, z, v, zo, yo, mu, dd, rho, irho));
     }
 };
 
@@ -1126,14 +1190,18 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
     }
     if (mask) {
         // the kept entries, every slot by its own thread (a slot of a sector that was moved
-        // to global memory above lies outside its sector's range and was written there)
+        // to global memory above lies outside its sector's range and was written there). With
+        // the products folded the slot's X replaces its v in shared memory (the caller adds the
+        // slots' share of B'X); otherwise it is stored
         __syncthreads();
         for (int q = tid; q < nslots; q += blockDim.x) {
             const int s = ssec[q];
             if (q >= sh.ce[s]) continue;
             const float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
             const float z = eval_l1(sh.v[q], sh.w0[q], sh.lo[q], sh.up[q], sh.k[q], arg, irho).z;
-            res.put(D, base + sh.pos[q], z, sh.v[q], sh.zo[q], sh.yo[q], smu[q], sdd[q], rho, irho);
+            const float X = res.put_zy(D, base + sh.pos[q], z, sh.v[q], sh.zo[q], sh.yo[q], smu[q], sdd[q], rho, irho);
+            if (D.fold) sh.v[q] = X;
+            else store_X(D, base + sh.pos[q], X);
         }
     }
     float rp = warp_max(res.rp), rd = warp_max(res.rd), nx = warp_max(res.nx), nz = warp_max(res.nz),
@@ -1156,6 +1224,7 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
             redo |= sh.red_bad[w] >> 1;
         }
         if (redo) { rp = INFINITY; rd = INFINITY; }    // entries were rewritten: no residual this call
+        sh.redo = redo;
         const int it = sh.it0 + 1;
         D.iters[a] = it;
         if (D.stats) atomicAdd(D.stats, 1ull);
@@ -1166,6 +1235,7 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
         // the next call's margin: four times the last move of nu, or more after a miss
         D.dnu[a] = redo ? fmaxf(fabsf(nu - nu0), margin) : fabsf(nu - nu0);
         int newj = j;
+        sh.cont = 0;
         if (bad) {
             D.status[a] = PRISM_NUMERICAL_FAILURE;
             D.active[a] = 0;
@@ -1175,13 +1245,16 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
         } else if (it >= D.max_iter) {
             D.active[a] = 0;
             D.status[a] = PRISM_TIMEOUT;
-        } else if (!redo && it % D.adapt_every == 0) {
-            const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
-            const float du = rd / fmaxf(ny, 1e-12f);
-            const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
-            int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
-            dj = max(-4, min(4, dj));
-            newj = max(0, min(NRHO - 1, j + dj));
+        } else {
+            sh.cont = 1;
+            if (!redo && it % D.adapt_every == 0) {
+                const float pr = rp / fmaxf(fmaxf(nx, nz), 1e-12f);
+                const float du = rd / fmaxf(ny, 1e-12f);
+                const float ratio = sqrtf(pr / fmaxf(du, 1e-20f));
+                int dj = int(lrintf(float(RHO_PER_DECADE) * log10f(fmaxf(ratio, 1e-12f))));
+                dj = max(-4, min(4, dj));
+                newj = max(0, min(NRHO - 1, j + dj));
+            }
         }
         sh.newj = newj;
     }
@@ -1193,10 +1266,13 @@ __device__ void stream_tail(const Dev& D, StreamShared& sh, const GlobalSrc& G, 
     }
     if (newj != j) {
         if (tid == 0) D.rho_idx[a] = newj;
-        const float rn = rho_val(newj);
-        for (int p = tid; p < D.N; p += blockDim.x) {
-            const size_t e = base + p;
-            store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+        if (!(mask && D.fold)) {
+            // (with the products folded the caller rewrites X itself: entries the pass pinned hold none)
+            const float rn = rho_val(newj);
+            for (int p = tid; p < D.N; p += blockDim.x) {
+                const size_t e = base + p;
+                store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+            }
         }
     }
 }
@@ -1316,6 +1392,68 @@ __device__ __forceinline__ int cand_rank(const RootsShared& R, int nq, int p) {
     const int q = p >> 5;
     if (q >= nq) return R.total;
     return R.qoff[q] + __popc(R.mask[q] & ((1u << (p & 31)) - 1u));
+}
+
+// P = B'X of account a for the next iteration, then its Q (G2 and G3 folded into the fused
+// iteration): the fused pass's partial sets hold the entries it pinned (tensor-core products,
+// X split into two BF16 terms), and the slots, whose X the tail left in place of their v, add
+// X_q B_q here (FP32, B in its BF16 rounding as in the products). Fixed summation order.
+static_assert(sizeof(SolveScratch) <= sizeof(float) * SP_WARPS * SP_CW, "the solve's scratch fits in a slot array");
+
+// X of every entry of account a at penalty index j, and the flag that sends the account through
+// the product kernels of the next iteration
+__device__ __noinline__ void rewrite_X(const Dev& D, int a, int j) {
+    const size_t base = (size_t)a * D.Npad;
+    const float rn = rho_val(j);
+    for (int p = threadIdx.x; p < D.N; p += blockDim.x) {
+        const size_t e = base + p;
+        store_X(D, e, (D.mu32[p] + rn * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rn));
+    }
+    if (threadIdx.x == 0) D.needP[a] = 1;
+}
+
+__device__ __noinline__ void fold_P_solve(const Dev& D, const RootsShared& R, StreamShared& sh, int a) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, tid = threadIdx.x;
+    float* red = sh.w0;                          // [SP_WARPS][KMAX]; the slot arrays are free now
+    const __nv_bfloat162* B2 = reinterpret_cast<const __nv_bfloat162*>(D.B16p);
+    float a0 = 0.f, a1 = 0.f;
+    const int n = R.nslots;
+    int q = warp;
+    for (; q + 3 * SP_WARPS < n; q += 4 * SP_WARPS) {
+        float2 b[4];
+        float x[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int qq = q + u * SP_WARPS;
+            b[u] = __bfloat1622float2(B2[(size_t)sh.pos[qq] * (KMAX / 2) + lane]);
+            x[u] = sh.v[qq];
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) { a0 = fmaf(b[u].x, x[u], a0); a1 = fmaf(b[u].y, x[u], a1); }
+    }
+    for (; q < n; q += SP_WARPS) {
+        const float2 b = __bfloat1622float2(B2[(size_t)sh.pos[q] * (KMAX / 2) + lane]);
+        a0 = fmaf(b.x, sh.v[q], a0);
+        a1 = fmaf(b.y, sh.v[q], a1);
+    }
+#pragma unroll 4
+    for (int set = warp; set < D.xp_sets; set += SP_WARPS) {
+        const float2 pp = reinterpret_cast<const float2*>(D.Pxp + ((size_t)set * D.M + a) * KMAX)[lane];
+        a0 += pp.x;
+        a1 += pp.y;
+    }
+    red[warp * KMAX + 2 * lane] = a0;
+    red[warp * KMAX + 2 * lane + 1] = a1;
+    __syncthreads();
+    float* sP = sh.up;
+    if (tid < KMAX) {
+        float t = 0.f;
+#pragma unroll
+        for (int w = 0; w < SP_WARPS; ++w) t += red[w * KMAX + tid];
+        sP[tid] = t;
+    }
+    __syncthreads();
+    solve_K<4>(D, a, sP, *reinterpret_cast<SolveScratch*>(sh.k), nullptr);
 }
 
 __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
@@ -1518,6 +1656,20 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
         }
     }
     stream_tail(D, sh, G, a, j, rho, irho, nu0, L, margin, res, R.mask, R.mu, R.dd, R.ssec, R.nslots);
+    // ---- the next iteration's P and Q of this account (products folded)
+    if (!D.fold) return;
+    __syncthreads();
+    if (!sh.cont) return;
+    const int newj = sh.newj;
+    if (sh.redo || newj != j || !all_fit) {
+        // P cannot be completed from the pass's partials (the penalty changed, entries the pass
+        // pinned were rewritten, or a sector's candidates were read from global memory): X of
+        // every entry at the penalty of the next iteration, for its product kernels
+        rewrite_X(D, a, newj);
+        return;
+    }
+    if (tid == 0) D.needP[a] = 0;
+    fold_P_solve(D, R, sh, a);
 }
 
 size_t prox_roots_smem_bytes() { return sizeof(RootsShared); }
@@ -1580,6 +1732,21 @@ void launch_prox(const Dev& D, cudaStream_t st, bool cold) {
     } else {
         k_prox<<<D.M, 32 * nw, 0, st>>>(D);
     }
+}
+
+// X = Delta^{-1} (mu + rho z - y) of every entry of the accounts still iterating (the fused
+// iteration keeps no X of the entries it pins: a return to the iterations rebuilds it)
+__global__ void k_refresh_X(Dev D) {
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)D.M * D.Npad) return;
+    const int a = int(e / D.Npad), p = int(e % D.Npad);
+    if (!D.active[a] || p >= D.N) return;
+    const float rho = rho_val(D.rho_idx[a]);
+    store_X(D, e, (D.mu32[p] + rho * D.z[e] - D.y[e]) / (2.f * D.d32[p] + rho));
+}
+
+void launch_refresh_X(const Dev& D, cudaStream_t st) {
+    k_refresh_X<<<(unsigned)cdiv64((int64_t)D.M * D.Npad, 256), 256, 0, st>>>(D);
 }
 
 __global__ void k_count_active(Dev D) {

@@ -147,6 +147,10 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
             c.g2_sets = gs;
             if ((rc = consider(c)) != PRISM_OK) return rc;
         }
+        // B'X of the pinned entries inside the fused x-update, the rest and Q in the roots kernel
+        prism_solve_opts c = best;
+        c.fold_products = 1 - best.fold_products;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
     }
     if (b->asset_idx) {
         // ragged accounts: dense-masked over the universe against packed per-account blocks

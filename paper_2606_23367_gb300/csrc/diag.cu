@@ -45,8 +45,13 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
                                        int32_t precision, double* P, double* BQ) {
     using namespace prism;
     if (!uh || M < 1 || !X || !Q || !P || !BQ) { set_error("bad argument"); return PRISM_ERR_ARGUMENT; }
+    const bool fused = (precision & PRISM_PRODUCTS_FUSED) != 0;
+    precision &= ~PRISM_PRODUCTS_FUSED;
     if (precision != PRISM_BATCHED_FP32 && precision != PRISM_BATCHED_BF16 && precision != PRISM_PLAIN_FP32) {
         set_error("unknown precision"); return PRISM_ERR_ARGUMENT;
+    }
+    if (fused && precision != PRISM_BATCHED_BF16) {
+        set_error("PRISM_PRODUCTS_FUSED needs PRISM_BATCHED_BF16"); return PRISM_ERR_ARGUMENT;
     }
     const bool bf16 = precision == PRISM_BATCHED_BF16;
     if (bf16 && !tc_available()) { set_error("tensor-core kernels unavailable"); return PRISM_ERR_UNSUPPORTED; }
@@ -90,14 +95,40 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
     D.bf16 = bf16;
     D.raw_out = 1;
     D.alpha = 1.f;
+    size_t n_alloc = 14;
+    if (fused) {
+        // the fused x-update's own B'X (its second product over the X tile, summed over the
+        // cluster's asset tiles): every account active, uniform l and c, the given X as the tile
+        D.active = (int*)take((size_t)M * 4);
+        D.iters = (int*)take((size_t)M * 4);
+        D.nu = (float*)take((size_t)M * 4);
+        D.dnu = (float*)take((size_t)M * 4);
+        D.lo_u = (float*)take((size_t)M * 4);
+        D.c_u = (float*)take((size_t)M * 4);
+        D.xp_sets = xp_sets_for(N);
+        D.Pxp = (float*)take((size_t)D.xp_sets * M * KMAX * 4);
+        D.nt = cdiv(N, 128);
+        D.nq = 0;
+        D.uniform = 1;
+        D.fold = 1;
+        D.adapt_every = 1 << 30;
+        D.w0 = D.z;
+        D.up = D.y;
+        n_alloc += 7;
+    }
     for (void* p : allocs) if (!p) { cleanup(); set_error("allocation failed"); return PRISM_ERR_ALLOCATION; }
-    if (allocs.size() != 14) { cleanup(); set_error("allocation failed"); return PRISM_ERR_ALLOCATION; }
+    if (allocs.size() != n_alloc) { cleanup(); set_error("allocation failed"); return PRISM_ERR_ALLOCATION; }
+    if (fused) {
+        std::vector<int> one(M, 1);
+        cudaMemcpy((void*)D.active, one.data(), (size_t)M * 4, cudaMemcpyHostToDevice);
+    }
     cudaMemcpy(dX, X, (size_t)M * N * 8, cudaMemcpyDefault);
     cudaMemcpy(dQ, Q, (size_t)M * K * 8, cudaMemcpyDefault);
     const int64_t work = std::max((int64_t)M * N, (int64_t)M * K);
     k_diag_in<<<(unsigned)cdiv64(work, 256), 256>>>(M, N, Npad, dX, dQ, K, U.d_inv_perm, D.X, D.Xhi, D.Xlo, D.Q,
                                                       D.Qhi, D.Qlo);
-    if (bf16) { launch_tc_gemm_P(D, 0); launch_tc_gemm_x(D, 0); }
+    if (fused) { launch_tc_xprox(D, 0); launch_tc_gemm_x(D, 0); }
+    else if (bf16) { launch_tc_gemm_P(D, 0); launch_tc_gemm_x(D, 0); }
     else { launch_gemm_P(D, 0); launch_gemm_x(D, 0); }
     cudaError_t e = cudaDeviceSynchronize();
     if (e == cudaSuccess) e = cudaGetLastError();
@@ -105,11 +136,12 @@ extern "C" int prism_shared_b_products(prism_universe* uh, int32_t M, const doub
     int err = 0;
     cudaMemcpy(&err, D.err, 4, cudaMemcpyDeviceToHost);
     if (err) { cleanup(); set_error("tensor-core pipeline wait timed out"); return PRISM_ERR_CUDA; }
-    std::vector<float> part((size_t)nsplit * M * D.pstride), v(MN);
-    cudaMemcpy(part.data(), D.Ppart, part.size() * 4, cudaMemcpyDeviceToHost);
+    const int nsets = fused ? D.xp_sets : nsplit;
+    std::vector<float> part((size_t)nsets * M * D.pstride), v(MN);
+    cudaMemcpy(part.data(), fused ? D.Pxp : D.Ppart, part.size() * 4, cudaMemcpyDeviceToHost);
     cudaMemcpy(v.data(), D.v, MN * 4, cudaMemcpyDeviceToHost);
     std::vector<double> hP((size_t)M * K, 0.0), hBQ((size_t)M * N);
-    for (int sp = 0; sp < nsplit; ++sp)
+    for (int sp = 0; sp < nsets; ++sp)
         for (int m = 0; m < M; ++m)
             for (int k = 0; k < K; ++k)
                 hP[(size_t)m * K + k] += part[((size_t)sp * M + m) * D.pstride + k];

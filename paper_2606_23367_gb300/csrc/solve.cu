@@ -587,6 +587,8 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.Rt = A.take<float>((size_t)5 * nt * M); D.Cm = A.take<unsigned>((size_t)U.nq * M);
         D.lo_u = A.take<float>(M); D.c_u = A.take<float>(M);
         D.crec = A.take<float>(MN * 8);
+        D.Pxp = A.take<float>(batched_mode_bf16 ? (size_t)xp_sets_for(N) * M * KMAX : 0);
+        D.needP = A.take<int>(M);
         D.pcount = A.take<unsigned long long>(2);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
@@ -844,6 +846,9 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     // the account's candidate masks
     D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && o->fuse_prox) ? 1 : 0;
     D.nq = U.nq; D.nseg = U.nseg; D.nt = cdiv(N, 128); D.qseg = U.d_qseg; D.sseg = U.d_sseg;
+    D.xp_sets = xp_sets_for(N);
+    int* const needP_buf = D.needP;            // set for the fused loop only (null: every account)
+    D.needP = nullptr;
     D.nsplit = nsplit;
     D.g2_sets = batched_mode_bf16 ? o->g2_sets : 0;
     D.pstride = batched_mode_bf16 ? KMAX : K;
@@ -1035,6 +1040,13 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     };
     auto admm_loop = [&](int iter_budget, bool overlap) -> int {
         int done_iters = 0;
+        if (D.needP) {
+            // the folded iteration keeps no X of the entries it pins and leaves P, Q only for the
+            // accounts that iterate on: on entry every active account gets X from its z, y, and
+            // its first P and Q from the product kernels
+            SC.prof.run(PRISM_K_OTHER, 1, st, [&] { launch_refresh_X(D, st); });
+            cudaMemsetAsync(D.needP, 0x01, (size_t)M * 4, st);
+        }
         overlap = overlap && SC.pst && !SC.prof.on && o->polish_overlap > 0;
         bool use_graph = o->use_graph != 0 && !SC.prof.on;
         if (use_graph) {
@@ -1131,6 +1143,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         SC.prof.run(PRISM_K_PROX, 1, st, [&] { launch_prox(D, st, true); });
     }
     std::memset(SC.hsel, 0, (size_t)M * 4);
+    if (D.fused && o->fold_products) { D.needP = needP_buf; D.fold = 1; }
     int total_iters = blockwise ? 0 : admm_loop(o->max_iter + check_every - cold, true);
     if (total_iters >= 0) total_iters += cold;
     if (total_iters == -2) { set_error("tensor-core pipeline wait timed out (error flags " + std::to_string(SC.pinned[1]) + ")"); return PRISM_ERR_CUDA; }
@@ -1317,7 +1330,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     if (b->lot_offsets && (!b->lot_size || !b->lot_kappa)) { set_error("lot arrays incomplete"); return PRISM_ERR_ARGUMENT; }
     if (!(o.eps_kkt > 0) || !(o.eps_admm > 0) || !(o.rho0 > 0) || !(o.alpha > 0 && o.alpha < 2) ||
         o.max_iter < 1 || o.check_every < 1 || o.g2_sets < 0 || o.g2_sets > 64 || o.ragged_layout < 0 ||
-        o.ragged_layout > 2) {
+        o.ragged_layout > 2 || o.fold_products < 0 || o.fold_products > 1) {
         set_error("invalid options");
         return PRISM_ERR_ARGUMENT;
     }

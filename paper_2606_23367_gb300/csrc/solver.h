@@ -86,6 +86,15 @@ struct Dev {
     unsigned* Cm = nullptr;             // M x nq: bit b of quarter q set = entry 32q + b not pinned at L
     unsigned long long* pcount = nullptr;   // profile mode: [0] candidates, [1] entries of the fused pass
     float* crec = nullptr;              // M x Npad x 8: (v, w0, u, z, y, mu, d, -) of each such candidate
+    // G2 and G3 folded into the fused iteration: k_tc_xprox leaves B'X of the entries it pinned
+    // (one partial set per asset tile, xp_sets x M x 64) and k_prox_roots adds the candidates and
+    // solves for Q. An account whose P cannot be completed that way (its penalty
+    // changed, or entries pinned by the fused pass were rewritten) has needP set and X rewritten in
+    // full: the next iteration's G2 and G3 run for such accounts only (needP == null: for all)
+    float* Pxp = nullptr;
+    int xp_sets = 0;
+    int fold = 0;                       // the fold is on (k_tc_xprox writes no X, forms its partial)
+    int* needP = nullptr;               // M, nonzero = P and Q from the product kernels
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
     // factor-exposure bounds (the Eq. 1 rows B'w in [flo, fhi]) as a second splitting block
     // s = B'x with penalty rho and unscaled dual ys; null when the book has none. The small
@@ -126,5 +135,7 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl = false);     // G4
 void launch_prox_roots(const Dev& D, cudaStream_t st, bool pdl = false);   // G5/G6 per account after k_tc_xprox
 void launch_uniform(const Dev& D, float* lo_u, float* c_u, cudaStream_t st);   // per-account uniform l, c
 constexpr int XP_NQMAX = 1024;                           // quarters the roots kernel holds (N <= 32768)
+inline int xp_sets_for(int N) { return (N + 127) / 128; }   // partial sets of the fused x-update
+void launch_refresh_X(const Dev& D, cudaStream_t st);    // X of every entry of the active accounts from z, y
 
 }  // namespace prism

@@ -119,16 +119,25 @@ __device__ __forceinline__ void fence_after_sync() {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 }
 
-// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups 1024 B apart.
-__device__ __forceinline__ uint64_t sw128_desc(const void* smem) {
+// Shared-memory matrix descriptor: 128-byte swizzle, 8-row groups 1024 B apart. K-major operands
+// (rows of 64 BF16 along K) leave the leading byte offset unused. An MN-major operand whose MN
+// extent is one 128-byte row (64 BF16) has a single swizzle atom along MN, so its leading offset
+// (the stride between MN atoms) is never applied either, and its 8-row groups run along K; the
+// offset is set to the 1024-byte group stride all the same.
+__device__ __forceinline__ uint64_t sw128_desc(const void* smem, uint32_t lbo = 16) {
     const uint32_t a = smem_u32(smem);
     uint64_t d = 0;
     d |= uint64_t((a & 0x3FFFF) >> 4);       // start address (16-byte units)
-    d |= uint64_t(1) << 16;                  // leading byte offset (unused for this layout)
+    d |= uint64_t(lbo >> 4) << 16;           // leading byte offset
     d |= uint64_t(1024 >> 4) << 32;          // stride byte offset: 8 rows x 128 B
     d |= uint64_t(1) << 46;                  // descriptor version for tcgen05
     d |= uint64_t(2) << 61;                  // swizzle: 128 B
     return d;
+}
+
+// generic-proxy shared-memory writes made visible to the tensor core (async proxy)
+__device__ __forceinline__ void fence_proxy_async_smem() {
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
 __device__ __forceinline__ void umma_bf16(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc, uint32_t acc) {
@@ -219,9 +228,11 @@ __global__ void __launch_bounds__(128) k_tc_gemm_P(const __grid_constant__ CUten
     pdl_wait();                            // X and the activity flags of the iteration before
     pdl_trigger();
     {
-        // a tile whose accounts have all stopped iterating has nothing to compute
+        // a tile whose accounts have all stopped iterating, or whose P all came from the fused
+        // iteration, has nothing to compute
         const int m = mrow + tid;
-        const int act = (D.active == nullptr) || (m < m_end && D.active[m]);
+        const int act = (D.active == nullptr) ||
+                        (m < m_end && D.active[m] && (D.needP == nullptr || D.needP[m] != 0));
         if (!__syncthreads_or(act)) return;
     }
     if (warp == 0) tmem_alloc(&s.tmem, 64);
@@ -493,13 +504,14 @@ static_assert(XP_SPLIT == 1 || XP_SPLIT == 2, "four or eight warps");
 constexpr uint32_t XP_Q_BYTES = XP_TN * KP * 2;
 
 struct __align__(1024) XPSmem {
-    __nv_bfloat16 a[TM * KP];         // B tile (operand A of the MMA)
+    __nv_bfloat16 a[TM * KP];         // B tile (operand A of both products); then the tile's P partial
     __nv_bfloat16 bhi[XP_TN * KP];    // Q split (operand B)
     __nv_bfloat16 blo[XP_TN * KP];
-    float in[4][XP_TN][TM];           // z, y, w0, u of the tile: [array][account][asset]
+    float in[4][XP_TN][TM];           // z, y, w0, u of the tile: [array][account][asset]; then the X tile
     uint64_t full;                    // operands landed
     uint64_t full_in[XP_TN / 4];      // inputs of accounts 4g .. 4g + 3 landed
     uint64_t done;                    // MMA complete
+    uint64_t done2;                   // the P product complete
     uint32_t tmem;
     int fail;
     float4 pa[XP_TN];                 // per account column: rho, 1/rho, L, c (NaN: c differs over positions)
@@ -571,9 +583,9 @@ __device__ __forceinline__ XPAsset xp_asset(const Dev& D, int at, int q, int lan
 // The epilogue of one tile for this warp's XP_JN accounts j0 .. j0 + XP_JN - 1: for each entry
 // v, the prox at L, the final z, y, X of a pinned entry or the record of a candidate; per
 // account and lane quarter the residual maxima and the candidate mask.
-template <bool UNIFORM>
+template <bool UNIFORM, bool FOLD>
 __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, const XPAsset& ax, const float* bq,
-                                            int j0, int q, int lane, int m_base, bool have) {
+                                            int j0, int q, int lane, int m_base, bool have, uint32_t* xpk) {
     const bool row_ok = have && ax.i < D.N;
     const float alpha = D.alpha;
     float4* crec = reinterpret_cast<float4*>(D.crec);
@@ -591,6 +603,12 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
         const float rho = pa.x, irho = pa.y, L = pa.z;
         const bool ok = row_ok && pb.y != 0.f;
         const int off = ax.obase + j * D.Npad;
+        if (FOLD && D.raw_out) {
+            // diagnostic (uniform over the launch): the X tile is the given split X, nothing is stored
+            xpk[jj] = ok ? (uint32_t(__bfloat16_as_ushort(D.Xhi[off])) |
+                            (uint32_t(__bfloat16_as_ushort(D.Xlo[off])) << 16)) : 0u;
+            continue;
+        }
         float lo = pb.x, cc = pa.w;
         const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
         if (!UNIFORM) {
@@ -612,16 +630,26 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
         const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
         const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
         // v of a pinned entry is not stored: it is l + y / rho from the y written below, which is
-        // all a later recomputation of its sector needs; z is stored only when it changes
+        // all a later recomputation of its sector needs; z is stored only when it changes. Its
+        // X = Delta^{-1} (mu + rho l - y), split into two BF16 terms, is stored for the product
+        // kernel, or with the products folded enters the tile's B'X partial through the X tile
+        // (zero for every other entry)
         if (cand) D.v[off] = v;
+        uint32_t xp = 0u;
         if (pin) {
             if (z0 != lo) D.z[off] = lo;
             D.y[off] = yn;
             const float X = (ax.mu + rho * lo - yn) * inv;
             const __nv_bfloat16 h = __float2bfloat16_rn(X);
-            D.Xhi[off] = h;
-            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+            const __nv_bfloat16 l = __float2bfloat16_rn(X - __bfloat162float(h));
+            if constexpr (FOLD) {
+                xp = uint32_t(__bfloat16_as_ushort(h)) | (uint32_t(__bfloat16_as_ushort(l)) << 16);
+            } else {
+                D.Xhi[off] = h;                     // for the separate product kernel
+                D.Xlo[off] = l;
+            }
         }
+        if constexpr (FOLD) xpk[jj] = xp;
         if (cand) {
             // what the roots kernel needs of a candidate, in one 32-byte record: v, w0, u,
             // z, y, mu, d (l and c are read per entry there when they differ over the account)
@@ -677,9 +705,29 @@ __device__ __forceinline__ void xp_tile_out(const Dev& D, const float (*r5)[5][X
     }
 }
 
+// The X tile of the B'X partial: [XP_TN accounts][128 positions] per BF16 term (4 KB), K-major
+// with the 128-byte swizzle: two 64-position blocks of 2 KB, in each the 8-row groups 1024 B
+// apart, and in each 128-byte row the 16-byte chunk (p % 64) / 8 stored at chunk XOR (row % 8).
+constexpr uint32_t XT_BYTES = XP_TN * TM * 2;
+
+static_assert(XP_TN == 16, "the P readback holds 16 accounts");
+static_assert(2 * XT_BYTES <= sizeof(float) * 4 * XP_TN * TM, "the X tile fits in the inputs' buffer");
+
+__device__ __forceinline__ uint32_t xtile_off(int j, int p) {
+    const int c = p & 63;
+    return uint32_t((p >> 6) * 2048 + (j >> 3) * 1024 + (j & 7) * 128 + (((c >> 3) ^ (j & 7)) << 4) + (c & 7) * 2);
+}
+
 // UNIFORM: every account has one l over its positions and one c over those with u > l (the
-// values come from shared memory; no per-entry l, c and no segment sums of l)
-template <bool UNIFORM>
+// values come from shared memory; no per-entry l, c and no segment sums of l).
+//
+// After the epilogue each CTA forms the B'X partial of its tile over the entries it pinned
+// (the G2 product of those entries; the candidates' share is added per account by
+// k_prox_roots): a second MMA, D2 (64 factors x XP_TN accounts) = B_tile' X_tile, reads the
+// B tile already in shared memory as an MN-major operand (factors contiguous) and the X tile
+// written by the epilogue, and the partial goes out as one set per asset tile,
+// Pxp[tile][m][0..63] (k_prox_roots sums the sets in a fixed order).
+template <bool UNIFORM, bool FOLD>
 __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constant__ XPMaps mp, Dev D) {
     extern __shared__ unsigned char raw[];
     XPSmem& s = *reinterpret_cast<XPSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
@@ -688,103 +736,154 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
     const int m_end = D.m1 ? D.m1 : D.M;
     const int m_base = D.m0 + blockIdx.y * XP_TN;       // first account of the tile
     constexpr uint32_t IDESC = idesc_bf16(TM, XP_TN);
+    constexpr uint32_t IDESC_P = idesc_bf16(64, XP_TN) | (1u << 15);   // operand A transposed (MN-major)
     {
         const int m = m_base + tid;
         const int act = tid < XP_TN && (m < m_end && D.active[m]);
         if (!__syncthreads_or(act)) return;
     }
-    if (warp == 0) tmem_alloc(&s.tmem, 32);
-    if (tid == 0) {
-        mbar_init(&s.full, 1);
-        for (int g = 0; g < XP_TN / 4; ++g) mbar_init(&s.full_in[g], 1);
-        mbar_init(&s.done, 1);
-        s.fail = 0;
-        fence_barrier_init();
-    }
-    if (tid < XP_TN) {
-        const int m = m_base + tid;
-        const bool ok = m < m_end;
-        const float r = ok ? rho_of_idx(D.rho_idx[m]) : 1.f;
-        const float L = ok ? D.nu[m] - fmaxf(4.f * D.dnu[m], 2e-3f) : 0.f;
-        s.pa[tid] = make_float4(r, 1.f / r, L, ok ? D.c_u[m] : 0.f);
-        const bool act = ok && D.active[m];
-        const bool adapt = act && ((D.iters[m] + 1) % D.adapt_every == 0);
-        s.pb[tid] = make_float4(ok ? D.lo_u[m] : 0.f, act ? 1.f : 0.f, adapt ? 1.f : 0.f, 0.f);
-    }
-    fence_before_sync();
-    __syncthreads();
-    fence_after_sync();
-    const uint32_t tmem = s.tmem;
-    if (tid == 0) {
-        // B and the tile's inputs first (columns beyond Npad and rows beyond M arrive as
-        // zeros): none of them comes from the small solve just before; Q after it. The inputs
-        // come in four groups of four accounts, each with its own barrier, so that the epilogue
-        // starts on the first group while the others are in flight. A group whose accounts all
-        // iterate takes one box per array; otherwise one 128-position row per active account
-        // and array, so that the traffic follows the accounts still iterating (the rows of
-        // inactive accounts are left unread: their entries are skipped).
-        mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
-        tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
-        for (int g = 0; g < XP_TN / 4; ++g) {
-            int nact = 0;
-            for (int j = 4 * g; j < 4 * g + 4; ++j) nact += s.pb[j].y != 0.f;
-            mbar_expect_tx(&s.full_in[g], (uint32_t)nact * 4u * (TM * 4u));
-            if (nact == 4) {
-                tma_load_2d(s.in[0][4 * g], &mp.z, &s.full_in[g], at * TM, m_base + 4 * g);
-                tma_load_2d(s.in[1][4 * g], &mp.y, &s.full_in[g], at * TM, m_base + 4 * g);
-                tma_load_2d(s.in[2][4 * g], &mp.w0, &s.full_in[g], at * TM, m_base + 4 * g);
-                tma_load_2d(s.in[3][4 * g], &mp.up, &s.full_in[g], at * TM, m_base + 4 * g);
-            } else {
-                for (int j = 4 * g; j < 4 * g + 4; ++j) {
-                    if (s.pb[j].y == 0.f) continue;
-                    const int m = m_base + j;
-                    tma_load_2d(s.in[0][j], &mp.zr, &s.full_in[g], at * TM, m);
-                    tma_load_2d(s.in[1][j], &mp.yr, &s.full_in[g], at * TM, m);
-                    tma_load_2d(s.in[2][j], &mp.w0r, &s.full_in[g], at * TM, m);
-                    tma_load_2d(s.in[3][j], &mp.upr, &s.full_in[g], at * TM, m);
+    {
+        if (warp == 0) tmem_alloc(&s.tmem, 32);
+        if (tid == 0) {
+            mbar_init(&s.full, 1);
+            for (int g = 0; g < XP_TN / 4; ++g) mbar_init(&s.full_in[g], 1);
+            mbar_init(&s.done, 1);
+            mbar_init(&s.done2, 1);
+            s.fail = 0;
+            fence_barrier_init();
+        }
+        if (tid < XP_TN) {
+            const int m = m_base + tid;
+            const bool ok = m < m_end;
+            const float r = ok ? rho_of_idx(D.rho_idx[m]) : 1.f;
+            const float L = ok ? D.nu[m] - fmaxf(4.f * D.dnu[m], 2e-3f) : 0.f;
+            s.pa[tid] = make_float4(r, 1.f / r, L, ok ? D.c_u[m] : 0.f);
+            const bool act = ok && D.active[m];
+            const bool adapt = act && ((D.iters[m] + 1) % D.adapt_every == 0);
+            s.pb[tid] = make_float4(ok ? D.lo_u[m] : 0.f, act ? 1.f : 0.f, adapt ? 1.f : 0.f, 0.f);
+        }
+        fence_before_sync();
+        __syncthreads();
+        fence_after_sync();
+        const uint32_t tmem = s.tmem;
+        if (tid == 0) {
+            // B and the tile's inputs first (columns beyond Npad and rows beyond M arrive as
+            // zeros): none of them comes from the small solve just before; Q after it. The inputs
+            // come in four groups of four accounts, each with its own barrier, so that the epilogue
+            // starts on the first group while the others are in flight. A group whose accounts all
+            // iterate takes one box per array; otherwise one 128-position row per active account
+            // and array, so that the traffic follows the accounts still iterating (the rows of
+            // inactive accounts are left unread: their entries are skipped).
+            mbar_expect_tx(&s.full, G4_TILE_BYTES + 2 * XP_Q_BYTES);
+            tma_load_2d(s.a, &mp.B, &s.full, 0, at * TM);
+            for (int g = 0; g < XP_TN / 4; ++g) {
+                int nact = 0;
+                for (int j = 4 * g; j < 4 * g + 4; ++j) nact += s.pb[j].y != 0.f;
+                mbar_expect_tx(&s.full_in[g], (uint32_t)nact * 4u * (TM * 4u));
+                if (nact == 4) {
+                    tma_load_2d(s.in[0][4 * g], &mp.z, &s.full_in[g], at * TM, m_base + 4 * g);
+                    tma_load_2d(s.in[1][4 * g], &mp.y, &s.full_in[g], at * TM, m_base + 4 * g);
+                    tma_load_2d(s.in[2][4 * g], &mp.w0, &s.full_in[g], at * TM, m_base + 4 * g);
+                    tma_load_2d(s.in[3][4 * g], &mp.up, &s.full_in[g], at * TM, m_base + 4 * g);
+                } else {
+                    for (int j = 4 * g; j < 4 * g + 4; ++j) {
+                        if (s.pb[j].y == 0.f) continue;
+                        const int m = m_base + j;
+                        tma_load_2d(s.in[0][j], &mp.zr, &s.full_in[g], at * TM, m);
+                        tma_load_2d(s.in[1][j], &mp.yr, &s.full_in[g], at * TM, m);
+                        tma_load_2d(s.in[2][j], &mp.w0r, &s.full_in[g], at * TM, m);
+                        tma_load_2d(s.in[3][j], &mp.upr, &s.full_in[g], at * TM, m);
+                    }
                 }
             }
         }
-    }
-    pdl_wait();
-    pdl_trigger();
-    if (tid == 0) {
-        tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, m_base);
-        tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, m_base);
-    }
-    const int q = warp & 3;                             // TMEM lane quarter
-    const int j0 = (warp >> 2) * XP_JN;                 // first account (column) of this warp
-    const XPAsset ax = xp_asset(D, at, q, lane, m_base);
-    if (tid == 0) {
-        if (mbar_wait(&s.full, 0, D.err, 16)) {
-            fence_after_sync();
-            const uint64_t da = sw128_desc(s.a), dh = sw128_desc(s.bhi), dl = sw128_desc(s.blo);
-#pragma unroll
-            for (int kk = 0; kk < KP / 16; ++kk) {
-                umma_bf16(tmem, da + 2 * kk, dh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
-                umma_bf16(tmem, da + 2 * kk, dl + 2 * kk, IDESC, 1u);
-            }
-            umma_commit(&s.done);
-        } else {
-            s.fail = 1;
+        pdl_wait();
+        pdl_trigger();
+        if (tid == 0) {
+            tma_load_2d(s.bhi, &mp.Qhi, &s.full, 0, m_base);
+            tma_load_2d(s.blo, &mp.Qlo, &s.full, 0, m_base);
         }
+        const int q = warp & 3;                             // TMEM lane quarter
+        const int j0 = (warp >> 2) * XP_JN;                 // first account (column) of this warp
+        const XPAsset ax = xp_asset(D, at, q, lane, m_base);
+        if (tid == 0) {
+            if (mbar_wait(&s.full, 0, D.err, 16)) {
+                fence_after_sync();
+                const uint64_t da = sw128_desc(s.a), dh = sw128_desc(s.bhi), dl = sw128_desc(s.blo);
+#pragma unroll
+                for (int kk = 0; kk < KP / 16; ++kk) {
+                    umma_bf16(tmem, da + 2 * kk, dh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
+                    umma_bf16(tmem, da + 2 * kk, dl + 2 * kk, IDESC, 1u);
+                }
+                umma_commit(&s.done);
+            } else {
+                s.fail = 1;
+            }
+        }
+        __syncthreads();
+        bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
+        have = __syncthreads_and(have);
+        fence_after_sync();
+        float bq[XP_JN];
+        if (have) {
+            if constexpr (XP_JN == 16) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
+            else tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(j0), bq);
+        }
+        const XPTileView tv{s.in, s.pa, s.pb, s.full_in, 0u, s.r5, s.cm};
+        uint32_t xpk[XP_JN];
+        xp_accounts<UNIFORM, FOLD>(D, tv, ax, bq, j0, q, lane, m_base, have, xpk);
+        fence_before_sync();
+        __syncthreads();
+        if constexpr (!FOLD) {
+            if (warp == 0) tmem_dealloc(tmem, 32);
+            if (have) xp_tile_out(D, s.r5, s.cm, s.pb, m_base, m_end, at, tid, XP_THREADS);
+            return;
+        }
+        // the staged inputs are consumed: their buffer takes the X tile (hi term, then lo)
+        uint8_t* xt = reinterpret_cast<uint8_t*>(&s.in[0][0][0]);
+#pragma unroll
+        for (int jj = 0; jj < XP_JN; ++jj) {
+            const uint32_t o = xtile_off(j0 + jj, ax.ia);
+            *reinterpret_cast<uint16_t*>(xt + o) = uint16_t(xpk[jj] & 0xffffu);
+            *reinterpret_cast<uint16_t*>(xt + XT_BYTES + o) = uint16_t(xpk[jj] >> 16);
+        }
+        fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0 && have) {
+            fence_after_sync();
+            const uint64_t da = sw128_desc(s.a, 1024), dh = sw128_desc(xt), dl = sw128_desc(xt + XT_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < TM / 16; ++kk) {
+                // 16 positions per MMA: 16 rows of 128 B further in the B tile; +32 B in the X
+                // tile's swizzled rows, and its next 64-position block 2 KB on
+                const uint64_t oa = uint64_t(kk * 16 * 128) >> 4;
+                const uint64_t ob = uint64_t((kk >> 2) * 2048 + (kk & 3) * 32) >> 4;
+                umma_bf16(tmem + 16u, da + oa, dh + ob, IDESC_P, kk > 0 ? 1u : 0u);
+                umma_bf16(tmem + 16u, da + oa, dl + ob, IDESC_P, 1u);
+            }
+            umma_commit(&s.done2);
+        }
+        __syncthreads();
+        bool have2 = have && mbar_wait(&s.done2, 0, D.err, 128);
+        have2 = __syncthreads_and(have2);
+        fence_after_sync();
+        // D2 with M = 64: factor 16 w + l in lane l < 16 of TMEM lane quarter w, accounts in columns;
+        // the partial set of this tile, 16 consecutive factors per warp and account
+        if (warp < 4) {
+            float pv[16];
+            if (have2) tmem_ld16(tmem + (uint32_t(warp * 32) << 16) + 16u, pv);
+            if (have2 && lane < 16)
+#pragma unroll
+                for (int j = 0; j < XP_TN; ++j) {
+                    const int m = m_base + j;
+                    if (m < m_end) D.Pxp[((size_t)at * D.M + m) * KP + warp * 16 + lane] = pv[j];
+                }
+        }
+        fence_before_sync();
+        __syncthreads();
+        if (warp == 0) tmem_dealloc(tmem, 32);
+        if (have && !D.raw_out) xp_tile_out(D, s.r5, s.cm, s.pb, m_base, m_end, at, tid, XP_THREADS);
     }
-    __syncthreads();
-    bool have = !s.fail && mbar_wait(&s.done, 0, D.err, 32);
-    have = __syncthreads_and(have);
-    fence_after_sync();
-    float bq[XP_JN];
-    if (have) {
-        if constexpr (XP_JN == 16) tmem_ld16(tmem + (uint32_t(q * 32) << 16), bq);
-        else tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(j0), bq);
-    }
-    const XPTileView tv{s.in, s.pa, s.pb, s.full_in, 0u, s.r5, s.cm};
-    xp_accounts<UNIFORM>(D, tv, ax, bq, j0, q, lane, m_base, have);
-    fence_before_sync();
-    __syncthreads();
-    if (warp == 0) tmem_dealloc(tmem, 32);
-    if (!have) return;
-    xp_tile_out(D, s.r5, s.cm, s.pb, m_base, m_end, at, tid, XP_THREADS);
 }
 
 // ---------------------------------------------------------------------------
@@ -909,13 +1008,10 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl) {
     if (!ok) { set_error("tensor map encoding failed (G4 fused)"); return; }
     const size_t smem = sizeof(tc::XPSmem) + 1024;
     dim3 grid(cdiv(D.N, tc::TM), cdiv((D.m1 ? D.m1 : D.M) - D.m0, tc::XP_TN));
-    if (D.uniform) {
-        cudaFuncSetAttribute(tc::k_tc_xprox<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        launch_ex(tc::k_tc_xprox<true>, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
-    } else {
-        cudaFuncSetAttribute(tc::k_tc_xprox<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-        launch_ex(tc::k_tc_xprox<false>, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
-    }
+    auto kern = D.fold ? (D.uniform ? tc::k_tc_xprox<true, true> : tc::k_tc_xprox<false, true>)
+                       : (D.uniform ? tc::k_tc_xprox<true, false> : tc::k_tc_xprox<false, false>);
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    launch_ex(kern, grid, dim3(tc::XP_THREADS), smem, st, pdl, mp, D);
 }
 
 }  // namespace prism

@@ -20,6 +20,7 @@ PRISM_ERR_ARGUMENT, PRISM_ERR_CUDA, PRISM_ERR_ALLOCATION, PRISM_ERR_UNSUPPORTED 
 PRISM_CERTIFIED, PRISM_FEASIBLE_NONCERTIFIED, PRISM_TIMEOUT, PRISM_DEADLINE_EXCEEDED = 0, 1, 2, 3
 PRISM_NO_FEASIBLE_RETURN, PRISM_ALLOCATION_FAILURE, PRISM_NUMERICAL_FAILURE = 4, 5, 6
 PRISM_PLAIN_FP32, PRISM_BATCHED_FP32, PRISM_BATCHED_BF16, PRISM_PLAIN_FP64 = 0, 1, 2, 3
+PRISM_PRODUCTS_FUSED = 0x100        # prism_shared_b_products: P from the fused x-update kernel
 PRISM_NDIAG = 8
 (PRISM_DIAG_BUDGET, PRISM_DIAG_BOX, PRISM_DIAG_EXPOSURE, PRISM_DIAG_TURNOVER, PRISM_DIAG_STAT, PRISM_DIAG_COMP,
  PRISM_DIAG_OBJ, PRISM_DIAG_ERR_EST) = range(8)
@@ -61,7 +62,8 @@ class _Opts(C.Structure):
                 ("check_every", C.c_int32), ("min_iter", C.c_int32), ("polish_rounds", C.c_int32),
                 ("precision", C.c_int32), ("use_graph", C.c_int32), ("keep_for_backward", C.c_int32),
                 ("profile", C.c_int32), ("polish_overlap", C.c_double), ("chains", C.c_int32), ("stream_after", C.c_int32), ("fuse_prox", C.c_int32),
-                ("cuda_stream", C.c_void_p), ("ragged_layout", C.c_int32), ("g2_sets", C.c_int32)]
+                ("cuda_stream", C.c_void_p), ("ragged_layout", C.c_int32), ("g2_sets", C.c_int32),
+                ("fold_products", C.c_int32)]
 
 
 class _Result(C.Structure):

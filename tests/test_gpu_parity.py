@@ -180,3 +180,20 @@ def test_g2_tile_shapes_keep_parity(sets):
     assert np.all(res["status"] == prism.PRISM_CERTIFIED)
     assert float(np.max(np.abs(res["w"] - ref["w"]))) <= 1e-9
     assert_parity(uni, batch, res, accounts=[0, 129])
+
+
+@pytest.mark.parametrize("varied", [False, True])
+@pytest.mark.parametrize("chains", [1, 4])
+def test_folded_products_keep_parity(varied, chains):
+    # B'X of the pinned entries inside the fused x-update and the rest plus the K x K solve in the
+    # roots kernel: the same products in another order (and split), so after the FP64 polish the
+    # same weights; the book's penalties change during the iterations, which takes the accounts
+    # concerned through the product kernels for one iteration
+    uni, batch = make_workload(1, N=1200, K=64, M=520)
+    if varied:
+        batch = _varied_costs_and_floors(batch)
+    ref = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, chains=chains)
+    res = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, chains=chains, fold_products=1)
+    assert np.all(res["status"] == prism.PRISM_CERTIFIED), res["status"]
+    assert float(np.max(np.abs(res["w"] - ref["w"]))) <= 1e-9
+    assert_parity(uni, batch, res, accounts=[0, 255, 519])

@@ -4,7 +4,10 @@ The reference restates each product in FP64 numpy with the operands the kernels
 are defined on: FP32-rounded X, Q and B for the SIMT path; for the tensor-core
 path B rounded to BF16 (round-to-nearest-even) and X, Q split as hi = bf16(v),
 lo = bf16(v - hi). What is left is FP32 accumulation, bounded here by
-1e-5 x sum |terms| (K or N terms of FP32 rounding, far below it).
+1e-5 x sum |terms| (K or N terms of FP32 rounding, far below it). The tensor-core
+P is checked twice: from the separate G2 kernel, and from the fused x-update
+kernel's own product (B tile read transposed, X tile from the epilogue, partials
+summed over each cluster of asset tiles), which carries G2 inside the iteration.
 """
 import numpy as np
 import pytest
@@ -37,7 +40,8 @@ def split(x):
 
 
 @pytest.mark.parametrize("N,K,M", [(1200, 64, 130), (700, 32, 5), (10000, 64, 500), (333, 48, 129)])
-@pytest.mark.parametrize("precision", [prism.PRISM_BATCHED_BF16, prism.PRISM_BATCHED_FP32])
+@pytest.mark.parametrize("precision", [prism.PRISM_BATCHED_BF16, prism.PRISM_BATCHED_BF16 | prism.PRISM_PRODUCTS_FUSED,
+                                       prism.PRISM_BATCHED_FP32])
 def test_products_match_restatement(N, K, M, precision):
     uni, _ = make_workload(1, N=N, K=K, M=1)
     rng = np.random.default_rng(N + K + M)
@@ -48,7 +52,7 @@ def test_products_match_restatement(N, K, M, precision):
         P, BQ = prism.prism_shared_b_products(h, X, Q, precision)
     finally:
         h.close()
-    if precision == prism.PRISM_BATCHED_BF16:
+    if precision & 0xff == prism.PRISM_BATCHED_BF16:
         Bm = bf16(uni.B.astype(np.float32))
         xh, xl = split(X)
         qh, ql = split(Q)
