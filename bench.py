@@ -520,7 +520,7 @@ def run_gpu(args, dist, rank, world, local_rank):
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
         tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm", "g2_sets",
-                                   "fold_products")}
+                                   "fold_products", "adapt_every")}
         opts.update(tuned)
 
     if args.chains is not None:

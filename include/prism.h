@@ -168,6 +168,9 @@ typedef struct {
                                  kernels work only for accounts whose penalty changed or whose pinned
                                  entries were rewritten; 0 = those kernels every iteration (default 0:
                                  faster on the workloads measured; searched by prism_autotune) */
+    int32_t adapt_every;      /* iterations between penalty adaptations of an account (residual
+                                 balancing on the rho grid; 0 = 25) (default 25; searched by
+                                 prism_autotune) */
 } prism_solve_opts;
 
 /* Fill *o with the defaults documented above. */
@@ -310,12 +313,13 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
  * before the streaming form (2 .. 10), the account chains (1, 2, 4) and the ADMM target
  * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16),
- * the folded products (fold_products 0, 1; BATCHED_BF16) and, for books of ragged accounts,
+ * the folded products (fold_products 0, 1; BATCHED_BF16), the penalty adaptation period
+ * (adapt_every 10 .. 50) and, for books of ragged accounts,
  * the layout (dense-masked or packed), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts
  * per second of device time; one that certifies fewer accounts never wins, and one that
  * certifies as many must be faster than the best so far by more than 1%. Writes the
- * chosen options to *tuned (the other fields copied from base). Runs about 70 full solves,
+ * chosen options to *tuned (the other fields copied from base). Runs about 100 full solves,
  * each allocated and timed like a normal call; the book's buffers may be host or device memory and are
  * only read. PLAIN_FP32 is returned unchanged. Returns PRISM_OK or the first failing
  * solve's error code. */

@@ -139,6 +139,12 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         c.eps_admm = eps;
         if ((rc = consider(c)) != PRISM_OK) return rc;
     }
+    for (int ae : {10, 15, 25, 50}) {
+        if (ae == best.adapt_every || (ae == 25 && best.adapt_every == 0)) continue;
+        prism_solve_opts c = best;
+        c.adapt_every = ae;
+        if ((rc = consider(c)) != PRISM_OK) return rc;
+    }
     if (o.precision == PRISM_BATCHED_BF16) {
         // the tile shape of the tensor-core B'X: clusters of 8 CTAs per account tile (asset chunk)
         for (int gs : {1, 2, 3, 4}) {

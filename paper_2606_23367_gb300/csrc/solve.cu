@@ -853,7 +853,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.g2_sets = batched_mode_bf16 ? o->g2_sets : 0;
     D.pstride = batched_mode_bf16 ? KMAX : K;
     D.alpha = (float)o->alpha; D.eps_admm = (float)o->eps_admm; D.min_iter = o->min_iter; D.max_iter = o->max_iter;
-    D.adapt_every = 25;
+    D.adapt_every = o->adapt_every > 0 ? o->adapt_every : 25;
     P.M = M; P.N = N; P.Npad = Npad; P.K = K; P.S = S;
     P.B64 = U.d_B64; P.f64 = U.d_f64; P.d64 = U.d_d64; P.mu64 = U.d_mu64; P.sec_start = U.d_sec_start; P.sector = U.d_sector;
     P.B32 = U.d_B32; P.B32p = U.d_B32p; P.Bn1 = U.d_Bn1; P.Bn1f = U.d_Bn1f; P.mu32 = U.d_mu32;
@@ -879,7 +879,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         P64.zf = D.z; P64.nu_f = D.nu; P64.eta_hi_f = D.eta_hi; P64.eta_lo_f = D.eta_lo; P64.theta_f = D.theta;
         P64.iters = D.iters; P64.active = D.active; P64.status = D.status;
         P64.alpha = o->alpha; P64.eps = o->eps_admm; P64.rho0 = o->rho0;
-        P64.max_iter = o->max_iter; P64.min_iter = o->min_iter; P64.adapt_every = 25;
+        P64.max_iter = o->max_iter; P64.min_iter = o->min_iter; P64.adapt_every = D.adapt_every;
     }
     std::vector<int> order_h;
     if (packed) {
@@ -894,7 +894,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         PK.zf = D.z; PK.nu_f = D.nu; PK.eta_hi_f = D.eta_hi; PK.eta_lo_f = D.eta_lo; PK.theta_f = D.theta;
         PK.iters = D.iters; PK.active = D.active; PK.status = D.status;
         PK.alpha = o->alpha; PK.eps = o->eps_admm; PK.rho0 = o->rho0;
-        PK.max_iter = o->max_iter; PK.min_iter = o->min_iter; PK.adapt_every = 25;
+        PK.max_iter = o->max_iter; PK.min_iter = o->min_iter; PK.adapt_every = D.adapt_every;
         // accounts largest first (the persistent blocks take them in this order); accounts of at
         // most stage_cap names keep their entries in shared memory
         int64_t nmax = 0;
@@ -1309,6 +1309,7 @@ extern "C" void prism_default_opts(prism_solve_opts* o) {
     o->use_graph = 1;
     o->fuse_prox = 1;
     o->stream_after = 6;
+    o->adapt_every = 25;
     o->chains = 0;
     o->polish_overlap = 0.0;
     o->keep_for_backward = 0;
@@ -1330,7 +1331,7 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     if (b->lot_offsets && (!b->lot_size || !b->lot_kappa)) { set_error("lot arrays incomplete"); return PRISM_ERR_ARGUMENT; }
     if (!(o.eps_kkt > 0) || !(o.eps_admm > 0) || !(o.rho0 > 0) || !(o.alpha > 0 && o.alpha < 2) ||
         o.max_iter < 1 || o.check_every < 1 || o.g2_sets < 0 || o.g2_sets > 64 || o.ragged_layout < 0 ||
-        o.ragged_layout > 2 || o.fold_products < 0 || o.fold_products > 1) {
+        o.ragged_layout > 2 || o.fold_products < 0 || o.fold_products > 1 || o.adapt_every < 0) {
         set_error("invalid options");
         return PRISM_ERR_ARGUMENT;
     }

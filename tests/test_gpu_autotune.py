@@ -29,9 +29,11 @@ def test_autotune_schedule_is_valid_and_certifies():
         assert tuned["chains"] in (0, 1, 2, 4)
         assert tuned["g2_sets"] in (0, 1, 2, 3, 4)
         assert tuned["ragged_layout"] in (0, 1, 2)
+        assert tuned["fold_products"] in (0, 1)
+        assert tuned["adapt_every"] in (10, 15, 25, 50)
         assert tuned["precision"] == prism.PRISM_BATCHED_BF16
         opts = {k: tuned[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm",
-                                      "precision")}
+                                      "precision", "g2_sets", "fold_products", "adapt_every")}
         res = prism.solve(h, batch, **opts)
         assert np.all(res["status"] == prism.PRISM_CERTIFIED)
         assert_parity(uni, batch, res, accounts=[0, 7, 15])
