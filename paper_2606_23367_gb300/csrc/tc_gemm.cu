@@ -514,7 +514,7 @@ struct __align__(1024) XPSmem {
     uint64_t done2;                   // the P product complete
     uint32_t tmem;
     int fail;
-    float4 pa[XP_TN];                 // per account column: rho, 1/rho, L, c (NaN: c differs over positions)
+    float4 pa[XP_TN];                 // per account column: rho, 1/rho, L/rho, c/rho (NaN: c differs over positions)
     float4 pb[XP_TN];                 // l (NaN: differs), active, adaptation call, unused
     float r5[4][5][XP_TN];            // per lane quarter and account: residual maxima
     unsigned cm[4][XP_TN];            // per lane quarter and account: candidate masks
@@ -600,7 +600,7 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
             if (have) mbar_wait(&tv.full_in[j / 4], tv.par, D.err, 64);
         }
         const float4 pa = tv.pa[j], pb = tv.pb[j];
-        const float rho = pa.x, irho = pa.y, L = pa.z;
+        const float rho = pa.x, irho = pa.y, Lr = pa.z;   // Lr = L / rho
         const bool ok = row_ok && pb.y != 0.f;
         const int off = ax.obase + j * D.Npad;
         if (FOLD && D.raw_out) {
@@ -609,26 +609,26 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
                             (uint32_t(__bfloat16_as_ushort(D.Xlo[off])) << 16)) : 0u;
             continue;
         }
-        float lo = pb.x, cc = pa.w;
+        float lo = pb.x, k = pa.w;                      // k = c / rho
         const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
         if (!UNIFORM) {
             if (ok && !lou) lo = D.lo[off];
-            if (ok && isnan(cc)) cc = D.c[off];
+            if (ok && isnan(k)) k = D.c[off] * irho;
         }
-        const float k = cc * irho;
         const float z0 = tv.in[0][j][ax.ia], y0 = tv.in[1][j][ax.ia], w0 = tv.in[2][j][ax.ia], up = tv.in[3][j][ax.ia];
         const float inv = rcp_approx(ax.dd + rho);
         const float x = (ax.mu + rho * z0 - y0 - bq[jj]) * inv;
         const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
-        const float t = v - L * irho;
+        const float t = v - Lr;
         float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
         z = fminf(fmaxf(z, lo), up);
         const bool pin = ok && (z == lo);
         const bool cand = ok && !pin;
         const float yn = rho * (v - lo);
-        // a non-finite pinned update makes rp NaN (reported as a numerical failure)
-        const float e_rp = pin ? (isfinite(yn) ? fabsf(yn - y0) * irho : NAN) : 0.f;
-        const float e_rd = pin ? rho * fabsf(lo - z0) : 0.f;
+        // the residual terms before their scale (1/rho, rho: applied to the warp's maxima, which
+        // gives the same values); a non-finite update gives an infinite or NaN maximum
+        const float e_rp = pin ? fabsf(yn - y0) : 0.f;
+        const float e_rd = pin ? fabsf(lo - z0) : 0.f;
         // v of a pinned entry is not stored: it is l + y / rho from the y written below, which is
         // all a later recomputation of its sector needs; z is stored only when it changes. Its
         // X = Delta^{-1} (mu + rho l - y), split into two BF16 terms, is stored for the product
@@ -657,7 +657,8 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
             crec[2 * (size_t)off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
-        const float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd);
+        float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd) * rho;
+        rp = (rp == INFINITY) ? NAN : rp * irho;        // a non-finite pinned update: NaN (numerical failure)
         float nx = 0.f, nz = 0.f, ny = 0.f;
         if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
             nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
@@ -757,7 +758,8 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
             const bool ok = m < m_end;
             const float r = ok ? rho_of_idx(D.rho_idx[m]) : 1.f;
             const float L = ok ? D.nu[m] - fmaxf(4.f * D.dnu[m], 2e-3f) : 0.f;
-            s.pa[tid] = make_float4(r, 1.f / r, L, ok ? D.c_u[m] : 0.f);
+            const float ir = 1.f / r;
+            s.pa[tid] = make_float4(r, ir, L * ir, (ok ? D.c_u[m] : 0.f) * ir);
             const bool act = ok && D.active[m];
             const bool adapt = act && ((D.iters[m] + 1) % D.adapt_every == 0);
             s.pb[tid] = make_float4(ok ? D.lo_u[m] : 0.f, act ? 1.f : 0.f, adapt ? 1.f : 0.f, 0.f);
