@@ -300,8 +300,8 @@ int prism_shared_b_products(prism_universe* u, int32_t n_accounts, const double*
  * the universe's device (PRISM_ERR_ARGUMENT for another GPU's memory).
  *
  * The first call on a device looks up the array's device address with
- * cudaGetSymbolAddress; make that first call before any stream capture. Every
- * call reuses the same array and clears what it reads, so calls that overlap on
+ * cudaGetSymbolAddress. Every call reuses the same array and clears what it
+ * reads, so calls that overlap on
  * the GPU (two streams, two threads) race and must be serialised by the caller.
  * Only opts->eps_kkt, opts->polish_rounds and opts->cuda_stream are used. */
 int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const double* w_in,
