@@ -520,7 +520,7 @@ def run_gpu(args, dist, rank, world, local_rank):
         # the library's autotuner picks the iteration schedule for this book (untimed setup)
         t = prism.autotune(h, batch, precision=precision)
         tuned = {k: t[k] for k in ("rho0", "alpha", "check_every", "stream_after", "chains", "eps_admm", "g2_sets",
-                                   "fold_products", "adapt_every")}
+                                   "fold_products", "adapt_every", "xupdate_form")}
         opts.update(tuned)
 
     if args.chains is not None:
@@ -531,6 +531,10 @@ def run_gpu(args, dist, rank, world, local_rank):
         opts["fold_products"] = args.fold_products
         if tuned is not None:
             tuned["fold_products"] = args.fold_products
+    if args.xupdate_form is not None:
+        opts["xupdate_form"] = args.xupdate_form
+        if tuned is not None:
+            tuned["xupdate_form"] = args.xupdate_form
 
     def step(inp, out, **extra):
         return prism.prism_solve_batch(h, **inp, out=out, **opts, **extra)
@@ -769,6 +773,9 @@ def main():
     ap.add_argument("--fold-products", type=int, default=None, choices=[0, 1],
                     help="fused iterations: B'X of the pinned entries inside the x-update (1) or the separate "
                          "product kernels every iteration (0); default: the library's, or the autotuner's choice")
+    ap.add_argument("--xupdate-form", type=int, default=None, choices=[0, 1],
+                    help="fused x-update: persistent CTAs taking tiles from a counter (0) or one CTA per tile (1); "
+                         "default: the library's, or the autotuner's choice")
     ap.add_argument("--ragged-layout", type=int, default=None, choices=[1, 2],
                     help="ragged books: 1 dense-masked, 2 packed per-account blocks")
     ap.add_argument("--no-others", action="store_true", help="skip the lines of the other workloads "

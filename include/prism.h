@@ -144,7 +144,8 @@ typedef struct {
                                  the whole book is polished after the iterations; default 0) */
     int32_t chains;           /* fused iterations: the book is cut into this many account ranges
                                  (multiples of 128) that iterate independently on their own
-                                 streams; 0 = as many as fit, up to 4 (default 0) */
+                                 streams; 0 = one with the persistent x-update (xupdate_form 0),
+                                 else as many as fit, up to 4 (default 0) */
     int32_t stream_after;     /* iterations of the staged prox before the streaming form, which
                                  needs settled multipliers for its margin (default 6) */
     int32_t fuse_prox;        /* 1: for books with the L1 cost only (no lots, no cap) in BATCHED_BF16,
@@ -171,6 +172,11 @@ typedef struct {
     int32_t adapt_every;      /* iterations between penalty adaptations of an account (residual
                                  balancing on the rho grid; 0 = 25) (default 25; searched by
                                  prism_autotune) */
+    int32_t xupdate_form;     /* fused iterations without folded products: 0 = the fused x-update as
+                                 persistent CTAs (two per SM) that take 128-position x 16-account
+                                 tiles from a counter, loading the next tiles while the current one
+                                 is evaluated; 1 = one CTA per tile (same arithmetic, bit for bit)
+                                 (default 0; searched by prism_autotune) */
 } prism_solve_opts;
 
 /* Fill *o with the defaults documented above. */
@@ -313,7 +319,8 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
  * before the streaming form (2 .. 10), the account chains (1, 2, 4) and the ADMM target
  * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16),
- * the folded products (fold_products 0, 1; BATCHED_BF16), the penalty adaptation period
+ * the folded products (fold_products 0, 1; BATCHED_BF16), the form of the fused x-update
+ * (xupdate_form 0, 1; BATCHED_BF16 without folded products), the penalty adaptation period
  * (adapt_every 10 .. 50) and, for books of ragged accounts,
  * the layout (dense-masked or packed), starting
  * from *base (or the defaults when base is NULL); a candidate's score is certified accounts

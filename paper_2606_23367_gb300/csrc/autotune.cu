@@ -157,6 +157,12 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
         prism_solve_opts c = best;
         c.fold_products = 1 - best.fold_products;
         if ((rc = consider(c)) != PRISM_OK) return rc;
+        // the fused x-update as persistent CTAs or one CTA per tile (unfolded products only)
+        if (best.fold_products == 0) {
+            prism_solve_opts c2 = best;
+            c2.xupdate_form = 1 - best.xupdate_form;
+            if ((rc = consider(c2)) != PRISM_OK) return rc;
+        }
     }
     if (b->asset_idx) {
         // ragged accounts: dense-masked over the universe against packed per-account blocks

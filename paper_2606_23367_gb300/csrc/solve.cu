@@ -590,6 +590,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         D.Pxp = A.take<float>(batched_mode_bf16 ? (size_t)xp_sets_for(N) * M * KMAX : 0);
         D.needP = A.take<int>(M);
         D.pcount = A.take<unsigned long long>(2);
+        D.xq_ctr = A.take<unsigned>(2 * SolveCache::MAXCH);
         P.st = A.take<int8_t>(MN); P.wband = A.take<int>((size_t)M * S); P.wcap = A.take<int>(M);
         P.done = A.take<int>(M); P.Flist = A.take<int>((size_t)M * FMAX); P.NZlist = A.take<int>((size_t)M * FMAX);
         P.Fsig = A.take<double>((size_t)M * FMAX);
@@ -847,6 +848,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     D.fused = (D.stream_prox && batched_mode_bf16 && U.nq <= XP_NQMAX && o->fuse_prox) ? 1 : 0;
     D.nq = U.nq; D.nseg = U.nseg; D.nt = cdiv(N, 128); D.qseg = U.d_qseg; D.sseg = U.d_sseg;
     D.xp_sets = xp_sets_for(N);
+    if (!D.fused || o->xupdate_form != 0) D.xq_ctr = nullptr;   // one CTA per tile
     int* const needP_buf = D.needP;            // set for the fused loop only (null: every account)
     D.needP = nullptr;
     D.nsplit = nsplit;
@@ -949,6 +951,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
         cudaMemsetAsync(D.n_active, 0, 8, st);
         if (D.stats) cudaMemsetAsync(D.stats, 0, 32, st);
         if (D.pcount) cudaMemsetAsync(D.pcount, 0, 16, st);
+        if (D.xq_ctr) cudaMemsetAsync(D.xq_ctr, 0, 2 * SolveCache::MAXCH * sizeof(unsigned), st);
     }
     SC.prof.run(PRISM_K_OTHER, 2, st, [&] {
         k_capacity<<<M, 256, 0, st>>>(S, N, Npad, U.d_sec_start, BD.lo, BD.up, BD.w0, BD.lof, BD.upf, BD.w0f,
@@ -974,8 +977,10 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
     // run beside another range's streaming x-update. Every cut is a multiple of 128 (a product
     // tile never straddles two ranges); a range holds at least 128 accounts.
     int nch = 1;
-    if (D.fused && SC.chains_ok) nch = std::min(SolveCache::MAXCH, std::max(1, M / 128));
-    if (o->chains > 0) nch = std::min(nch, o->chains);
+    // automatic: as many chains as fit for the one-CTA-per-tile x-update; one for the persistent
+    // form, whose CTAs take every SM (measured: several chains then lose more than they overlap)
+    if (D.fused && SC.chains_ok && !D.xq_ctr) nch = std::min(SolveCache::MAXCH, std::max(1, M / 128));
+    if (D.fused && SC.chains_ok && o->chains > 0) nch = std::min(std::min(SolveCache::MAXCH, std::max(1, M / 128)), o->chains);
     auto run_chunk = [&](int n) {
         if (nch > 1 && !SC.prof.on) {
             Dev DC[SolveCache::MAXCH];
@@ -984,6 +989,7 @@ static int solve_core(prism_universe* uh, const prism_batch* b, const prism_solv
                 DC[c] = D;
                 DC[c].m0 = ((M * c / nch) + 64) / 128 * 128;
                 DC[c].m1 = (c + 1 == nch) ? M : ((M * (c + 1) / nch) + 64) / 128 * 128;
+                if (D.xq_ctr) { DC[c].xq_ctr = D.xq_ctr + 2 * c; DC[c].xq_share = nch; }   // own tile counter
                 cs[c] = c == 0 ? st : SC.chst[c - 1];
             }
             cudaEventRecord(SC.ev_fork, st);
@@ -1331,7 +1337,8 @@ extern "C" int prism_solve_batch(prism_universe* uh, const prism_batch* b, const
     if (b->lot_offsets && (!b->lot_size || !b->lot_kappa)) { set_error("lot arrays incomplete"); return PRISM_ERR_ARGUMENT; }
     if (!(o.eps_kkt > 0) || !(o.eps_admm > 0) || !(o.rho0 > 0) || !(o.alpha > 0 && o.alpha < 2) ||
         o.max_iter < 1 || o.check_every < 1 || o.g2_sets < 0 || o.g2_sets > 64 || o.ragged_layout < 0 ||
-        o.ragged_layout > 2 || o.fold_products < 0 || o.fold_products > 1 || o.adapt_every < 0) {
+        o.ragged_layout > 2 || o.fold_products < 0 || o.fold_products > 1 || o.adapt_every < 0 ||
+        o.xupdate_form < 0 || o.xupdate_form > 1) {
         set_error("invalid options");
         return PRISM_ERR_ARGUMENT;
     }

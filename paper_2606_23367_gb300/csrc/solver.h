@@ -70,10 +70,10 @@ struct Dev {
     // the streaming pass fused into the tensor-core x-update (k_tc_xprox), finished per
     // account by k_prox_roots. Partials are indexed [row][account], rows as follows.
     int fused = 0;
-    int uniform = 0;
+    int uniform = 0;                    // every account has uniform l and c (lo_u, c_u not NaN)
     // the accounts [m0, m1) this launch works on (m1 = 0: all M); G2, G3 and the fused kernels
     // take it, so that two halves of a book can iterate as independent chains
-    int m0 = 0, m1 = 0;                    // every account has uniform l and c (lo_u, c_u not NaN)
+    int m0 = 0, m1 = 0;
     int nq = 0, nseg = 0, nt = 0;       // quarters (32 positions), segments, asset tiles (128 positions)
     const int* qseg = nullptr;          // nq + 1: first segment of each quarter
     const int* sseg = nullptr;          // S + 1: first segment of each sector
@@ -94,6 +94,10 @@ struct Dev {
     float* Pxp = nullptr;
     int xp_sets = 0;
     int fold = 0;                       // the fold is on (k_tc_xprox writes no X, forms its partial)
+    // tile counter of the persistent fused x-update for this launch's chain: [0] next tile,
+    // [1] CTAs done claiming (the last resets both); null = one CTA per tile
+    unsigned* xq_ctr = nullptr;
+    int xq_share = 1;                   // chains iterating side by side (each launches 2 x SMs / this CTAs)
     int* needP = nullptr;               // M, nonzero = P and Q from the product kernels
     unsigned long long* stats = nullptr;  // [0] prox calls, [1] sector-edge evaluations, [2] budget evaluations
     // factor-exposure bounds (the Eq. 1 rows B'w in [flo, fhi]) as a second splitting block

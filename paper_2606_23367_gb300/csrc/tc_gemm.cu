@@ -542,6 +542,7 @@ __device__ __forceinline__ float warp_max_nn(float v) {
 struct XPMaps {
     CUtensorMap B, Qhi, Qlo, z, y, w0, up;   // inputs in boxes of 4 accounts
     CUtensorMap zr, yr, w0r, upr;            // the same arrays one account row at a time
+    CUtensorMap mu, d;                       // mu and d of 128 positions (persistent form)
 };
 
 // The shared-memory views of one tile, for the per-tile epilogue of the fused x-update.
@@ -889,6 +890,490 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
 }
 
 // ---------------------------------------------------------------------------
+// The same fused x-update as a persistent, warp-specialised kernel over the accounts that still
+// iterate. Two CTAs per SM (a share of that when several chains iterate side by side), each
+// taking tiles of 128 positions x 16 accounts from its chain's tile counter until none is left.
+// A tile's accounts are 16 consecutive ones of the chain's active accounts (the list is formed
+// by each CTA at its start), so an account that has stopped iterating costs no work:
+//   warp 8 (producer): claims a tile, writes its accounts and their constants into a stage of a
+//     two-stage ring, loads the B tile, mu, d and the accounts' input rows by TMA, and copies
+//     the accounts' Q split rows into the stage in the product's 128-byte-swizzled layout;
+//   warp 9 (MMA): one thread issues the B Q product of each stage into that stage's 16 TMEM
+//     columns once its operands are in place;
+//   warps 0-7 (epilogue): for each entry the pass of k_tc_xprox (the same arithmetic), then the
+//     tile's residual maxima and candidate masks; the stage goes back to the producer.
+// Every mbarrier wait is bounded; after an expired wait each role leaves its loop, waits
+// (bounded) for its own copies and products still in flight, and the CTA frees its tensor
+// memory and returns (the error flag fails the call). The last CTA to finish claiming resets
+// the counter for the next launch.
+// ---------------------------------------------------------------------------
+constexpr int XQ_STAGES = 2;
+constexpr int XQ_EPI = 256;                       // epilogue threads (warps 0-7)
+constexpr int XQ_THREADS = XQ_EPI + 64;           // + producer warp + MMA warp
+constexpr int XQ_WMAX = 256;                      // 32-account words of the active list (8,192 accounts)
+static_assert(XP_THREADS == XQ_EPI, "the epilogue assumes eight warps");
+
+struct __align__(1024) XQStage {
+    __nv_bfloat16 a[TM * KP];         // B tile (operand A)
+    __nv_bfloat16 bhi[XP_TN * KP];    // Q split rows of the tile's accounts (operand B)
+    __nv_bfloat16 blo[XP_TN * KP];
+    float in[4][XP_TN][TM];           // z, y, w0, u: [array][account column][position]
+    float md[2][TM];                  // mu, d of the tile's positions
+};
+static_assert(sizeof(XQStage) % 1024 == 0, "stages keep the operands' 1024-byte alignment");
+
+struct __align__(1024) XQSmem {
+    XQStage st[XQ_STAGES];
+    uint64_t full_bq[XQ_STAGES];              // B, mu, d landed (TMA) and the Q rows written: 2 arrivals
+    uint64_t full_in[XQ_STAGES][XP_TN / 4];   // input rows of columns 4g .. 4g + 3 landed
+    uint64_t done[XQ_STAGES];                 // the stage's product is in its TMEM columns
+    uint64_t tfree[XQ_STAGES];                // the epilogue has read those columns
+    uint64_t empty[XQ_STAGES];                // the epilogue is done with the stage
+    int at[XQ_STAGES];                        // position tile; -1: no more tiles
+    int acc[XQ_STAGES][XP_TN];                // account of each column (-1: padding)
+    float4 pa[XQ_STAGES][XP_TN];              // rho, 1/rho, L/rho, c/rho (NaN: c differs over positions)
+    float4 pb[XQ_STAGES][XP_TN];              // l (NaN: differs), active, adaptation call, unused
+    float r5[XQ_STAGES][4][5][XP_TN];         // per lane quarter and column: residual maxima
+    unsigned cm[XQ_STAGES][4][XP_TN];         // per lane quarter and column: candidate masks
+    unsigned amask[XQ_WMAX];                  // bit b of word w: account m0 + 32 w + b iterates
+    uint16_t apre[XQ_WMAX];                   // active accounts in the words before w
+    int nact;
+    uint32_t tmem;
+};
+// two CTAs per SM: 2 x (this + its alignment slack + 1 KB reserved per CTA) <= 228 KB
+static_assert(2 * (sizeof(XQSmem) + 1024 + 1024) <= 228 * 1024, "two persistent CTAs fit one SM");
+constexpr uint32_t XQ_BMD_BYTES = G4_TILE_BYTES + 2 * TM * 4;   // B tile, mu, d (by TMA)
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// the epilogue warps only (named barrier 1)
+__device__ __forceinline__ void xq_epi_sync() { asm volatile("bar.sync 1, %0;" ::"n"(XQ_EPI) : "memory"); }
+
+// the same barrier, returning to every epilogue thread whether v was true for any of them
+__device__ __forceinline__ bool xq_epi_sync_or(bool v) {
+    uint32_t r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.u32 q, %1, 0;\n bar.red.or.pred p, 1, %2, q;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(r)
+        : "r"(uint32_t(v)), "n"(XQ_EPI)
+        : "memory");
+    return r != 0;
+}
+
+// bit index of the n-th (from 0) set bit of w (w has more than n set bits)
+__device__ __forceinline__ int nth_set_bit(unsigned w, int n) {
+    for (int i = 0; i < n; ++i) w &= w - 1u;
+    return __ffs(w) - 1;
+}
+
+// The epilogue of one stage's tile for this warp's columns j0 .. j0 + XP_JN - 1: the arithmetic of
+// xp_accounts (products not folded) with each column's account taken from the stage. A padding
+// column is evaluated like the others and nothing of it is stored (no branch on the column, so
+// that the columns' reductions interleave). ax.obase is the position alone.
+template <bool UNIFORM>
+__device__ __forceinline__ void xq_accounts(const Dev& D, XQSmem& s, int sti, const XPAsset& ax, const float* bq,
+                                            int j0, int q, int lane, uint32_t par, bool have) {
+    const bool row_ok = have && ax.i < D.N;
+    const float alpha = D.alpha;
+    float4* crec = reinterpret_cast<float4*>(D.crec);
+    const XQStage& S = s.st[sti];
+#pragma unroll
+    for (int jj = 0; jj < XP_JN; ++jj) {
+        const int j = j0 + jj;
+        if (jj % 4 == 0 && have) mbar_wait(&s.full_in[sti][j / 4], par, D.err, 64);
+        const int m = s.acc[sti][j];
+        const float4 pa = s.pa[sti][j], pb = s.pb[sti][j];
+        const float rho = pa.x, irho = pa.y, Lr = pa.z;   // Lr = L / rho
+        const bool ok = row_ok && m >= 0;
+        const size_t off = (size_t)(m >= 0 ? m : 0) * D.Npad + ax.obase;
+        float lo = pb.x, k = pa.w;                      // k = c / rho
+        const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
+        if (!UNIFORM) {
+            if (ok && !lou) lo = D.lo[off];
+            if (ok && isnan(k)) k = D.c[off] * irho;
+        }
+        const float z0 = S.in[0][j][ax.ia], y0 = S.in[1][j][ax.ia], w0 = S.in[2][j][ax.ia], up = S.in[3][j][ax.ia];
+        const float inv = rcp_approx(ax.dd + rho);
+        const float x = (ax.mu + rho * z0 - y0 - bq[jj]) * inv;
+        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
+        const float t = v - Lr;
+        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
+        z = fminf(fmaxf(z, lo), up);
+        const bool pin = ok && (z == lo);
+        const bool cand = ok && !pin;
+        const float yn = rho * (v - lo);
+        const float e_rp = pin ? fabsf(yn - y0) : 0.f;
+        const float e_rd = pin ? fabsf(lo - z0) : 0.f;
+        if (cand) D.v[off] = v;
+        if (pin) {
+            if (z0 != lo) D.z[off] = lo;
+            D.y[off] = yn;
+            const float X = (ax.mu + rho * lo - yn) * inv;
+            const __nv_bfloat16 h = __float2bfloat16_rn(X);
+            D.Xhi[off] = h;
+            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+        }
+        if (cand) {
+            crec[2 * off] = make_float4(v, w0, up, z0);
+            crec[2 * off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
+        }
+        const unsigned cm = __ballot_sync(0xffffffffu, cand);
+        float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd) * rho;
+        rp = (rp == INFINITY) ? NAN : rp * irho;        // a non-finite pinned update: NaN (numerical failure)
+        float nx = 0.f, nz = 0.f, ny = 0.f;
+        if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
+            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
+            ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
+            if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);
+        }
+        if (!UNIFORM && !lou) {
+            for (int g = 0; g < ax.nsegq; ++g) {
+                const bool mine = (ax.i < D.N) && ax.segl == g && pin;
+                const float sg = warp_sum_f(mine ? lo : 0.f);
+                if (lane == 0 && m >= 0) D.SOp[(size_t)(ax.sbase + g) * D.M + m] = sg;
+            }
+        }
+        if (lane == 0) {
+            s.r5[sti][q][0][j] = rp;
+            s.r5[sti][q][1][j] = rd; s.r5[sti][q][2][j] = nx; s.r5[sti][q][3][j] = nz; s.r5[sti][q][4][j] = ny;
+            s.cm[sti][q][j] = cm;
+        }
+    }
+}
+
+// Per-tile outputs of a stage: the residual maxima over the four quarters (NaN kept) and the
+// masks, by account. Epilogue thread t.
+__device__ __forceinline__ void xq_tile_out(const Dev& D, const XQSmem& s, int sti, int at, int t) {
+    if (t < 5 * XP_TN) {
+        const int kq = t / XP_TN, col = t % XP_TN, m = s.acc[sti][col];
+        if (m >= 0) {
+            float r = 0.f;
+            bool nan_ = false;
+#pragma unroll
+            for (int qq = 0; qq < 4; ++qq) {
+                const float x = s.r5[sti][qq][kq][col];
+                nan_ |= isnan(x);
+                r = fmaxf(r, x);
+            }
+            D.Rt[((size_t)m * 5 + kq) * D.nt + at] = nan_ ? NAN : r;
+        }
+    } else if (t >= 128 && t < 128 + 4 * XP_TN) {
+        const int w = (t - 128) / XP_TN, col = (t - 128) % XP_TN, m = s.acc[sti][col];
+        const int g = at * 4 + w;
+        if (m >= 0 && g < D.nq) D.Cm[(size_t)m * D.nq + g] = s.cm[sti][w][col];
+    }
+}
+
+template <bool UNIFORM>
+__global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_constant__ XPMaps mp, Dev D) {
+    extern __shared__ unsigned char raw[];
+    XQSmem& s = *reinterpret_cast<XQSmem*>((reinterpret_cast<uintptr_t>(raw) + 1023) & ~uintptr_t(1023));
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int m_end = D.m1 ? D.m1 : D.M;
+    const int nat = D.nt;
+    const int nw = cdiv(m_end - D.m0, 32);              // <= XQ_WMAX (checked by the host)
+    constexpr int PROD = XQ_EPI / 32, MMAW = PROD + 1;
+    constexpr uint32_t IDESC = idesc_bf16(TM, XP_TN);
+    if (warp == 0) tmem_alloc(&s.tmem, 32);
+    if (warp == PROD) {
+        // the chain's accounts that iterate (the flags were written by kernels two or more
+        // launches back, so they are readable before the dependency wait): a bit mask per 32
+        // accounts and the count before each word
+        for (int w0 = 0; w0 < nw; w0 += 8) {
+            bool a[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const int m = D.m0 + 32 * (w0 + u) + lane;
+                a[u] = (w0 + u < nw) && m < m_end && D.active[m] != 0;
+            }
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                const unsigned b = __ballot_sync(0xffffffffu, a[u]);
+                if (lane == 0 && w0 + u < nw) s.amask[w0 + u] = b;
+            }
+        }
+        __syncwarp();
+        int c = 0;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int w = lane * 8 + u;
+            if (w < nw) c += __popc(s.amask[w]);
+        }
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += v;
+        }
+        int run = incl - c;
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int w = lane * 8 + u;
+            if (w < nw) {
+                s.apre[w] = (uint16_t)run;
+                run += __popc(s.amask[w]);
+            }
+        }
+        if (lane == 31) s.nact = incl;
+        if (lane == 0) {
+            for (int i = 0; i < XQ_STAGES; ++i) {
+                mbar_init(&s.full_bq[i], 2);
+                for (int g = 0; g < XP_TN / 4; ++g) mbar_init(&s.full_in[i][g], 1);
+                mbar_init(&s.done[i], 1);
+                mbar_init(&s.tfree[i], XQ_EPI / 32);
+                mbar_init(&s.empty[i], XQ_EPI / 32);
+            }
+            fence_barrier_init();
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    const uint32_t tmem = s.tmem;
+    if (warp == PROD) {
+        // ---- producer. The claim of the next tile and the constants of its accounts are fetched
+        // before the wait for a free stage, so that their latency overlaps it.
+        unsigned* ctr = D.xq_ctr;
+        const int nact = s.nact;
+        const int total = cdiv(nact, XP_TN) * nat;
+        static_assert(XQ_STAGES == 2, "the last use of each stage is kept in two registers");
+        int last0 = -1, last1 = -1;      // last use of each stage that issued loads
+        bool waited = false;
+        int t = 0;
+        if (lane == 0) t = (int)atomicAdd(ctr, 1u);
+        t = __shfl_sync(0xffffffffu, t, 0);
+        for (int k = 0;; ++k) {
+            const int sti = k % XQ_STAGES, use = k / XQ_STAGES;
+            XQStage& S = s.st[sti];
+            const bool more = t < total;
+            const int grp = more ? t / nat : 0, at = more ? t % nat : 0;
+            // lane j < 16: the (16 grp + j)-th active account of the chain, and its constants
+            int m = -1, ridx = 0, itr = 0;
+            float nu = 0.f, dnu = 0.f, cu = 0.f, lu = 0.f;
+            if (more && lane < XP_TN) {
+                const int r = grp * XP_TN + lane;
+                if (r < nact) {
+                    int lo = 0, hi = nw - 1;                 // the last word with apre <= r
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if ((int)s.apre[mid] <= r) lo = mid; else hi = mid - 1;
+                    }
+                    m = D.m0 + 32 * lo + nth_set_bit(s.amask[lo], r - (int)s.apre[lo]);
+                    ridx = D.rho_idx[m]; nu = D.nu[m]; dnu = D.dnu[m]; cu = D.c_u[m]; lu = D.lo_u[m];
+                    itr = D.iters[m];
+                }
+            }
+            int tn = 0;
+            if (more && lane == 0) tn = (int)atomicAdd(ctr, 1u);
+            if (use > 0 && !mbar_wait(&s.empty[sti], (use - 1) & 1, D.err, 256)) break;
+            if (!more) {
+                if (lane == 0) {
+                    s.at[sti] = -1;
+                    mbar_arrive(&s.full_in[sti][0]);
+                    mbar_arrive(&s.full_bq[sti]);
+                    mbar_arrive(&s.full_bq[sti]);
+                    if (atomicAdd(ctr + 1, 1u) == gridDim.x - 1) {
+                        ctr[0] = 0;
+                        ctr[1] = 0;
+                    }
+                }
+                if (sti == 0) last0 = -1; else last1 = -1;   // released by the epilogue, no loads since
+                break;
+            }
+            if (lane < XP_TN) {
+                const bool ok = m >= 0;
+                const float r = ok ? rho_of_idx(ridx) : 1.f;
+                const float L = ok ? nu - fmaxf(4.f * dnu, 2e-3f) : 0.f;
+                const float ir = 1.f / r;
+                const bool adapt = ok && ((itr + 1) % D.adapt_every == 0);
+                s.acc[sti][lane] = m;
+                s.pa[sti][lane] = make_float4(r, ir, L * ir, (ok ? cu : 0.f) * ir);
+                s.pb[sti][lane] = make_float4(ok ? lu : 0.f, ok ? 1.f : 0.f, adapt ? 1.f : 0.f, 0.f);
+            }
+            // columns with an account; groups of four whose accounts are consecutive take one
+            // box of four rows per array, the others a row per account; a tile of 16 consecutive
+            // accounts takes its Q split as a box too
+            const int m0c = __shfl_sync(0xffffffffu, m, 0);
+            const unsigned have_col = __ballot_sync(0xffffffffu, lane < XP_TN && m >= 0);
+            const unsigned cons = __ballot_sync(0xffffffffu, lane < XP_TN && m >= 0 && m == m0c + lane);
+            const bool qbox = (cons & 0xffffu) == 0xffffu;
+            unsigned gbox = 0u;                              // bit g: group g as one box
+#pragma unroll
+            for (int g = 0; g < XP_TN / 4; ++g) {
+                const unsigned gm = 0xfu << (4 * g);
+                const int mg = __shfl_sync(0xffffffffu, m, 4 * g);
+                const unsigned gc = __ballot_sync(0xffffffffu, lane >= 4 * g && lane < 4 * g + 4 && m >= 0 &&
+                                                                   m == mg + (lane - 4 * g));
+                if ((gc & gm) == gm) gbox |= 1u << g;
+            }
+            if (lane == 0) {
+                s.at[sti] = at;
+                mbar_expect_tx(&s.full_bq[sti], XQ_BMD_BYTES + (qbox ? 2 * XP_Q_BYTES : 0u));
+                tma_load_2d(S.a, &mp.B, &s.full_bq[sti], 0, at * TM);
+                tma_load_2d(S.md[0], &mp.mu, &s.full_bq[sti], at * TM, 0);
+                tma_load_2d(S.md[1], &mp.d, &s.full_bq[sti], at * TM, 0);
+                for (int g = 0; g < XP_TN / 4; ++g)
+                    mbar_expect_tx(&s.full_in[sti][g], (uint32_t)__popc((have_col >> (4 * g)) & 0xfu) * 4u * (TM * 4u));
+            }
+            __syncwarp();
+            if (lane < XP_TN && m >= 0) {
+                uint64_t* bar = &s.full_in[sti][lane / 4];
+                if (gbox & (1u << (lane / 4))) {
+                    if ((lane & 3) == 0) {
+                        tma_load_2d(S.in[0][lane], &mp.z, bar, at * TM, m);
+                        tma_load_2d(S.in[1][lane], &mp.y, bar, at * TM, m);
+                        tma_load_2d(S.in[2][lane], &mp.w0, bar, at * TM, m);
+                        tma_load_2d(S.in[3][lane], &mp.up, bar, at * TM, m);
+                    }
+                } else {
+                    tma_load_2d(S.in[0][lane], &mp.zr, bar, at * TM, m);
+                    tma_load_2d(S.in[1][lane], &mp.yr, bar, at * TM, m);
+                    tma_load_2d(S.in[2][lane], &mp.w0r, bar, at * TM, m);
+                    tma_load_2d(S.in[3][lane], &mp.upr, bar, at * TM, m);
+                }
+            }
+            // Q comes from the small solve just before: the first tile's other operands go out
+            // before the dependency wait, its Q after. Without the box, lane l copies 64 bytes of
+            // row l / 2 of each split term into the K-major 128-byte-swizzled layout (16-byte
+            // chunk c of row r at chunk c ^ (r % 8)); a padding row is zero.
+            if (!waited) {
+                pdl_wait();
+                pdl_trigger();
+                waited = true;
+            }
+            if (qbox) {
+                if (lane == 0) {
+                    tma_load_2d(S.bhi, &mp.Qhi, &s.full_bq[sti], 0, m0c);
+                    tma_load_2d(S.blo, &mp.Qlo, &s.full_bq[sti], 0, m0c);
+                }
+            } else {
+                const int r = lane >> 1, h = lane & 1;
+                const int mr = __shfl_sync(0xffffffffu, m, r);
+                uint4 vh[4], vl[4];
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int ch = h * 4 + c4;
+                    if (mr >= 0) {
+                        vh[c4] = reinterpret_cast<const uint4*>(D.Qhi + (size_t)mr * KP)[ch];
+                        vl[c4] = reinterpret_cast<const uint4*>(D.Qlo + (size_t)mr * KP)[ch];
+                    } else {
+                        vh[c4] = make_uint4(0u, 0u, 0u, 0u);
+                        vl[c4] = make_uint4(0u, 0u, 0u, 0u);
+                    }
+                }
+                uint8_t* bh = reinterpret_cast<uint8_t*>(S.bhi);
+                uint8_t* bl = reinterpret_cast<uint8_t*>(S.blo);
+#pragma unroll
+                for (int c4 = 0; c4 < 4; ++c4) {
+                    const int ch = h * 4 + c4;
+                    const uint32_t o = uint32_t(r * 128 + ((ch ^ (r & 7)) << 4));
+                    *reinterpret_cast<uint4*>(bh + o) = vh[c4];
+                    *reinterpret_cast<uint4*>(bl + o) = vl[c4];
+                }
+                fence_proxy_async_smem();
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.full_bq[sti]);
+            if (sti == 0) last0 = use; else last1 = use;
+            t = __shfl_sync(0xffffffffu, tn, 0);
+        }
+        if (!waited) {
+            pdl_wait();
+            pdl_trigger();
+        }
+        // copies of this CTA still in flight (none unless a wait expired)
+        if (lane == 0)
+            for (int i = 0; i < XQ_STAGES; ++i) {
+                const int lu = i == 0 ? last0 : last1;
+                if (lu < 0) continue;
+                const uint32_t par = lu & 1;
+                mbar_wait(&s.full_bq[i], par, D.err, 256);
+                for (int g = 0; g < XP_TN / 4; ++g) mbar_wait(&s.full_in[i][g], par, D.err, 256);
+            }
+        __syncwarp();
+    } else if (warp == MMAW) {
+        // ---- MMA issue
+        pdl_wait();
+        pdl_trigger();
+        if (lane == 0) {
+            int last0 = -1, last1 = -1;  // last use of each stage that issued a product
+            for (int k = 0;; ++k) {
+                const int sti = k % XQ_STAGES, use = k / XQ_STAGES;
+                if (!mbar_wait(&s.full_bq[sti], use & 1, D.err, 16)) break;
+                if (*reinterpret_cast<volatile int*>(&s.at[sti]) < 0) break;
+                if (use > 0 && !mbar_wait(&s.tfree[sti], (use - 1) & 1, D.err, 16)) break;
+                fence_after_sync();
+                const XQStage& S = s.st[sti];
+                const uint64_t da = sw128_desc(S.a), dh = sw128_desc(S.bhi), dl = sw128_desc(S.blo);
+                const uint32_t dt = tmem + uint32_t(sti * XP_TN);
+#pragma unroll
+                for (int kk = 0; kk < KP / 16; ++kk) {
+                    umma_bf16(dt, da + 2 * kk, dh + 2 * kk, IDESC, kk > 0 ? 1u : 0u);
+                    umma_bf16(dt, da + 2 * kk, dl + 2 * kk, IDESC, 1u);
+                }
+                umma_commit(&s.done[sti]);
+                if (sti == 0) last0 = use; else last1 = use;
+            }
+            // products of this CTA still running (none unless a wait expired)
+            if (last0 >= 0) mbar_wait(&s.done[0], last0 & 1, D.err, 16);
+            if (last1 >= 0) mbar_wait(&s.done[1], last1 & 1, D.err, 16);
+        }
+        __syncwarp();
+    } else {
+        // ---- epilogue
+        pdl_wait();
+        pdl_trigger();
+        const int q = warp & 3;                              // TMEM lane quarter
+        const int j0 = (warp >> 2) * XP_JN;                  // first account column of this warp
+        bool bad = false;                                    // a wait of this warp expired
+        for (int k = 0;; ++k) {
+            const int sti = k % XQ_STAGES, use = k / XQ_STAGES;
+            const uint32_t par = use & 1;
+            const bool got = mbar_wait(&s.full_in[sti][0], par, D.err, 64);
+            const int at = got ? *reinterpret_cast<volatile int*>(&s.at[sti]) : -1;
+            // every epilogue warp takes the same branch: the tile word is the same for all, and
+            // an expired wait of any warp stops all of them
+            if (xq_epi_sync_or(bad || !got || at < 0)) break;
+            // the product, and the stage's operands it followed (mu and d among them)
+            const bool have = mbar_wait(&s.done[sti], par, D.err, 32) && mbar_wait(&s.full_bq[sti], par, D.err, 32);
+            float bq[XP_JN];
+            if (have) {
+                fence_after_sync();
+                tmem_ld8(tmem + (uint32_t(q * 32) << 16) + uint32_t(sti * XP_TN + j0), bq);
+            } else {
+                bad = true;
+            }
+            fence_before_sync();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.tfree[sti]);
+            XPAsset ax;
+            if constexpr (UNIFORM) {
+                // no sector segments in this form: the position, and mu, d from the stage
+                ax.ia = q * 32 + lane;
+                ax.i = at * TM + ax.ia;
+                ax.obase = ax.i < D.N ? ax.i : 0;
+                ax.mu = s.st[sti].md[0][ax.ia];
+                ax.dd = 2.f * s.st[sti].md[1][ax.ia];
+                ax.nsegq = 0; ax.segl = 0; ax.sbase = 0;
+            } else {
+                ax = xp_asset(D, at, q, lane, 0);
+            }
+            xq_accounts<UNIFORM>(D, s, sti, ax, bq, j0, q, lane, par, have);
+            xq_epi_sync();
+            if (have) xq_tile_out(D, s, sti, at, tid);
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&s.empty[sti]);
+        }
+    }
+    fence_before_sync();
+    __syncthreads();
+    fence_after_sync();
+    if (warp == 0) tmem_dealloc(tmem, 32);
+}
+
+// ---------------------------------------------------------------------------
 // host side: tensor maps and launches
 // ---------------------------------------------------------------------------
 using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
@@ -1006,10 +1491,31 @@ void launch_tc_xprox(const Dev& D, cudaStream_t st, bool pdl) {
               tc::map2d_f32(&mp.zr, D.z, D.Npad, D.M, tc::TM, 1) &&
               tc::map2d_f32(&mp.yr, D.y, D.Npad, D.M, tc::TM, 1) &&
               tc::map2d_f32(&mp.w0r, D.w0, D.Npad, D.M, tc::TM, 1) &&
-              tc::map2d_f32(&mp.upr, D.up, D.Npad, D.M, tc::TM, 1);
+              tc::map2d_f32(&mp.upr, D.up, D.Npad, D.M, tc::TM, 1) &&
+              tc::map2d_f32(&mp.mu, D.mu32, D.Npad, 1, tc::TM, 1) &&
+              tc::map2d_f32(&mp.d, D.d32, D.Npad, 1, tc::TM, 1);
     if (!ok) { set_error("tensor map encoding failed (G4 fused)"); return; }
     const size_t smem = sizeof(tc::XPSmem) + 1024;
     dim3 grid(cdiv(D.N, tc::TM), cdiv((D.m1 ? D.m1 : D.M) - D.m0, tc::XP_TN));
+    const int mspan = (D.m1 ? D.m1 : D.M) - D.m0;
+    if (!D.fold && D.xq_ctr && cdiv(mspan, 32) <= tc::XQ_WMAX) {
+        // persistent CTAs, two per SM (no more than there are tiles)
+        int dev = 0, nsm = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) {
+            cudaGetLastError();
+            nsm = 1;
+        }
+        const size_t psmem = sizeof(tc::XQSmem) + 1024;
+        const int tiles = cdiv(D.N, tc::TM) * cdiv(mspan, tc::XP_TN);
+        auto pk = D.uniform ? tc::k_tc_xprox_pers<true> : tc::k_tc_xprox_pers<false>;
+        cudaFuncSetAttribute(pk, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)psmem);
+        // a chain of several takes its share of the SMs, so that the other chains' kernels
+        // keep room beside it
+        const int ctas = std::max(1, 2 * nsm / std::max(1, D.xq_share));
+        launch_ex(pk, dim3(std::min(tiles, ctas)), dim3(tc::XQ_THREADS), psmem, st, pdl, mp, D);
+        return;
+    }
     auto kern = D.fold ? (D.uniform ? tc::k_tc_xprox<true, true> : tc::k_tc_xprox<false, true>)
                        : (D.uniform ? tc::k_tc_xprox<true, false> : tc::k_tc_xprox<false, false>);
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);

@@ -63,7 +63,8 @@ class _Opts(C.Structure):
                 ("precision", C.c_int32), ("use_graph", C.c_int32), ("keep_for_backward", C.c_int32),
                 ("profile", C.c_int32), ("polish_overlap", C.c_double), ("chains", C.c_int32), ("stream_after", C.c_int32), ("fuse_prox", C.c_int32),
                 ("cuda_stream", C.c_void_p), ("ragged_layout", C.c_int32), ("g2_sets", C.c_int32),
-                ("fold_products", C.c_int32), ("adapt_every", C.c_int32)]
+                ("fold_products", C.c_int32), ("adapt_every", C.c_int32),
+                ("xupdate_form", C.c_int32)]
 
 
 class _Result(C.Structure):

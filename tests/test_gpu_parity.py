@@ -197,3 +197,22 @@ def test_folded_products_keep_parity(varied, chains):
     assert np.all(res["status"] == prism.PRISM_CERTIFIED), res["status"]
     assert float(np.max(np.abs(res["w"] - ref["w"]))) <= 1e-9
     assert_parity(uni, batch, res, accounts=[0, 255, 519])
+
+
+@pytest.mark.parametrize("varied", [False, True])
+@pytest.mark.parametrize("chains", [1, 4])
+def test_persistent_xupdate_matches_one_cta_per_tile(varied, chains):
+    # the fused x-update as persistent CTAs claiming tiles from a counter against one CTA per
+    # tile: the same arithmetic on every entry and the same per-tile outputs, so the same
+    # iterations and weights bit for bit; accounts stop iterating at different iterations, so
+    # the tile list of the persistent form shrinks along the way
+    uni, batch = make_workload(1, N=1200, K=64, M=520)
+    if varied:
+        batch = _varied_costs_and_floors(batch)
+    one = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, chains=chains, xupdate_form=1)
+    per = gpu_solve(uni, batch, precision=prism.PRISM_BATCHED_BF16, chains=chains, xupdate_form=0)
+    assert np.all(per["status"] == prism.PRISM_CERTIFIED), per["status"]
+    assert np.array_equal(per["iters"], one["iters"])
+    assert np.array_equal(per["w"], one["w"])
+    assert len(set(per["iters"].tolist())) > 1
+    assert_parity(uni, batch, per, accounts=[0, 255, 519])
