@@ -512,6 +512,7 @@ __device__ __forceinline__ void root_update(Root& R, float g, int cnt, float rho
 }
 
 struct ProxShared {
+    int nflag;                          // sectors whose band edge was found binding in this round
     float eta_hi[SMAX], eta_lo[SMAX];
     float cap_hi[SMAX], floor_lo[SMAX];
     float red_f[32];
@@ -521,73 +522,103 @@ struct ProxShared {
     int newj;
 };
 
-// Inner projection at fixed theta: per-sector edge roots, then the budget root.
-// Returns nu; sector edge multipliers in sh.eta_*. Block-collective.
+// Inner projection at fixed theta: the budget root nu of sum_s S_s(clamp(nu, eta_hi_s, eta_lo_s)) = 1
+// (S_s the sum of z over sector s, nonincreasing), with edge roots only for the sectors whose band
+// binds. Every sector starts unclamped (eta_hi = -inf, eta_lo = +inf: S_s(nu) itself); after each
+// budget root the sectors are checked at it, one whose sum leaves its band gets that edge's root
+// (after which its clamp is exact at every nu), and the budget root is solved again, until no
+// sector leaves its band. Returns nu; the edge multipliers in sh.eta_* (-inf / +inf for an edge
+// that does not bind). Block-collective.
 template <class Src>
 __device__ float project_inner(const Dev& D, const Src& S, int a, float theta, float rho, float irho, float nu0,
                                ProxShared& sh) {
-    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    const int warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5, lane = threadIdx.x & 31;
     const float step0 = 0.05f * rho + 1e-6f;
-    // phase A: sector edges (one warp per sector, no block synchronisation)
-    for (int s = warp; s < D.S; s += nwarps) {
-        const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-        const float hi = D.band_hi[a * D.S + s], lo = D.band_lo[a * D.S + s];
-        float eh = -FLT_MAX, el = FLT_MAX;
-        if (p1 > p0 && hi < sh.cap_hi[s]) {
-            Root R;
-            const float w = D.eta_hi[a * D.S + s];
-            root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
-            int it = 0;
-            for (; it < PROX_MAXIT && !R.done; ++it) {
-                float sum; int cnt;
-                warp_sector_sum(D, S, p0, p1, R.x, theta, irho, sum, cnt);
-                root_update(R, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
-            }
-            if (D.stats && (threadIdx.x & 31) == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
-            eh = R.x;
-        }
-        if (p1 > p0 && lo > sh.floor_lo[s]) {
-            Root R;
-            const float w = D.eta_lo[a * D.S + s];
-            root_init(R, (w > -FLT_MAX && w < FLT_MAX) ? w : nu0, step0);
-            for (int it = 0; it < PROX_MAXIT && !R.done; ++it) {
-                float sum; int cnt;
-                warp_sector_sum(D, S, p0, p1, R.x, theta, irho, sum, cnt);
-                root_update(R, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
-            }
-            el = R.x;
-        }
-        if ((threadIdx.x & 31) == 0) {
-            sh.eta_hi[s] = eh;
-            sh.eta_lo[s] = el;
-        }
+    for (int s = threadIdx.x; s < D.S; s += blockDim.x) {
+        sh.eta_hi[s] = -FLT_MAX;
+        sh.eta_lo[s] = FLT_MAX;
     }
+    if (threadIdx.x == 0) sh.nflag = 0;
     __syncthreads();
-    // phase B: budget multiplier
-    Root R;
-    root_init(R, nu0, step0);
-    for (int it = 0; it < PROX_MAXIT; ++it) {
-        float part = 0.f;
-        int pc = 0;
+    float nu = nu0;
+    for (int round = 0; round <= 2 * D.S; ++round) {
+        // budget root with the current clamps
+        Root R;
+        root_init(R, nu, step0);
+        for (int it = 0; it < PROX_MAXIT; ++it) {
+            float part = 0.f;
+            int pc = 0;
+            for (int s = warp; s < D.S; s += nwarps) {
+                const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
+                const float arg = fminf(fmaxf(R.x, sh.eta_hi[s]), sh.eta_lo[s]);
+                float sum; int cnt;
+                warp_sector_sum(D, S, p0, p1, arg, theta, irho, sum, cnt);
+                part += sum;
+                if (arg == R.x) pc += cnt;
+            }
+            if (lane == 0) { sh.red_f[warp] = part; sh.red_i[warp] = pc; }
+            __syncthreads();
+            float T = 0.f;
+            int C = 0;
+            for (int w = 0; w < nwarps; ++w) { T += sh.red_f[w]; C += sh.red_i[w]; }
+            __syncthreads();
+            root_update(R, T - 1.f, C, rho, 1e-6f);
+            if (D.stats && threadIdx.x == 0) atomicAdd(D.stats + 2, 1ull);
+            if (R.done) break;
+        }
+        nu = R.x;
+        // each sector at nu: an edge its sum leaves gets its root (one warp per sector)
         for (int s = warp; s < D.S; s += nwarps) {
             const int p0 = D.sec_start[s], p1 = D.sec_start[s + 1];
-            const float arg = fminf(fmaxf(R.x, sh.eta_hi[s]), sh.eta_lo[s]);
-            float sum; int cnt;
-            warp_sector_sum(D, S, p0, p1, arg, theta, irho, sum, cnt);
-            part += sum;
-            if (arg == R.x) pc += cnt;
+            if (p1 <= p0) continue;
+            const float hi = D.band_hi[a * D.S + s], lo = D.band_lo[a * D.S + s];
+            const bool free_hi = sh.eta_hi[s] == -FLT_MAX, free_lo = sh.eta_lo[s] == FLT_MAX;
+            const float arg = fminf(fmaxf(nu, sh.eta_hi[s]), sh.eta_lo[s]);
+            float Sv; int cv;
+            warp_sector_sum(D, S, p0, p1, arg, theta, irho, Sv, cv);
+            float eh = sh.eta_hi[s], el = sh.eta_lo[s];
+            bool flag = false;
+            if (free_hi && hi < sh.cap_hi[s] && Sv > hi + 1e-6f * fmaxf(hi, 1e-3f)) {
+                Root E;
+                const float w = D.eta_hi[a * D.S + s];
+                root_init(E, (w > arg && w < FLT_MAX) ? w : arg, step0);
+                E.a = arg;                                  // S_s(arg) > hi: the root lies above arg
+                int it = 0;
+                for (; it < PROX_MAXIT && !E.done; ++it) {
+                    float sum; int cnt;
+                    warp_sector_sum(D, S, p0, p1, E.x, theta, irho, sum, cnt);
+                    root_update(E, sum - hi, cnt, rho, 1e-6f * fmaxf(hi, 1e-3f));
+                }
+                if (D.stats && lane == 0) atomicAdd(D.stats + 1, (unsigned long long)it);
+                eh = E.x;
+                flag = true;
+            } else if (free_lo && lo > sh.floor_lo[s] && Sv < lo - 1e-6f * fmaxf(fabsf(lo), 1e-3f)) {
+                Root E;
+                const float w = D.eta_lo[a * D.S + s];
+                root_init(E, (w < arg && w > -FLT_MAX) ? w : arg, step0);
+                E.b = arg;                                  // S_s(arg) < lo: the root lies below arg
+                for (int it = 0; it < PROX_MAXIT && !E.done; ++it) {
+                    float sum; int cnt;
+                    warp_sector_sum(D, S, p0, p1, E.x, theta, irho, sum, cnt);
+                    root_update(E, sum - lo, cnt, rho, 1e-6f * fmaxf(fabsf(lo), 1e-3f));
+                }
+                el = E.x;
+                flag = true;
+            }
+            if (lane == 0 && flag) {
+                sh.eta_hi[s] = eh;
+                sh.eta_lo[s] = el;
+                atomicAdd(&sh.nflag, 1);
+            }
         }
-        if ((threadIdx.x & 31) == 0) { sh.red_f[warp] = part; sh.red_i[warp] = pc; }
         __syncthreads();
-        float T = 0.f;
-        int C = 0;
-        for (int w = 0; w < nwarps; ++w) { T += sh.red_f[w]; C += sh.red_i[w]; }
+        const int nf = sh.nflag;
         __syncthreads();
-        root_update(R, T - 1.f, C, rho, 1e-6f);
-        if (D.stats && threadIdx.x == 0) atomicAdd(D.stats + 2, 1ull);
-        if (R.done) break;
+        if (threadIdx.x == 0) sh.nflag = 0;
+        if (nf == 0) break;
     }
-    return R.x;
+    __syncthreads();
+    return nu;
 }
 
 // Turnover sum_i |z_i - w0_i| at the current (nu, eta, theta). Block-collective.
