@@ -643,8 +643,9 @@ def run_gpu(args, dist, rank, world, local_rank):
         pass
     peak = float(peaks.get("hbm_gbs", 6800.0))
     achieved = alg[dom] / (avg_ms / 1000.0) / 1e9
+    persistent = opts.get("xupdate_form", 0) == 0 and not opts.get("fold_products", 0)
     kernel_of = {"gemm_P": "k_tc_gemm_P", "gemm_x": "k_tc_gemm_x", "prox": "k_prox_stream / k_prox_smem",
-                 "xprox": "k_tc_xprox", "block": "k_block_admm"}
+                 "xprox": "k_tc_xprox_pers" if persistent else "k_tc_xprox", "block": "k_block_admm"}
     # the whole iteration: the method's bytes of every account-iteration of the step over the
     # step's device time (setup, polish and certification included in the time)
     iter_bytes = METHOD_BYTES * N * float(iters.sum())
