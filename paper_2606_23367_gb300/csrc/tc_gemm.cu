@@ -581,6 +581,32 @@ __device__ __forceinline__ XPAsset xp_asset(const Dev& D, int at, int q, int lan
     return ax;
 }
 
+// The per-entry arithmetic of the fused pass, written with explicitly rounded operations so that
+// the compiler cannot fuse a product into a neighbouring add differently in the two forms of the
+// fused x-update (which must give the same iterations bit for bit): the x-update
+// x = (mu + rho z - y - (BQ)) / (2d + rho), the relaxation v = alpha x + (1 - alpha) z + y / rho,
+// the prox at L, z = clip(soft(v - L/rho - w0, c/rho) + w0, l, u), and for an entry pinned at l its
+// y = rho (v - l) and X = (mu + rho l - y) / (2d + rho).
+struct XPEntry {
+    float v, z, yn, X, yir;   // yir = y / rho (the adaptation's term v - y / rho)
+};
+
+__device__ __forceinline__ XPEntry xp_entry(float mu, float dd, float rho, float irho, float Lr, float k, float lo,
+                                            float up, float z0, float y0, float w0, float bq, float alpha,
+                                            float oma) {
+    XPEntry e;
+    const float inv = rcp_approx(__fadd_rn(dd, rho));
+    const float x = __fmul_rn(__fsub_rn(__fsub_rn(__fmaf_rn(rho, z0, mu), y0), bq), inv);
+    e.yir = __fmul_rn(y0, irho);
+    e.v = __fmaf_rn(alpha, x, __fmaf_rn(oma, z0, e.yir));
+    const float t = __fsub_rn(e.v, Lr);
+    float z = (t > __fadd_rn(w0, k)) ? __fsub_rn(t, k) : ((t < __fsub_rn(w0, k)) ? __fadd_rn(t, k) : w0);
+    e.z = fminf(fmaxf(z, lo), up);
+    e.yn = __fmul_rn(rho, __fsub_rn(e.v, lo));
+    e.X = __fmul_rn(__fsub_rn(__fmaf_rn(rho, lo, mu), e.yn), inv);
+    return e;
+}
+
 // The epilogue of one tile for this warp's XP_JN accounts j0 .. j0 + XP_JN - 1: for each entry
 // v, the prox at L, the final z, y, X of a pinned entry or the record of a candidate; per
 // account and lane quarter the residual maxima and the candidate mask.
@@ -588,7 +614,7 @@ template <bool UNIFORM, bool FOLD>
 __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, const XPAsset& ax, const float* bq,
                                             int j0, int q, int lane, int m_base, bool have, uint32_t* xpk) {
     const bool row_ok = have && ax.i < D.N;
-    const float alpha = D.alpha;
+    const float alpha = D.alpha, oma = __fsub_rn(1.f, alpha);
     float4* crec = reinterpret_cast<float4*>(D.crec);
     // The accounts are processed without branches on the entry (an inactive account's values
     // are zero and nothing of it is stored), so their reductions interleave.
@@ -614,22 +640,17 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
         const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
         if (!UNIFORM) {
             if (ok && !lou) lo = D.lo[off];
-            if (ok && isnan(k)) k = D.c[off] * irho;
+            if (ok && isnan(k)) k = __fmul_rn(D.c[off], irho);
         }
         const float z0 = tv.in[0][j][ax.ia], y0 = tv.in[1][j][ax.ia], w0 = tv.in[2][j][ax.ia], up = tv.in[3][j][ax.ia];
-        const float inv = rcp_approx(ax.dd + rho);
-        const float x = (ax.mu + rho * z0 - y0 - bq[jj]) * inv;
-        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
-        const float t = v - Lr;
-        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
-        z = fminf(fmaxf(z, lo), up);
-        const bool pin = ok && (z == lo);
+        const XPEntry en = xp_entry(ax.mu, ax.dd, rho, irho, Lr, k, lo, up, z0, y0, w0, bq[jj], alpha, oma);
+        const float v = en.v, yn = en.yn;
+        const bool pin = ok && (en.z == lo);
         const bool cand = ok && !pin;
-        const float yn = rho * (v - lo);
         // the residual terms before their scale (1/rho, rho: applied to the warp's maxima, which
         // gives the same values); a non-finite update gives an infinite or NaN maximum
-        const float e_rp = pin ? fabsf(yn - y0) : 0.f;
-        const float e_rd = pin ? fabsf(lo - z0) : 0.f;
+        const float e_rp = pin ? fabsf(__fsub_rn(yn, y0)) : 0.f;
+        const float e_rd = pin ? fabsf(__fsub_rn(lo, z0)) : 0.f;
         // v of a pinned entry is not stored: it is l + y / rho from the y written below, which is
         // all a later recomputation of its sector needs; z is stored only when it changes. Its
         // X = Delta^{-1} (mu + rho l - y), split into two BF16 terms, is stored for the product
@@ -640,9 +661,9 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
         if (pin) {
             if (z0 != lo) D.z[off] = lo;
             D.y[off] = yn;
-            const float X = (ax.mu + rho * lo - yn) * inv;
+            const float X = en.X;
             const __nv_bfloat16 h = __float2bfloat16_rn(X);
-            const __nv_bfloat16 l = __float2bfloat16_rn(X - __bfloat162float(h));
+            const __nv_bfloat16 l = __float2bfloat16_rn(__fsub_rn(X, __bfloat162float(h)));
             if constexpr (FOLD) {
                 xp = uint32_t(__bfloat16_as_ushort(h)) | (uint32_t(__bfloat16_as_ushort(l)) << 16);
             } else {
@@ -658,11 +679,11 @@ __device__ __forceinline__ void xp_accounts(const Dev& D, const XPTileView& tv, 
             crec[2 * (size_t)off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
-        float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd) * rho;
-        rp = (rp == INFINITY) ? NAN : rp * irho;        // a non-finite pinned update: NaN (numerical failure)
+        float rp = warp_max_nn(e_rp), rd = __fmul_rn(warp_max_nn(e_rd), rho);
+        rp = (rp == INFINITY) ? NAN : __fmul_rn(rp, irho);        // a non-finite pinned update: NaN (numerical failure)
         float nx = 0.f, nz = 0.f, ny = 0.f;
         if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
-            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
+            nx = warp_max_nn(pin ? fabsf(__fsub_rn(v, en.yir)) : 0.f);
             ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
             if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);   // else |l| itself, added later
         }
@@ -934,6 +955,7 @@ struct __align__(1024) XQSmem {
     uint64_t tfree[XQ_STAGES];                // the epilogue has read those columns
     uint64_t empty[XQ_STAGES];                // the epilogue is done with the stage
     int at[XQ_STAGES];                        // position tile; -1: no more tiles
+    int tad[XQ_STAGES];                       // some column adapts its penalty on this call
     int acc[XQ_STAGES][XP_TN];                // account of each column (-1: padding)
     float4 pa[XQ_STAGES][XP_TN];              // rho, 1/rho, L/rho, c/rho (NaN: c differs over positions)
     float4 pb[XQ_STAGES][XP_TN];              // l (NaN: differs), active, adaptation call, unused
@@ -976,17 +998,22 @@ __device__ __forceinline__ int nth_set_bit(unsigned w, int n) {
 // xp_accounts (products not folded) with each column's account taken from the stage. A padding
 // column is evaluated like the others and nothing of it is stored (no branch on the column, so
 // that the columns' reductions interleave). ax.obase is the position alone.
-template <bool UNIFORM>
+// ADAPT: some column of the tile adapts its penalty on this call (the terms of the adaptation's
+// residual ratio are formed for the columns that do); chosen per tile, so that the loop over the
+// columns has no branch on a column's flag. The inputs of all the warp's columns are waited for
+// before the loop, for the same reason.
+template <bool UNIFORM, bool ADAPT>
 __device__ __forceinline__ void xq_accounts(const Dev& D, XQSmem& s, int sti, const XPAsset& ax, const float* bq,
                                             int j0, int q, int lane, uint32_t par, bool have) {
     const bool row_ok = have && ax.i < D.N;
-    const float alpha = D.alpha;
+    const float alpha = D.alpha, oma = __fsub_rn(1.f, alpha);
     float4* crec = reinterpret_cast<float4*>(D.crec);
     const XQStage& S = s.st[sti];
+    if (have)
+        for (int g = j0 / 4; g < (j0 + XP_JN) / 4; ++g) mbar_wait(&s.full_in[sti][g], par, D.err, 64);
 #pragma unroll
     for (int jj = 0; jj < XP_JN; ++jj) {
         const int j = j0 + jj;
-        if (jj % 4 == 0 && have) mbar_wait(&s.full_in[sti][j / 4], par, D.err, 64);
         const int m = s.acc[sti][j];
         const float4 pa = s.pa[sti][j], pb = s.pb[sti][j];
         const float rho = pa.x, irho = pa.y, Lr = pa.z;   // Lr = L / rho
@@ -996,41 +1023,37 @@ __device__ __forceinline__ void xq_accounts(const Dev& D, XQSmem& s, int sti, co
         const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
         if (!UNIFORM) {
             if (ok && !lou) lo = D.lo[off];
-            if (ok && isnan(k)) k = D.c[off] * irho;
+            if (ok && isnan(k)) k = __fmul_rn(D.c[off], irho);
         }
         const float z0 = S.in[0][j][ax.ia], y0 = S.in[1][j][ax.ia], w0 = S.in[2][j][ax.ia], up = S.in[3][j][ax.ia];
-        const float inv = rcp_approx(ax.dd + rho);
-        const float x = (ax.mu + rho * z0 - y0 - bq[jj]) * inv;
-        const float v = alpha * x + (1.f - alpha) * z0 + y0 * irho;
-        const float t = v - Lr;
-        float z = (t > w0 + k) ? t - k : ((t < w0 - k) ? t + k : w0);
-        z = fminf(fmaxf(z, lo), up);
-        const bool pin = ok && (z == lo);
+        const XPEntry en = xp_entry(ax.mu, ax.dd, rho, irho, Lr, k, lo, up, z0, y0, w0, bq[jj], alpha, oma);
+        const float v = en.v, yn = en.yn;
+        const bool pin = ok && (en.z == lo);
         const bool cand = ok && !pin;
-        const float yn = rho * (v - lo);
-        const float e_rp = pin ? fabsf(yn - y0) : 0.f;
-        const float e_rd = pin ? fabsf(lo - z0) : 0.f;
+        const float e_rp = pin ? fabsf(__fsub_rn(yn, y0)) : 0.f;
+        const float e_rd = pin ? fabsf(__fsub_rn(lo, z0)) : 0.f;
         if (cand) D.v[off] = v;
         if (pin) {
             if (z0 != lo) D.z[off] = lo;
             D.y[off] = yn;
-            const float X = (ax.mu + rho * lo - yn) * inv;
+            const float X = en.X;
             const __nv_bfloat16 h = __float2bfloat16_rn(X);
             D.Xhi[off] = h;
-            D.Xlo[off] = __float2bfloat16_rn(X - __bfloat162float(h));
+            D.Xlo[off] = __float2bfloat16_rn(__fsub_rn(X, __bfloat162float(h)));
         }
         if (cand) {
             crec[2 * off] = make_float4(v, w0, up, z0);
             crec[2 * off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
-        float rp = warp_max_nn(e_rp), rd = warp_max_nn(e_rd) * rho;
-        rp = (rp == INFINITY) ? NAN : rp * irho;        // a non-finite pinned update: NaN (numerical failure)
+        float rp = warp_max_nn(e_rp), rd = __fmul_rn(warp_max_nn(e_rd), rho);
+        rp = (rp == INFINITY) ? NAN : __fmul_rn(rp, irho);        // a non-finite pinned update: NaN (numerical failure)
         float nx = 0.f, nz = 0.f, ny = 0.f;
-        if (pb.z != 0.f) {                              // penalty adaptation on this call (uniform)
-            nx = warp_max_nn(pin ? fabsf(v - y0 * irho) : 0.f);
-            ny = warp_max_nn(pin ? fabsf(yn) : 0.f);
-            if (!lou) nz = warp_max_nn(pin ? fabsf(lo) : 0.f);
+        if constexpr (ADAPT) {                          // penalty adaptation on this call (per column)
+            const bool ad = pin && pb.z != 0.f;
+            nx = warp_max_nn(ad ? fabsf(__fsub_rn(v, en.yir)) : 0.f);
+            ny = warp_max_nn(ad ? fabsf(yn) : 0.f);
+            if (!lou) nz = warp_max_nn(ad ? fabsf(lo) : 0.f);
         }
         if (!UNIFORM && !lou) {
             for (int g = 0; g < ax.nsegq; ++g) {
@@ -1201,6 +1224,8 @@ __global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_co
             // accounts takes its Q split as a box too
             const int m0c = __shfl_sync(0xffffffffu, m, 0);
             const unsigned have_col = __ballot_sync(0xffffffffu, lane < XP_TN && m >= 0);
+            const unsigned adapt_col =
+                __ballot_sync(0xffffffffu, lane < XP_TN && m >= 0 && (itr + 1) % D.adapt_every == 0);
             const unsigned cons = __ballot_sync(0xffffffffu, lane < XP_TN && m >= 0 && m == m0c + lane);
             const bool qbox = (cons & 0xffffu) == 0xffffu;
             unsigned gbox = 0u;                              // bit g: group g as one box
@@ -1214,6 +1239,7 @@ __global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_co
             }
             if (lane == 0) {
                 s.at[sti] = at;
+                s.tad[sti] = adapt_col != 0u;
                 mbar_expect_tx(&s.full_bq[sti], XQ_BMD_BYTES + (qbox ? 2 * XP_Q_BYTES : 0u));
                 tma_load_2d(S.a, &mp.B, &s.full_bq[sti], 0, at * TM);
                 tma_load_2d(S.md[0], &mp.mu, &s.full_bq[sti], at * TM, 0);
@@ -1364,7 +1390,8 @@ __global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_co
             } else {
                 ax = xp_asset(D, at, q, lane, 0);
             }
-            xq_accounts<UNIFORM>(D, s, sti, ax, bq, j0, q, lane, par, have);
+            if (s.tad[sti]) xq_accounts<UNIFORM, true>(D, s, sti, ax, bq, j0, q, lane, par, have);
+            else xq_accounts<UNIFORM, false>(D, s, sti, ax, bq, j0, q, lane, par, have);
             xq_epi_sync();
             if (have) xq_tile_out(D, s, sti, at, tid);
             __syncwarp();
