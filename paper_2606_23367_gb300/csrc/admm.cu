@@ -512,7 +512,7 @@ __device__ __forceinline__ void root_update(Root& R, float g, int cnt, float rho
 }
 
 struct ProxShared {
-    int nflag;                          // sectors whose band edge was found binding in this round
+    int nflag;                          // sectors whose band edge was found binding in the latest check
     float eta_hi[SMAX], eta_lo[SMAX];
     float cap_hi[SMAX], floor_lo[SMAX];
     float red_f[32];
@@ -1618,26 +1618,71 @@ __global__ void __launch_bounds__(32 * SP_WARPS, 4) k_prox_roots(Dev D) {
             sh.k[r] = (isnan(c_u) ? G.c[p] : c_u) * irho;
         }
     }
-    if (tid == 0) {
-        int used = 0;
-        for (int s = 0; s < NS; ++s) {
-            const int p0 = sh.sec[s], p1 = sh.sec[s + 1];
-            const int r0 = cand_rank(R, nq, p0), n = cand_rank(R, nq, p1) - r0;
-            R.rank0[s] = r0;
-            if (!isnan(lo_u)) sh.sumlo[s] = lo_u * float(p1 - p0 - n);
-            sh.cb[s] = used;
-            if (used + n <= CAP) {
-                sh.ce[s] = used + n;
-                sh.gs[s] = p1;
-                used += n;
-            } else {
-                sh.ce[s] = used;
-                sh.gs[s] = p0;
-                sh.sumlo[s] = 0.f;
+    if (warp == 0) {
+        // warp 0, lane s over sectors s and s + 32: the candidates of each sector (from the
+        // ranks of its end positions), their prefix over the sectors in order, and the slot
+        // ranges; when they all fit (the common case) every sector takes its own candidates'
+        // slots, else lane 0 lays the sectors out in order while the slots last
+        static_assert(SMAX <= 64, "two sectors per lane");
+        int r0[2], n[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int sct = lane + 32 * h;
+            r0[h] = 0; n[h] = 0;
+            if (sct < NS) {
+                r0[h] = cand_rank(R, nq, sh.sec[sct]);
+                n[h] = cand_rank(R, nq, sh.sec[sct + 1]) - r0[h];
             }
         }
-        R.all_fit = (used == R.total);
-        R.nslots = used;
+        int ex[2], tot = 0;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            int inc = n[h];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= o) inc += v;
+            }
+            ex[h] = tot + inc - n[h];
+            tot += __shfl_sync(0xffffffffu, inc, 31);
+        }
+        if (tot <= CAP) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int sct = lane + 32 * h;
+                if (sct >= NS) continue;
+                const int p0 = sh.sec[sct], p1 = sh.sec[sct + 1];
+                R.rank0[sct] = r0[h];
+                if (!isnan(lo_u)) sh.sumlo[sct] = lo_u * float(p1 - p0 - n[h]);
+                sh.cb[sct] = ex[h];
+                sh.ce[sct] = ex[h] + n[h];
+                sh.gs[sct] = p1;
+            }
+            if (lane == 0) {
+                R.all_fit = (tot == R.total);
+                R.nslots = tot;
+            }
+        } else if (lane == 0) {
+            int used = 0;
+            for (int sct = 0; sct < NS; ++sct) {
+                const int p0 = sh.sec[sct], p1 = sh.sec[sct + 1];
+                const int q0 = cand_rank(R, nq, p0), nn = cand_rank(R, nq, p1) - q0;
+                R.rank0[sct] = q0;
+                if (!isnan(lo_u)) sh.sumlo[sct] = lo_u * float(p1 - p0 - nn);
+                sh.cb[sct] = used;
+                if (used + nn <= CAP) {
+                    sh.ce[sct] = used + nn;
+                    sh.gs[sct] = p1;
+                    used += nn;
+                } else {
+                    sh.ce[sct] = used;
+                    sh.gs[sct] = p0;
+                    sh.sumlo[sct] = 0.f;
+                }
+            }
+            R.all_fit = (used == R.total);
+            R.nslots = used;
+        }
     }
     __syncthreads();
     const bool all_fit = R.all_fit;

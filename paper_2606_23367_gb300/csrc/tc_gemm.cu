@@ -1104,19 +1104,22 @@ __global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_co
     constexpr int PROD = XQ_EPI / 32, MMAW = PROD + 1;
     constexpr uint32_t IDESC = idesc_bf16(TM, XP_TN);
     if (warp == 0) tmem_alloc(&s.tmem, 32);
+    int t_first = 0;                                    // the producer's first claim
     if (warp == PROD) {
+        // the first tile is claimed now, so that the atomic's round trip overlaps the list below
+        if (lane == 0) t_first = (int)atomicAdd(D.xq_ctr, 1u);
         // the chain's accounts that iterate (the flags were written by kernels two or more
         // launches back, so they are readable before the dependency wait): a bit mask per 32
-        // accounts and the count before each word
-        for (int w0 = 0; w0 < nw; w0 += 8) {
-            bool a[8];
+        // accounts and the count before each word; the loads of up to 16 words in flight at once
+        for (int w0 = 0; w0 < nw; w0 += 16) {
+            bool a[16];
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const int m = D.m0 + 32 * (w0 + u) + lane;
                 a[u] = (w0 + u < nw) && m < m_end && D.active[m] != 0;
             }
 #pragma unroll
-            for (int u = 0; u < 8; ++u) {
+            for (int u = 0; u < 16; ++u) {
                 const unsigned b = __ballot_sync(0xffffffffu, a[u]);
                 if (lane == 0 && w0 + u < nw) s.amask[w0 + u] = b;
             }
@@ -1168,9 +1171,7 @@ __global__ void __launch_bounds__(XQ_THREADS, 2) k_tc_xprox_pers(const __grid_co
         static_assert(XQ_STAGES == 2, "the last use of each stage is kept in two registers");
         int last0 = -1, last1 = -1;      // last use of each stage that issued loads
         bool waited = false;
-        int t = 0;
-        if (lane == 0) t = (int)atomicAdd(ctr, 1u);
-        t = __shfl_sync(0xffffffffu, t, 0);
+        int t = __shfl_sync(0xffffffffu, t_first, 0);
         for (int k = 0;; ++k) {
             const int sti = k % XQ_STAGES, use = k / XQ_STAGES;
             XQStage& S = s.st[sti];
