@@ -917,8 +917,9 @@ __global__ void __launch_bounds__(XP_THREADS, 4) k_tc_xprox(const __grid_constan
 // A tile's accounts are 16 consecutive ones of the chain's active accounts (the list is formed
 // by each CTA at its start), so an account that has stopped iterating costs no work:
 //   warp 8 (producer): claims a tile, writes its accounts and their constants into a stage of a
-//     two-stage ring, loads the B tile, mu, d and the accounts' input rows by TMA, and copies
-//     the accounts' Q split rows into the stage in the product's 128-byte-swizzled layout;
+//     two-stage ring, loads the B tile, mu, d and the accounts' input rows by TMA (one box of four
+//     rows where four accounts are consecutive), and the Q split rows (a box when all 16 accounts
+//     are consecutive, else copied by the warp into the product's 128-byte-swizzled layout);
 //   warp 9 (MMA): one thread issues the B Q product of each stage into that stage's 16 TMEM
 //     columns once its operands are in place;
 //   warps 0-7 (epilogue): for each entry the pass of k_tc_xprox (the same arithmetic), then the
