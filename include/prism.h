@@ -318,7 +318,7 @@ int prism_polish_noalloc(prism_universe* u, const prism_batch* batch, const doub
  * Coordinate-wise search over the initial penalty rho0 (0.5 .. 8), the over-relaxation alpha
  * (1.4 .. 1.8), the iterations per captured graph (5, 10, 20), the staged prox iterations
  * before the streaming form (2 .. 10), the account chains (1, 2, 4) and the ADMM target
- * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 4, BATCHED_BF16),
+ * eps_admm (1e-4 .. 7e-4), the tile shape of the tensor-core product B'X (g2_sets 1 .. 8, BATCHED_BF16),
  * the folded products (fold_products 0, 1; BATCHED_BF16), the form of the fused x-update
  * (xupdate_form 0, 1; BATCHED_BF16 without folded products), the penalty adaptation period
  * (adapt_every 10 .. 50) and, for books of ragged accounts,

@@ -147,7 +147,7 @@ extern "C" int prism_autotune(prism_universe* u, const prism_batch* b, const pri
     }
     if (o.precision == PRISM_BATCHED_BF16) {
         // the tile shape of the tensor-core B'X: clusters of 8 CTAs per account tile (asset chunk)
-        for (int gs : {1, 2, 3, 4}) {
+        for (int gs : {1, 2, 3, 4, 6, 8}) {
             if (gs == best.g2_sets) continue;
             prism_solve_opts c = best;
             c.g2_sets = gs;

@@ -170,7 +170,7 @@ def test_account_chains_do_not_change_results():
     assert_parity(uni, batch, res[4], accounts=[0, 200, 519])
 
 
-@pytest.mark.parametrize("sets", [1, 2, 4])
+@pytest.mark.parametrize("sets", [1, 2, 4, 8])
 def test_g2_tile_shapes_keep_parity(sets):
     # the tile shape the autotuner searches (asset chunk per CTA of the tensor-core B'X): every
     # shape is the same product summed in another order, so the polished weights agree
