@@ -1019,7 +1019,9 @@ __device__ __forceinline__ void xq_accounts(const Dev& D, XQSmem& s, int sti, co
         const float4 pa = s.pa[sti][j], pb = s.pb[sti][j];
         const float rho = pa.x, irho = pa.y, Lr = pa.z;   // Lr = L / rho
         const bool ok = row_ok && m >= 0;
-        const size_t off = (size_t)(m >= 0 ? m : 0) * D.Npad + ax.obase;
+        // element offset in 32 bits (as in k_tc_xprox): a book of 2^32 entries could not hold its
+        // workspace in device memory
+        const uint32_t off = uint32_t(m >= 0 ? m : 0) * uint32_t(D.Npad) + uint32_t(ax.obase);
         float lo = pb.x, k = pa.w;                      // k = c / rho
         const bool lou = UNIFORM || !isnan(lo);         // warp-uniform
         if (!UNIFORM) {
@@ -1043,8 +1045,8 @@ __device__ __forceinline__ void xq_accounts(const Dev& D, XQSmem& s, int sti, co
             D.Xlo[off] = __float2bfloat16_rn(__fsub_rn(X, __bfloat162float(h)));
         }
         if (cand) {
-            crec[2 * off] = make_float4(v, w0, up, z0);
-            crec[2 * off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
+            crec[2 * (size_t)off] = make_float4(v, w0, up, z0);
+            crec[2 * (size_t)off + 1] = make_float4(y0, ax.mu, 0.5f * ax.dd, 0.f);
         }
         const unsigned cm = __ballot_sync(0xffffffffu, cand);
         float rp = warp_max_nn(e_rp), rd = __fmul_rn(warp_max_nn(e_rd), rho);
