@@ -248,10 +248,11 @@ class Clocks:
         return out
 
 
-def profiled_traffic(kernel_class, entries_per_launch):
+def profiled_traffic(kernel_class, entries_per_launch, kernel_name=None):
     """DRAM bytes per launch of a kernel class, from the committed ncu summary of the default
     workload: the captured launch's bytes per account-entry times the entries of this run's
-    average launch. None when the kernel's source files have changed since the capture."""
+    average launch. None when the kernel's source files have changed since the capture, or when
+    kernel_name is given and the captured kernel is another one of the class."""
     import hashlib
     import re
     path = os.path.join(ROOT, "profiles", "dram_traffic_500x10000.md")
@@ -260,19 +261,21 @@ def profiled_traffic(kernel_class, entries_per_launch):
     except OSError:
         return None
     # | class | `kernel` | entries | read MB | write MB | bytes | files | sha256 prefixes |
-    pat = re.compile(r"^\| (\w+) \| `[^`]+` \| (\d+) \| [\d.]+ \| [\d.]+ \| (\d+) \| (\S+) \| (\S+) \|$")
+    pat = re.compile(r"^\| (\w+) \| `([^`]+)` \| (\d+) \| [\d.]+ \| [\d.]+ \| (\d+) \| (\S+) \| (\S+) \|$")
     for line in text.splitlines():
         m = pat.match(line.strip())
         if not m or m.group(1) != kernel_class:
             continue
-        for f, h in zip(m.group(4).split("+"), m.group(5).split("+")):
+        if kernel_name is not None and m.group(2).split("::")[-1] != kernel_name:
+            return None
+        for f, h in zip(m.group(5).split("+"), m.group(6).split("+")):
             try:
                 cur = hashlib.sha256(open(os.path.join(ROOT, f), "rb").read()).hexdigest()
             except OSError:
                 return None
             if not cur.startswith(h):
                 return None
-        return int(m.group(3)) / int(m.group(2)) * entries_per_launch
+        return int(m.group(4)) / int(m.group(3)) * entries_per_launch
     return None
 
 
@@ -651,7 +654,7 @@ def run_gpu(args, dist, rank, world, local_rank):
     iter_bytes = METHOD_BYTES * N * float(iters.sum())
     iter_gbs = iter_bytes / (ms / args.steps / 1000.0) / 1e9
     roofline = {"kernel": kernel_of.get(dom, dom), "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": profiled_traffic(dom, ent[dom]),
+                "frac": achieved / peak, "traffic": profiled_traffic(dom, ent[dom], kernel_of.get(dom)),
                 "peak_source": "measured" if "hbm_gbs" in peaks else "fallback",
                 "alg_bytes_per_unit": ALG_BYTES[dom], "units_per_launch": ent[dom],
                 "alg_bytes_per_launch": alg[dom], "avg_launch_ms": avg_ms,
