@@ -133,6 +133,36 @@ def test_brute_force_tiny(seed, n, cap, with_lots):
     assert abs(obj - obj_bf) <= 1e-12 * max(1.0, abs(obj_bf))
 
 
+@pytest.mark.parametrize("seed,upper_range,band_hi0,tilt,binding", [
+    (21, (0.2, 0.35), 0.4, 0.05, "band"),      # sector 0's band held at its upper edge
+    (22, (0.13, 0.16), 1.0, 0.0, "box"),       # four weights held at their upper bounds
+])
+def test_brute_force_n8_fresh_accounts(seed, upper_range, band_hi0, tilt, binding):
+    """Enumeration of every active set at N = 8 (budget, box, two sector bands, transition cost)
+    for accounts without holdings: with w0 = 0 = l the cost's kink sits on the lower bound, so
+    each weight has three states and the 3^8 x 9 assignments run in seconds."""
+    rng = np.random.default_rng(seed)
+    n, k, S = 8, 2, 2
+    B, f, d = rng.normal(0, 0.3, size=(n, k)), rng.uniform(0.01, 0.04, size=k), rng.uniform(0.005, 0.05, size=n) * 4
+    mu = rng.normal(0.05, 0.03, size=n)
+    w0, lower = np.zeros(n), np.zeros(n)
+    upper = rng.uniform(*upper_range, size=n)
+    tc = rng.uniform(0.005, 0.03, size=n)
+    sector = np.arange(n) % S
+    band_lo, band_hi = np.zeros(S), np.array([band_hi0, 1.0])
+    mu[sector == 0] += tilt
+    args = (B, f, d, mu, sector, S, w0, lower, upper, tc, band_lo, band_hi)
+    r = AccountProblem(*args).solve()
+    w_bf, obj_bf = brute.solve_brute(*args)
+    assert np.max(np.abs(r.w - w_bf)) <= 1e-10
+    obj = kkt.objective(B, f, d, mu, r.w, w0, tc, None)
+    assert abs(obj - obj_bf) <= 1e-12 * max(1.0, abs(obj_bf))
+    if binding == "band":
+        assert abs(w_bf[sector == 0].sum() - band_hi0) <= 1e-12 and r.lam[0] > 0
+    else:
+        assert int(np.sum(np.abs(w_bf - upper) <= 1e-12)) >= 3
+
+
 def _diag_of(P, r):
     return kkt.diagnostics(P.B, P.f, P.d, P.mu, P.sector, P.S, r.w, P.w0, P.lower, P.upper,
                            P.tc, P.band_lo, P.band_hi, P.tau, r.nu, r.lam, r.theta, P.lots)
